@@ -1,0 +1,160 @@
+"""The CPU oracle of the Jacobi SVD hot path -- TEST INFRASTRUCTURE ONLY.
+
+A plain, slow, FP64 restatement of arXiv 2202.08361 in C (jsvd_oracle.c),
+loaded through ctypes.  Only tests/, __graft_entry__.smoke() and bench.py's
+CPU-baseline leg may import this package; the library under
+paper_2202_08361_gb300/ never does.
+
+Functions:
+  dsjac2 / zsjac2     batched 2x2 EVD (Alg. d8jac2 / Listing 1)
+  zsjac2_scaled       the scaled eigenvalues lambda' of Listing 1
+  pairs               the round-robin parallel ordering (section 4.1 reading)
+  vjsvd               one-sided Jacobi SVD after Alg. zvjsvd (section 4.3)
+  svd_adjoint         thin real SVD adjoint (Townsend 2016)
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+OK = 0
+E_ARG = -1
+E_NONFINITE = -2
+NOT_CONVERGED = 1
+
+_d = ctypes.POINTER(ctypes.c_double)
+_i32 = ctypes.POINTER(ctypes.c_int32)
+_i64 = ctypes.POINTER(ctypes.c_int64)
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        L.orc_dsjac2.argtypes = [ctypes.c_int64, _d, _d, _d, _d, _d, _d, _d, _i32]
+        L.orc_dsjac2.restype = None
+        L.orc_zsjac2.argtypes = [ctypes.c_int64, _d, _d, _d, _d, _d, _d, _d, _d, _d, _i32]
+        L.orc_zsjac2.restype = None
+        L.orc_zsjac2_scaled.argtypes = [ctypes.c_int64, _d, _d, _d, _d, _d, _d]
+        L.orc_zsjac2_scaled.restype = None
+        L.orc_pairs.argtypes = [ctypes.c_int, _i32]
+        L.orc_pairs.restype = ctypes.c_int
+        L.orc_vjsvd.argtypes = [ctypes.c_int64, ctypes.c_int64, _d, _d, ctypes.c_int64, _d, _d,
+                                _d, _d, _d, ctypes.c_int, ctypes.c_int, _i32, _i64]
+        L.orc_vjsvd.restype = ctypes.c_int
+        L.orc_svd_adjoint.argtypes = [ctypes.c_int64, ctypes.c_int64, _d, _d, _d, _d, _d, _d, _d]
+        L.orc_svd_adjoint.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(_d) if a is not None else None
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def dsjac2(a11, a22, a21):
+    """Real symmetric 2x2 EVD of each (a11, a22, a21): returns
+    (cos_phi, sign(a21) tan_phi, lambda1, lambda2, zeta_p)."""
+    a11, a22, a21 = _f64(a11), _f64(a22), _f64(a21)
+    r = a11.size
+    out = [np.empty(r) for _ in range(4)]
+    zp = np.empty(r, dtype=np.int32)
+    lib().orc_dsjac2(r, _dp(a11), _dp(a22), _dp(a21), *[_dp(o) for o in out],
+                     zp.ctypes.data_as(_i32))
+    return (*out, zp)
+
+
+def zsjac2(a11, a22, a21r, a21i):
+    """Complex Hermitian 2x2 EVD (Listing 1): returns (cos_phi,
+    cos_alpha tan_phi, sin_alpha tan_phi, lambda1, lambda2, zeta_p)."""
+    a11, a22, a21r, a21i = _f64(a11), _f64(a22), _f64(a21r), _f64(a21i)
+    r = a11.size
+    out = [np.empty(r) for _ in range(5)]
+    zp = np.empty(r, dtype=np.int32)
+    lib().orc_zsjac2(r, _dp(a11), _dp(a22), _dp(a21r), _dp(a21i), *[_dp(o) for o in out],
+                     zp.ctypes.data_as(_i32))
+    return (*out, zp)
+
+
+def zsjac2_scaled(a11, a22, a21r, a21i):
+    """The scaled eigenvalues (lambda1', lambda2') of Listing 1."""
+    a11, a22, a21r, a21i = _f64(a11), _f64(a22), _f64(a21r), _f64(a21i)
+    r = a11.size
+    l1, l2 = np.empty(r), np.empty(r)
+    lib().orc_zsjac2_scaled(r, _dp(a11), _dp(a22), _dp(a21r), _dp(a21i), _dp(l1), _dp(l2))
+    return l1, l2
+
+
+def pairs(n):
+    """The round-robin ordering: int32 array [n_steps, n_pairs, 2] of (p, q)."""
+    nt = n + (n & 1)
+    K, L = max(nt - 1, 1), max(nt // 2, 1)
+    tab = np.zeros((K, L, 2), dtype=np.int32)
+    if nt >= 2:
+        lib().orc_pairs(n, tab.ctypes.data_as(_i32))
+    return tab[: nt - 1] if nt >= 2 else tab[:0]
+
+
+def vjsvd(A, max_sweeps=100, nthreads=0):
+    """One-sided Jacobi SVD of A (m x n, m >= n; real or complex).
+
+    Returns dict(U, sigma, sigma_e, sigma_f, V, status, sweeps, rotations,
+    rescales).  sigma is sorted non-increasingly; A ~= U diag(sigma) V^H.
+    """
+    A = np.asarray(A)
+    m, n = A.shape
+    cplx = np.iscomplexobj(A)
+    Gr = np.asfortranarray(A.real, dtype=np.float64).copy(order="F")
+    Gi = np.asfortranarray(A.imag, dtype=np.float64).copy(order="F") if cplx else None
+    Vr = np.zeros((n, n), order="F")
+    Vi = np.zeros((n, n), order="F") if cplx else None
+    sig, se, sf = np.empty(n), np.empty(n), np.empty(n)
+    info = np.zeros(4, dtype=np.int32)
+    rot = np.zeros(1, dtype=np.int64)
+    rc = lib().orc_vjsvd(m, n, _dp(Gr), _dp(Gi), m, _dp(Vr), _dp(Vi), _dp(sig), _dp(se),
+                         _dp(sf), int(max_sweeps), int(nthreads), info.ctypes.data_as(_i32),
+                         rot.ctypes.data_as(_i64))
+    if rc < 0:
+        raise ValueError("orc_vjsvd failed with %d" % rc)
+    U = Gr + 1j * Gi if cplx else Gr
+    V = Vr + 1j * Vi if cplx else Vr
+    return dict(U=U, sigma=sig, sigma_e=se, sigma_f=sf,
+                V=V, status=int(info[0]), sweeps=int(info[1]), rotations=int(rot[0]),
+                rescales=int(info[3]))
+
+
+def svd_adjoint(U, s, V, Ubar, sbar, Vbar=None):
+    """Abar from the thin real SVD adjoint (Townsend 2016)."""
+    U = np.asfortranarray(U, dtype=np.float64)
+    V = np.asfortranarray(V, dtype=np.float64)
+    Ubar = np.asfortranarray(Ubar, dtype=np.float64)
+    s = _f64(s)
+    sbar = _f64(sbar)
+    Vb = np.asfortranarray(Vbar, dtype=np.float64) if Vbar is not None else None
+    m, n = U.shape
+    Abar = np.zeros((m, n), order="F")
+    rc = lib().orc_svd_adjoint(m, n, _dp(U), _dp(s), _dp(V), _dp(Ubar), _dp(sbar), _dp(Vb),
+                               _dp(Abar))
+    if rc != 0:
+        raise ValueError("orc_svd_adjoint failed with %d" % rc)
+    return Abar
+
+
+def sign_gauge(U, V):
+    """Flip each (u_j, v_j) so that the largest-magnitude entry of u_j is
+    positive (first index on ties).  Real only."""
+    U = U.copy()
+    V = V.copy()
+    idx = np.argmax(np.abs(U), axis=0)
+    sg = np.sign(U[idx, np.arange(U.shape[1])])
+    sg[sg == 0] = 1.0
+    return U * sg, V * sg

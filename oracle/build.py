@@ -1,0 +1,33 @@
+"""Build the CPU oracle (test infrastructure only) into oracle/_build/.
+
+The oracle is plain C compiled with -ffp-contract=off so that no multiply
+and add are fused behind the source's back: every fused multiply-add in the
+oracle is an explicit fma() call, as in the paper's listings.
+"""
+import os
+import subprocess
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "jsvd_oracle.c")
+OUT_DIR = os.path.join(HERE, "_build")
+LIB = os.path.join(OUT_DIR, "libjsvd_oracle.so")
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle shared library if it is missing or stale; return its path."""
+    os.makedirs(OUT_DIR, exist_ok=True)
+    if (not force and os.path.exists(LIB)
+            and os.path.getmtime(LIB) >= os.path.getmtime(SRC)):
+        return LIB
+    tmp = LIB + ".tmp.%d" % os.getpid()
+    cmd = ["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-fopenmp",
+           "-ffp-contract=off", "-fno-fast-math", "-fvisibility=hidden",
+           "-Wall", "-Wextra", "-o", tmp, SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, LIB)
+    return LIB
+
+
+if __name__ == "__main__":
+    print(build(force="--force" in sys.argv))

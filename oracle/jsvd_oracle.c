@@ -1,0 +1,684 @@
+/*
+ * jsvd_oracle.c -- the CPU oracle of the Jacobi SVD hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This is a plain, slow, scalar FP64
+ * restatement of Novakovic, "Vectorization of a thread-parallel Jacobi
+ * singular value decomposition method" (arXiv 2202.08361).  It shares no
+ * code, header, table or constant generator with the CUDA library; only
+ * tests/, __graft_entry__.smoke() and bench.py's CPU-baseline leg may load
+ * it.  The product path never calls it.
+ *
+ * Contents (each function cites the passage it follows):
+ *   orc_dsjac2 / orc_zsjac2  batched 2x2 real symmetric / complex Hermitian
+ *                            EVD, Alg. d8jac2 (supplement SM2.1) and
+ *                            Listing 1 (section 2.3.1), element by element.
+ *   orc_pairs                the cyclic parallel pivot ordering (round-robin
+ *                            reading of section 4.1).
+ *   orc_vjsvd                one-sided Jacobi SVD after Alg. zvjsvd
+ *                            (section 4.3), real or complex (split planes),
+ *                            with the rescaling heuristic of section 3.2,
+ *                            the scaled dot-products of Alg. zdpscl
+ *                            (section 3.3), the convergence test of Eq.
+ *                            "e:tol", the scaled Grammians of Alg. Gram
+ *                            (section 3.4) and the transformations of
+ *                            Eq. "e:transf" / Alg. zjrot (section 3.5).
+ *   orc_svd_adjoint          thin real SVD adjoint (Townsend 2016), used for
+ *                            the differentiated batched SVD.
+ *
+ * Compile with -ffp-contract=off: every fused multiply-add below is an
+ * explicit fma() call, exactly where the paper writes one.
+ *
+ * Readings of the paper where it is silent (also listed in the design doc):
+ *   - zeta of an all-zero 2x2 matrix follows Listing 1 (frexp of the
+ *     smallest subnormal), so zeta is a finite int in [-3, 2094];
+ *   - the packed (zeta' << 1) | p is formed by an unsigned shift;
+ *   - the EVD is computed for every pivot pair, and a pair that is not
+ *     rotated is swapped iff its EVD says lambda1' < lambda2';
+ *   - a pair with a zero column is never rotated; it is swapped iff the
+ *     norm of g_p is below that of g_q;
+ *   - column norms are computed by a two-pass, overflow-free scaled sum of
+ *     squares (max-exponent prescaling), standing in for xNRM2; the norm
+ *     overflow branch of Alg. zvjsvd therefore never fires;
+ *   - odd n: a phantom column n is added to the ordering and pairs that
+ *     contain it are skipped;
+ *   - after convergence the singular values are sorted non-increasingly
+ *     (stable), permuting the columns of U and V alike.
+ */
+#include <float.h>
+#include <limits.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_EXPORT __attribute__((visibility("default")))
+
+/* fl(sqrt(nu)) from Eq. (2.4 "e:tan2"), as printed in Listing 1. */
+static const double SQRT_NU = 1.34078079299425956E+154;
+
+/* x with its sign bit XOR-ed with the sign bit of s (the AVX-512 `xor`
+ * sign transfer of Alg. d8jac2). */
+static double xorsign(double x, double s)
+{
+  uint64_t a, b;
+  memcpy(&a, &x, 8);
+  memcpy(&b, &s, 8);
+  a ^= (b & 0x8000000000000000ull);
+  memcpy(&x, &a, 8);
+  return x;
+}
+
+/* One element of Eq. "e:z" as Listing 1 computes it: eta' - frexp exponent
+ * of max(|x|, smallest subnormal), eta' = DBL_MAX_EXP - 3 = 1021.  This is
+ * eta - floor(lg|x|) with eta = 1020, and 2094 for x = 0. */
+static int zeta_of(double x)
+{
+  int e;
+  (void)frexp(fmax(fabs(x), DBL_TRUE_MIN), &e);
+  return (DBL_MAX_EXP - 3) - e;
+}
+
+static int imin(int a, int b) { return (a <= b) ? a : b; }
+
+/* Pack (zeta' << 1) | p, zeta' = -zeta, through an unsigned shift (a
+ * negative int may not be left-shifted in C). */
+static int32_t pack_zp(int zeta, int p)
+{
+  uint32_t u = ((uint32_t)(-zeta)) << 1;
+  return (int32_t)(u | (uint32_t)(p != 0));
+}
+
+/* Real symmetric 2x2 EVD, Alg. d8jac2 with s = 1 (supplement SM2.1).
+ * Outputs cos(phi), sign(a21)*tan(phi), the backscaled eigenvalues, the
+ * packed (zeta', p).  lam1s/lam2s receive the scaled lambda' (may be NULL). */
+static void dsjac2_1(double a11, double a22, double a21, double *cphi, double *tphi,
+                     double *lam1, double *lam2, int32_t *zp, double *lam1s, double *lam2s)
+{
+  /* Eq. "e:z": the power-of-two scaling exponent, then A' = 2^zeta A. */
+  const int zeta = imin(imin(zeta_of(a11), zeta_of(a22)), zeta_of(a21));
+  a21 = scalbn(a21, zeta);
+  a11 = scalbn(a11, zeta);
+  a22 = scalbn(a22, zeta);
+  /* "polar form" of a real a21: |a21| and sign(a21) */
+  const double aa21 = fabs(a21);
+  /* Eq. "e:tan2" */
+  const double o = 2.0 * aa21; /* exact doubling (scalef by 1) */
+  const double a = a11 - a22;
+  const double tan2 = copysign(fmin(fmax(o / fabs(a), 0.0), SQRT_NU), a);
+  /* Eq. "e:jactan" */
+  const double tan1 = tan2 / (1.0 + sqrt(fma(tan2, tan2, 1.0)));
+  /* Eq. "e:jacsec" */
+  const double sec2 = fma(tan1, tan1, 1.0);
+  const double sec = sqrt(sec2);
+  *cphi = 1.0 / sec;
+  *tphi = xorsign(tan1, a21);
+  /* Eq. "e:lamsec" */
+  const double l1 = fma(tan1, fma(a22, tan1, o), a11) / sec2;
+  const double l2 = fma(tan1, fma(a11, tan1, -o), a22) / sec2;
+  if (lam1) *lam1 = scalbn(l1, -zeta);
+  if (lam2) *lam2 = scalbn(l2, -zeta);
+  if (lam1s) *lam1s = l1;
+  if (lam2s) *lam2s = l2;
+  if (zp) *zp = pack_zp(zeta, l1 < l2);
+}
+
+/* Complex Hermitian 2x2 EVD, Listing 1 (section 2.3.1).  Outputs
+ * cos(phi), cos(alpha)tan(phi), sin(alpha)tan(phi), lambda1, lambda2 and
+ * the packed (zeta', p). */
+static void zsjac2_1(double a11, double a22, double a21r, double a21i, double *cphi,
+                     double *catphi, double *satphi, double *lam1, double *lam2,
+                     int32_t *zp, double *lam1s, double *lam2s)
+{
+  const int zeta = imin(imin(zeta_of(a11), zeta_of(a22)), imin(zeta_of(a21r), zeta_of(a21i)));
+  a21r = scalbn(a21r, zeta);
+  a21i = scalbn(a21i, zeta);
+  a11 = scalbn(a11, zeta);
+  a22 = scalbn(a22, zeta);
+  /* polar form of a21', Eq. "e:zpolar" with the naive hypot of Alg. hypot */
+  const double ar = fabs(a21r), ai = fabs(a21i);
+  const double am = fmin(ar, ai), aM = fmax(ar, ai);
+  const double mM = fmax(am / aM, 0.0);
+  const double aa21 = sqrt(fma(mM, mM, 1.0)) * aM;
+  const double calpha = copysign(fmin(ar / aa21, 1.0), a21r);
+  const double salpha = a21i / fmax(aa21, DBL_TRUE_MIN);
+  /* the Jacobi rotation, section 2.1 */
+  const double o = aa21 * 2.0;
+  const double a = a11 - a22;
+  const double tan2 = copysign(fmin(fmax(o / fabs(a), 0.0), SQRT_NU), a);
+  const double tan1 = tan2 / (1.0 + sqrt(fma(tan2, tan2, 1.0)));
+  const double sec2 = fma(tan1, tan1, 1.0);
+  const double sec = sqrt(sec2);
+  *cphi = 1.0 / sec;
+  *catphi = calpha * tan1;
+  *satphi = salpha * tan1;
+  const double l1 = fma(tan1, fma(a22, tan1, o), a11) / sec2;
+  const double l2 = fma(tan1, fma(a11, tan1, -o), a22) / sec2;
+  if (lam1) *lam1 = scalbn(l1, -zeta);
+  if (lam2) *lam2 = scalbn(l2, -zeta);
+  if (lam1s) *lam1s = l1;
+  if (lam2s) *lam2s = l2;
+  if (zp) *zp = pack_zp(zeta, l1 < l2);
+}
+
+/* Batched real EVD (Alg. dbjac2); any pointer except the inputs, cphi and
+ * tphi may be NULL. */
+ORC_EXPORT void orc_dsjac2(int64_t r, const double *a11, const double *a22, const double *a21,
+                           double *cphi, double *tphi, double *lam1, double *lam2, int32_t *zp)
+{
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < r; ++i)
+    dsjac2_1(a11[i], a22[i], a21[i], cphi + i, tphi + i, lam1 ? lam1 + i : NULL,
+             lam2 ? lam2 + i : NULL, zp ? zp + i : NULL, NULL, NULL);
+}
+
+/* Batched complex EVD (Alg. zbjac2). */
+ORC_EXPORT void orc_zsjac2(int64_t r, const double *a11, const double *a22, const double *a21r,
+                           const double *a21i, double *cphi, double *catphi, double *satphi,
+                           double *lam1, double *lam2, int32_t *zp)
+{
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < r; ++i)
+    zsjac2_1(a11[i], a22[i], a21r[i], a21i[i], cphi + i, catphi + i, satphi + i,
+             lam1 ? lam1 + i : NULL, lam2 ? lam2 + i : NULL, zp ? zp + i : NULL, NULL, NULL);
+}
+
+/* Scaled eigenvalues lambda' (before backscaling) for the pins. */
+ORC_EXPORT void orc_zsjac2_scaled(int64_t r, const double *a11, const double *a22,
+                                  const double *a21r, const double *a21i, double *lam1s,
+                                  double *lam2s)
+{
+  for (int64_t i = 0; i < r; ++i) {
+    double c, ct, st;
+    zsjac2_1(a11[i], a22[i], a21r[i], a21i[i], &c, &ct, &st, NULL, NULL, NULL, lam1s + i,
+             lam2s + i);
+  }
+}
+
+/* ------------------------------------------------------------------------
+ * The cyclic parallel ordering.  Section 4.1 asks for a parallel strategy
+ * with nt/2 disjoint pairs per step; the MM and ME strategies are defined
+ * only in cited work, so the round-robin ("circle") tournament is used:
+ * for nt even (nt = n, or n + 1 with a phantom column n when n is odd),
+ * step k in [0, nt-1), pair l in [0, nt/2):
+ *   l = 0 : (k, nt-1)
+ *   l > 0 : {(k + l) mod (nt-1), (k - l) mod (nt-1)}, ordered p < q.
+ * Every unordered pair occurs exactly once per sweep.
+ * tab receives (nt-1) * (nt/2) * 2 ints, laid out [k][l][p,q].
+ * Returns nt. */
+ORC_EXPORT int orc_pairs(int n, int32_t *tab)
+{
+  const int nt = n + (n & 1);
+  const int K = nt - 1, L = nt / 2;
+  for (int k = 0; k < K; ++k) {
+    for (int l = 0; l < L; ++l) {
+      int p, q;
+      if (l == 0) {
+        p = k;
+        q = nt - 1;
+      } else {
+        const int a = (k + l) % K;
+        const int b = ((k - l) % K + K) % K;
+        p = (a < b) ? a : b;
+        q = (a < b) ? b : a;
+      }
+      tab[2 * ((int64_t)k * L + l)] = p;
+      tab[2 * ((int64_t)k * L + l) + 1] = q;
+    }
+  }
+  return nt;
+}
+
+/* ------------------------------------------------------------------------
+ * One-sided Jacobi SVD (Alg. zvjsvd, section 4.3). */
+
+/* floor(lg x) for finite x > 0 (the AVX-512 getexp). */
+static int flg(double x)
+{
+  int e;
+  (void)frexp(x, &e);
+  return e - 1;
+}
+
+/* The Frobenius norm of a column (one or two planes, length m) as (e, f):
+ * ||x|| = 2^e f, 1 <= f < 2; zero is (INT_MIN, 1) (section 3.2, the (e,f)
+ * representation; supplement SM6.1).  Overflow-free: the column is first
+ * divided by 2^E, E the exponent of its max-norm, then the squares are
+ * summed in row order with fma. */
+static void colnorm(int64_t m, const double *xr, const double *xi, int *e, double *f)
+{
+  double M = 0.0;
+  for (int64_t i = 0; i < m; ++i) M = fmax(M, fabs(xr[i]));
+  if (xi)
+    for (int64_t i = 0; i < m; ++i) M = fmax(M, fabs(xi[i]));
+  if (M == 0.0) {
+    *e = INT_MIN;
+    *f = 1.0;
+    return;
+  }
+  const int E = flg(M);
+  double ssq = 0.0;
+  for (int64_t i = 0; i < m; ++i) {
+    const double y = ldexp(xr[i], -E);
+    ssq = fma(y, y, ssq);
+  }
+  if (xi)
+    for (int64_t i = 0; i < m; ++i) {
+      const double y = ldexp(xi[i], -E);
+      ssq = fma(y, y, ssq);
+    }
+  /* ||x|| = 2^E sqrt(ssq), 1 <= ssq */
+  const double r = sqrt(ssq);
+  const int er = flg(r);
+  *f = ldexp(r, -er);
+  *e = E + er;
+}
+
+/* (e,f) comparison: x < y for norms */
+static int ef_less(int ex, double fx, int ey, double fy)
+{
+  if (ex != ey) return ex < ey;
+  return fx < fy;
+}
+
+/* Alg. zdpscl: z = fl(g_q^* g_p / (||g_q|| ||g_p||)), the columns prescaled
+ * by 2^-e_j in the loop, a single final division by f_q * f_p.  For a real
+ * pair qi = pi = NULL and *zi = 0. */
+static void zdpscl(int64_t m, const double *qr, const double *qi, const double *pr,
+                   const double *pi, int eq, double fq, int ep, double fp, double *zr,
+                   double *zi)
+{
+  double re = 0.0, im = 0.0;
+  if (qi) {
+    for (int64_t i = 0; i < m; ++i) {
+      const double gqr = ldexp(qr[i], -eq), gqi = ldexp(qi[i], -eq);
+      const double gpr = ldexp(pr[i], -ep), gpi = ldexp(pi[i], -ep);
+      re = fma(gqr, gpr, re);
+      im = fma(gqr, gpi, im);
+      re = fma(gqi, gpi, re);
+      im = fma(-gqi, gpr, im);
+    }
+  } else {
+    for (int64_t i = 0; i < m; ++i) re = fma(ldexp(qr[i], -eq), ldexp(pr[i], -ep), re);
+  }
+  const double d = fq * fp;
+  *zr = re / d;
+  *zi = im / d;
+}
+
+/* Alg. hypot, the naive reproducible |z| used by Alg. cvg. */
+static double hypot_naive(double x, double y)
+{
+  x = fabs(x);
+  y = fabs(y);
+  const double m = fmin(x, y), M = fmax(x, y);
+  const double q = fmax(m / M, 0.0);
+  return sqrt(fma(q, q, 1.0)) * M;
+}
+
+/* Alg. Gram: the non-overflowing scaled Grammian A'' from a21' and the
+ * (e,f) norms of g_p (1) and g_q (2). */
+static void gram(double a21r, double a21i, int e1, double f1, int e2, double f2, double *a11,
+                 double *a22, double *b21r, double *b21i)
+{
+  double f12 = f1 / f2, f21 = f2 / f1;
+  int e12 = e1 - e2, e21 = e2 - e1;
+  e12 += flg(f12);
+  f12 = ldexp(f12, -flg(f12));
+  e21 += flg(f21);
+  f21 = ldexp(f21, -flg(f21));
+  const int emax = (e12 > e21) ? e12 : e21;
+  const int sA = imin((DBL_MAX_EXP - 1) - emax, 0);
+  e12 += sA;
+  e21 += sA;
+  *a11 = ldexp(f12, e12);
+  *a22 = ldexp(f21, e21);
+  *b21r = ldexp(a21r, sA);
+  *b21i = ldexp(a21i, sA);
+}
+
+/* Eq. "e:transf" / Alg. zjrot: [x_p x_q] <- [x_p x_q] U P, rows 0..l-1.
+ * Real if xpi == NULL (then S is ignored).  Returns the max-norm of the
+ * transformed pair (max of |Re| and |Im| parts). */
+static double zjrot(int64_t l, double *xpr, double *xpi, double *xqr, double *xqi, double c,
+                    double C, double S, int swap)
+{
+  double M = 0.0;
+  for (int64_t i = 0; i < l; ++i) {
+    double npr, npi = 0.0, nqr, nqi = 0.0;
+    if (xpi) {
+      const double pr = xpr[i], pi = xpi[i], qr = xqr[i], qi = xqi[i];
+      /* fma(x_q, e', x_p) c, e' = C + iS, complex fma of Eq. "e:zfma" */
+      npr = fma(qr, C, fma(-qi, S, pr)) * c;
+      npi = fma(qr, S, fma(qi, C, pi)) * c;
+      /* fma(x_p, -conj(e'), x_q) c, -conj(e') = -C + iS */
+      nqr = fma(pr, -C, fma(-pi, S, qr)) * c;
+      nqi = fma(pr, S, fma(pi, -C, qi)) * c;
+    } else {
+      const double pr = xpr[i], qr = xqr[i];
+      npr = fma(qr, C, pr) * c;
+      nqr = fma(pr, -C, qr) * c;
+    }
+    M = fmax(M, fmax(fabs(npr), fabs(nqr)));
+    if (xpi) M = fmax(M, fmax(fabs(npi), fabs(nqi)));
+    if (swap) {
+      xpr[i] = nqr;
+      xqr[i] = npr;
+      if (xpi) {
+        xpi[i] = nqi;
+        xqi[i] = npi;
+      }
+    } else {
+      xpr[i] = npr;
+      xqr[i] = nqr;
+      if (xpi) {
+        xpi[i] = npi;
+        xqi[i] = nqi;
+      }
+    }
+  }
+  return M;
+}
+
+static void swap_cols(int64_t l, double *a, double *b)
+{
+  for (int64_t i = 0; i < l; ++i) {
+    const double t = a[i];
+    a[i] = b[i];
+    b[i] = t;
+  }
+}
+
+/* max-norm of a plane (NaN -> inf), section 3.2 */
+static double maxnorm(int64_t m, int64_t n, const double *x, int64_t ld)
+{
+  double M = 0.0;
+  for (int64_t j = 0; j < n; ++j)
+    for (int64_t i = 0; i < m; ++i) M = fmax(M, fmin(fabs(x[i + j * ld]), INFINITY));
+  return M;
+}
+
+/* Return codes shared with tests (not with the library). */
+#define ORC_OK 0
+#define ORC_E_ARG (-1)
+#define ORC_E_NONFINITE (-2)
+#define ORC_NOT_CONVERGED 1
+
+/*
+ * orc_vjsvd: Alg. zvjsvd (complex, Gi != NULL) or its real variant dvjsvd.
+ *   G (Gr, Gi): m x n, column-major, leading dimension ld, m >= n >= 1;
+ *     overwritten by U (columns of unit norm, zero columns stay zero).
+ *   V (Vr, Vi): n x n, leading dimension n, overwritten by V.
+ *   sig, sig_e, sig_f: n singular values, as doubles and as (e, f).
+ *   out_info[4] = {status, sweeps, rotations (low 31 bits), rescales}.
+ *   rotations64 receives the 64-bit rotation count (may be NULL).
+ * nthreads <= 0 leaves the OpenMP default.
+ */
+ORC_EXPORT int orc_vjsvd(int64_t m, int64_t n, double *Gr, double *Gi, int64_t ld, double *Vr,
+                         double *Vi, double *sig, double *sig_e, double *sig_f, int max_sweeps,
+                         int nthreads, int32_t *out_info, int64_t *rotations64)
+{
+  if (m < 1 || n < 1 || m < n || ld < m || max_sweeps < 1) return ORC_E_ARG;
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+  (void)nthreads;
+#endif
+  const int cplx = (Gi != NULL);
+  /* V_1 = I */
+  for (int64_t j = 0; j < n; ++j)
+    for (int64_t i = 0; i < n; ++i) {
+      Vr[i + j * n] = (i == j) ? 1.0 : 0.0;
+      if (cplx) Vi[i + j * n] = 0.0;
+    }
+  /* section 3.2, step 1: M~_0 and s_0 = s_[0] (Eq. "e:skn") */
+  double Mt = maxnorm(m, n, Gr, ld);
+  if (cplx) Mt = fmax(Mt, maxnorm(m, n, Gi, ld));
+  if (!(Mt < INFINITY)) return ORC_E_NONFINITE;
+  int64_t rotations = 0;
+  int rescales = 0, sweeps = 0, status = ORC_OK;
+  int s = 0;
+  /* floor(lg(nu/(varsigma m))) and friends, Eq. "e:skn" / "e:skr" */
+  const int lg_skn = cplx ? flg(DBL_MAX / (4.0 * (double)m) / M_SQRT2) : flg(DBL_MAX / (2.0 * (double)m));
+  const int lg_skr = cplx ? flg(DBL_MAX / 4.0 / M_SQRT2) : flg(DBL_MAX / 2.0);
+  int32_t *tab = NULL;
+  int nt = (int)(n + (n & 1));
+  if (Mt > 0.0) {
+    s = lg_skn - flg(Mt) - 1;
+    for (int64_t j = 0; j < n; ++j)
+      for (int64_t i = 0; i < m; ++i) {
+        Gr[i + j * ld] = ldexp(Gr[i + j * ld], s);
+        if (cplx) Gi[i + j * ld] = ldexp(Gi[i + j * ld], s);
+      }
+    Mt = ldexp(Mt, s);
+    tab = (int32_t *)malloc(sizeof(int32_t) * 2 * (size_t)(nt - 1 > 0 ? nt - 1 : 1) * (size_t)(nt / 2 > 0 ? nt / 2 : 1));
+    if (!tab) return ORC_E_ARG;
+    if (nt >= 2) (void)orc_pairs((int)n, tab);
+    /* Eq. "e:tol": upsilon = fl(eps sqrt(m)), eps = 2^-53 */
+    const double ups = ldexp(sqrt((double)m), -53);
+    const int K = nt - 1, L = nt / 2;
+    int converged = (nt < 2);
+    for (int C = 0; C < max_sweeps && !converged; ++C) {
+      int64_t T = 0;
+      for (int k = 0; k < K; ++k) {
+        /* step 2 of the heuristic: s_(k) < 0 => downscale by 2^{s_[k]} */
+        const int sk_r = lg_skr - flg(Mt) - (cplx ? 1 : 0);
+        if (sk_r < 0) {
+          const int sk_n = lg_skn - flg(Mt) - 1;
+          for (int64_t j = 0; j < n; ++j)
+            for (int64_t i = 0; i < m; ++i) {
+              Gr[i + j * ld] = ldexp(Gr[i + j * ld], sk_n);
+              if (cplx) Gi[i + j * ld] = ldexp(Gi[i + j * ld], sk_n);
+            }
+          Mt = ldexp(Mt, sk_n);
+          s += sk_n;
+          ++rescales;
+        }
+        int64_t t = 0;
+        double Mstep = 0.0;
+#pragma omp parallel for schedule(static) reduction(+ : t) reduction(max : Mstep)
+        for (int l = 0; l < L; ++l) {
+          const int p = tab[2 * ((int64_t)k * L + l)], q = tab[2 * ((int64_t)k * L + l) + 1];
+          if (q >= n) continue; /* phantom column */
+          double *gpr = Gr + p * ld, *gqr = Gr + q * ld;
+          double *gpi = cplx ? Gi + p * ld : NULL, *gqi = cplx ? Gi + q * ld : NULL;
+          double *vpr = Vr + p * n, *vqr = Vr + q * n;
+          double *vpi = cplx ? Vi + p * n : NULL, *vqi = cplx ? Vi + q * n : NULL;
+          int ep, eq;
+          double fp, fq;
+          colnorm(m, gpr, gpi, &ep, &fp);
+          colnorm(m, gqr, gqi, &eq, &fq);
+          if (ep == INT_MIN || eq == INT_MIN) {
+            if (ef_less(ep, fp, eq, fq)) {
+              swap_cols(m, gpr, gqr);
+              swap_cols(n, vpr, vqr);
+              if (cplx) {
+                swap_cols(m, gpi, gqi);
+                swap_cols(n, vpi, vqi);
+              }
+            }
+            continue;
+          }
+          double zr, zi;
+          zdpscl(m, gqr, gqi, gpr, gpi, eq, fq, ep, fp, &zr, &zi);
+          /* Alg. cvg */
+          const double az = cplx ? hypot_naive(zr, zi) : fabs(zr);
+          const int rot = (ups <= az);
+          /* Alg. Gram, then the EVD (Alg. zbjac2 / dbjac2) */
+          double b11, b22, b21r, b21i;
+          gram(zr, zi, ep, fp, eq, fq, &b11, &b22, &b21r, &b21i);
+          double c, Ct, St = 0.0;
+          int32_t zp;
+          if (cplx)
+            zsjac2_1(b11, b22, b21r, b21i, &c, &Ct, &St, NULL, NULL, &zp, NULL, NULL);
+          else
+            dsjac2_1(b11, b22, b21r, &c, &Ct, NULL, NULL, &zp, NULL, NULL);
+          const int pbit = zp & 1;
+          if (rot) {
+            const double Mp = zjrot(m, gpr, gpi, gqr, gqi, c, Ct, St, pbit);
+            (void)zjrot(n, vpr, vpi, vqr, vqi, c, Ct, St, pbit);
+            Mstep = fmax(Mstep, Mp);
+            ++t;
+          } else if (pbit) {
+            swap_cols(m, gpr, gqr);
+            swap_cols(n, vpr, vqr);
+            if (cplx) {
+              swap_cols(m, gpi, gqi);
+              swap_cols(n, vpi, vqi);
+            }
+          }
+        }
+        T += t;
+        Mt = fmax(Mt, Mstep);
+      }
+      rotations += T;
+      sweeps = C + 1;
+      if (T == 0) converged = 1;
+    }
+    if (!converged) status = ORC_NOT_CONVERGED;
+  }
+  /* section 4.2.1: U = G columns scaled by 2^-e_j and divided by f_j;
+   * sigma_j = (e_j - s, f_j) */
+  int *ee = (int *)malloc(sizeof(int) * (size_t)n);
+  double *ff = (double *)malloc(sizeof(double) * (size_t)n);
+  int64_t *perm = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+  if (!ee || !ff || !perm) {
+    free(tab); free(ee); free(ff); free(perm);
+    return ORC_E_ARG;
+  }
+  for (int64_t j = 0; j < n; ++j) {
+    colnorm(m, Gr + j * ld, cplx ? Gi + j * ld : NULL, &ee[j], &ff[j]);
+    if (ee[j] == INT_MIN) {
+      for (int64_t i = 0; i < m; ++i) {
+        Gr[i + j * ld] = 0.0;
+        if (cplx) Gi[i + j * ld] = 0.0;
+      }
+      continue;
+    }
+    for (int64_t i = 0; i < m; ++i) {
+      Gr[i + j * ld] = ldexp(Gr[i + j * ld], -ee[j]) / ff[j];
+      if (cplx) Gi[i + j * ld] = ldexp(Gi[i + j * ld], -ee[j]) / ff[j];
+    }
+    ee[j] -= s;
+  }
+  /* stable sort by sigma, non-increasing (insertion sort: n is small here) */
+  for (int64_t j = 0; j < n; ++j) perm[j] = j;
+  for (int64_t j = 1; j < n; ++j) {
+    const int64_t x = perm[j];
+    int64_t i = j - 1;
+    while (i >= 0) {
+      const int64_t y = perm[i];
+      /* y goes after x iff sigma_y < sigma_x (zero norms are smallest) */
+      const int y_zero = (ee[y] == INT_MIN), x_zero = (ee[x] == INT_MIN);
+      int y_less;
+      if (y_zero || x_zero) y_less = y_zero && !x_zero;
+      else y_less = ef_less(ee[y], ff[y], ee[x], ff[x]);
+      if (!y_less) break;
+      perm[i + 1] = y;
+      --i;
+    }
+    perm[i + 1] = x;
+  }
+  double *tmp = (double *)malloc(sizeof(double) * (size_t)(m > n ? m : n) * (size_t)n);
+  if (!tmp) {
+    free(tab); free(ee); free(ff); free(perm);
+    return ORC_E_ARG;
+  }
+  for (int plane = 0; plane < (cplx ? 2 : 1); ++plane) {
+    double *Gx = plane ? Gi : Gr, *Vx = plane ? Vi : Vr;
+    for (int64_t j = 0; j < n; ++j) memcpy(tmp + j * m, Gx + perm[j] * ld, sizeof(double) * (size_t)m);
+    for (int64_t j = 0; j < n; ++j) memcpy(Gx + j * ld, tmp + j * m, sizeof(double) * (size_t)m);
+    for (int64_t j = 0; j < n; ++j) memcpy(tmp + j * n, Vx + perm[j] * n, sizeof(double) * (size_t)n);
+    for (int64_t j = 0; j < n; ++j) memcpy(Vx + j * n, tmp + j * n, sizeof(double) * (size_t)n);
+  }
+  for (int64_t j = 0; j < n; ++j) {
+    const int64_t y = perm[j];
+    const int zero = (ee[y] == INT_MIN);
+    if (sig) sig[j] = zero ? 0.0 : ldexp(ff[y], ee[y]);
+    if (sig_e) sig_e[j] = zero ? -INFINITY : (double)ee[y];
+    if (sig_f) sig_f[j] = zero ? 1.0 : ff[y];
+  }
+  free(tmp);
+  free(tab);
+  free(ee);
+  free(ff);
+  free(perm);
+  if (out_info) {
+    out_info[0] = status;
+    out_info[1] = sweeps;
+    out_info[2] = (int32_t)(rotations & 0x7fffffff);
+    out_info[3] = rescales;
+  }
+  if (rotations64) *rotations64 = rotations;
+  return status;
+}
+
+/* ------------------------------------------------------------------------
+ * Thin real SVD adjoint (Townsend 2016, "Differentiating the singular value
+ * decomposition"; Ionescu, Vantzos, Sminchisescu 2015):
+ *   Abar = U [ (F o (U^T Ubar - Ubar^T U)) S + diag(Sbar)
+ *              + S (F o (V^T Vbar - Vbar^T V)) ] V^T
+ *        + (I - U U^T) Ubar S^-1 V^T,
+ *   F_ij = 1/(s_j^2 - s_i^2) for i != j, F_ii = 0.
+ * U, Ubar, Abar: m x n; V, Vbar: n x n; all column-major, leading dimension
+ * m or n.  Vbar may be NULL (zero).  Plain triple loops. */
+ORC_EXPORT int orc_svd_adjoint(int64_t m, int64_t n, const double *U, const double *s,
+                               const double *V, const double *Ubar, const double *sbar,
+                               const double *Vbar, double *Abar)
+{
+  double *J = (double *)calloc((size_t)(n * n), sizeof(double));
+  double *Kv = (double *)calloc((size_t)(n * n), sizeof(double));
+  double *In = (double *)calloc((size_t)(n * n), sizeof(double));
+  double *W = (double *)calloc((size_t)(m * n), sizeof(double));
+  if (!J || !Kv || !In || !W) {
+    free(J); free(Kv); free(In); free(W);
+    return ORC_E_ARG;
+  }
+  /* J = U^T Ubar, Kv = V^T Vbar */
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t j = 0; j < n; ++j) {
+      double acc = 0.0;
+      for (int64_t r = 0; r < m; ++r) acc += U[r + i * m] * Ubar[r + j * m];
+      J[i + j * n] = acc;
+      double acc2 = 0.0;
+      if (Vbar)
+        for (int64_t r = 0; r < n; ++r) acc2 += V[r + i * n] * Vbar[r + j * n];
+      Kv[i + j * n] = acc2;
+    }
+  /* inner = (F o (J - J^T)) S + diag(sbar) + S (F o (Kv - Kv^T)) */
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t j = 0; j < n; ++j) {
+      double v = 0.0;
+      if (i != j) {
+        const double F = 1.0 / (s[j] * s[j] - s[i] * s[i]);
+        v = F * (J[i + j * n] - J[j + i * n]) * s[j] + s[i] * F * (Kv[i + j * n] - Kv[j + i * n]);
+      } else {
+        v = sbar ? sbar[i] : 0.0;
+      }
+      In[i + j * n] = v;
+    }
+  /* W = U inner + (Ubar - U J) diag(1/s) */
+  for (int64_t r = 0; r < m; ++r)
+    for (int64_t j = 0; j < n; ++j) {
+      double a = 0.0, uj = 0.0;
+      for (int64_t i = 0; i < n; ++i) {
+        a += U[r + i * m] * In[i + j * n];
+        uj += U[r + i * m] * J[i + j * n];
+      }
+      W[r + j * m] = a + (Ubar[r + j * m] - uj) / s[j];
+    }
+  /* Abar = W V^T */
+  for (int64_t r = 0; r < m; ++r)
+    for (int64_t c = 0; c < n; ++c) {
+      double acc = 0.0;
+      for (int64_t j = 0; j < n; ++j) acc += W[r + j * m] * V[c + j * n];
+      Abar[r + c * m] = acc;
+    }
+  free(J);
+  free(Kv);
+  free(In);
+  free(W);
+  return ORC_OK;
+}

@@ -1,0 +1,176 @@
+"""Seeded synthetic inputs shaped like the paper's workloads.
+
+This module holds no arithmetic of the method itself: it only draws the
+matrices that the library, the tests and the benchmark feed in.  The same
+generators serve the CUDA path and the CPU oracle.
+
+Seeds: numpy.random.Generator(PCG64(20220217 + workload_id)), so a workload
+is the same on every machine.
+
+Workloads (ids):
+  1  real 256 x 128 matrix, i.i.d. N(0, 1)                     (one SVD)
+  2  2x2 EVD batches: 2^24 real + 2^24 complex, entries
+     sign * (1 + u) * 2^e, u ~ U[0,1), e ~ U{-1074..1023}, 1 % exact zeros
+  3  complex 4096 x 2048, A = Q1 diag(s) Q2^H, Haar Q1, Q2, s geometric
+     from 1 to 1e-6
+  4  10,000 real matrices, n ~ U{16..256}, m ~ U{n..2n}, s geometric with
+     condition 1e4, random orthogonal factors
+  5  4096 real 64 x 32 matrices, s geometric with condition 1e3,
+     w ~ U[0,1)^32, C ~ N(0,1)^(64 x 8) per matrix
+"""
+import numpy as np
+
+BASE_SEED = 20220217
+
+
+def rng(workload_id: int, salt: int = 0) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(BASE_SEED + workload_id + 1000 * salt))
+
+
+# ---------------------------------------------------------------------------
+# 2x2 EVD inputs (workload 2)
+
+def wide_range_values(g: np.random.Generator, r: int, zero_frac: float = 0.01) -> np.ndarray:
+    """sign * (1 + u) * 2^e with e uniform in [-1074, 1023] (ldexp rounds the
+    subnormal ones), sign +-1 equiprobable, each entry exactly 0 w.p. zero_frac."""
+    u = g.random(r)
+    e = g.integers(-1074, 1024, size=r)
+    s = np.where(g.random(r) < 0.5, -1.0, 1.0)
+    x = np.ldexp(1.0 + u, e) * s
+    x[g.random(r) < zero_frac] = 0.0
+    return x
+
+
+def evd_batch(r: int, complex_: bool, seed_salt: int = 0):
+    """SoA streams (a11, a22, a21_re[, a21_im]) of r Hermitian 2x2 matrices."""
+    g = rng(2, seed_salt + (1 if complex_ else 0))
+    a11 = wide_range_values(g, r)
+    a22 = wide_range_values(g, r)
+    a21r = wide_range_values(g, r)
+    if complex_:
+        a21i = wide_range_values(g, r)
+        return a11, a22, a21r, a21i
+    return a11, a22, a21r
+
+
+def evd_prescribed(r: int, complex_: bool, seed_salt: int = 0):
+    """Matrices built from prescribed eigenvalues, tan(phi) and cos(alpha)
+    as in the paper's EVD test data (Eq. 2.2, section 5.1), in FP64 here:
+    |lambda_j| <= nu/16 reinterpreted from random bits, tan(phi), cos(alpha)
+    uniform in [-1, 1)."""
+    g = rng(2, 10 + seed_salt + (1 if complex_ else 0))
+
+    def lam():
+        out = np.empty(r)
+        filled = 0
+        while filled < r:
+            bits = g.integers(0, 2**63, size=2 * (r - filled), dtype=np.int64)
+            bits ^= g.integers(0, 2, size=bits.size, dtype=np.int64) << 63
+            v = bits.view(np.float64)
+            v = v[np.isfinite(v) & (np.abs(v) <= np.finfo(np.float64).max / 16)]
+            take = min(v.size, r - filled)
+            out[filled:filled + take] = v[:take]
+            filled += take
+        return out
+
+    l1, l2 = lam(), lam()
+    t = g.random(r) * 2.0 - 1.0
+    c2 = 1.0 / (1.0 + t * t)
+    if complex_:
+        ca = g.random(r) * 2.0 - 1.0
+        sa = np.sqrt(np.maximum(1.0 - ca * ca, 0.0)) * np.where(g.random(r) < 0.5, -1.0, 1.0)
+    else:
+        ca, sa = np.ones(r), np.zeros(r)
+    with np.errstate(over="ignore", invalid="ignore"):
+        a11 = c2 * (l1 + l2 * t * t)
+        a22 = c2 * (l1 * t * t + l2)
+        off = c2 * t * (l1 - l2)
+    a21r, a21i = off * ca, off * sa
+    ok = np.isfinite(a11) & np.isfinite(a22) & np.isfinite(a21r) & np.isfinite(a21i)
+    a11[~ok] = 1.0
+    a22[~ok] = 2.0
+    a21r[~ok] = 0.5
+    a21i[~ok] = 0.0
+    if complex_:
+        return a11, a22, a21r, a21i
+    return a11, a22, a21r
+
+
+# ---------------------------------------------------------------------------
+# SVD inputs
+
+def haar(g: np.random.Generator, m: int, n: int, complex_: bool) -> np.ndarray:
+    """m x n matrix with orthonormal columns, Haar-distributed (QR of a
+    Gaussian with the R-diagonal phase fix, Mezzadri 2007)."""
+    if complex_:
+        Z = (g.standard_normal((m, n)) + 1j * g.standard_normal((m, n))) / np.sqrt(2.0)
+    else:
+        Z = g.standard_normal((m, n))
+    Q, R = np.linalg.qr(Z)
+    d = np.diagonal(R).copy()
+    ph = d / np.where(np.abs(d) == 0, 1.0, np.abs(d))
+    return Q * ph
+
+
+def geometric_sigma(n: int, cond: float) -> np.ndarray:
+    """sigma_i = cond^{-(i-1)/(n-1)}, i = 1..n (log-equidistributed, as the
+    paper's Xi datasets, section 5.1)."""
+    if n == 1:
+        return np.ones(1)
+    return cond ** (-np.arange(n) / (n - 1.0))
+
+
+def svd_geometric(m: int, n: int, cond: float, complex_: bool, g: np.random.Generator):
+    """A = Q1 diag(s) Q2^H, returns (A, s)."""
+    s = geometric_sigma(n, cond)
+    Q1 = haar(g, m, n, complex_)
+    Q2 = haar(g, n, n, complex_)
+    A = (Q1 * s) @ Q2.conj().T
+    return np.asfortranarray(A), s
+
+
+def svd_normal(m: int = 256, n: int = 128, seed_salt: int = 0) -> np.ndarray:
+    """Workload 1: real m x n, i.i.d. N(0,1), column-major."""
+    g = rng(1, seed_salt)
+    return np.asfortranarray(g.standard_normal((m, n)))
+
+
+def svd_complex_geometric(m: int = 4096, n: int = 2048, cond: float = 1e6, seed_salt: int = 0):
+    """Workload 3: complex A = Q1 diag(s) Q2^H, s from 1 down to 1/cond."""
+    return svd_geometric(m, n, cond, True, rng(3, seed_salt))
+
+
+def uneven_shapes(count: int = 10000, nmin: int = 16, nmax: int = 256, seed_salt: int = 0):
+    """Workload 4 shapes: n ~ U{nmin..nmax}, m ~ U{n..2n}."""
+    g = rng(4, seed_salt)
+    n = g.integers(nmin, nmax + 1, size=count)
+    m = np.array([g.integers(k, 2 * k + 1) for k in n])
+    return m.astype(np.int64), n.astype(np.int64)
+
+
+def uneven_batch(count: int = 10000, nmin: int = 16, nmax: int = 256, cond: float = 1e4,
+                 seed_salt: int = 0, indices=None):
+    """Workload 4 matrices (list of Fortran-ordered arrays).  `indices`
+    selects a subset (each matrix has its own generator, so a subset is
+    bit-identical to the same matrices drawn inside the full batch)."""
+    m, n = uneven_shapes(count, nmin, nmax, seed_salt)
+    idx = range(count) if indices is None else indices
+    out = []
+    for i in idx:
+        g = np.random.Generator(np.random.PCG64([BASE_SEED + 4, seed_salt, int(i)]))
+        A, _ = svd_geometric(int(m[i]), int(n[i]), cond, False, g)
+        out.append(A)
+    return out, m, n
+
+
+def diff_batch(count: int = 4096, m: int = 64, n: int = 32, cond: float = 1e3, k: int = 8,
+               seed_salt: int = 0):
+    """Workload 5: (A[count, m, n] column-major per matrix as a C array of
+    shape (count, n, m) transposed views, w[count, n], C[count, m, k])."""
+    g = rng(5, seed_salt)
+    A = np.empty((count, m, n))
+    for i in range(count):
+        A[i], _ = svd_geometric(m, n, cond, False, g)
+    w = g.random((count, n))
+    C = g.standard_normal((count, m, k))
+    return A, w, C
