@@ -49,8 +49,14 @@ def lib():
         L.orc_vjsvd.restype = ctypes.c_int
         L.orc_svd_adjoint.argtypes = [ctypes.c_int64, ctypes.c_int64, _d, _d, _d, _d, _d, _d, _d]
         L.orc_svd_adjoint.restype = ctypes.c_int
+        L.orc_num_threads.restype = ctypes.c_int
         _lib = L
     return _lib
+
+
+def num_threads():
+    """OpenMP threads the oracle's parallel loops use."""
+    return int(lib().orc_num_threads())
 
 
 def _dp(a):

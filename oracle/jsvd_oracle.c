@@ -400,6 +400,16 @@ static double maxnorm(int64_t m, int64_t n, const double *x, int64_t ld)
   return M;
 }
 
+/* Number of OpenMP threads a parallel region of the oracle uses. */
+ORC_EXPORT int orc_num_threads(void)
+{
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
 /* Return codes shared with tests (not with the library). */
 #define ORC_OK 0
 #define ORC_E_ARG (-1)

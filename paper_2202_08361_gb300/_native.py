@@ -1,0 +1,79 @@
+"""ctypes binding of libjsvd.so (include/jsvd.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels of the library.  There is no CPU fallback; if the library has not
+been built the first call raises.
+"""
+import ctypes
+import os
+
+from . import build as _build
+
+JSVD_OK = 0
+JSVD_E_CUDA = -100
+JSVD_E_NONFINITE = -101
+JSVD_E_TIMEOUT = -102
+JSVD_E_WORKSPACE = -103
+JSVD_E_UNSUPPORTED = -104
+JSVD_NOT_CONVERGED = 1
+
+JSVD_REAL = 0
+JSVD_COMPLEX = 1
+
+JSVD_TUNE_EVD_LAUNCH = 1
+
+
+class JsvdError(RuntimeError):
+    def __init__(self, code, what):
+        self.code = code
+        msg = "%s failed: %d (%s)" % (what, code, strerror(code))
+        if code == JSVD_E_CUDA:
+            msg += ": " + last_cuda_error()
+        super().__init__(msg)
+
+
+class EvdStreams(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_void_p) for name in
+                ("a11", "a22", "a21_re", "a21_im", "cos_phi", "ea_tan_re", "ea_tan_im",
+                 "lambda1", "lambda2", "zeta_p")]
+
+
+_lib = None
+_vp = ctypes.c_void_p
+_i64 = ctypes.c_int64
+
+
+def lib():
+    """The loaded library (raises if it is not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError(
+                "libjsvd.so is not built: run `python -c \"import __graft_entry__ as g; "
+                "g.build()\"` (or python -m paper_2202_08361_gb300.build); there is no "
+                "CPU fallback")
+        L = ctypes.CDLL(_build.LIB)
+        L.jsvd_version.restype = ctypes.c_int
+        L.jsvd_strerror.argtypes = [ctypes.c_int]
+        L.jsvd_strerror.restype = ctypes.c_char_p
+        L.jsvd_last_cuda_error.restype = ctypes.c_char_p
+        L.jsvd_tune_set.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
+        L.jsvd_tune_set.restype = ctypes.c_int
+        L.jsvd_evd2x2_batched.argtypes = [ctypes.c_int, ctypes.POINTER(EvdStreams), _i64, _vp]
+        L.jsvd_evd2x2_batched.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def strerror(code):
+    return lib().jsvd_strerror(int(code)).decode()
+
+
+def last_cuda_error():
+    return lib().jsvd_last_cuda_error().decode()
+
+
+def check(rc, what):
+    if rc != JSVD_OK:
+        raise JsvdError(rc, what)
+    return rc

@@ -1,0 +1,61 @@
+// api.cu -- library-wide entry points: version, error strings, tuning knobs.
+#include <mutex>
+
+#include "common.cuh"
+#include "jsvd_internal.h"
+
+namespace jsvd {
+
+static thread_local cudaError_t g_last_cuda = cudaSuccess;
+
+int cuda_fail(cudaError_t e)
+{
+  g_last_cuda = e;
+  return JSVD_E_CUDA;
+}
+
+int sm_count()
+{
+  static std::mutex mu;
+  static int cache[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!cache[dev]) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0)
+      v = 152;
+    cache[dev] = v;
+  }
+  return cache[dev];
+}
+
+}  // namespace jsvd
+
+extern "C" int jsvd_version(void) { return 100; }
+
+extern "C" const char *jsvd_strerror(int code)
+{
+  switch (code) {
+    case JSVD_OK: return "success";
+    case JSVD_E_CUDA: return "a CUDA runtime call failed";
+    case JSVD_E_NONFINITE: return "the input holds a non-finite value";
+    case JSVD_E_TIMEOUT: return "a bounded device-side wait gave up";
+    case JSVD_E_WORKSPACE: return "the workspace is too small";
+    case JSVD_E_UNSUPPORTED: return "unsupported combination of arguments";
+    default: return (code < 0 && code > -32) ? "invalid argument" : "unknown code";
+  }
+}
+
+extern "C" const char *jsvd_last_cuda_error(void)
+{
+  return cudaGetErrorString(jsvd::g_last_cuda);
+}
+
+extern "C" int jsvd_tune_set(int knob, int value, int value2)
+{
+  switch (knob) {
+    case JSVD_TUNE_EVD_LAUNCH: return jsvd::evd2_set_launch(value, value2);
+    default: return -1;
+  }
+}

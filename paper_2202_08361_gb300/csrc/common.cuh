@@ -1,0 +1,30 @@
+// common.cuh -- host-side plumbing shared by the library's .cu files.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "jsvd.h"
+
+namespace jsvd {
+
+// Number of SMs of the current device (cached per device).
+int sm_count();
+
+// Map a CUDA error to the ABI code (JSVD_E_CUDA), remembering the text.
+int cuda_fail(cudaError_t e);
+
+inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+#define JSVD_CHECK_LAUNCH()                                   \
+  do {                                                        \
+    cudaError_t e_ = cudaGetLastError();                      \
+    if (e_ != cudaSuccess) return ::jsvd::cuda_fail(e_);      \
+  } while (0)
+
+#define JSVD_CUDA(call)                                       \
+  do {                                                        \
+    cudaError_t e_ = (call);                                  \
+    if (e_ != cudaSuccess) return ::jsvd::cuda_fail(e_);      \
+  } while (0)
+
+}  // namespace jsvd

@@ -1,0 +1,84 @@
+// evd2.cu -- jsvd_evd2x2_batched: the batched 2x2 Hermitian EVD.
+//
+// One thread per matrix over structure-of-arrays streams (section 2.4.1),
+// the GPU form the paper sketches in supplement SM10, here as a persistent
+// grid-stride kernel sized to the SM count.  Inputs are read once with
+// streaming loads, outputs written with streaming stores; each matrix is
+// independent, so any grid shape and any sub-range give the same bits.
+#include "common.cuh"
+#include "evd2.cuh"
+#include "jsvd_internal.h"
+
+namespace jsvd {
+
+template <bool CPLX>
+__global__ void __launch_bounds__(256) evd2_kernel(const double *__restrict__ a11p,
+                                                   const double *__restrict__ a22p,
+                                                   const double *__restrict__ a21rp,
+                                                   const double *__restrict__ a21ip,
+                                                   double *__restrict__ cphip,
+                                                   double *__restrict__ etrp,
+                                                   double *__restrict__ etip,
+                                                   double *__restrict__ l1p,
+                                                   double *__restrict__ l2p,
+                                                   int32_t *__restrict__ zpp, int64_t n)
+{
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const double a11 = __ldcs(a11p + i), a22 = __ldcs(a22p + i), a21r = __ldcs(a21rp + i);
+    Rot2 r;
+    if (CPLX) {
+      r = zsjac2(a11, a22, a21r, __ldcs(a21ip + i));
+    } else {
+      r = dsjac2(a11, a22, a21r);
+    }
+    __stcs(cphip + i, r.cphi);
+    __stcs(etrp + i, r.etr);
+    if (CPLX) __stcs(etip + i, r.eti);
+    if (l1p) __stcs(l1p + i, ldexp_rn(r.l1s, -r.zeta));
+    if (l2p) __stcs(l2p + i, ldexp_rn(r.l2s, -r.zeta));
+    if (zpp) __stcs(zpp + i, pack_zp(r));
+  }
+}
+
+static int g_evd_block = 256;
+static int g_evd_blocks_per_sm = 8;
+
+int evd2_set_launch(int block, int blocks_per_sm)
+{
+  if (block != 64 && block != 128 && block != 256) return -2;
+  if (blocks_per_sm < 1 || blocks_per_sm > 64) return -3;
+  g_evd_block = block;
+  g_evd_blocks_per_sm = blocks_per_sm;
+  return JSVD_OK;
+}
+
+}  // namespace jsvd
+
+extern "C" int jsvd_evd2x2_batched(jsvd_field field, const jsvd_evd2_streams *s, int64_t n,
+                                   void *stream)
+{
+  using namespace jsvd;
+  if (field != JSVD_REAL && field != JSVD_COMPLEX) return -1;
+  if (!s) return -2;
+  if (n < 0) return -3;
+  if (n == 0) return JSVD_OK;
+  const bool cplx = (field == JSVD_COMPLEX);
+  if (!s->a11 || !s->a22 || !s->a21_re || !s->cos_phi || !s->ea_tan_re) return -2;
+  if (cplx && (!s->a21_im || !s->ea_tan_im)) return -2;
+  const int block = g_evd_block;
+  const int64_t need = (n + block - 1) / block;
+  const int64_t cap = (int64_t)sm_count() * g_evd_blocks_per_sm;
+  const int grid = (int)(need < cap ? need : cap);
+  cudaStream_t st = as_stream(stream);
+  if (cplx)
+    evd2_kernel<true><<<grid, block, 0, st>>>(s->a11, s->a22, s->a21_re, s->a21_im, s->cos_phi,
+                                              s->ea_tan_re, s->ea_tan_im, s->lambda1,
+                                              s->lambda2, s->zeta_p, n);
+  else
+    evd2_kernel<false><<<grid, block, 0, st>>>(s->a11, s->a22, s->a21_re, nullptr, s->cos_phi,
+                                               s->ea_tan_re, nullptr, s->lambda1, s->lambda2,
+                                               s->zeta_p, n);
+  JSVD_CHECK_LAUNCH();
+  return JSVD_OK;
+}

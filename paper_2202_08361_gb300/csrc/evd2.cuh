@@ -1,0 +1,110 @@
+// evd2.cuh -- the branch-free eigendecomposition of one Hermitian matrix of
+// order two, as a device function (one thread, one matrix).
+//
+// It computes what Listing 1 (complex) and Alg. d8jac2 (real, supplement
+// SM2.1) of the paper compute, operation for operation in binary64 with
+// round-to-nearest: the prescaling exponent of Eq. e:z, the polar form of
+// Eq. e:zpolar with the naive hypot of Alg. hypot, tan(2 phi) clamped as in
+// Eq. e:tan2, tan(phi) from Eq. e:jactan, sec^2, sec and cos(phi) from
+// Eq. e:jacsec (never rsqrt), the eigenvalues of Eq. e:lamsec and the
+// permutation bit p = (lambda1' < lambda2').  Exponent and sign
+// manipulations run on the integer pipe (fp64bits.cuh); the IEEE
+// min/max filtering of NaN becomes explicit integer selects that give the
+// same result for the only NaNs that can arise (0/0).
+#pragma once
+#include "fp64bits.cuh"
+
+namespace jsvd {
+
+// fl(sqrt(nu)) of Eq. e:tan2: the largest double whose square is below
+// DBL_MAX; as a bit pattern.
+constexpr uint64_t kSqrtNuBits = 0x5FEFFFFFFFFFFFFFull;
+
+// Eq. e:tan2 after the division: q = o/|a| in [0, +inf] or NaN (0/0).
+// Returns min(fmax(q, 0), fl(sqrt nu)) with the sign of a.
+__device__ __forceinline__ double clamp_tan2(double q, double a)
+{
+  uint64_t qb = bits(q);
+  qb = (qb > kInf) ? 0ull : qb;                   // fmax(NaN, 0) = 0
+  qb = (qb > kSqrtNuBits) ? kSqrtNuBits : qb;     // fmin(., fl(sqrt nu))
+  return dbl(qb | (bits(a) & kSign));
+}
+
+struct Rot2 {
+  double cphi;   // cos(phi)
+  double etr;    // Re(e^{i alpha} tan(phi)) (real: sign(a21) tan(phi))
+  double eti;    // Im(e^{i alpha} tan(phi)) (real: 0)
+  double l1s;    // lambda1' (scaled)
+  double l2s;    // lambda2' (scaled)
+  int zeta;      // Eq. e:z exponent
+};
+
+// The rotation part shared by the real and the complex case, from the
+// scaled a11', a22' and |a21'| (section 2.1).
+__device__ __forceinline__ void rot_core(double a11, double a22, double aa21, double &tan1,
+                                         double &sec2, double &o, double &cphi)
+{
+  o = twice_abs(aa21);                          // o = 2|a21'|, exact
+  const double a = __dsub_rn(a11, a22);
+  const double tan2 = clamp_tan2(__ddiv_rn(o, dabs(a)), a);
+  tan1 = __ddiv_rn(tan2, __dadd_rn(1.0, __dsqrt_rn(__fma_rn(tan2, tan2, 1.0))));
+  sec2 = __fma_rn(tan1, tan1, 1.0);
+  cphi = __drcp_rn(__dsqrt_rn(sec2));
+}
+
+// Real symmetric matrix (Alg. d8jac2).
+__device__ __forceinline__ Rot2 dsjac2(double a11, double a22, double a21)
+{
+  Rot2 r;
+  const int E = max(max(flg_sat(a11), flg_sat(a22)), flg_sat(a21));
+  r.zeta = 1020 - E;  // eta - floor(lg max|a_ij|), eta = 1020
+  a11 = ldexp_rn(a11, r.zeta);
+  a22 = ldexp_rn(a22, r.zeta);
+  a21 = ldexp_rn(a21, r.zeta);
+  double tan1, sec2, o;
+  rot_core(a11, a22, dabs(a21), tan1, sec2, o, r.cphi);
+  r.etr = xor_sign(tan1, a21);
+  r.eti = 0.0;
+  r.l1s = __ddiv_rn(__fma_rn(tan1, __fma_rn(a22, tan1, o), a11), sec2);
+  r.l2s = __ddiv_rn(__fma_rn(tan1, __fma_rn(a11, tan1, -o), a22), sec2);
+  return r;
+}
+
+// Complex Hermitian matrix (Listing 1).
+__device__ __forceinline__ Rot2 zsjac2(double a11, double a22, double a21r, double a21i)
+{
+  Rot2 r;
+  const int E = max(max(flg_sat(a11), flg_sat(a22)), max(flg_sat(a21r), flg_sat(a21i)));
+  r.zeta = 1020 - E;
+  a11 = ldexp_rn(a11, r.zeta);
+  a22 = ldexp_rn(a22, r.zeta);
+  a21r = ldexp_rn(a21r, r.zeta);
+  a21i = ldexp_rn(a21i, r.zeta);
+  // polar form of a21' (Eq. e:zpolar), |a21'| by Alg. hypot
+  const double ar = dabs(a21r), ai = dabs(a21i);
+  const bool rmin = bits(ar) <= bits(ai);
+  const double am = rmin ? ar : ai, aM = rmin ? ai : ar;
+  const bool zero = (bits(aM) == 0ull);
+  const double mM = zero ? 0.0 : __ddiv_rn(am, aM);              // fmax(am/aM, 0)
+  const double aa21 = __dmul_rn(__dsqrt_rn(__fma_rn(mM, mM, 1.0)), aM);
+  const double ca = with_sign(zero ? 1.0 : __ddiv_rn(ar, aa21), a21r);  // fmin(., 1)
+  const double sa = zero ? a21i : __ddiv_rn(a21i, aa21);        // / fmax(|a21|, mu)
+  double tan1, sec2, o;
+  rot_core(a11, a22, aa21, tan1, sec2, o, r.cphi);
+  r.etr = __dmul_rn(ca, tan1);
+  r.eti = __dmul_rn(sa, tan1);
+  r.l1s = __ddiv_rn(__fma_rn(tan1, __fma_rn(a22, tan1, o), a11), sec2);
+  r.l2s = __ddiv_rn(__fma_rn(tan1, __fma_rn(a11, tan1, -o), a22), sec2);
+  return r;
+}
+
+// p = (lambda1' < lambda2'), as an IEEE comparison (lambda' finite).
+__device__ __forceinline__ int perm_bit(const Rot2 &r) { return ord(r.l1s) < ord(r.l2s); }
+
+// (zeta' << 1) | p with zeta' = -zeta, formed by an unsigned shift.
+__device__ __forceinline__ int32_t pack_zp(const Rot2 &r)
+{
+  return (int32_t)((((uint32_t)(-r.zeta)) << 1) | (uint32_t)perm_bit(r));
+}
+
+}  // namespace jsvd

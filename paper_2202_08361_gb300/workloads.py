@@ -55,7 +55,7 @@ def evd_batch(r: int, complex_: bool, seed_salt: int = 0):
 
 def evd_prescribed(r: int, complex_: bool, seed_salt: int = 0):
     """Matrices built from prescribed eigenvalues, tan(phi) and cos(alpha)
-    as in the paper's EVD test data (Eq. 2.2, section 5.1), in FP64 here:
+    as in the paper's EVD test data (Eq. e:2, section 5.1), in FP64 here:
     |lambda_j| <= nu/16 reinterpreted from random bits, tan(phi), cos(alpha)
     uniform in [-1, 1)."""
     g = rng(2, 10 + seed_salt + (1 if complex_ else 0))

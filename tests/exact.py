@@ -31,7 +31,7 @@ def eig2_exact(a11, a22, a21r, a21i=0.0):
 
 def rotation_exact(a11, a22, a21r, a21i=0.0):
     """Exact (tan(phi), cos(phi), cos(alpha), sin(alpha)) of the diagonalising
-    rotation of Eq. 2.1: tan(2 phi) = 2|a21|/(a11 - a22), phi in [-pi/4, pi/4],
+    rotation of Eq. e:1: tan(2 phi) = 2|a21|/(a11 - a22), phi in [-pi/4, pi/4],
     alpha = arg a21 (arg 0 = 0)."""
     aa = (D(a21r) ** 2 + D(a21i) ** 2).sqrt()
     a = D(a11) - D(a22)

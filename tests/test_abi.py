@@ -1,0 +1,64 @@
+"""The C-ABI library loads and exports every symbol include/*.h declares
+(no GPU needed: nothing here launches a kernel)."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        for m in re.finditer(r"JSVD_API\s+[^;(]*?\b(jsvd_\w+)\s*\(", text):
+            names.add(m.group(1))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2202_08361_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_entry_points():
+    names = declared_symbols()
+    for required in ("jsvd_evd2x2_batched", "jsvd_version", "jsvd_strerror"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in sorted(declared_symbols()) if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_host_only_calls(lib):
+    lib.jsvd_version.restype = ctypes.c_int
+    assert lib.jsvd_version() >= 100
+    lib.jsvd_strerror.restype = ctypes.c_char_p
+    lib.jsvd_strerror.argtypes = [ctypes.c_int]
+    assert lib.jsvd_strerror(0) == b"success"
+    assert b"invalid" in lib.jsvd_strerror(-3)
+
+
+def test_argument_errors_need_no_gpu(lib):
+    """Argument checks return -i before anything touches the device."""
+    from paper_2202_08361_gb300 import _native
+    L = _native.lib()
+    s = _native.EvdStreams()
+    assert L.jsvd_evd2x2_batched(7, ctypes.byref(s), 10, None) == -1
+    assert L.jsvd_evd2x2_batched(0, None, 10, None) == -2
+    assert L.jsvd_evd2x2_batched(0, ctypes.byref(s), 10, None) == -2
+    assert L.jsvd_evd2x2_batched(0, ctypes.byref(s), 0, None) == 0  # n = 0: no-op
+    s.a11 = s.a22 = s.a21_re = s.cos_phi = s.ea_tan_re = 8
+    assert L.jsvd_evd2x2_batched(0, ctypes.byref(s), -1, None) == -3
+    assert L.jsvd_evd2x2_batched(1, ctypes.byref(s), 10, None) == -2  # complex needs a21_im
+    assert L.jsvd_evd2x2_batched(0, ctypes.byref(s), 0, None) == 0  # n = 0: no-op
+    assert L.jsvd_tune_set(99, 0, 0) == -1
+    assert L.jsvd_tune_set(1, 100, 8) == -2
+    assert L.jsvd_tune_set(1, 256, 0) == -3

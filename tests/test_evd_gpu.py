@@ -1,0 +1,159 @@
+"""Parity of the CUDA batched 2x2 EVD (jsvd_evd2x2_batched) with the oracle.
+
+The kernel evaluates the same binary64 operation sequence as the oracle
+(Listing 1 / Alg. d8jac2), so bit-for-bit equality is expected; the
+acceptance bounds (4 ulp on eigenvalues, 8 ulp on rotation entries) are
+checked as well."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2202_08361_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+NU = np.finfo(np.float64).max
+MU = 5e-324
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def ordered(x):
+    i = np.ascontiguousarray(x, dtype=np.float64).view(np.int64)
+    return np.where(i >= 0, i, -(i & 0x7FFFFFFFFFFFFFFF))
+
+
+def ulp_dist(x, y):
+    return np.abs(ordered(x) - ordered(y))
+
+
+def run_gpu(streams, complex_):
+    torch = _torch()
+    import paper_2202_08361_gb300 as J
+    dev = torch.device("cuda:0")
+    t = [torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in streams]
+    out = J.evd2x2_batched(t[0], t[1], t[2], t[3] if complex_ else None)
+    torch.cuda.synchronize()
+    return {k: v.cpu().numpy() for k, v in out.items()}
+
+
+def run_oracle(streams, complex_):
+    if complex_:
+        c, ct, st, l1, l2, zp = oracle.zsjac2(*streams)
+        return dict(cos_phi=c, ea_tan_re=ct, ea_tan_im=st, lambda1=l1, lambda2=l2, zeta_p=zp)
+    c, ct, l1, l2, zp = oracle.dsjac2(*streams)
+    return dict(cos_phi=c, ea_tan_re=ct, lambda1=l1, lambda2=l2, zeta_p=zp)
+
+
+def assert_parity(g, o):
+    for k in ("cos_phi", "ea_tan_re", "ea_tan_im"):
+        if k in o:
+            assert ulp_dist(g[k], o[k]).max(initial=0) <= 8, k
+    for k in ("lambda1", "lambda2"):
+        gi, oi = g[k], o[k]
+        inf = np.isinf(oi)
+        assert np.array_equal(np.isinf(gi), inf) and np.array_equal(gi[inf], oi[inf]), k
+        assert ulp_dist(gi[~inf], oi[~inf]).max(initial=0) <= 4, k
+    assert np.array_equal(g["zeta_p"], o["zeta_p"])
+    # expected: the identical operation sequence gives identical bits
+    for k in o:
+        assert np.array_equal(np.asarray(g[k]).view(np.uint8), np.asarray(o[k]).view(np.uint8)), k
+
+
+@pytest.mark.parametrize("complex_", [False, True])
+@pytest.mark.parametrize("n", [1, 7, 255, 1000, 65537, (1 << 20) + 13])
+def test_parity_wide_range(n, complex_):
+    streams = workloads.evd_batch(n, complex_, seed_salt=n % 97)
+    assert_parity(run_gpu(streams, complex_), run_oracle(streams, complex_))
+
+
+@pytest.mark.parametrize("complex_", [False, True])
+def test_parity_full_size(complex_):
+    """The benchmark's batch size (2^24), in the benchmark's launch shape,
+    every output compared."""
+    streams = workloads.evd_batch(1 << 24, complex_)
+    assert_parity(run_gpu(streams, complex_), run_oracle(streams, complex_))
+
+
+@pytest.mark.parametrize("complex_", [False, True])
+def test_parity_prescribed_eigenvalues(complex_):
+    streams = workloads.evd_prescribed(1 << 16, complex_)
+    assert_parity(run_gpu(streams, complex_), run_oracle(streams, complex_))
+
+
+def special_cases():
+    rows = [
+        (NU / 8, NU / 8, MU, MU),      # Eq. e:evil
+        (NU / 8, NU / 8, MU, -MU),
+        (0.0, 0.0, 0.0, 0.0),          # all zero
+        (-0.0, 0.0, -0.0, -0.0),
+        (1.0, 1.0, 0.5, 0.0),          # equal diagonal
+        (3.0, -2.0, 0.0, 0.0),         # diagonal
+        (NU, -NU, NU, NU),             # everything at the top of the range
+        (MU, MU, MU, MU),              # everything subnormal
+        (MU, 2 * MU, 3 * MU, -MU),
+        (1e-310, 1e300, 2e-320, 0.0),  # wide spread
+        (1.0, 1.0 + 2**-52, 1e-300, 1e-300),
+        (-5.0, 7.0, -0.0, 3.0),
+        (2.0**1023, 2.0**-1074, 2.0**-1000, 2.0**1000),
+    ]
+    cols = list(zip(*rows))
+    return [np.array(c) for c in cols]
+
+
+@pytest.mark.parametrize("complex_", [False, True])
+def test_parity_special_cases(complex_):
+    a11, a22, ar, ai = special_cases()
+    streams = (a11, a22, ar, ai) if complex_ else (a11, a22, ar)
+    g = run_gpu(streams, complex_)
+    assert_parity(g, run_oracle(streams, complex_))
+    if complex_:
+        assert g["ea_tan_re"][0] == 1.0 and g["ea_tan_im"][0] == 1.0
+        assert g["cos_phi"][0] == 1.0 / np.sqrt(2.0)
+
+
+def same_bits(x, y):
+    torch = _torch()
+    if x.dtype == torch.float64:
+        x, y = x.view(torch.int64), y.view(torch.int64)
+    return torch.equal(x, y)
+
+
+def test_subranges_and_launch_shapes_bit_identical():
+    """Results depend neither on the batch size, the sub-range nor the
+    launch shape."""
+    torch = _torch()
+    import paper_2202_08361_gb300 as J
+    n = 300001
+    a11, a22, ar, ai = (torch.from_numpy(x).cuda() for x in workloads.evd_batch(n, True, 5))
+    ref = J.evd2x2_batched(a11, a22, ar, ai)
+    try:
+        for block, per_sm in ((64, 1), (128, 3), (256, 32)):
+            J.tune_set(J.JSVD_TUNE_EVD_LAUNCH, block, per_sm)
+            out = J.evd2x2_batched(a11, a22, ar, ai)
+            for k in ref:
+                assert same_bits(out[k], ref[k]), (block, per_sm, k)
+    finally:
+        J.tune_set(J.JSVD_TUNE_EVD_LAUNCH, 256, 8)
+    for lo, hi in ((0, 1), (17, 1000), (123456, n)):
+        out = J.evd2x2_batched(a11[lo:hi], a22[lo:hi], ar[lo:hi], ai[lo:hi])
+        for k in ref:
+            assert same_bits(out[k], ref[k][lo:hi]), (lo, hi, k)
+    torch.cuda.synchronize()
+
+
+def test_empty_batch_and_optional_outputs():
+    torch = _torch()
+    import paper_2202_08361_gb300 as J
+    z = torch.empty(0, dtype=torch.float64, device="cuda")
+    out = J.evd2x2_batched(z, z, z, z)
+    assert all(v.numel() == 0 for v in out.values())
+    a11, a22, ar = (torch.from_numpy(x).cuda() for x in workloads.evd_batch(1000, False, 3))
+    full = J.evd2x2_batched(a11, a22, ar)
+    part = J.evd2x2_batched(a11, a22, ar, want_lambda=False, want_zeta_p=False)
+    assert set(part) == {"cos_phi", "ea_tan_re"}
+    assert torch.equal(part["cos_phi"], full["cos_phi"])
+    assert torch.equal(part["ea_tan_re"], full["ea_tan_re"])

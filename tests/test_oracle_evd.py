@@ -20,8 +20,8 @@ def bits(x):
 
 
 def normal_range_inputs(r, complex_, seed=7):
-    """Entries in the normal range with moderate exponents: the Eq. 2.5
-    power-of-two scaling is then exact, so the Prop. 2.1 bounds apply to the
+    """Entries in the normal range with moderate exponents: the Eq. e:z
+    power-of-two scaling is then exact, so the Prop. p:s2 bounds apply to the
     exact rotation of the input itself."""
     g = np.random.default_rng(seed)
     e = lambda: g.integers(-300, 300, size=r)
@@ -39,7 +39,7 @@ def normal_range_inputs(r, complex_, seed=7):
 
 @pytest.mark.parametrize("complex_", [False, True])
 def test_prop_2_1_rotation_bounds(complex_):
-    """Prop. 2.1 (Eq. 2.8): relative errors of tan(phi), cos(phi) and
+    """Prop. p:s2 (Eq. e:prop): relative errors of tan(phi), cos(phi) and
     e^{i alpha} against the exact diagonalising rotation."""
     r = 400
     a11, a22, a21r, a21i = normal_range_inputs(r, complex_)
@@ -129,7 +129,7 @@ def _check_roots(a11, a22, ar, ai, l1, l2):
 
 @pytest.mark.parametrize("complex_", [False, True])
 def test_residual_and_orientation(complex_):
-    """U from Eq. 2.1 built from the outputs, U = cos(phi) [[1, -conj(e)],
+    """U from Eq. e:1 built from the outputs, U = cos(phi) [[1, -conj(e)],
     [e, 1]], e = e^{i alpha} tan(phi), diagonalises A: ||A U - U Lambda||
     is a few eps of ||A||.  A wrong sign, conjugation or index fails it."""
     r = 300
@@ -188,7 +188,7 @@ def test_equal_diagonal():
 
 
 def test_evil_matrix():
-    """Eq. 5.1: [[nu/8, mu - i mu], [mu + i mu, nu/8]] gives
+    """Eq. e:evil: [[nu/8, mu - i mu], [mu + i mu, nu/8]] gives
     fl(e^{i alpha}) = 1 + i, fl(tan phi) = 1, fl(cos phi) = fl(1/fl(sqrt 2)),
     zeta = 0."""
     for sgn in (1.0, -1.0):
@@ -205,7 +205,7 @@ def test_zero_matrix():
 
 
 def test_scaling_exponent_cases():
-    """Eq. 2.5: zeta = eta - floor(lg max|component|), eta = 1020, packed as
+    """Eq. e:z: zeta = eta - floor(lg max|component|), eta = 1020, packed as
     (zeta' << 1) | p with zeta' = -zeta."""
     cases = [(1.0, 0.0, 0.0, 0.0, 1020), (2.0, 0.0, 0.0, 0.0, 1019), (0.0, 0.0, 0.75, 0.0, 1021),
              (NU, 0.0, 0.0, 0.0, -3), (MU, 0.0, 0.0, 0.0, 2094), (0.0, 0.0, 0.0, 3.0, 1019),
@@ -229,7 +229,7 @@ def test_complex_on_real_input_bit_equals_real():
 
 @pytest.mark.parametrize("complex_", [False, True])
 def test_wide_range_outputs_finite(complex_):
-    """Prop. 2.1: after the Eq. 2.5 scaling nothing avoidable overflows, for
+    """Prop. p:s2: after the Eq. e:z scaling nothing avoidable overflows, for
     entries anywhere from subnormal to near DBL_MAX and exact zeros."""
     b = workloads.evd_batch(1 << 15, complex_)
     if complex_:
@@ -251,7 +251,7 @@ def test_wide_range_outputs_finite(complex_):
 
 
 def test_prescribed_eigenvalue_batch():
-    """The paper's test data (Eq. 2.2 construction): every output finite and
+    """The paper's test data (Eq. e:2 construction): every output finite and
     the residual small for matrices built from prescribed eigenvalues."""
     a11, a22, a21r, a21i = workloads.evd_prescribed(2000, True)
     c, ct, st, l1, l2, _ = oracle.zsjac2(a11, a22, a21r, a21i)
