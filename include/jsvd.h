@@ -65,6 +65,9 @@ JSVD_API const char *jsvd_last_cuda_error(void);
  *   JSVD_TUNE_EVD_LAUNCH: value = threads per block of the 2x2 EVD kernel
  *     (64, 128 or 256), value2 = resident blocks per SM (1..64). */
 #define JSVD_TUNE_EVD_LAUNCH 1
+/*   JSVD_TUNE_SVD_GRID: value = most blocks of the persistent SVD sweep
+ *     kernel (0 = as many as the pairs of a step, capped by residency). */
+#define JSVD_TUNE_SVD_GRID 2
 JSVD_API int jsvd_tune_set(int knob, int value, int value2);
 
 /* ------------------------------------------------------------------------
@@ -109,6 +112,80 @@ typedef struct {
 } jsvd_evd2_streams;
 
 JSVD_API int jsvd_evd2x2_batched(jsvd_field field, const jsvd_evd2_streams *s, int64_t n, void *stream);
+
+/* ------------------------------------------------------------------------
+ * One-sided Jacobi SVD (section 4, Alg. zvjsvd; real variant dvjsvd).
+ *
+ * A = U diag(sigma) V^H for an m x n matrix A, m >= n >= 1, by repeated
+ * parallel steps: for every pivot pair (p, q) of a cyclic parallel ordering
+ * (n/2 disjoint pairs per step, n-1 steps per sweep; the round-robin
+ * ordering, a phantom column added for odd n -- section 4.1), the column
+ * norms and the scaled dot-product g_q^* g_p / (||g_p|| ||g_q||)
+ * (Alg. zdpscl), the convergence test |a21'| >= fl(eps sqrt(m)),
+ * eps = 2^-53 (Eq. e:tol, Alg. cvg), the scaled Grammian (Alg. Gram), its
+ * 2x2 EVD (as jsvd_evd2x2_batched) and the transformation of the column pair
+ * of G and of V (Eq. e:transf, Alg. zjrot).  With opts->permute the pair is
+ * transformed by U P, the columns swapped when the EVD's permutation bit says
+ * so (section 2; optional there, and with the round-robin ordering it more
+ * than doubles the sweep count, so it is off by default: the columns are
+ * sorted once after convergence instead).  Sweeps stop when a whole sweep
+ * performs no rotation (section 3.3.1), or after opts->max_sweeps.  The
+ * iteration matrix is kept at a power-of-two scale with max-norm in [1, 2)
+ * and rescaled if it grows past 2^opts->rescale_exp (section 3.2); the
+ * singular values are returned unscaled, also as (e, f) pairs,
+ * sigma = 2^e f, 1 <= f < 2 (section 4.2.1), sorted non-increasingly with the
+ * columns of U and V permuted alike.
+ *
+ * Layout: column-major.  JSVD_REAL: A, U, V are double.  JSVD_COMPLEX: A, U,
+ * V are interleaved complex double (re, im), lda/ldu/ldv counted in complex
+ * elements; the library splits them into separate planes internally
+ * (section 2.4.1, supplement SM5).
+ */
+#define JSVD_FP64 0
+#define JSVD_MIXED_FP32_FP64 1
+
+typedef struct {
+  int32_t max_sweeps;  /* S; <= 0 selects the default, 100 */
+  int32_t mode;        /* JSVD_FP64 or JSVD_MIXED_FP32_FP64 */
+  int32_t rescale_exp; /* rescale G when ||G||_max reaches 2^rescale_exp;
+                          0 selects 256; must be in [1, 480] */
+  int32_t permute;     /* 1: apply the column swap P during the sweeps;
+                          0 (default): do not */
+} jsvd_opts;
+
+/* Per-matrix outcome, written to DEVICE memory by the kernels. */
+typedef struct {
+  int32_t status;    /* 0 = converged; JSVD_NOT_CONVERGED; JSVD_E_NONFINITE
+                        (A holds Inf/NaN: outputs are NaN); JSVD_E_TIMEOUT */
+  int32_t sweeps;    /* sweeps performed, the last (rotation-free) included */
+  int64_t rotations; /* transformations applied in total */
+  int32_t rescales;  /* downscalings of the iteration matrix */
+  int32_t sweeps_fp32; /* mixed mode: sweeps of the FP32 phase */
+} jsvd_info;
+
+#define JSVD_NOT_CONVERGED 1
+
+/* Bytes of device workspace jsvd_svd needs for these arguments.
+ * Errors: -1 field, -2 opts invalid, -3 m, -4 n (m >= n >= 1), -5 bytes NULL. */
+JSVD_API int jsvd_svd_workspace_size(jsvd_field field, const jsvd_opts *opts, int64_t m,
+                                     int64_t n, size_t *bytes);
+
+/* SVD of one matrix.  opts may be NULL (all defaults).  A is read only; U
+ * (m x n, ldu >= m), sigma (n), V (n x n, ldv >= n) are written; sigma_e,
+ * sigma_f (n doubles each) and info may be NULL.  work must be 256-byte
+ * aligned and hold jsvd_svd_workspace_size bytes; its contents on entry do
+ * not matter.  Errors: -i for argument i, JSVD_E_WORKSPACE, JSVD_E_CUDA. */
+JSVD_API int jsvd_svd(jsvd_field field, const jsvd_opts *opts, int64_t m, int64_t n,
+                      const void *A, int64_t lda, void *U, int64_t ldu, double *sigma,
+                      double *sigma_e, double *sigma_f, void *V, int64_t ldv, void *work,
+                      size_t work_bytes, jsvd_info *info, void *stream);
+
+/* The parallel pivot ordering the SVD kernels use (section 4.1; the
+ * round-robin reading): writes (nt - 1) x (nt / 2) pairs (p, q), p < q, as
+ * int32 [step][pair][2] into the DEVICE buffer tab, nt = n + (n & 1) (a
+ * phantom column n for odd n), computed by the same device function the
+ * sweeps use.  Errors: -1 n < 2, -2 tab NULL, JSVD_E_CUDA. */
+JSVD_API int jsvd_ordering(int32_t n, int32_t *tab, void *stream);
 
 #ifdef __cplusplus
 }

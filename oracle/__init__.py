@@ -45,7 +45,7 @@ def lib():
         L.orc_pairs.argtypes = [ctypes.c_int, _i32]
         L.orc_pairs.restype = ctypes.c_int
         L.orc_vjsvd.argtypes = [ctypes.c_int64, ctypes.c_int64, _d, _d, ctypes.c_int64, _d, _d,
-                                _d, _d, _d, ctypes.c_int, ctypes.c_int, _i32, _i64]
+                                _d, _d, _d, ctypes.c_int, ctypes.c_int, ctypes.c_int, _i32, _i64]
         L.orc_vjsvd.restype = ctypes.c_int
         L.orc_svd_adjoint.argtypes = [ctypes.c_int64, ctypes.c_int64, _d, _d, _d, _d, _d, _d, _d]
         L.orc_svd_adjoint.restype = ctypes.c_int
@@ -110,8 +110,9 @@ def pairs(n):
     return tab[: nt - 1] if nt >= 2 else tab[:0]
 
 
-def vjsvd(A, max_sweeps=100, nthreads=0):
-    """One-sided Jacobi SVD of A (m x n, m >= n; real or complex).
+def vjsvd(A, max_sweeps=100, nthreads=0, permute=False):
+    """One-sided Jacobi SVD of A (m x n, m >= n; real or complex).  permute
+    applies the column swap P of section 2 during the sweeps.
 
     Returns dict(U, sigma, sigma_e, sigma_f, V, status, sweeps, rotations,
     rescales).  sigma is sorted non-increasingly; A ~= U diag(sigma) V^H.
@@ -127,7 +128,8 @@ def vjsvd(A, max_sweeps=100, nthreads=0):
     info = np.zeros(4, dtype=np.int32)
     rot = np.zeros(1, dtype=np.int64)
     rc = lib().orc_vjsvd(m, n, _dp(Gr), _dp(Gi), m, _dp(Vr), _dp(Vi), _dp(sig), _dp(se),
-                         _dp(sf), int(max_sweeps), int(nthreads), info.ctypes.data_as(_i32),
+                         _dp(sf), int(max_sweeps), 1 if permute else 0, int(nthreads),
+                         info.ctypes.data_as(_i32),
                          rot.ctypes.data_as(_i64))
     if rc < 0:
         raise ValueError("orc_vjsvd failed with %d" % rc)

@@ -32,10 +32,15 @@
  *   - zeta of an all-zero 2x2 matrix follows Listing 1 (frexp of the
  *     smallest subnormal), so zeta is a finite int in [-3, 2094];
  *   - the packed (zeta' << 1) | p is formed by an unsigned shift;
- *   - the EVD is computed for every pivot pair, and a pair that is not
- *     rotated is swapped iff its EVD says lambda1' < lambda2';
- *   - a pair with a zero column is never rotated; it is swapped iff the
- *     norm of g_p is below that of g_q;
+ *   - the column swap P of section 2 (Alg. zvjsvd: U P) is optional, as
+ *     section 2 makes it ("if the orthogonalized pivot columns are also to
+ *     be ordered"): with permute != 0 the EVD is computed for every pivot
+ *     pair, a rotated pair is transformed by U P and a pair that is not
+ *     rotated is swapped iff its EVD says lambda1' < lambda2'; with
+ *     permute == 0 (the default) no column moves during the sweeps -- with
+ *     the round-robin ordering, P more than doubles the sweep count;
+ *   - a pair with a zero column is never rotated; with permute != 0 it is
+ *     swapped iff the norm of g_p is below that of g_q;
  *   - column norms are computed by a two-pass, overflow-free scaled sum of
  *     squares (max-exponent prescaling), standing in for xNRM2; the norm
  *     overflow branch of Alg. zvjsvd therefore never fires;
@@ -424,11 +429,12 @@ ORC_EXPORT int orc_num_threads(void)
  *   sig, sig_e, sig_f: n singular values, as doubles and as (e, f).
  *   out_info[4] = {status, sweeps, rotations (low 31 bits), rescales}.
  *   rotations64 receives the 64-bit rotation count (may be NULL).
+ *   permute != 0 applies the column swap P during the sweeps.
  * nthreads <= 0 leaves the OpenMP default.
  */
 ORC_EXPORT int orc_vjsvd(int64_t m, int64_t n, double *Gr, double *Gi, int64_t ld, double *Vr,
                          double *Vi, double *sig, double *sig_e, double *sig_f, int max_sweeps,
-                         int nthreads, int32_t *out_info, int64_t *rotations64)
+                         int permute, int nthreads, int32_t *out_info, int64_t *rotations64)
 {
   if (m < 1 || n < 1 || m < n || ld < m || max_sweeps < 1) return ORC_E_ARG;
 #ifdef _OPENMP
@@ -501,7 +507,7 @@ ORC_EXPORT int orc_vjsvd(int64_t m, int64_t n, double *Gr, double *Gi, int64_t l
           colnorm(m, gpr, gpi, &ep, &fp);
           colnorm(m, gqr, gqi, &eq, &fq);
           if (ep == INT_MIN || eq == INT_MIN) {
-            if (ef_less(ep, fp, eq, fq)) {
+            if (permute && ef_less(ep, fp, eq, fq)) {
               swap_cols(m, gpr, gqr);
               swap_cols(n, vpr, vqr);
               if (cplx) {
@@ -525,7 +531,7 @@ ORC_EXPORT int orc_vjsvd(int64_t m, int64_t n, double *Gr, double *Gi, int64_t l
             zsjac2_1(b11, b22, b21r, b21i, &c, &Ct, &St, NULL, NULL, &zp, NULL, NULL);
           else
             dsjac2_1(b11, b22, b21r, &c, &Ct, NULL, NULL, &zp, NULL, NULL);
-          const int pbit = zp & 1;
+          const int pbit = permute ? (zp & 1) : 0;
           if (rot) {
             const double Mp = zjrot(m, gpr, gpi, gqr, gqi, c, Ct, St, pbit);
             (void)zjrot(n, vpr, vpi, vqr, vqi, c, Ct, St, pbit);

@@ -8,10 +8,12 @@ import ctypes
 
 from . import _native
 from ._native import (JSVD_COMPLEX, JSVD_E_CUDA, JSVD_E_NONFINITE, JSVD_E_TIMEOUT,
-                      JSVD_E_UNSUPPORTED, JSVD_E_WORKSPACE, JSVD_NOT_CONVERGED, JSVD_OK,
-                      JSVD_REAL, JSVD_TUNE_EVD_LAUNCH, JsvdError)
+                      JSVD_E_UNSUPPORTED, JSVD_E_WORKSPACE, JSVD_FP64, JSVD_MIXED_FP32_FP64,
+                      JSVD_NOT_CONVERGED, JSVD_OK, JSVD_REAL, JSVD_TUNE_EVD_LAUNCH,
+                      JSVD_TUNE_SVD_GRID, JsvdError)
 
-__all__ = ["evd2x2_batched", "version", "tune_set", "JsvdError", "JSVD_REAL", "JSVD_COMPLEX"]
+__all__ = ["evd2x2_batched", "svd", "svd_workspace_size", "ordering", "decode_info", "version",
+           "tune_set", "JsvdError", "JSVD_REAL", "JSVD_COMPLEX"]
 
 
 def _torch():
@@ -86,3 +88,108 @@ def evd2x2_batched(a11, a22, a21_re, a21_im=None, *, out=None, want_lambda=True,
                                            ctypes.byref(s), n, _stream_handle(stream))
     _native.check(rc, "jsvd_evd2x2_batched")
     return out
+
+
+# ---------------------------------------------------------------------------
+# SVD
+
+def _opts(max_sweeps=0, mode=JSVD_FP64, rescale_exp=0, permute=False):
+    o = _native.Opts()
+    o.max_sweeps = int(max_sweeps)
+    o.mode = int(mode)
+    o.rescale_exp = int(rescale_exp)
+    o.permute = 1 if permute else 0
+    return o
+
+
+def _mode(mode):
+    if mode in (JSVD_FP64, "fp64"):
+        return JSVD_FP64
+    if mode in (JSVD_MIXED_FP32_FP64, "mixed"):
+        return JSVD_MIXED_FP32_FP64
+    raise ValueError("mode must be 'fp64' or 'mixed'")
+
+
+def colmajor(t):
+    """A column-major view of a 2-D tensor (copying only if needed) and its
+    leading dimension."""
+    m, n = t.shape
+    if t.stride(0) == 1 and t.stride(1) >= max(m, 1):
+        return t, t.stride(1)
+    c = t.t().contiguous().t()
+    return c, max(m, 1)
+
+
+def colmajor_empty(m, n, dtype, device):
+    torch = _torch()
+    return torch.empty((n, m), dtype=dtype, device=device).t()
+
+
+def svd_workspace_size(m, n, complex_=False, mode="fp64"):
+    sz = ctypes.c_size_t(0)
+    o = _opts(mode=_mode(mode))
+    rc = _native.lib().jsvd_svd_workspace_size(JSVD_COMPLEX if complex_ else JSVD_REAL,
+                                               ctypes.byref(o), int(m), int(n), ctypes.byref(sz))
+    _native.check(rc, "jsvd_svd_workspace_size")
+    return sz.value
+
+
+def decode_info(info):
+    """jsvd_info tensor(s) (uint8, 24 bytes each, on any device) -> dict or
+    list of dicts.  Synchronises with the device if info lives there."""
+    import struct
+    raw = bytes(info.detach().cpu().numpy().tobytes())
+    out = []
+    for k in range(len(raw) // _native.INFO_BYTES):
+        st, sw, rot, resc, s32 = struct.unpack_from("<iiqii", raw, k * _native.INFO_BYTES)
+        out.append(dict(status=st, sweeps=sw, rotations=rot, rescales=resc, sweeps_fp32=s32))
+    return out[0] if len(out) == 1 else out
+
+
+def svd(A, *, max_sweeps=0, mode="fp64", rescale_exp=0, permute=False, work=None, out=None,
+        stream=None):
+    """One-sided Jacobi SVD of a CUDA tensor A (m x n, m >= n; float64 or
+    complex128), jsvd_svd.  Returns dict(U, sigma, sigma_e, sigma_f, V,
+    info); U and V are column-major views, info a 24-byte device tensor
+    (decode_info)."""
+    torch = _torch()
+    if not isinstance(A, torch.Tensor) or not A.is_cuda or A.dim() != 2:
+        raise TypeError("A must be a 2-D CUDA tensor")
+    cplx = A.dtype == torch.complex128
+    if not cplx and A.dtype != torch.float64:
+        raise TypeError("A must be float64 or complex128")
+    m, n = A.shape
+    Ac, lda = colmajor(A)
+    dev = A.device
+    if out is None:
+        out = {"U": colmajor_empty(m, n, A.dtype, dev), "V": colmajor_empty(n, n, A.dtype, dev),
+               "sigma": torch.empty(n, dtype=torch.float64, device=dev),
+               "sigma_e": torch.empty(n, dtype=torch.float64, device=dev),
+               "sigma_f": torch.empty(n, dtype=torch.float64, device=dev),
+               "info": torch.zeros(_native.INFO_BYTES, dtype=torch.uint8, device=dev)}
+    U, ldu = colmajor(out["U"])
+    V, ldv = colmajor(out["V"])
+    o = _opts(max_sweeps, _mode(mode), rescale_exp, permute)
+    need = svd_workspace_size(m, n, cplx, mode)
+    if work is None:
+        work = torch.empty(need, dtype=torch.uint8, device=dev)
+    ptr = lambda k: out[k].data_ptr() if out.get(k) is not None else None
+    rc = _native.lib().jsvd_svd(JSVD_COMPLEX if cplx else JSVD_REAL, ctypes.byref(o), m, n,
+                                Ac.data_ptr(), lda, U.data_ptr(), ldu, ptr("sigma"),
+                                ptr("sigma_e"), ptr("sigma_f"), V.data_ptr(), ldv,
+                                work.data_ptr(), work.numel(), ptr("info"),
+                                _stream_handle(stream))
+    _native.check(rc, "jsvd_svd")
+    out["U"], out["V"] = U, V
+    return out
+
+
+def ordering(n, stream=None):
+    """The device-side parallel pivot ordering as an int32 CUDA tensor
+    [n_steps, n_pairs, 2]."""
+    torch = _torch()
+    nt = n + (n & 1)
+    tab = torch.empty((nt - 1, nt // 2, 2), dtype=torch.int32, device="cuda")
+    _native.check(_native.lib().jsvd_ordering(int(n), tab.data_ptr(), _stream_handle(stream)),
+                  "jsvd_ordering")
+    return tab

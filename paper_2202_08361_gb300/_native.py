@@ -21,6 +21,10 @@ JSVD_REAL = 0
 JSVD_COMPLEX = 1
 
 JSVD_TUNE_EVD_LAUNCH = 1
+JSVD_TUNE_SVD_GRID = 2
+
+JSVD_FP64 = 0
+JSVD_MIXED_FP32_FP64 = 1
 
 
 class JsvdError(RuntimeError):
@@ -36,6 +40,16 @@ class EvdStreams(ctypes.Structure):
     _fields_ = [(name, ctypes.c_void_p) for name in
                 ("a11", "a22", "a21_re", "a21_im", "cos_phi", "ea_tan_re", "ea_tan_im",
                  "lambda1", "lambda2", "zeta_p")]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("max_sweeps", ctypes.c_int32), ("mode", ctypes.c_int32),
+                ("rescale_exp", ctypes.c_int32), ("permute", ctypes.c_int32)]
+
+
+# jsvd_info as laid out in device memory: int32 status, int32 sweeps,
+# int64 rotations, int32 rescales, int32 sweeps_fp32 (24 bytes)
+INFO_BYTES = 24
 
 
 _lib = None
@@ -61,6 +75,16 @@ def lib():
         L.jsvd_tune_set.restype = ctypes.c_int
         L.jsvd_evd2x2_batched.argtypes = [ctypes.c_int, ctypes.POINTER(EvdStreams), _i64, _vp]
         L.jsvd_evd2x2_batched.restype = ctypes.c_int
+        _sz = ctypes.c_size_t
+        L.jsvd_svd_workspace_size.argtypes = [ctypes.c_int, ctypes.POINTER(Opts), _i64, _i64,
+                                              ctypes.POINTER(_sz)]
+        L.jsvd_svd_workspace_size.restype = ctypes.c_int
+        _d = ctypes.c_void_p
+        L.jsvd_svd.argtypes = [ctypes.c_int, ctypes.POINTER(Opts), _i64, _i64, _vp, _i64, _vp, _i64,
+                               _d, _d, _d, _vp, _i64, _vp, _sz, _vp, _vp]
+        L.jsvd_svd.restype = ctypes.c_int
+        L.jsvd_ordering.argtypes = [ctypes.c_int32, _vp, _vp]
+        L.jsvd_ordering.restype = ctypes.c_int
         _lib = L
     return _lib
 

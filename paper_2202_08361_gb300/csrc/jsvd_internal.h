@@ -4,4 +4,18 @@
 
 namespace jsvd {
 int evd2_set_launch(int block, int blocks_per_sm);
+int svd_set_grid(int cap);
+}  // namespace jsvd
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+namespace jsvd {
+int svd_check_opts(const jsvd_opts *o, int &S, int &mode, int &rexp, int &permute);
+size_t svd_fp64_workspace(bool cplx, int64_t m, int64_t n);
+size_t svd_mixed_workspace(bool cplx, int64_t m, int64_t n);
+int svd_mixed_run(bool cplx, int64_t m, int64_t n, const void *A, int64_t lda, void *U,
+                  int64_t ldu, double *sigma, double *sigma_e, double *sigma_f, void *V,
+                  int64_t ldv, char *work, jsvd_info *info, int S, int rexp, int permute,
+                  cudaStream_t st);
 }  // namespace jsvd

@@ -1,0 +1,497 @@
+// svd.cu -- jsvd_svd: the one-sided Jacobi SVD of one matrix (Alg. zvjsvd).
+//
+// Phases (one stream, no host synchronisation):
+//   1. maxnorm_kernel   M~_0 = ||A||_max (NaN -> Inf), section 3.2
+//   2. init_kernel      G_1 = 2^{s_0} A split into planes, V_1 = I
+//   3. sweeps_kernel    persistent cooperative kernel: every sweep, every
+//                       step, one warp per pivot pair (svd_core.cuh), a
+//                       bounded grid barrier between steps, stop on a
+//                       rotation-free sweep
+//   4. colnorm_kernel   final (e,f) norms of the columns
+//   5. rank_kernel      stable non-increasing order of sigma, info
+//   6. output_kernel    U = G 2^{-e_j} / f_j, V, sigma, merged planes
+//
+// Scaling (section 3.2, adapted): the paper keeps ||G||_max below
+// nu/(varsigma m) so that an xNRM2-style norm cannot overflow.  Here the
+// three sums of a pair are formed in one pass as plain sums of squares and
+// products, which is safe while the entries stay near 1 (the safe region of
+// supplement SM3): G_1 is scaled to max-norm in [1, 2) and downscaled back
+// to that range whenever the tracked max-norm M~ reaches 2^rescale_exp.
+#include <algorithm>
+#include <climits>
+
+#include "common.cuh"
+#include "jsvd_internal.h"
+#include "svd_core.cuh"
+
+namespace jsvd {
+
+constexpr int kMaxSweepsCap = 4096;
+constexpr unsigned long long kBarrierLimitNs = 20ull * 1000ull * 1000ull * 1000ull;  // 20 s
+
+// Device-side state at the start of the workspace.
+struct SvdState {
+  unsigned long long Mbuf[3];  // running max-norm (bits), triple-buffered by step
+  unsigned long long M0;       // ||A||_max bits
+  unsigned int bar_count;
+  unsigned int bar_gen;
+  int err;                     // barrier timeout
+  int nonfinite;
+  int s;                       // accumulated scaling exponent: G = 2^s (A V)
+  int rescales;
+  int sweeps;
+  int converged;
+  int T[kMaxSweepsCap];        // rotations per sweep
+};
+
+struct SvdLayout {
+  size_t state, gr, gi, vr, vi, e, f, rank, total;
+  int mp, np;
+  int64_t ldg, ldv;
+};
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static SvdLayout svd_layout(bool cplx, int64_t m, int64_t n)
+{
+  SvdLayout L;
+  L.mp = (int)((m + 31) / 32 * 32);
+  L.np = (int)((n + 31) / 32 * 32);
+  L.ldg = L.mp;
+  L.ldv = L.np;
+  size_t o = 0;
+  L.state = o;
+  o = align256(o + sizeof(SvdState));
+  L.gr = o;
+  o = align256(o + sizeof(double) * (size_t)L.ldg * (size_t)n);
+  L.gi = o;
+  if (cplx) o = align256(o + sizeof(double) * (size_t)L.ldg * (size_t)n);
+  L.vr = o;
+  o = align256(o + sizeof(double) * (size_t)L.ldv * (size_t)n);
+  L.vi = o;
+  if (cplx) o = align256(o + sizeof(double) * (size_t)L.ldv * (size_t)n);
+  L.e = o;
+  o = align256(o + sizeof(int) * (size_t)n);
+  L.f = o;
+  o = align256(o + sizeof(double) * (size_t)n);
+  L.rank = o;
+  o = align256(o + sizeof(int) * (size_t)n);
+  L.total = o;
+  return L;
+}
+
+// ---------------------------------------------------------------------------
+
+// max over count doubles of |x| with NaN -> Inf, as ordered bits
+__global__ void maxnorm_kernel(const double *__restrict__ A, int64_t lda, int64_t rows, int64_t cols,
+                               unsigned long long *out)
+{
+  unsigned long long mx = 0ull;
+  const int64_t total = rows * cols;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = t / rows, i = t - j * rows;
+    unsigned long long a = abits(A[j * lda + i]);
+    a = (a > kInf) ? kInf : a;  // min(|y|, Inf): NaN -> Inf
+    mx = (a > mx) ? a : mx;
+  }
+  mx = warp_umax(mx);
+  if ((threadIdx.x & 31) == 0) atomicMax(out, mx);
+}
+
+// G_1 = 2^{s_0} A (planes), V_1 = I; s_0 brings ||A||_max into [1, 2).
+// Complex A is interleaved: plane r takes the even doubles, plane i the odd.
+template <bool CPLX>
+__global__ void init_kernel(const double *__restrict__ A, int64_t lda, MatView M, SvdState *st)
+{
+  const unsigned long long m0 = st->M0;
+  const bool nonfinite = m0 >= kInf;
+  const int s0 = (m0 == 0ull || nonfinite) ? 0 : -flg(dbl(m0));
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+    st->s = s0;
+    st->nonfinite = nonfinite ? 1 : 0;
+    st->Mbuf[0] = (m0 == 0ull || nonfinite) ? 0ull : bits(ldexp_rn(dbl(m0), s0));
+  }
+  for (int j = blockIdx.y; j < M.n; j += gridDim.y) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < max(M.mp, M.np);
+         i += gridDim.x * blockDim.x) {
+      if (i < M.mp) {
+        double xr = 0.0, xi = 0.0;
+        if (i < M.m && !nonfinite) {
+          if (CPLX) {
+            xr = ldexp_rn(A[2 * (j * lda + i)], s0);
+            xi = ldexp_rn(A[2 * (j * lda + i) + 1], s0);
+          } else {
+            xr = ldexp_rn(A[j * lda + i], s0);
+          }
+        }
+        M.gr[j * M.ldg + i] = xr;
+        if (CPLX) M.gi[j * M.ldg + i] = xi;
+      }
+      if (i < M.np) {
+        M.vr[j * M.ldv + i] = (i == j) ? 1.0 : 0.0;
+        if (CPLX) M.vi[j * M.ldv + i] = 0.0;
+      }
+    }
+  }
+}
+
+// All sweeps of Alg. zvjsvd; blockDim = 32 (one warp per block), warps
+// stride over the nt/2 pairs of every step.
+template <bool CPLX>
+__global__ void __launch_bounds__(32) sweeps_kernel(MatView M, SvdState *st, double ups,
+                                                    int max_sweeps, int rescale_exp, int permute)
+{
+  if (st->nonfinite) return;
+  const int nt = M.n + (M.n & 1);
+  const int K = nt - 1, L = nt / 2;
+  const int lane = threadIdx.x & 31;
+  if (K < 1) {
+    if (blockIdx.x == 0 && lane == 0) {
+      st->sweeps = 1;
+      st->converged = 1;
+    }
+    return;
+  }
+  unsigned long long gstep = 0;
+  int sweep = 0;
+  bool converged = false;
+  for (; sweep < max_sweeps && !converged; ++sweep) {
+    for (int k = 0; k < K; ++k, ++gstep) {
+      const int cur = (int)(gstep % 3), nxt = (int)((gstep + 1) % 3), old = (int)((gstep + 2) % 3);
+      const double Mcur = dbl(((volatile unsigned long long *)st->Mbuf)[cur]);
+      // section 3.2, step 2: rescale when M~ has grown past 2^rescale_exp
+      const int rk = (bits(Mcur) != 0ull && flg(Mcur) >= rescale_exp) ? -flg(Mcur) : 0;
+      if (blockIdx.x == 0 && lane == 0) {
+        st->Mbuf[old] = 0ull;
+        atomicMax(&st->Mbuf[nxt], bits(rk ? ldexp_rn(Mcur, rk) : Mcur));
+        if (rk) {
+          st->s += rk;
+          st->rescales += 1;
+        }
+      }
+      unsigned long long Mloc = 0ull;
+      int rots = 0;
+      for (int l = blockIdx.x; l < L; l += gridDim.x) {
+        int p, q;
+        pair_of(k, l, nt, p, q);
+        if (q >= M.n) {  // phantom partner: only a pending rescale applies
+          if (rk) {
+            scale_col(M.gr + p * M.ldg, M.mp, rk, lane);
+            if (CPLX) scale_col(M.gi + p * M.ldg, M.mp, rk, lane);
+          }
+          continue;
+        }
+        rots += pair_step<CPLX>(M, p, q, ups, rk, permute != 0, Mloc) ? 1 : 0;
+      }
+      Mloc = warp_umax(Mloc);
+      if (lane == 0) {
+        if (Mloc) atomicMax(&st->Mbuf[nxt], Mloc);
+        if (rots) atomicAdd(&st->T[sweep], rots);
+      }
+      if (!grid_barrier(&st->bar_count, &st->bar_gen, &st->err, kBarrierLimitNs)) return;
+    }
+    converged = (((volatile int *)st->T)[sweep] == 0);
+  }
+  if (blockIdx.x == 0 && lane == 0) {
+    st->sweeps = sweep;
+    st->converged = converged ? 1 : 0;
+  }
+}
+
+// Final column norms as (e, f); a zero column gets e = INT_MIN.
+template <bool CPLX>
+__global__ void colnorm_kernel(MatView M, int *e_out, double *f_out)
+{
+  const int lane = threadIdx.x & 31;
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int W = (gridDim.x * blockDim.x) >> 5;
+  for (int j = w; j < M.n; j += W) {
+    const double *xr = M.gr + j * M.ldg, *xi = CPLX ? M.gi + j * M.ldg : nullptr;
+    double s = 0.0;
+    for (int i = lane; i < M.mp; i += 32) {
+      s = __fma_rn(xr[i], xr[i], s);
+      if (CPLX) s = __fma_rn(xi[i], xi[i], s);
+    }
+    s = warp_sum(s);
+    if (lane == 0) {
+      if (bits(s) == 0ull) {
+        e_out[j] = INT_MIN;
+        f_out[j] = 1.0;
+      } else {
+        const double r = __dsqrt_rn(s);
+        const int e = flg(r);
+        e_out[j] = e;
+        f_out[j] = ldexp_rn(r, -e);
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ bool ef_less(int ea, double fa, int eb, double fb)
+{
+  return (ea != eb) ? (ea < eb) : (bits(fa) < bits(fb));
+}
+
+// rank_j = #{i : sigma_i > sigma_j, or sigma_i == sigma_j and i < j}
+__global__ void rank_kernel(int n, const int *e, const double *f, int *rank, SvdState *st,
+                            jsvd_info *info, int sweeps_fp32)
+{
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    int r = 0;
+    const int ej = e[j];
+    const double fj = f[j];
+    for (int i = 0; i < n; ++i) {
+      const int ei = e[i];
+      const double fi = f[i];
+      const bool gt = ef_less(ej, fj, ei, fi);
+      const bool eq = (ei == ej) && (bits(fi) == bits(fj));
+      r += (gt || (eq && i < j)) ? 1 : 0;
+    }
+    rank[j] = r;
+  }
+  if (info && blockIdx.x == 0 && threadIdx.x == 0) {
+    jsvd_info out;
+    long long rot = 0;
+    for (int s = 0; s < st->sweeps && s < kMaxSweepsCap; ++s) rot += st->T[s];
+    out.status = st->nonfinite ? JSVD_E_NONFINITE
+                 : st->err      ? JSVD_E_TIMEOUT
+                 : st->converged ? 0
+                                 : JSVD_NOT_CONVERGED;
+    out.sweeps = st->sweeps;
+    out.rotations = rot;
+    out.rescales = st->rescales;
+    out.sweeps_fp32 = sweeps_fp32;
+    *info = out;
+  }
+}
+
+// U(:, rank_j) = G(:, j) 2^{-e_j} / f_j; V(:, rank_j) = V_k(:, j);
+// sigma(rank_j) = 2^{e_j - s} f_j (section 4.2.1).
+template <bool CPLX>
+__global__ void output_kernel(MatView M, const int *e, const double *f, const int *rank,
+                              const SvdState *st, double *U, int64_t ldu, double *V, int64_t ldv,
+                              double *sigma, double *sigma_e, double *sigma_f)
+{
+  const int s = st->s;
+  const bool bad = st->nonfinite != 0;
+  const double nan = __longlong_as_double(0x7FF8000000000000ll);
+  for (int j = blockIdx.y; j < M.n; j += gridDim.y) {
+    const int r = rank[j];
+    const int ej = e[j];
+    const double fj = f[j];
+    const bool zero = (ej == INT_MIN);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      if (sigma) sigma[r] = bad ? nan : zero ? 0.0 : ldexp_rn(fj, ej - s);
+      if (sigma_e) sigma_e[r] = bad ? nan : zero ? -__longlong_as_double((long long)kInf) : (double)(ej - s);
+      if (sigma_f) sigma_f[r] = bad ? nan : fj;
+    }
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < max(M.m, M.n);
+         i += gridDim.x * blockDim.x) {
+      if (i < M.m) {
+        double ur = 0.0, ui = 0.0;
+        if (bad) {
+          ur = ui = nan;
+        } else if (!zero) {
+          ur = __ddiv_rn(ldexp_rn(M.gr[j * M.ldg + i], -ej), fj);
+          if (CPLX) ui = __ddiv_rn(ldexp_rn(M.gi[j * M.ldg + i], -ej), fj);
+        }
+        if (CPLX) {
+          U[2 * (r * ldu + i)] = ur;
+          U[2 * (r * ldu + i) + 1] = ui;
+        } else {
+          U[r * ldu + i] = ur;
+        }
+      }
+      if (i < M.n) {
+        const double vr = bad ? nan : M.vr[j * M.ldv + i];
+        if (CPLX) {
+          V[2 * (r * ldv + i)] = vr;
+          V[2 * (r * ldv + i) + 1] = bad ? nan : M.vi[j * M.ldv + i];
+        } else {
+          V[r * ldv + i] = vr;
+        }
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+
+static int g_svd_grid_cap = 0;
+
+int svd_set_grid(int cap)
+{
+  if (cap < 0 || cap > (1 << 20)) return -2;
+  g_svd_grid_cap = cap;
+  return JSVD_OK;
+}
+
+__global__ void ordering_kernel(int n, int32_t *tab)
+{
+  const int nt = n + (n & 1), K = nt - 1, L = nt / 2;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < K * L; t += gridDim.x * blockDim.x) {
+    int p, q;
+    pair_of(t / L, t % L, nt, p, q);
+    tab[2 * t] = p;
+    tab[2 * t + 1] = q;
+  }
+}
+
+int svd_check_opts(const jsvd_opts *o, int &S, int &mode, int &rexp, int &permute)
+{
+  S = 100;
+  mode = JSVD_FP64;
+  rexp = 256;
+  permute = 0;
+  if (!o) return 0;
+  if (o->permute != 0 && o->permute != 1) return -1;
+  permute = o->permute;
+  if (o->max_sweeps > 0) S = o->max_sweeps;
+  if (S > kMaxSweepsCap) return -1;
+  if (o->mode != JSVD_FP64 && o->mode != JSVD_MIXED_FP32_FP64) return -1;
+  mode = o->mode;
+  if (o->rescale_exp != 0) {
+    if (o->rescale_exp < 1 || o->rescale_exp > 480) return -1;
+    rexp = o->rescale_exp;
+  }
+  return 0;
+}
+
+size_t svd_fp64_workspace(bool cplx, int64_t m, int64_t n) { return svd_layout(cplx, m, n).total; }
+
+// The FP64 SVD on a workspace laid out by svd_layout; V_1 = I.
+template <bool CPLX>
+static int svd_fp64_run(int64_t m, int64_t n, const double *A, int64_t lda, double *U, int64_t ldu,
+                        double *sigma, double *sigma_e, double *sigma_f, double *V, int64_t ldv,
+                        char *work, jsvd_info *info, int S, int rexp, int permute,
+                        cudaStream_t st)
+{
+  const SvdLayout L = svd_layout(CPLX, m, n);
+  SvdState *state = reinterpret_cast<SvdState *>(work + L.state);
+  MatView M;
+  M.gr = reinterpret_cast<double *>(work + L.gr);
+  M.gi = CPLX ? reinterpret_cast<double *>(work + L.gi) : nullptr;
+  M.vr = reinterpret_cast<double *>(work + L.vr);
+  M.vi = CPLX ? reinterpret_cast<double *>(work + L.vi) : nullptr;
+  M.m = (int)m;
+  M.n = (int)n;
+  M.mp = L.mp;
+  M.np = L.np;
+  M.ldg = L.ldg;
+  M.ldv = L.ldv;
+  int *e = reinterpret_cast<int *>(work + L.e);
+  double *f = reinterpret_cast<double *>(work + L.f);
+  int *rank = reinterpret_cast<int *>(work + L.rank);
+  const int sms = sm_count();
+
+  JSVD_CUDA(cudaMemsetAsync(state, 0, sizeof(SvdState), st));
+  {
+    const int64_t rows = CPLX ? 2 * m : m;
+    const int64_t ld = CPLX ? 2 * lda : lda;
+    int64_t blocks = (rows * n + 255) / 256;
+    if (blocks > (int64_t)sms * 8) blocks = (int64_t)sms * 8;
+    maxnorm_kernel<<<(int)blocks, 256, 0, st>>>(A, ld, rows, n, &state->M0);
+    JSVD_CHECK_LAUNCH();
+  }
+  {
+    dim3 grid((unsigned)((std::max(L.mp, L.np) + 255) / 256), (unsigned)std::min<int64_t>(n, 65535));
+    init_kernel<CPLX><<<grid, 256, 0, st>>>(A, lda, M, state);
+    JSVD_CHECK_LAUNCH();
+  }
+  {
+    const double ups = ldexp(sqrt((double)m), -53);  // Eq. e:tol
+    const int nt = (int)(n + (n & 1));
+    const int Lp = nt / 2;
+    int per_sm = 0;
+    JSVD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweeps_kernel<CPLX>, 32, 0));
+    if (per_sm < 1) return JSVD_E_UNSUPPORTED;
+    int grid = std::min(Lp, per_sm * sms);
+    if (g_svd_grid_cap > 0) grid = std::min(grid, g_svd_grid_cap);
+    if (grid < 1) grid = 1;
+    MatView Mk = M;
+    SvdState *sk = state;
+    int Sk = S, rk = rexp, pk = permute;
+    double upsk = ups;
+    void *args[] = {&Mk, &sk, &upsk, &Sk, &rk, &pk};
+    JSVD_CUDA(cudaLaunchCooperativeKernel((const void *)sweeps_kernel<CPLX>, dim3(grid), dim3(32),
+                                          args, 0, st));
+  }
+  {
+    const int blocks = (int)std::min<int64_t>((n * 32 + 255) / 256, (int64_t)sms * 8);
+    colnorm_kernel<CPLX><<<blocks, 256, 0, st>>>(M, e, f);
+    JSVD_CHECK_LAUNCH();
+    rank_kernel<<<(int)((n + 127) / 128), 128, 0, st>>>((int)n, e, f, rank, state, info, 0);
+    JSVD_CHECK_LAUNCH();
+    dim3 grid((unsigned)((std::max<int64_t>(m, n) + 255) / 256), (unsigned)std::min<int64_t>(n, 65535));
+    output_kernel<CPLX><<<grid, 256, 0, st>>>(M, e, f, rank, state, U, ldu, V, ldv, sigma, sigma_e,
+                                              sigma_f);
+    JSVD_CHECK_LAUNCH();
+  }
+  return JSVD_OK;
+}
+
+}  // namespace jsvd
+
+using namespace jsvd;
+
+extern "C" int jsvd_ordering(int32_t n, int32_t *tab, void *stream)
+{
+  if (n < 2) return -1;
+  if (!tab) return -2;
+  const int nt = n + (n & 1);
+  const int64_t total = (int64_t)(nt - 1) * (nt / 2);
+  const int blocks = (int)std::min<int64_t>((total + 255) / 256, 4096);
+  ordering_kernel<<<blocks, 256, 0, as_stream(stream)>>>(n, tab);
+  JSVD_CHECK_LAUNCH();
+  return JSVD_OK;
+}
+
+extern "C" int jsvd_svd_workspace_size(jsvd_field field, const jsvd_opts *opts, int64_t m,
+                                       int64_t n, size_t *bytes)
+{
+  if (field != JSVD_REAL && field != JSVD_COMPLEX) return -1;
+  int S, mode, rexp, permute;
+  if (svd_check_opts(opts, S, mode, rexp, permute)) return -2;
+  if (m < 1 || m > (1 << 28)) return -3;
+  if (n < 1 || n > m || n > (1 << 20)) return -4;
+  if (!bytes) return -5;
+  const bool cplx = field == JSVD_COMPLEX;
+  *bytes = (mode == JSVD_MIXED_FP32_FP64) ? svd_mixed_workspace(cplx, m, n)
+                                          : svd_fp64_workspace(cplx, m, n);
+  return JSVD_OK;
+}
+
+extern "C" int jsvd_svd(jsvd_field field, const jsvd_opts *opts, int64_t m, int64_t n,
+                        const void *A, int64_t lda, void *U, int64_t ldu, double *sigma,
+                        double *sigma_e, double *sigma_f, void *V, int64_t ldv, void *work,
+                        size_t work_bytes, jsvd_info *info, void *stream)
+{
+  if (field != JSVD_REAL && field != JSVD_COMPLEX) return -1;
+  int S, mode, rexp, permute;
+  if (svd_check_opts(opts, S, mode, rexp, permute)) return -2;
+  if (m < 1 || m > (1 << 28)) return -3;
+  if (n < 1 || n > m || n > (1 << 20)) return -4;
+  const bool cplx = field == JSVD_COMPLEX;
+  const uintptr_t al = cplx ? 15 : 7;
+  if (!A || ((uintptr_t)A & al)) return -5;
+  if (lda < m) return -6;
+  if (!U || ((uintptr_t)U & al)) return -7;
+  if (ldu < m) return -8;
+  if (!sigma) return -9;
+  if (!V || ((uintptr_t)V & al)) return -12;
+  if (ldv < n) return -13;
+  if (!work || ((uintptr_t)work & 255)) return -14;
+  size_t need = 0;
+  jsvd_svd_workspace_size(field, opts, m, n, &need);
+  if (work_bytes < need) return JSVD_E_WORKSPACE;
+  cudaStream_t st = as_stream(stream);
+  if (mode == JSVD_MIXED_FP32_FP64)
+    return svd_mixed_run(cplx, m, n, A, lda, U, ldu, sigma, sigma_e, sigma_f, V, ldv,
+                         (char *)work, info, S, rexp, permute, st);
+  if (cplx)
+    return svd_fp64_run<true>(m, n, (const double *)A, lda, (double *)U, ldu, sigma, sigma_e,
+                              sigma_f, (double *)V, ldv, (char *)work, info, S, rexp, permute, st);
+  return svd_fp64_run<false>(m, n, (const double *)A, lda, (double *)U, ldu, sigma, sigma_e,
+                             sigma_f, (double *)V, ldv, (char *)work, info, S, rexp, permute, st);
+}

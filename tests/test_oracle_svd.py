@@ -70,6 +70,16 @@ def test_svd_real_geometric(m, n):
     assert np.abs(r["sigma"] - s).max() <= tol(n) * s[0]
 
 
+@pytest.mark.parametrize("cplx", [False, True])
+def test_svd_with_column_swaps(cplx):
+    """The column swap P of section 2 applied during the sweeps."""
+    A, s = workloads.svd_geometric(40, 21, 1e5, cplx, np.random.default_rng(21))
+    r = oracle.vjsvd(A, permute=True)
+    assert r["status"] == oracle.OK
+    check_svd(A, r)
+    assert np.abs(r["sigma"] - s).max() <= tol(21) * s[0]
+
+
 @pytest.mark.parametrize("m,n", [(48, 24), (31, 31), (20, 7)])
 def test_svd_complex_geometric(m, n):
     A, s = workloads.svd_geometric(m, n, 1e6, True, np.random.default_rng(m * 7 + n))
