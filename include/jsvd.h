@@ -180,6 +180,39 @@ JSVD_API int jsvd_svd(jsvd_field field, const jsvd_opts *opts, int64_t m, int64_
                       double *sigma_e, double *sigma_f, void *V, int64_t ldv, void *work,
                       size_t work_bytes, jsvd_info *info, void *stream);
 
+/* jsvd_svd for callers that cannot allocate device memory at run time --
+ * for instance code inside a framework whose caching allocator already holds
+ * the GPU's memory (another cudaMalloc may fail there), latency-critical
+ * loops that cannot afford cudaMalloc's implicit synchronisation, or
+ * processes whose memory footprint is fixed at start-up.  The paper has no
+ * counterpart; it is the same computation as jsvd_svd.
+ *
+ * It takes no workspace and allocates nothing (no cudaMalloc, cudaFree or
+ * allocating library call).  Its scratch is one static device array of
+ * JSVD_NOALLOC_SCRATCH_BYTES (16 MiB) inside the library, which every GPU
+ * that loads the library keeps until the process exits.  A problem whose
+ * jsvd_svd_workspace_size exceeds that is rejected with JSVD_E_WORKSPACE
+ * (e.g. real 2048 x 512 and complex 512 x 512 fit; real 1024 x 1024 does
+ * not).
+ *
+ * The first call on a device looks up the array's device address there
+ * (cudaGetSymbolAddress, which may load the library's device code on that
+ * device); make that first call before any stream capture.  All calls share
+ * the one array and it keeps the last call's contents: each call clears the
+ * state that must start at zero, but calls whose work overlaps on the GPU
+ * (different streams, or different host threads) race on it and give wrong
+ * results -- serialise them.
+ *
+ * Arguments and results as jsvd_svd, without work/work_bytes; A, U, sigma,
+ * V (and the optional sigma_e, sigma_f, info) remain the caller's device
+ * buffers.  Errors: -i for argument i (1..13), JSVD_E_WORKSPACE when the
+ * problem does not fit the scratch, JSVD_E_CUDA. */
+#define JSVD_NOALLOC_SCRATCH_BYTES (16u << 20)
+JSVD_API int jsvd_svd_noalloc(jsvd_field field, const jsvd_opts *opts, int64_t m, int64_t n,
+                              const void *A, int64_t lda, void *U, int64_t ldu, double *sigma,
+                              double *sigma_e, double *sigma_f, void *V, int64_t ldv,
+                              jsvd_info *info, void *stream);
+
 /* The parallel pivot ordering the SVD kernels use (section 4.1; the
  * round-robin reading): writes (nt - 1) x (nt / 2) pairs (p, q), p < q, as
  * int32 [step][pair][2] into the DEVICE buffer tab, nt = n + (n & 1) (a

@@ -51,6 +51,9 @@ class Opts(ctypes.Structure):
 # int64 rotations, int32 rescales, int32 sweeps_fp32 (24 bytes)
 INFO_BYTES = 24
 
+# size of the static scratch of jsvd_svd_noalloc (JSVD_NOALLOC_SCRATCH_BYTES)
+NOALLOC_SCRATCH_BYTES = 16 << 20
+
 
 _lib = None
 _vp = ctypes.c_void_p
@@ -83,6 +86,9 @@ def lib():
         L.jsvd_svd.argtypes = [ctypes.c_int, ctypes.POINTER(Opts), _i64, _i64, _vp, _i64, _vp, _i64,
                                _d, _d, _d, _vp, _i64, _vp, _sz, _vp, _vp]
         L.jsvd_svd.restype = ctypes.c_int
+        L.jsvd_svd_noalloc.argtypes = [ctypes.c_int, ctypes.POINTER(Opts), _i64, _i64, _vp, _i64,
+                                       _vp, _i64, _d, _d, _d, _vp, _i64, _vp, _vp]
+        L.jsvd_svd_noalloc.restype = ctypes.c_int
         L.jsvd_ordering.argtypes = [ctypes.c_int32, _vp, _vp]
         L.jsvd_ordering.restype = ctypes.c_int
         _lib = L
