@@ -213,6 +213,17 @@ JSVD_API int jsvd_svd_noalloc(jsvd_field field, const jsvd_opts *opts, int64_t m
                               double *sigma_e, double *sigma_f, void *V, int64_t ldv,
                               jsvd_info *info, void *stream);
 
+/* C = alpha op(A) B + beta C for column-major FP64 matrices on the FP64
+ * tensor path (mma.sync m8n8k4 f64): the dense products of the mixed SVD
+ * (G = A V0 and the Newton-Schulz re-orthogonalisation of V).  op(A) = A
+ * (M x K, lda >= M) for transA == 0, A^T (A stored K x M, lda >= K) for
+ * transA == 1; B is K x N (ldb >= K); C is M x N (ldc >= M) and must not
+ * overlap A or B.  M, N or K = 0 is allowed (K = 0 scales C by beta).
+ * Errors: -i for argument i, JSVD_E_CUDA. */
+JSVD_API int jsvd_dgemm(int transA, int64_t M, int64_t N, int64_t K, double alpha,
+                        const double *A, int64_t lda, const double *B, int64_t ldb, double beta,
+                        double *C, int64_t ldc, void *stream);
+
 /* The parallel pivot ordering the SVD kernels use (section 4.1; the
  * round-robin reading): writes (nt - 1) x (nt / 2) pairs (p, q), p < q, as
  * int32 [step][pair][2] into the DEVICE buffer tab, nt = n + (n & 1) (a

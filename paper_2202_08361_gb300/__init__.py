@@ -12,8 +12,8 @@ from ._native import (JSVD_COMPLEX, JSVD_E_CUDA, JSVD_E_NONFINITE, JSVD_E_TIMEOU
                       JSVD_NOT_CONVERGED, JSVD_OK, JSVD_REAL, JSVD_TUNE_EVD_LAUNCH,
                       JSVD_TUNE_SVD_GRID, JsvdError)
 
-__all__ = ["evd2x2_batched", "svd", "svd_workspace_size", "ordering", "decode_info", "version",
-           "tune_set", "JsvdError", "JSVD_REAL", "JSVD_COMPLEX"]
+__all__ = ["evd2x2_batched", "svd", "svd_workspace_size", "ordering", "decode_info", "dgemm",
+           "version", "tune_set", "JsvdError", "JSVD_REAL", "JSVD_COMPLEX"]
 
 
 def _torch():
@@ -193,3 +193,27 @@ def ordering(n, stream=None):
     _native.check(_native.lib().jsvd_ordering(int(n), tab.data_ptr(), _stream_handle(stream)),
                   "jsvd_ordering")
     return tab
+
+
+def dgemm(A, B, *, transA=False, alpha=1.0, beta=0.0, C=None, stream=None):
+    """C = alpha op(A) B + beta C (jsvd_dgemm) for float64 CUDA tensors, any
+    layout (column-major copies are made when needed)."""
+    torch = _torch()
+    Ac, lda = colmajor(A)
+    Bc, ldb = colmajor(B)
+    M = A.shape[1] if transA else A.shape[0]
+    K = A.shape[0] if transA else A.shape[1]
+    N = B.shape[1]
+    if B.shape[0] != K:
+        raise ValueError("inner dimensions differ")
+    if C is None:
+        C = colmajor_empty(M, N, torch.float64, A.device)
+        beta = 0.0
+    Cc, ldc = colmajor(C)
+    if Cc.data_ptr() != C.data_ptr():
+        raise ValueError("C must be column-major")
+    rc = _native.lib().jsvd_dgemm(1 if transA else 0, M, N, K, float(alpha), Ac.data_ptr(), lda,
+                                  Bc.data_ptr(), ldb, float(beta), Cc.data_ptr(), ldc,
+                                  _stream_handle(stream))
+    _native.check(rc, "jsvd_dgemm")
+    return C

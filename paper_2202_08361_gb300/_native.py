@@ -89,6 +89,9 @@ def lib():
         L.jsvd_svd_noalloc.argtypes = [ctypes.c_int, ctypes.POINTER(Opts), _i64, _i64, _vp, _i64,
                                        _vp, _i64, _d, _d, _d, _vp, _i64, _vp, _vp]
         L.jsvd_svd_noalloc.restype = ctypes.c_int
+        L.jsvd_dgemm.argtypes = [ctypes.c_int, _i64, _i64, _i64, ctypes.c_double, _vp, _i64, _vp,
+                                 _i64, ctypes.c_double, _vp, _i64, _vp]
+        L.jsvd_dgemm.restype = ctypes.c_int
         L.jsvd_ordering.argtypes = [ctypes.c_int32, _vp, _vp]
         L.jsvd_ordering.restype = ctypes.c_int
         _lib = L

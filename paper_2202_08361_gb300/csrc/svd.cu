@@ -137,9 +137,10 @@ __global__ void init_kernel(const double *__restrict__ A, int64_t lda, MatView M
 }
 
 // All sweeps of Alg. zvjsvd; blockDim = 32 (one warp per block), warps
-// stride over the nt/2 pairs of every step.
-template <bool CPLX>
-__global__ void __launch_bounds__(32) sweeps_kernel(MatView M, SvdState *st, double ups,
+// stride over the nt/2 pairs of every step.  T is the precision of the
+// columns (double; float in the FP32 phase of the mixed SVD).
+template <typename T, bool CPLX>
+__global__ void __launch_bounds__(32) sweeps_kernel(MatViewT<T> M, SvdState *st, double ups,
                                                     int max_sweeps, int rescale_exp, int permute)
 {
   if (st->nonfinite) return;
@@ -182,11 +183,11 @@ __global__ void __launch_bounds__(32) sweeps_kernel(MatView M, SvdState *st, dou
           }
           continue;
         }
-        rots += pair_step<CPLX>(M, p, q, ups, rk, permute != 0, Mloc) ? 1 : 0;
+        rots += pair_step<T, CPLX>(M, p, q, ups, rk, permute != 0, Mloc) ? 1 : 0;
       }
       Mloc = warp_umax(Mloc);
       if (lane == 0) {
-        if (Mloc) atomicMax(&st->Mbuf[nxt], Mloc);
+        if (Mloc) atomicMax(&st->Mbuf[nxt], bits(magbits_to_double(Mloc, T(0))));
         if (rots) atomicAdd(&st->T[sweep], rots);
       }
       if (!grid_barrier(&st->bar_count, &st->bar_gen, &st->err, kBarrierLimitNs)) return;
@@ -235,7 +236,7 @@ __device__ __forceinline__ bool ef_less(int ea, double fa, int eb, double fb)
 
 // rank_j = #{i : sigma_i > sigma_j, or sigma_i == sigma_j and i < j}
 __global__ void rank_kernel(int n, const int *e, const double *f, int *rank, SvdState *st,
-                            jsvd_info *info, int sweeps_fp32)
+                            jsvd_info *info, const SvdState *st32)
 {
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
     int r = 0;
@@ -254,14 +255,20 @@ __global__ void rank_kernel(int n, const int *e, const double *f, int *rank, Svd
     jsvd_info out;
     long long rot = 0;
     for (int s = 0; s < st->sweeps && s < kMaxSweepsCap; ++s) rot += st->T[s];
-    out.status = st->nonfinite ? JSVD_E_NONFINITE
-                 : st->err      ? JSVD_E_TIMEOUT
-                 : st->converged ? 0
-                                 : JSVD_NOT_CONVERGED;
+    int sw32 = 0, err32 = 0;
+    if (st32) {
+      sw32 = st32->sweeps;
+      err32 = st32->err;
+      for (int s = 0; s < st32->sweeps && s < kMaxSweepsCap; ++s) rot += st32->T[s];
+    }
+    out.status = st->nonfinite        ? JSVD_E_NONFINITE
+                 : (st->err || err32) ? JSVD_E_TIMEOUT
+                 : st->converged      ? 0
+                                      : JSVD_NOT_CONVERGED;
     out.sweeps = st->sweeps;
     out.rotations = rot;
     out.rescales = st->rescales;
-    out.sweeps_fp32 = sweeps_fp32;
+    out.sweeps_fp32 = sw32;
     *info = out;
   }
 }
@@ -358,9 +365,183 @@ int svd_check_opts(const jsvd_opts *o, int &S, int &mode, int &rexp, int &permut
   return 0;
 }
 
+
+// ---------------------------------------------------------------------------
+// mixed precision: FP32 copies of the iteration matrix, FP64 conversion
+
+// G32 = fl32(G64) (planes), V32 = I, and the FP32 phase's state.
+template <bool CPLX>
+__global__ void to_fp32_kernel(MatView M64, MatViewT<float> M32, const SvdState *st64,
+                               SvdState *st32)
+{
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+    st32->nonfinite = st64->nonfinite;
+    st32->s = st64->s;
+    st32->Mbuf[0] = st64->Mbuf[0];
+  }
+  for (int j = blockIdx.y; j < M64.n; j += gridDim.y) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < max(M64.mp, M64.np);
+         i += gridDim.x * blockDim.x) {
+      if (i < M64.mp) {
+        M32.gr[j * M32.ldg + i] = __double2float_rn(M64.gr[j * M64.ldg + i]);
+        if (CPLX) M32.gi[j * M32.ldg + i] = __double2float_rn(M64.gi[j * M64.ldg + i]);
+      }
+      if (i < M64.np) {
+        M32.vr[j * M32.ldv + i] = (i == j) ? 1.0f : 0.0f;
+        if (CPLX) M32.vi[j * M32.ldv + i] = 0.0f;
+      }
+    }
+  }
+}
+
+// V64 = (double) V32 (exact widening)
+template <bool CPLX>
+__global__ void v_to_fp64_kernel(MatViewT<float> M32, double *vr, double *vi, int64_t ldv)
+{
+  for (int j = blockIdx.y; j < M32.n; j += gridDim.y)
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M32.np; i += gridDim.x * blockDim.x) {
+      vr[j * ldv + i] = (double)M32.vr[j * M32.ldv + i];
+      if (CPLX) vi[j * ldv + i] = (double)M32.vi[j * M32.ldv + i];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+
 size_t svd_fp64_workspace(bool cplx, int64_t m, int64_t n) { return svd_layout(cplx, m, n).total; }
 
-// The FP64 SVD on a workspace laid out by svd_layout; V_1 = I.
+// Extra regions of the mixed SVD after the FP64 layout.
+struct MixedLayout {
+  SvdLayout L;
+  size_t st32, g32r, g32i, v32r, v32i, gtr, gti, br, bi, xr, xi, total;
+};
+
+static MixedLayout mixed_layout(bool cplx, int64_t m, int64_t n)
+{
+  MixedLayout X;
+  X.L = svd_layout(cplx, m, n);
+  size_t o = X.L.total;
+  const size_t g32 = sizeof(float) * (size_t)X.L.ldg * (size_t)n;
+  const size_t v32 = sizeof(float) * (size_t)X.L.ldv * (size_t)n;
+  const size_t g64 = sizeof(double) * (size_t)X.L.ldg * (size_t)n;
+  const size_t v64 = sizeof(double) * (size_t)X.L.ldv * (size_t)n;
+  X.st32 = o;
+  o = align256(o + sizeof(SvdState));
+  X.g32r = o;
+  o = align256(o + g32);
+  X.g32i = o;
+  if (cplx) o = align256(o + g32);
+  X.v32r = o;
+  o = align256(o + v32);
+  X.v32i = o;
+  if (cplx) o = align256(o + v32);
+  X.gtr = o;
+  o = align256(o + g64);
+  X.gti = o;
+  if (cplx) o = align256(o + g64);
+  X.br = o;
+  o = align256(o + v64);
+  X.bi = o;
+  if (cplx) o = align256(o + v64);
+  X.xr = o;
+  o = align256(o + v64);
+  X.xi = o;
+  if (cplx) o = align256(o + v64);
+  X.total = o;
+  return X;
+}
+
+size_t svd_mixed_workspace(bool cplx, int64_t m, int64_t n) { return mixed_layout(cplx, m, n).total; }
+
+template <typename T>
+static MatViewT<T> view_at(char *work, size_t gr, size_t gi, size_t vr, size_t vi, bool cplx,
+                           const SvdLayout &L, int64_t m, int64_t n)
+{
+  MatViewT<T> M;
+  M.gr = reinterpret_cast<T *>(work + gr);
+  M.gi = cplx ? reinterpret_cast<T *>(work + gi) : nullptr;
+  M.vr = reinterpret_cast<T *>(work + vr);
+  M.vi = cplx ? reinterpret_cast<T *>(work + vi) : nullptr;
+  M.m = (int)m;
+  M.n = (int)n;
+  M.mp = L.mp;
+  M.np = L.np;
+  M.ldg = L.ldg;
+  M.ldv = L.ldv;
+  return M;
+}
+
+// A1: ||A||_max, G_1 = 2^{s_0} A (planes) in M, V_1 = I.
+template <bool CPLX>
+static int phase_init(const MatView &M, const double *A, int64_t lda, SvdState *state,
+                      cudaStream_t st)
+{
+  const int sms = sm_count();
+  const int64_t m = M.m, n = M.n;
+  JSVD_CUDA(cudaMemsetAsync(state, 0, sizeof(SvdState), st));
+  const int64_t rows = CPLX ? 2 * m : m;
+  const int64_t ld = CPLX ? 2 * lda : lda;
+  int64_t blocks = (rows * n + 255) / 256;
+  if (blocks > (int64_t)sms * 8) blocks = (int64_t)sms * 8;
+  maxnorm_kernel<<<(int)blocks, 256, 0, st>>>(A, ld, rows, n, &state->M0);
+  JSVD_CHECK_LAUNCH();
+  dim3 grid((unsigned)((std::max(M.mp, M.np) + 255) / 256), (unsigned)std::min<int64_t>(n, 65535));
+  init_kernel<CPLX><<<grid, 256, 0, st>>>(A, lda, M, state);
+  JSVD_CHECK_LAUNCH();
+  return JSVD_OK;
+}
+
+// A2-A8: every sweep, in one cooperative launch.
+template <typename T, bool CPLX>
+static int phase_sweeps(const MatViewT<T> &M, SvdState *state, double ups, int S, int rexp,
+                        int permute, cudaStream_t st)
+{
+  const int nt = M.n + (M.n & 1);
+  const int Lp = nt / 2;
+  int per_sm = 0;
+  JSVD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweeps_kernel<T, CPLX>, 32, 0));
+  if (per_sm < 1) return JSVD_E_UNSUPPORTED;
+  int grid = std::min(Lp, per_sm * sm_count());
+  if (g_svd_grid_cap > 0) grid = std::min(grid, g_svd_grid_cap);
+  if (grid < 1) grid = 1;
+  MatViewT<T> Mk = M;
+  SvdState *sk = state;
+  int Sk = S, rk = rexp, pk = permute;
+  double upsk = ups;
+  void *args[] = {&Mk, &sk, &upsk, &Sk, &rk, &pk};
+  JSVD_CUDA(cudaLaunchCooperativeKernel((const void *)sweeps_kernel<T, CPLX>, dim3(grid), dim3(32),
+                                        args, 0, st));
+  return JSVD_OK;
+}
+
+// A9: norms, order, U = G 2^{-e_j}/f_j, sigma, V, info.
+template <bool CPLX>
+static int phase_finish(const MatView &M, int *e, double *f, int *rank, SvdState *state,
+                        const SvdState *st32, double *U, int64_t ldu, double *sigma,
+                        double *sigma_e, double *sigma_f, double *V, int64_t ldv, jsvd_info *info,
+                        cudaStream_t st)
+{
+  const int sms = sm_count();
+  const int64_t m = M.m, n = M.n;
+  const int blocks = (int)std::min<int64_t>((n * 32 + 255) / 256, (int64_t)sms * 8);
+  colnorm_kernel<CPLX><<<blocks, 256, 0, st>>>(M, e, f);
+  JSVD_CHECK_LAUNCH();
+  rank_kernel<<<(int)((n + 127) / 128), 128, 0, st>>>((int)n, e, f, rank, state, info, st32);
+  JSVD_CHECK_LAUNCH();
+  dim3 grid((unsigned)((std::max<int64_t>(m, n) + 255) / 256), (unsigned)std::min<int64_t>(n, 65535));
+  output_kernel<CPLX><<<grid, 256, 0, st>>>(M, e, f, rank, state, U, ldu, V, ldv, sigma, sigma_e,
+                                            sigma_f);
+  JSVD_CHECK_LAUNCH();
+  return JSVD_OK;
+}
+
+#define JSVD_TRY(...)                 \
+  do {                                \
+    const int rc_ = (__VA_ARGS__);    \
+    if (rc_ != JSVD_OK) return rc_;   \
+  } while (0)
+
+// The FP64 SVD (Alg. zvjsvd) with V_1 = I.
 template <bool CPLX>
 static int svd_fp64_run(int64_t m, int64_t n, const double *A, int64_t lda, double *U, int64_t ldu,
                         double *sigma, double *sigma_e, double *sigma_f, double *V, int64_t ldv,
@@ -369,66 +550,111 @@ static int svd_fp64_run(int64_t m, int64_t n, const double *A, int64_t lda, doub
 {
   const SvdLayout L = svd_layout(CPLX, m, n);
   SvdState *state = reinterpret_cast<SvdState *>(work + L.state);
-  MatView M;
-  M.gr = reinterpret_cast<double *>(work + L.gr);
-  M.gi = CPLX ? reinterpret_cast<double *>(work + L.gi) : nullptr;
-  M.vr = reinterpret_cast<double *>(work + L.vr);
-  M.vi = CPLX ? reinterpret_cast<double *>(work + L.vi) : nullptr;
-  M.m = (int)m;
-  M.n = (int)n;
-  M.mp = L.mp;
-  M.np = L.np;
-  M.ldg = L.ldg;
-  M.ldv = L.ldv;
-  int *e = reinterpret_cast<int *>(work + L.e);
-  double *f = reinterpret_cast<double *>(work + L.f);
-  int *rank = reinterpret_cast<int *>(work + L.rank);
-  const int sms = sm_count();
+  const MatView M = view_at<double>(work, L.gr, L.gi, L.vr, L.vi, CPLX, L, m, n);
+  JSVD_TRY(phase_init<CPLX>(M, A, lda, state, st));
+  JSVD_TRY(phase_sweeps<double, CPLX>(M, state, ldexp(sqrt((double)m), -53), S, rexp, permute, st));
+  return phase_finish<CPLX>(M, reinterpret_cast<int *>(work + L.e),
+                            reinterpret_cast<double *>(work + L.f),
+                            reinterpret_cast<int *>(work + L.rank), state, nullptr, U, ldu, sigma,
+                            sigma_e, sigma_f, V, ldv, info, st);
+}
 
-  JSVD_CUDA(cudaMemsetAsync(state, 0, sizeof(SvdState), st));
+// Exponent of the FP32 phase's convergence threshold 2^kMixedTolExp sqrt(m):
+// 16 times the FP32 unit roundoff 2^-24, since the lane partial sums of
+// that phase are FP32 and carry noise of order sqrt(m) 2^-24; the FP64
+// phase finishes the convergence from there.
+constexpr int kMixedTolExp = -20;
+constexpr int kNewtonSchulzSteps = 2;
+
+// The mixed SVD: FP32 sweeps accumulate V32; V0 = V32 re-orthogonalised in
+// FP64 by Newton-Schulz steps X <- X (3I - X^H X)/2; G = 2^{s_0} A V0 by
+// FP64 GEMM; FP64 sweeps from (G, V0); finish as the FP64 SVD.
+template <bool CPLX>
+static int svd_mixed_run_t(int64_t m, int64_t n, const double *A, int64_t lda, double *U,
+                           int64_t ldu, double *sigma, double *sigma_e, double *sigma_f, double *V,
+                           int64_t ldv, char *work, jsvd_info *info, int S, int rexp, int permute,
+                           cudaStream_t st)
+{
+  const MixedLayout X = mixed_layout(CPLX, m, n);
+  const SvdLayout &L = X.L;
+  SvdState *st64 = reinterpret_cast<SvdState *>(work + L.state);
+  SvdState *st32 = reinterpret_cast<SvdState *>(work + X.st32);
+  const MatView M0 = view_at<double>(work, L.gr, L.gi, L.vr, L.vi, CPLX, L, m, n);
+  const MatViewT<float> M32 = view_at<float>(work, X.g32r, X.g32i, X.v32r, X.v32i, CPLX, L, m, n);
+  const MatView M64 = view_at<double>(work, X.gtr, X.gti, L.vr, L.vi, CPLX, L, m, n);
+  double *Br = reinterpret_cast<double *>(work + X.br), *Bi = reinterpret_cast<double *>(work + X.bi);
+  double *Xr = reinterpret_cast<double *>(work + X.xr), *Xi = reinterpret_cast<double *>(work + X.xi);
+  if (!CPLX) Bi = Xi = nullptr;
+
+  // A1 on the FP64 planes: M0.g = 2^{s_0} A
+  JSVD_TRY(phase_init<CPLX>(M0, A, lda, st64, st));
+  // FP32 phase
+  JSVD_CUDA(cudaMemsetAsync(st32, 0, sizeof(SvdState), st));
+  dim3 grid((unsigned)((std::max(L.mp, L.np) + 255) / 256), (unsigned)std::min<int64_t>(n, 65535));
+  to_fp32_kernel<CPLX><<<grid, 256, 0, st>>>(M0, M32, st64, st32);
+  JSVD_CHECK_LAUNCH();
+  const double ups32 = ldexp(sqrt((double)m), kMixedTolExp);
+  JSVD_TRY(phase_sweeps<float, CPLX>(M32, st32, ups32, S, 1 << 20, permute, st));
+  // V0 = orth(V32) in FP64 (in M64.v = the FP64 layout's V planes)
+  dim3 gv((unsigned)((L.np + 255) / 256), (unsigned)std::min<int64_t>(n, 65535));
+  v_to_fp64_kernel<CPLX><<<gv, 256, 0, st>>>(M32, M64.vr, M64.vi, L.ldv);
+  JSVD_CHECK_LAUNCH();
+  // every product runs over the zero-padded rows too, so the padding rows
+  // the sweeps read stay exactly zero
+  const int ni = (int)n, npi = L.np, mpi = L.mp;
+  for (int it = 0; it < kNewtonSchulzSteps; ++it) {
+    double *Vr = M64.vr, *Vi = M64.vi;
+    // B = V^H V; X = 1.5 V - 0.5 V B; V = X
+    if (CPLX) {
+      JSVD_TRY(zgemm_split(true, ni, ni, npi, 1.0, Vr, Vi, L.ldv, Vr, Vi, L.ldv, 0.0, Br, Bi, L.ldv, st));
+      JSVD_CUDA(cudaMemcpyAsync(Xr, Vr, sizeof(double) * L.ldv * n, cudaMemcpyDeviceToDevice, st));
+      JSVD_CUDA(cudaMemcpyAsync(Xi, Vi, sizeof(double) * L.ldv * n, cudaMemcpyDeviceToDevice, st));
+      JSVD_TRY(zgemm_split(false, npi, ni, ni, -0.5, Vr, Vi, L.ldv, Br, Bi, L.ldv, 1.5, Xr, Xi, L.ldv, st));
+      JSVD_CUDA(cudaMemcpyAsync(Vr, Xr, sizeof(double) * L.ldv * n, cudaMemcpyDeviceToDevice, st));
+      JSVD_CUDA(cudaMemcpyAsync(Vi, Xi, sizeof(double) * L.ldv * n, cudaMemcpyDeviceToDevice, st));
+    } else {
+      JSVD_TRY(dgemm(true, ni, ni, npi, 1.0, Vr, L.ldv, Vr, L.ldv, 0.0, Br, L.ldv, st));
+      JSVD_CUDA(cudaMemcpyAsync(Xr, Vr, sizeof(double) * L.ldv * n, cudaMemcpyDeviceToDevice, st));
+      JSVD_TRY(dgemm(false, npi, ni, ni, -0.5, Vr, L.ldv, Br, L.ldv, 1.5, Xr, L.ldv, st));
+      JSVD_CUDA(cudaMemcpyAsync(Vr, Xr, sizeof(double) * L.ldv * n, cudaMemcpyDeviceToDevice, st));
+    }
+  }
+  // G = 2^{s_0} A V0 (FP64 GEMM on the FP64 tensor path)
+  if (CPLX)
+    JSVD_TRY(zgemm_split(false, mpi, ni, ni, 1.0, M0.gr, M0.gi, L.ldg, M64.vr, M64.vi, L.ldv, 0.0,
+                         M64.gr, M64.gi, L.ldg, st));
+  else
+    JSVD_TRY(dgemm(false, mpi, ni, ni, 1.0, M0.gr, L.ldg, M64.vr, L.ldv, 0.0, M64.gr, L.ldg, st));
+  // the FP64 phase restarts the step state from the max-norm of the new G
+  JSVD_CUDA(cudaMemsetAsync(st64->Mbuf, 0, sizeof(st64->Mbuf), st));
   {
-    const int64_t rows = CPLX ? 2 * m : m;
-    const int64_t ld = CPLX ? 2 * lda : lda;
-    int64_t blocks = (rows * n + 255) / 256;
+    const int sms = sm_count();
+    int64_t blocks = ((int64_t)L.mp * n + 255) / 256;
     if (blocks > (int64_t)sms * 8) blocks = (int64_t)sms * 8;
-    maxnorm_kernel<<<(int)blocks, 256, 0, st>>>(A, ld, rows, n, &state->M0);
+    maxnorm_kernel<<<(int)blocks, 256, 0, st>>>(M64.gr, L.ldg, L.mp, n, &st64->Mbuf[0]);
     JSVD_CHECK_LAUNCH();
+    if (CPLX) {
+      maxnorm_kernel<<<(int)blocks, 256, 0, st>>>(M64.gi, L.ldg, L.mp, n, &st64->Mbuf[0]);
+      JSVD_CHECK_LAUNCH();
+    }
   }
-  {
-    dim3 grid((unsigned)((std::max(L.mp, L.np) + 255) / 256), (unsigned)std::min<int64_t>(n, 65535));
-    init_kernel<CPLX><<<grid, 256, 0, st>>>(A, lda, M, state);
-    JSVD_CHECK_LAUNCH();
-  }
-  {
-    const double ups = ldexp(sqrt((double)m), -53);  // Eq. e:tol
-    const int nt = (int)(n + (n & 1));
-    const int Lp = nt / 2;
-    int per_sm = 0;
-    JSVD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweeps_kernel<CPLX>, 32, 0));
-    if (per_sm < 1) return JSVD_E_UNSUPPORTED;
-    int grid = std::min(Lp, per_sm * sms);
-    if (g_svd_grid_cap > 0) grid = std::min(grid, g_svd_grid_cap);
-    if (grid < 1) grid = 1;
-    MatView Mk = M;
-    SvdState *sk = state;
-    int Sk = S, rk = rexp, pk = permute;
-    double upsk = ups;
-    void *args[] = {&Mk, &sk, &upsk, &Sk, &rk, &pk};
-    JSVD_CUDA(cudaLaunchCooperativeKernel((const void *)sweeps_kernel<CPLX>, dim3(grid), dim3(32),
-                                          args, 0, st));
-  }
-  {
-    const int blocks = (int)std::min<int64_t>((n * 32 + 255) / 256, (int64_t)sms * 8);
-    colnorm_kernel<CPLX><<<blocks, 256, 0, st>>>(M, e, f);
-    JSVD_CHECK_LAUNCH();
-    rank_kernel<<<(int)((n + 127) / 128), 128, 0, st>>>((int)n, e, f, rank, state, info, 0);
-    JSVD_CHECK_LAUNCH();
-    dim3 grid((unsigned)((std::max<int64_t>(m, n) + 255) / 256), (unsigned)std::min<int64_t>(n, 65535));
-    output_kernel<CPLX><<<grid, 256, 0, st>>>(M, e, f, rank, state, U, ldu, V, ldv, sigma, sigma_e,
-                                              sigma_f);
-    JSVD_CHECK_LAUNCH();
-  }
-  return JSVD_OK;
+  JSVD_TRY(phase_sweeps<double, CPLX>(M64, st64, ldexp(sqrt((double)m), -53), S, rexp, permute, st));
+  return phase_finish<CPLX>(M64, reinterpret_cast<int *>(work + L.e),
+                            reinterpret_cast<double *>(work + L.f),
+                            reinterpret_cast<int *>(work + L.rank), st64, st32, U, ldu, sigma,
+                            sigma_e, sigma_f, V, ldv, info, st);
+}
+
+int svd_mixed_run(bool cplx, int64_t m, int64_t n, const void *A, int64_t lda, void *U,
+                  int64_t ldu, double *sigma, double *sigma_e, double *sigma_f, void *V,
+                  int64_t ldv, char *work, jsvd_info *info, int S, int rexp, int permute,
+                  cudaStream_t st)
+{
+  if (cplx)
+    return svd_mixed_run_t<true>(m, n, (const double *)A, lda, (double *)U, ldu, sigma, sigma_e,
+                                 sigma_f, (double *)V, ldv, work, info, S, rexp, permute, st);
+  return svd_mixed_run_t<false>(m, n, (const double *)A, lda, (double *)U, ldu, sigma, sigma_e,
+                                sigma_f, (double *)V, ldv, work, info, S, rexp, permute, st);
 }
 
 }  // namespace jsvd

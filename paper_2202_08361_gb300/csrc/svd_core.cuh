@@ -23,14 +23,46 @@ namespace jsvd {
 // orders L2).
 __device__ __forceinline__ double ldg2(const double *p) { return __ldcg(p); }
 __device__ __forceinline__ void stg2(double *p, double v) { __stcg(p, v); }
+__device__ __forceinline__ float ldg2(const float *p) { return __ldcg(p); }
+__device__ __forceinline__ void stg2(float *p, float v) { __stcg(p, v); }
 
-struct MatView {
-  double *gr, *gi;   // G planes (gi == nullptr for real), column j at + j*ldg
-  double *vr, *vi;   // V planes, column j at + j*ldv
+// One rounding per operation in the column precision T.
+__device__ __forceinline__ double fma_t(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float fma_t(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double mul_t(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float mul_t(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double to_t(double x, double) { return x; }
+__device__ __forceinline__ float to_t(double x, float) { return __double2float_rn(x); }
+
+// Magnitude bits of a finite value, widened so that the order of the
+// magnitudes is the order of the integers; magbits_to_double inverts it.
+__device__ __forceinline__ unsigned long long magbits(double x)
+{
+  return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+}
+__device__ __forceinline__ unsigned long long magbits(float x)
+{
+  return (unsigned long long)((unsigned)__float_as_int(x) & 0x7FFFFFFFu);
+}
+__device__ __forceinline__ double magbits_to_double(unsigned long long b, double)
+{
+  return __longlong_as_double((long long)b);
+}
+__device__ __forceinline__ double magbits_to_double(unsigned long long b, float)
+{
+  return (double)__int_as_float((int)(unsigned)b);  // exact widening
+}
+
+// The iteration matrix G (m x n) and V (n x n) in column precision T.
+template <typename T>
+struct MatViewT {
+  T *gr, *gi;        // G planes (gi == nullptr for real), column j at + j*ldg
+  T *vr, *vi;        // V planes, column j at + j*ldv
   int m, n;          // true sizes
   int mp, np;        // rows padded to a multiple of 32 (padding rows are 0)
   int64_t ldg, ldv;
 };
+using MatView = MatViewT<double>;
 
 // The round-robin parallel ordering (section 4.1): pair l of step k among
 // nt (even) columns; pairs with q >= n are phantom pairs.
@@ -80,8 +112,13 @@ __device__ __forceinline__ double hypot_naive(double x, double y)
   return __dmul_rn(__dsqrt_rn(__fma_rn(q, q, 1.0)), M);
 }
 
+// x 2^k for the FP32 phase (never used with k != 0 there: that phase does
+// not rescale; scalbnf is exact unless the result leaves the normal range).
+__device__ __forceinline__ float ldexp_rn(float x, int k) { return scalbnf(x, k); }
+
 // Scale a column by 2^k in place (rows < mp).
-__device__ __forceinline__ void scale_col(double *x, int mp, int k, int lane)
+template <typename T>
+__device__ __forceinline__ void scale_col(T *x, int mp, int k, int lane)
 {
   for (int i = lane; i < mp; i += 32) stg2(x + i, ldexp_rn(ldg2(x + i), k));
 }
@@ -139,133 +176,158 @@ __device__ __forceinline__ PairOut pair_rotation(double spp, double sqq, double 
   return o;
 }
 
-// The fused step for pair (p, q), executed by one full warp.  rk != 0
-// downscales both columns of G by 2^rk first (section 3.2, step 2);
-// permute applies the column swap P.
-// Returns (in lane 0) whether the pair was rotated; Mloc collects the
-// magnitude bits of the transformed G entries.
-template <bool CPLX>
-__device__ __forceinline__ bool pair_step(const MatView &M, int p, int q, double ups, int rk,
+// The fused step for pair (p, q), executed by one full warp, with the
+// columns in precision T (double, or float in the FP32 phase of the mixed
+// SVD).  rk != 0 downscales both columns of G by 2^rk first (section 3.2,
+// step 2; FP64 only); permute applies the column swap P.  Mloc collects
+// magbits() of the transformed G entries (in T's encoding).  Returns
+// whether the pair was rotated (the same in every lane).
+template <typename T, bool CPLX>
+__device__ __forceinline__ bool pair_step(const MatViewT<T> &M, int p, int q, double ups, int rk,
                                           bool permute, unsigned long long &Mloc)
 {
+  // rows per lane per loop trip: their loads are all issued before the
+  // arithmetic, which then consumes them in ascending row order, so the
+  // accumulation order (and the bits) are those of the one-row loop
+  constexpr int U = (sizeof(T) == 4) ? 8 : 4;
   const int lane = threadIdx.x & 31;
-  double *gpr = M.gr + p * M.ldg, *gqr = M.gr + q * M.ldg;
-  double *gpi = CPLX ? M.gi + p * M.ldg : nullptr, *gqi = CPLX ? M.gi + q * M.ldg : nullptr;
-  double spp = 0.0, sqq = 0.0, sqr = 0.0, sqi = 0.0;
-  for (int i = lane; i < M.mp; i += 32) {
-    double xpr = ldg2(gpr + i), xqr = ldg2(gqr + i);
-    double xpi = 0.0, xqi = 0.0;
-    if (CPLX) {
-      xpi = ldg2(gpi + i);
-      xqi = ldg2(gqi + i);
-    }
-    if (rk) {
-      xpr = ldexp_rn(xpr, rk);
-      xqr = ldexp_rn(xqr, rk);
-      stg2(gpr + i, xpr);
-      stg2(gqr + i, xqr);
-      if (CPLX) {
-        xpi = ldexp_rn(xpi, rk);
-        xqi = ldexp_rn(xqi, rk);
-        stg2(gpi + i, xpi);
-        stg2(gqi + i, xqi);
+  T *gpr = M.gr + p * M.ldg, *gqr = M.gr + q * M.ldg;
+  T *gpi = CPLX ? M.gi + p * M.ldg : nullptr, *gqi = CPLX ? M.gi + q * M.ldg : nullptr;
+  T spp = T(0), sqq = T(0), sqr = T(0), sqi = T(0);
+  for (int base = lane; base < M.mp; base += 32 * U) {
+    T xpr[U], xqr[U], xpi[U], xqi[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = base + 32 * u;  // the same bound for every lane: mp is a multiple of 32
+      xpr[u] = xqr[u] = xpi[u] = xqi[u] = T(0);
+      if (i < M.mp) {
+        xpr[u] = ldg2(gpr + i);
+        xqr[u] = ldg2(gqr + i);
+        if (CPLX) {
+          xpi[u] = ldg2(gpi + i);
+          xqi[u] = ldg2(gqi + i);
+        }
       }
     }
-    spp = __fma_rn(xpr, xpr, spp);
-    sqq = __fma_rn(xqr, xqr, sqq);
-    sqr = __fma_rn(xqr, xpr, sqr);
-    if (CPLX) {
-      spp = __fma_rn(xpi, xpi, spp);
-      sqq = __fma_rn(xqi, xqi, sqq);
-      sqi = __fma_rn(xqr, xpi, sqi);
-      sqr = __fma_rn(xqi, xpi, sqr);
-      sqi = __fma_rn(-xqi, xpr, sqi);
+    if (rk) {
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int i = base + 32 * u;
+        if (i < M.mp) {
+          xpr[u] = ldexp_rn(xpr[u], rk);
+          xqr[u] = ldexp_rn(xqr[u], rk);
+          stg2(gpr + i, xpr[u]);
+          stg2(gqr + i, xqr[u]);
+          if (CPLX) {
+            xpi[u] = ldexp_rn(xpi[u], rk);
+            xqi[u] = ldexp_rn(xqi[u], rk);
+            stg2(gpi + i, xpi[u]);
+            stg2(gqi + i, xqi[u]);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (base + 32 * u < M.mp) {
+        spp = fma_t(xpr[u], xpr[u], spp);
+        sqq = fma_t(xqr[u], xqr[u], sqq);
+        sqr = fma_t(xqr[u], xpr[u], sqr);
+        if (CPLX) {
+          spp = fma_t(xpi[u], xpi[u], spp);
+          sqq = fma_t(xqi[u], xqi[u], sqq);
+          sqi = fma_t(xqr[u], xpi[u], sqi);
+          sqr = fma_t(xqi[u], xpi[u], sqr);
+          sqi = fma_t(-xqi[u], xpr[u], sqi);
+        }
+      }
     }
   }
-  spp = warp_sum(spp);
-  sqq = warp_sum(sqq);
-  sqr = warp_sum(sqr);
-  if (CPLX) sqi = warp_sum(sqi);
+  // the lane partial sums are combined, and everything after them is
+  // computed, in FP64 whatever the column precision
+  const double dpp = warp_sum((double)spp), dqq = warp_sum((double)sqq);
+  const double dqr = warp_sum((double)sqr), dqi = CPLX ? warp_sum((double)sqi) : 0.0;
   PairOut o = {};
   if (lane == 0) {
-    o = pair_rotation<CPLX>(spp, sqq, sqr, sqi, ups);
+    o = pair_rotation<CPLX>(dpp, dqq, dqr, dqi, ups);
     o.swap = o.swap && permute;
   }
   const unsigned full = 0xffffffffu;
   const int flags = __shfl_sync(full, lane == 0 ? ((o.rot ? 1 : 0) | (o.swap ? 2 : 0)) : 0, 0);
   const bool rot = flags & 1, swp = (flags >> 1) & 1;
   if (rot) {
-    const double c = __shfl_sync(full, o.c, 0), C = __shfl_sync(full, o.C, 0);
-    const double S = CPLX ? __shfl_sync(full, o.S, 0) : 0.0;
-    double *dpr = swp ? gqr : gpr, *dqr = swp ? gpr : gqr;
-    double *dpi = swp ? gqi : gpi, *dqi = swp ? gpi : gqi;
-    // Eq. e:transf on G: g_p' = fma(g_q, e', g_p) c, g_q' = fma(g_p, -conj(e'), g_q) c
-    for (int i = lane; i < M.mp; i += 32) {
-      const double pr = ldg2(gpr + i), qr = ldg2(gqr + i);
-      if (CPLX) {
-        const double pi = ldg2(gpi + i), qi = ldg2(gqi + i);
-        const double npr = __dmul_rn(__fma_rn(qr, C, __fma_rn(-qi, S, pr)), c);
-        const double npi = __dmul_rn(__fma_rn(qr, S, __fma_rn(qi, C, pi)), c);
-        const double nqr = __dmul_rn(__fma_rn(pr, -C, __fma_rn(-pi, S, qr)), c);
-        const double nqi = __dmul_rn(__fma_rn(pr, S, __fma_rn(pi, -C, qi)), c);
-        stg2(dpr + i, npr);
-        stg2(dpi + i, npi);
-        stg2(dqr + i, nqr);
-        stg2(dqi + i, nqi);
-        unsigned long long a = max(max(abits(npr), abits(npi)), max(abits(nqr), abits(nqi)));
-        Mloc = max(Mloc, a);
-      } else {
-        const double npr = __dmul_rn(__fma_rn(qr, C, pr), c);
-        const double nqr = __dmul_rn(__fma_rn(pr, -C, qr), c);
-        stg2(dpr + i, npr);
-        stg2(dqr + i, nqr);
-        Mloc = max(Mloc, max(abits(npr), abits(nqr)));
-      }
-    }
-    double *vpr = M.vr + p * M.ldv, *vqr = M.vr + q * M.ldv;
-    double *vpi = CPLX ? M.vi + p * M.ldv : nullptr, *vqi = CPLX ? M.vi + q * M.ldv : nullptr;
-    double *wpr = swp ? vqr : vpr, *wqr = swp ? vpr : vqr;
-    double *wpi = swp ? vqi : vpi, *wqi = swp ? vpi : vqi;
-    for (int i = lane; i < M.np; i += 32) {
-      const double pr = ldg2(vpr + i), qr = ldg2(vqr + i);
-      if (CPLX) {
-        const double pi = ldg2(vpi + i), qi = ldg2(vqi + i);
-        const double npr = __dmul_rn(__fma_rn(qr, C, __fma_rn(-qi, S, pr)), c);
-        const double npi = __dmul_rn(__fma_rn(qr, S, __fma_rn(qi, C, pi)), c);
-        const double nqr = __dmul_rn(__fma_rn(pr, -C, __fma_rn(-pi, S, qr)), c);
-        const double nqi = __dmul_rn(__fma_rn(pr, S, __fma_rn(pi, -C, qi)), c);
-        stg2(wpr + i, npr);
-        stg2(wpi + i, npi);
-        stg2(wqr + i, nqr);
-        stg2(wqi + i, nqi);
-      } else {
-        const double npr = __dmul_rn(__fma_rn(qr, C, pr), c);
-        const double nqr = __dmul_rn(__fma_rn(pr, -C, qr), c);
-        stg2(wpr + i, npr);
-        stg2(wqr + i, nqr);
+    const T c = to_t(__shfl_sync(full, o.c, 0), T(0)), C = to_t(__shfl_sync(full, o.C, 0), T(0));
+    const T S = CPLX ? to_t(__shfl_sync(full, o.S, 0), T(0)) : T(0);
+    // Eq. e:transf: x_p' = fma(x_q, e', x_p) c, x_q' = fma(x_p, -conj(e'), x_q) c,
+    // e' = C + iS, on the G rows (tracking the max-norm) and the V rows
+    for (int pass = 0; pass < 2; ++pass) {
+      const bool onG = (pass == 0);
+      const int rows = onG ? M.mp : M.np;
+      T *xpr = onG ? gpr : M.vr + p * M.ldv, *xqr = onG ? gqr : M.vr + q * M.ldv;
+      T *xpi = CPLX ? (onG ? gpi : M.vi + p * M.ldv) : nullptr;
+      T *xqi = CPLX ? (onG ? gqi : M.vi + q * M.ldv) : nullptr;
+      T *dpr = swp ? xqr : xpr, *dqr = swp ? xpr : xqr;
+      T *dpi = swp ? xqi : xpi, *dqi = swp ? xpi : xqi;
+      for (int base = lane; base < rows; base += 32 * U) {
+        T pr[U], qr[U], pi[U], qi[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int i = base + 32 * u;
+          pr[u] = qr[u] = pi[u] = qi[u] = T(0);
+          if (i < rows) {
+            pr[u] = ldg2(xpr + i);
+            qr[u] = ldg2(xqr + i);
+            if (CPLX) {
+              pi[u] = ldg2(xpi + i);
+              qi[u] = ldg2(xqi + i);
+            }
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int i = base + 32 * u;
+          if (i < rows) {
+            if (CPLX) {
+              const T npr = mul_t(fma_t(qr[u], C, fma_t(-qi[u], S, pr[u])), c);
+              const T npi = mul_t(fma_t(qr[u], S, fma_t(qi[u], C, pi[u])), c);
+              const T nqr = mul_t(fma_t(pr[u], -C, fma_t(-pi[u], S, qr[u])), c);
+              const T nqi = mul_t(fma_t(pr[u], S, fma_t(pi[u], -C, qi[u])), c);
+              stg2(dpr + i, npr);
+              stg2(dpi + i, npi);
+              stg2(dqr + i, nqr);
+              stg2(dqi + i, nqi);
+              if (onG) {
+                const unsigned long long a =
+                    max(max(magbits(npr), magbits(npi)), max(magbits(nqr), magbits(nqi)));
+                Mloc = max(Mloc, a);
+              }
+            } else {
+              const T npr = mul_t(fma_t(qr[u], C, pr[u]), c);
+              const T nqr = mul_t(fma_t(pr[u], -C, qr[u]), c);
+              stg2(dpr + i, npr);
+              stg2(dqr + i, nqr);
+              if (onG) Mloc = max(Mloc, max(magbits(npr), magbits(nqr)));
+            }
+          }
+        }
       }
     }
   } else if (swp) {
-    for (int i = lane; i < M.mp; i += 32) {
-      const double a = ldg2(gpr + i), b = ldg2(gqr + i);
-      stg2(gpr + i, b);
-      stg2(gqr + i, a);
-      if (CPLX) {
-        const double ai = ldg2(gpi + i), bi = ldg2(gqi + i);
-        stg2(gpi + i, bi);
-        stg2(gqi + i, ai);
-      }
-    }
-    double *vpr = M.vr + p * M.ldv, *vqr = M.vr + q * M.ldv;
-    for (int i = lane; i < M.np; i += 32) {
-      const double a = ldg2(vpr + i), b = ldg2(vqr + i);
-      stg2(vpr + i, b);
-      stg2(vqr + i, a);
-      if (CPLX) {
-        double *vpi = M.vi + p * M.ldv, *vqi = M.vi + q * M.ldv;
-        const double ai = ldg2(vpi + i), bi = ldg2(vqi + i);
-        stg2(vpi + i, bi);
-        stg2(vqi + i, ai);
+    for (int pass = 0; pass < 2; ++pass) {
+      const bool onG = (pass == 0);
+      const int rows = onG ? M.mp : M.np;
+      T *xpr = onG ? gpr : M.vr + p * M.ldv, *xqr = onG ? gqr : M.vr + q * M.ldv;
+      T *xpi = CPLX ? (onG ? gpi : M.vi + p * M.ldv) : nullptr;
+      T *xqi = CPLX ? (onG ? gqi : M.vi + q * M.ldv) : nullptr;
+      for (int i = lane; i < rows; i += 32) {
+        const T a = ldg2(xpr + i), b = ldg2(xqr + i);
+        stg2(xpr + i, b);
+        stg2(xqr + i, a);
+        if (CPLX) {
+          const T ai = ldg2(xpi + i), bi = ldg2(xqi + i);
+          stg2(xpi + i, bi);
+          stg2(xqi + i, ai);
+        }
       }
     }
   }

@@ -1,0 +1,116 @@
+"""The mixed FP32 -> FP64 SVD (jsvd_svd with JSVD_MIXED_FP32_FP64) and its
+FP64 GEMM (jsvd_dgemm, the DMMA tensor path).
+
+The mixed SVD must meet the same bounds as the FP64 one against the FP64
+oracle: ||A - U S V^H||_F/||A||_F, max|U^H U - I|, max|V^H V - I| <= 64 n eps
+and singular values within 64 n eps sigma_max."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2202_08361_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+EPS = np.finfo(np.float64).eps
+
+
+def tol(n):
+    return 64 * n * EPS
+
+
+def _torch():
+    import torch
+    return torch
+
+
+@pytest.mark.parametrize("transA", [False, True])
+@pytest.mark.parametrize("M,N,K", [(1, 1, 1), (7, 5, 3), (64, 64, 16), (65, 130, 17), (130, 65, 100),
+                                   (256, 128, 256), (33, 1, 64), (5, 9, 0)])
+def test_dgemm_against_torch(M, N, K, transA):
+    torch = _torch()
+    import paper_2202_08361_gb300 as J
+    g = torch.Generator(device="cpu").manual_seed(M * 1000 + N * 10 + K)
+    A = torch.randn((K, M) if transA else (M, K), generator=g, dtype=torch.float64).cuda()
+    B = torch.randn((K, N), generator=g, dtype=torch.float64).cuda()
+    C0 = torch.randn((M, N), generator=g, dtype=torch.float64).cuda()
+    opA = A.t() if transA else A
+    C = J.colmajor(C0.clone())[0]
+    J.dgemm(A, B, transA=transA, alpha=-0.75, beta=1.5, C=C)
+    ref = -0.75 * (opA @ B) + 1.5 * C0
+    bound = 4 * max(K, 1) * EPS * (opA.abs() @ B.abs() + C0.abs()).max().item() + 1e-300
+    assert (C - ref).abs().max().item() <= bound
+    C2 = J.dgemm(A, B, transA=transA)
+    assert (C2 - opA @ B).abs().max().item() <= bound
+
+
+def gpu_svd(A, **kw):
+    torch = _torch()
+    import paper_2202_08361_gb300 as J
+    out = J.svd(torch.from_numpy(np.asfortranarray(A)).cuda(), **kw)
+    torch.cuda.synchronize()
+    res = {k: out[k].cpu().numpy() for k in ("U", "V", "sigma", "sigma_e", "sigma_f")}
+    res["info"] = J.decode_info(out["info"])
+    return res
+
+
+def check_bounds(A, g, sigma_ref):
+    n = A.shape[1]
+    U, s, V = g["U"], g["sigma"], g["V"]
+    assert g["info"]["status"] == 0, g["info"]
+    res = np.linalg.norm(A - (U * s) @ V.conj().T) / np.linalg.norm(A)
+    assert res <= tol(n), res
+    assert np.abs(U.conj().T @ U - np.eye(n)).max() <= tol(n)
+    assert np.abs(V.conj().T @ V - np.eye(n)).max() <= tol(n)
+    assert np.abs(s - sigma_ref).max() <= tol(n) * sigma_ref[0]
+    assert np.all(np.diff(s) <= 0)
+
+
+@pytest.mark.parametrize("m,n", [(256, 128), (100, 64), (64, 63), (9, 2), (1, 1)])
+def test_mixed_real_against_oracle(m, n):
+    if (m, n) == (256, 128):
+        A = workloads.svd_normal(256, 128)
+    else:
+        A, _ = workloads.svd_geometric(m, n, 1e4, False, np.random.default_rng(m * 31 + n))
+    g = gpu_svd(A, mode="mixed")
+    check_bounds(A, g, oracle.vjsvd(A)["sigma"])
+    if n > 1:
+        assert g["info"]["sweeps_fp32"] > 0
+
+
+@pytest.mark.parametrize("m,n,cond", [(512, 256, 1e6), (65, 33, 1e3), (40, 40, 1e6)])
+def test_mixed_complex_against_oracle(m, n, cond):
+    A, s = workloads.svd_geometric(m, n, cond, True, np.random.default_rng(m * 13 + n))
+    g = gpu_svd(A, mode="mixed")
+    check_bounds(A, g, oracle.vjsvd(A)["sigma"])
+    assert np.abs(g["sigma"] - s).max() <= tol(n) * s[0]
+
+
+def test_mixed_full_size_complex_4096x2048():
+    """The complex 4096 x 2048 workload in mixed mode: the same bounds as the
+    FP64 path, checked with torch matmuls on the GPU."""
+    torch = _torch()
+    import paper_2202_08361_gb300 as J
+    A, s = workloads.svd_complex_geometric()
+    At = torch.from_numpy(A).cuda()
+    out = J.svd(At, mode="mixed")
+    info = J.decode_info(out["info"])
+    assert info["status"] == 0, info
+    n = A.shape[1]
+    U, V, sg = out["U"], out["V"], out["sigma"]
+    I = torch.eye(n, dtype=torch.complex128, device="cuda")
+    res = torch.linalg.norm(At - (U * sg) @ V.conj().T) / torch.linalg.norm(At)
+    assert res.item() <= tol(n)
+    assert (U.conj().T @ U - I).abs().max().item() <= tol(n)
+    assert (V.conj().T @ V - I).abs().max().item() <= tol(n)
+    assert np.abs(sg.cpu().numpy() - s).max() <= tol(n) * s[0]
+
+
+def test_mixed_nonfinite_and_zero():
+    import paper_2202_08361_gb300 as J
+    A = workloads.svd_normal(8, 4, seed_salt=5)
+    A[2, 2] = np.nan
+    g = gpu_svd(A, mode="mixed")
+    assert g["info"]["status"] == J.JSVD_E_NONFINITE
+    g = gpu_svd(np.zeros((6, 3)), mode="mixed")
+    assert g["info"]["status"] == 0 and np.all(g["sigma"] == 0)
