@@ -66,8 +66,13 @@ JSVD_API const char *jsvd_last_cuda_error(void);
  *     (64, 128 or 256), value2 = resident blocks per SM (1..64). */
 #define JSVD_TUNE_EVD_LAUNCH 1
 /*   JSVD_TUNE_SVD_GRID: value = most blocks of the persistent SVD sweep
- *     kernel (0 = as many as the pairs of a step, capped by residency). */
+ *     kernel (0 = as many as the pair chunks of a step, capped by
+ *     residency); value2 = warps per block (1, 2, 4 or 8; 0 = chosen from
+ *     the number of pairs and SMs). */
 #define JSVD_TUNE_SVD_GRID 2
+/*   JSVD_TUNE_BATCH_WARPS: value = warps per block of the batched SVD
+ *     kernel (1, 2, 4, 8 or 16; default 8). */
+#define JSVD_TUNE_BATCH_WARPS 3
 JSVD_API int jsvd_tune_set(int knob, int value, int value2);
 
 /* ------------------------------------------------------------------------
@@ -179,6 +184,68 @@ JSVD_API int jsvd_svd(jsvd_field field, const jsvd_opts *opts, int64_t m, int64_
                       const void *A, int64_t lda, void *U, int64_t ldu, double *sigma,
                       double *sigma_e, double *sigma_f, void *V, int64_t ldv, void *work,
                       size_t work_bytes, jsvd_info *info, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Batched SVD of many matrices of uneven sizes: the same computation as
+ * jsvd_svd for each matrix (bit for bit), in one persistent launch whose
+ * blocks take whole matrices from a queue ordered longest first.  The
+ * descriptor arrays (m, n, A, lda, U, ldu, sigma, sigma_e, sigma_f, V, ldv;
+ * count entries each) are HOST arrays; the matrices they point to are
+ * device memory, laid out as for jsvd_svd.  sigma_e and sigma_f may be
+ * NULL (not wanted).  info is a DEVICE array of count jsvd_info (may be
+ * NULL).  opts->mode must be JSVD_FP64.
+ *
+ * jsvd_svd_batched = jsvd_svd_batched_prepare + jsvd_svd_batched_launch.
+ * prepare copies the descriptors into work (it returns after the copy is
+ * done, so the host arrays may then be reused); launch only enqueues device
+ * work (a memset and one kernel) and may be repeated on the same prepared
+ * workspace, e.g. as a captured CUDA graph.
+ * Errors: -i for argument i (-4 also for an invalid m[i] or n[i], -6 for
+ * an invalid A[i]/lda[i], -8 U[i]/ldu[i], -10 sigma[i], -13 V[i]/ldv[i]),
+ * JSVD_E_WORKSPACE, JSVD_E_CUDA. */
+JSVD_API int jsvd_svd_batched_workspace_size(jsvd_field field, const jsvd_opts *opts,
+                                             int64_t count, const int64_t *m, const int64_t *n,
+                                             size_t *bytes);
+JSVD_API int jsvd_svd_batched_prepare(jsvd_field field, const jsvd_opts *opts, int64_t count,
+                                      const int64_t *m, const int64_t *n, const void *const *A,
+                                      const int64_t *lda, void *const *U, const int64_t *ldu,
+                                      double *const *sigma, double *const *sigma_e,
+                                      double *const *sigma_f, void *const *V, const int64_t *ldv,
+                                      void *work, size_t work_bytes, void *stream);
+JSVD_API int jsvd_svd_batched_launch(jsvd_field field, const jsvd_opts *opts, int64_t count,
+                                     void *work, jsvd_info *info, void *stream);
+JSVD_API int jsvd_svd_batched(jsvd_field field, const jsvd_opts *opts, int64_t count,
+                              const int64_t *m, const int64_t *n, const void *const *A,
+                              const int64_t *lda, void *const *U, const int64_t *ldu,
+                              double *const *sigma, double *const *sigma_e, double *const *sigma_f,
+                              void *const *V, const int64_t *ldv, void *work, size_t work_bytes,
+                              jsvd_info *info, void *stream);
+
+/* ------------------------------------------------------------------------
+ * The SVD adjoint (not in the paper; the differentiated form of the SVD):
+ * for count real matrices A_b = U_b diag(s_b) V_b^T (m x n, m >= n, distinct
+ * singular values) and cotangents Ubar_b, sbar_b, Vbar_b, computes
+ *   Abar = U [(F o (U^T Ubar - Ubar^T U)) S + diag(sbar)
+ *             + S (F o (V^T Vbar - Vbar^T V))] V^T + (I - U U^T) Ubar S^-1 V^T,
+ *   F_ij = 1/(s_j^2 - s_i^2) (i != j), 0 on the diagonal
+ * (Townsend 2016).  All arrays are DEVICE memory, packed: matrix b of U,
+ * Ubar, Abar (m x n, column-major, ld = m) at b m n, of V, Vbar (n x n) at
+ * b n n, of s, sbar at b n.  Ubar, sbar, Vbar may be NULL (zero).  One
+ * block per matrix with its operands in shared memory: needs
+ * 8 (3 m n + 4 n n) <= 200 KiB (else JSVD_E_UNSUPPORTED).
+ * Errors: -i for argument i, JSVD_E_UNSUPPORTED, JSVD_E_CUDA. */
+JSVD_API int jsvd_svd_adjoint_batched(int64_t count, int64_t m, int64_t n, const double *U,
+                                      const double *s, const double *V, const double *Ubar,
+                                      const double *sbar, const double *Vbar, double *Abar,
+                                      void *stream);
+
+/* Sign gauge of real singular vectors: flips each pair (u_j, v_j) of the
+ * count packed matrices (layout as above) so that the entry of largest
+ * magnitude of u_j is positive (the first such entry on ties).  Makes U and
+ * V functions of A wherever the singular values are distinct, as a
+ * differentiated loss on U needs.  Errors: -i for argument i, JSVD_E_CUDA. */
+JSVD_API int jsvd_sign_gauge_batched(int64_t count, int64_t m, int64_t n, double *U, double *V,
+                                     void *stream);
 
 /* jsvd_svd for callers that cannot allocate device memory at run time --
  * for instance code inside a framework whose caching allocator already holds

@@ -9,11 +9,13 @@ import ctypes
 from . import _native
 from ._native import (JSVD_COMPLEX, JSVD_E_CUDA, JSVD_E_NONFINITE, JSVD_E_TIMEOUT,
                       JSVD_E_UNSUPPORTED, JSVD_E_WORKSPACE, JSVD_FP64, JSVD_MIXED_FP32_FP64,
-                      JSVD_NOT_CONVERGED, JSVD_OK, JSVD_REAL, JSVD_TUNE_EVD_LAUNCH,
-                      JSVD_TUNE_SVD_GRID, JsvdError)
+                      JSVD_NOT_CONVERGED, JSVD_OK, JSVD_REAL, JSVD_TUNE_BATCH_WARPS,
+                      JSVD_TUNE_EVD_LAUNCH, JSVD_TUNE_SVD_GRID, JsvdError)
 
 __all__ = ["evd2x2_batched", "svd", "svd_workspace_size", "ordering", "decode_info", "dgemm",
-           "version", "tune_set", "JsvdError", "JSVD_REAL", "JSVD_COMPLEX"]
+           "BatchedSVD", "pack_matrices", "svd_batched", "svd_adjoint_batched",
+           "sign_gauge_batched", "svd_diff", "version", "tune_set", "JsvdError", "JSVD_REAL",
+           "JSVD_COMPLEX"]
 
 
 def _torch():
@@ -217,3 +219,187 @@ def dgemm(A, B, *, transA=False, alpha=1.0, beta=0.0, C=None, stream=None):
                                   _stream_handle(stream))
     _native.check(rc, "jsvd_dgemm")
     return C
+
+
+# ---------------------------------------------------------------------------
+# batched SVD over packed buffers
+
+class BatchedSVD:
+    """A prepared jsvd_svd_batched over packed device buffers.
+
+    A is a 1-D CUDA tensor (float64 or complex128) holding the matrices back
+    to back, matrix i column-major with lda = m[i] at element offset
+    sum_{j<i} m[j] n[j].  Results: U (packed like A), V (matrix i, n[i] x
+    n[i], at sum_{j<i} n[j]^2), sigma (sum_{j<i} n[j]), sigma_e, sigma_f,
+    info (count * 24 bytes).  The constructor runs jsvd_svd_batched_prepare;
+    launch() enqueues the computation (it may be captured in a CUDA graph and
+    replayed)."""
+
+    def __init__(self, A, m, n, *, max_sweeps=0, permute=False, want_ef=True):
+        import numpy as np
+        torch = _torch()
+        self.m = np.asarray(m, dtype=np.int64)
+        self.n = np.asarray(n, dtype=np.int64)
+        self.count = int(self.m.size)
+        self.cplx = A.dtype == torch.complex128
+        if not self.cplx and A.dtype != torch.float64:
+            raise TypeError("A must be float64 or complex128")
+        if not A.is_cuda or A.dim() != 1 or not A.is_contiguous():
+            raise ValueError("A must be a contiguous 1-D CUDA tensor")
+        mn = self.m * self.n
+        self.offA = np.concatenate([[0], np.cumsum(mn)[:-1]]) if self.count else np.zeros(0, np.int64)
+        self.offV = (np.concatenate([[0], np.cumsum(self.n * self.n)[:-1]]) if self.count
+                     else np.zeros(0, np.int64))
+        self.offS = np.concatenate([[0], np.cumsum(self.n)[:-1]]) if self.count else np.zeros(0, np.int64)
+        if A.numel() < int(mn.sum()):
+            raise ValueError("A is smaller than the packed matrices")
+        dev = A.device
+        self.A = A
+        self.U = torch.empty_like(A)
+        self.V = torch.empty(int((self.n * self.n).sum()), dtype=A.dtype, device=dev)
+        ns = int(self.n.sum())
+        self.sigma = torch.empty(ns, dtype=torch.float64, device=dev)
+        self.sigma_e = torch.empty(ns, dtype=torch.float64, device=dev) if want_ef else None
+        self.sigma_f = torch.empty(ns, dtype=torch.float64, device=dev) if want_ef else None
+        self.info = torch.zeros(max(self.count, 1) * _native.INFO_BYTES, dtype=torch.uint8, device=dev)
+        self.opts = _opts(max_sweeps, JSVD_FP64, 0, permute)
+        es = 16 if self.cplx else 8
+        cnt = self.count
+        P = ctypes.c_void_p * max(cnt, 1)
+        I64 = ctypes.c_int64 * max(cnt, 1)
+        ptrs = lambda base, off, sz: P(*[base + int(o) * sz for o in off])
+        self._m = I64(*self.m.tolist())
+        self._n = I64(*self.n.tolist())
+        self._A = ptrs(A.data_ptr(), self.offA, es)
+        self._U = ptrs(self.U.data_ptr(), self.offA, es)
+        self._V = ptrs(self.V.data_ptr(), self.offV, es)
+        self._s = ptrs(self.sigma.data_ptr(), self.offS, 8)
+        self._se = ptrs(self.sigma_e.data_ptr(), self.offS, 8) if want_ef else None
+        self._sf = ptrs(self.sigma_f.data_ptr(), self.offS, 8) if want_ef else None
+        self._lda = I64(*self.m.tolist())
+        self._ldv = I64(*self.n.tolist())
+        sz = ctypes.c_size_t(0)
+        field = JSVD_COMPLEX if self.cplx else JSVD_REAL
+        self.field = field
+        L = _native.lib()
+        _native.check(L.jsvd_svd_batched_workspace_size(field, ctypes.byref(self.opts), cnt,
+                                                        self._m, self._n, ctypes.byref(sz)),
+                      "jsvd_svd_batched_workspace_size")
+        self.work = torch.empty(max(sz.value, 256), dtype=torch.uint8, device=dev)
+        _native.check(L.jsvd_svd_batched_prepare(
+            field, ctypes.byref(self.opts), cnt, self._m, self._n, self._A, self._lda, self._U,
+            self._lda, self._s, self._se, self._sf, self._V, self._ldv, self.work.data_ptr(),
+            self.work.numel(), _stream_handle(None)), "jsvd_svd_batched_prepare")
+
+    def launch(self, stream=None):
+        rc = _native.lib().jsvd_svd_batched_launch(self.field, ctypes.byref(self.opts), self.count,
+                                                   self.work.data_ptr(), self.info.data_ptr(),
+                                                   _stream_handle(stream))
+        _native.check(rc, "jsvd_svd_batched_launch")
+        return self
+
+    def matrix(self, i):
+        """(U_i, sigma_i, V_i) views of matrix i's results (column-major)."""
+        m, n = int(self.m[i]), int(self.n[i])
+        a, v, s = int(self.offA[i]), int(self.offV[i]), int(self.offS[i])
+        U = self.U[a:a + m * n].view(n, m).t()
+        V = self.V[v:v + n * n].view(n, n).t()
+        return U, self.sigma[s:s + n], V
+
+
+def pack_matrices(mats, device="cuda"):
+    """Pack a list of 2-D arrays/tensors (m_i x n_i) column-major into one
+    1-D CUDA tensor; returns (A, m, n)."""
+    import numpy as np
+    torch = _torch()
+    ts = [torch.as_tensor(x) for x in mats]
+    dtype = torch.complex128 if any(t.is_complex() for t in ts) else torch.float64
+    m = np.array([t.shape[0] for t in ts], dtype=np.int64)
+    n = np.array([t.shape[1] for t in ts], dtype=np.int64)
+    flat = torch.cat([t.to(dtype).t().contiguous().reshape(-1) for t in ts]) if ts else \
+        torch.empty(0, dtype=dtype)
+    return flat.to(device), m, n
+
+
+def svd_batched(mats, *, max_sweeps=0, permute=False, stream=None):
+    """Batched SVD of a list of matrices (jsvd_svd_batched): returns the
+    BatchedSVD after launching it."""
+    A, m, n = pack_matrices(mats)
+    return BatchedSVD(A, m, n, max_sweeps=max_sweeps, permute=permute).launch(stream)
+
+
+# ---------------------------------------------------------------------------
+# differentiated batched SVD
+
+def _packed_cm(t):
+    """(count, r, c) tensor -> 1-D float64 CUDA tensor of the column-major
+    matrices back to back."""
+    return t.transpose(1, 2).contiguous().reshape(-1)
+
+
+def sign_gauge_batched(U, V, count, m, n, stream=None):
+    """In place on packed column-major U (count m n) and V (count n n):
+    jsvd_sign_gauge_batched."""
+    _native.check(_native.lib().jsvd_sign_gauge_batched(count, m, n, U.data_ptr(), V.data_ptr(),
+                                                        _stream_handle(stream)),
+                  "jsvd_sign_gauge_batched")
+
+
+def svd_adjoint_batched(U, s, V, Ubar=None, sbar=None, Vbar=None, stream=None):
+    """Abar for count real SVDs (jsvd_svd_adjoint_batched).  U, Ubar:
+    (count, m, n); s, sbar: (count, n); V, Vbar: (count, n, n); float64 CUDA
+    tensors.  Returns Abar (count, m, n)."""
+    torch = _torch()
+    count, m, n = U.shape
+    Uc, Vc = _packed_cm(U), _packed_cm(V)
+    sc = s.contiguous()
+    Ubc = _packed_cm(Ubar) if Ubar is not None else None
+    Vbc = _packed_cm(Vbar) if Vbar is not None else None
+    sbc = sbar.contiguous() if sbar is not None else None
+    Ab = torch.empty(count * m * n, dtype=torch.float64, device=U.device)
+    p = lambda t: t.data_ptr() if t is not None else None
+    rc = _native.lib().jsvd_svd_adjoint_batched(count, m, n, p(Uc), p(sc), p(Vc), p(Ubc), p(sbc),
+                                                p(Vbc), Ab.data_ptr(), _stream_handle(stream))
+    _native.check(rc, "jsvd_svd_adjoint_batched")
+    return Ab.view(count, n, m).transpose(1, 2)
+
+
+def _diff_svd_class():
+    torch = _torch()
+
+    class DifferentiableSVD(torch.autograd.Function):
+        """Batched real SVD with a hand-written adjoint: forward is
+        jsvd_svd_batched followed by the sign gauge, backward is
+        jsvd_svd_adjoint_batched."""
+
+        @staticmethod
+        def forward(ctx, A):
+            count, m, n = A.shape
+            flat = _packed_cm(A.detach().to(torch.float64))
+            B = BatchedSVD(flat, [m] * count, [n] * count, want_ef=False).launch()
+            sign_gauge_batched(B.U, B.V, count, m, n)
+            U = B.U.view(count, n, m).transpose(1, 2)
+            S = B.sigma.view(count, n)
+            V = B.V.view(count, n, n).transpose(1, 2)
+            ctx.save_for_backward(U, S, V)
+            ctx.batch = B
+            return U, S, V
+
+        @staticmethod
+        def backward(ctx, gU, gS, gV):
+            U, S, V = ctx.saved_tensors
+            return svd_adjoint_batched(U, S, V, gU, gS, gV)
+
+    return DifferentiableSVD
+
+
+_DIFF = None
+
+
+def svd_diff(A):
+    """(U, S, V) of a (count, m, n) float64 CUDA tensor, differentiable
+    through the hand-written adjoint kernel."""
+    global _DIFF
+    if _DIFF is None:
+        _DIFF = _diff_svd_class()
+    return _DIFF.apply(A)

@@ -22,6 +22,7 @@ JSVD_COMPLEX = 1
 
 JSVD_TUNE_EVD_LAUNCH = 1
 JSVD_TUNE_SVD_GRID = 2
+JSVD_TUNE_BATCH_WARPS = 3
 
 JSVD_FP64 = 0
 JSVD_MIXED_FP32_FP64 = 1
@@ -92,6 +93,23 @@ def lib():
         L.jsvd_dgemm.argtypes = [ctypes.c_int, _i64, _i64, _i64, ctypes.c_double, _vp, _i64, _vp,
                                  _i64, ctypes.c_double, _vp, _i64, _vp]
         L.jsvd_dgemm.restype = ctypes.c_int
+        _pi64 = ctypes.POINTER(ctypes.c_int64)
+        _pvp = ctypes.POINTER(ctypes.c_void_p)
+        L.jsvd_svd_batched_workspace_size.argtypes = [ctypes.c_int, ctypes.POINTER(Opts), _i64,
+                                                      _pi64, _pi64, ctypes.POINTER(_sz)]
+        L.jsvd_svd_batched_workspace_size.restype = ctypes.c_int
+        L.jsvd_svd_batched_prepare.argtypes = [ctypes.c_int, ctypes.POINTER(Opts), _i64, _pi64,
+                                               _pi64, _pvp, _pi64, _pvp, _pi64, _pvp, _pvp, _pvp,
+                                               _pvp, _pi64, _vp, _sz, _vp]
+        L.jsvd_svd_batched_prepare.restype = ctypes.c_int
+        L.jsvd_svd_batched_launch.argtypes = [ctypes.c_int, ctypes.POINTER(Opts), _i64, _vp, _vp,
+                                              _vp]
+        L.jsvd_svd_batched_launch.restype = ctypes.c_int
+        L.jsvd_svd_adjoint_batched.argtypes = [_i64, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
+                                               _vp]
+        L.jsvd_svd_adjoint_batched.restype = ctypes.c_int
+        L.jsvd_sign_gauge_batched.argtypes = [_i64, _i64, _i64, _vp, _vp, _vp]
+        L.jsvd_sign_gauge_batched.restype = ctypes.c_int
         L.jsvd_ordering.argtypes = [ctypes.c_int32, _vp, _vp]
         L.jsvd_ordering.restype = ctypes.c_int
         _lib = L

@@ -4,7 +4,8 @@
 
 namespace jsvd {
 int evd2_set_launch(int block, int blocks_per_sm);
-int svd_set_grid(int cap);
+int svd_set_grid(int cap, int warps);
+int batch_set_warps(int w);
 }  // namespace jsvd
 
 #include <cuda_runtime.h>

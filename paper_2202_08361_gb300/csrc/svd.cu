@@ -136,19 +136,23 @@ __global__ void init_kernel(const double *__restrict__ A, int64_t lda, MatView M
   }
 }
 
-// All sweeps of Alg. zvjsvd; blockDim = 32 (one warp per block), warps
-// stride over the nt/2 pairs of every step.  T is the precision of the
-// columns (double; float in the FP32 phase of the mixed SVD).
+// All sweeps of Alg. zvjsvd in one cooperative launch.  Each block of W
+// warps takes chunks of W pivot pairs of a step (one pair per warp; the
+// chunk's 2x2 EVDs run one per lane), blocks stride over the nt/2 pairs,
+// and a bounded grid barrier separates the steps.  T is the precision of
+// the columns (double; float in the FP32 phase of the mixed SVD).
 template <typename T, bool CPLX>
-__global__ void __launch_bounds__(32) sweeps_kernel(MatViewT<T> M, SvdState *st, double ups,
-                                                    int max_sweeps, int rescale_exp, int permute)
+__global__ void __launch_bounds__(256) sweeps_kernel(MatViewT<T> M, SvdState *st, double ups,
+                                                     int max_sweeps, int rescale_exp, int permute)
 {
+  __shared__ PairSums s_sums[32];
+  __shared__ PairOut s_out[32];
   if (st->nonfinite) return;
   const int nt = M.n + (M.n & 1);
   const int K = nt - 1, L = nt / 2;
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, W = blockDim.x >> 5;
   if (K < 1) {
-    if (blockIdx.x == 0 && lane == 0) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
       st->sweeps = 1;
       st->converged = 1;
     }
@@ -163,7 +167,7 @@ __global__ void __launch_bounds__(32) sweeps_kernel(MatViewT<T> M, SvdState *st,
       const double Mcur = dbl(((volatile unsigned long long *)st->Mbuf)[cur]);
       // section 3.2, step 2: rescale when M~ has grown past 2^rescale_exp
       const int rk = (bits(Mcur) != 0ull && flg(Mcur) >= rescale_exp) ? -flg(Mcur) : 0;
-      if (blockIdx.x == 0 && lane == 0) {
+      if (blockIdx.x == 0 && threadIdx.x == 0) {
         st->Mbuf[old] = 0ull;
         atomicMax(&st->Mbuf[nxt], bits(rk ? ldexp_rn(Mcur, rk) : Mcur));
         if (rk) {
@@ -173,18 +177,8 @@ __global__ void __launch_bounds__(32) sweeps_kernel(MatViewT<T> M, SvdState *st,
       }
       unsigned long long Mloc = 0ull;
       int rots = 0;
-      for (int l = blockIdx.x; l < L; l += gridDim.x) {
-        int p, q;
-        pair_of(k, l, nt, p, q);
-        if (q >= M.n) {  // phantom partner: only a pending rescale applies
-          if (rk) {
-            scale_col(M.gr + p * M.ldg, M.mp, rk, lane);
-            if (CPLX) scale_col(M.gi + p * M.ldg, M.mp, rk, lane);
-          }
-          continue;
-        }
-        rots += pair_step<T, CPLX>(M, p, q, ups, rk, permute != 0, Mloc) ? 1 : 0;
-      }
+      for (int base = blockIdx.x * W; base < L; base += gridDim.x * W)
+        step_chunk<T, CPLX>(M, k, nt, base, W, ups, rk, permute != 0, s_sums, s_out, Mloc, rots);
       Mloc = warp_umax(Mloc);
       if (lane == 0) {
         if (Mloc) atomicMax(&st->Mbuf[nxt], bits(magbits_to_double(Mloc, T(0))));
@@ -194,7 +188,7 @@ __global__ void __launch_bounds__(32) sweeps_kernel(MatViewT<T> M, SvdState *st,
     }
     converged = (((volatile int *)st->T)[sweep] == 0);
   }
-  if (blockIdx.x == 0 && lane == 0) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
     st->sweeps = sweep;
     st->converged = converged ? 1 : 0;
   }
@@ -207,50 +201,15 @@ __global__ void colnorm_kernel(MatView M, int *e_out, double *f_out)
   const int lane = threadIdx.x & 31;
   const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int W = (gridDim.x * blockDim.x) >> 5;
-  for (int j = w; j < M.n; j += W) {
-    const double *xr = M.gr + j * M.ldg, *xi = CPLX ? M.gi + j * M.ldg : nullptr;
-    double s = 0.0;
-    for (int i = lane; i < M.mp; i += 32) {
-      s = __fma_rn(xr[i], xr[i], s);
-      if (CPLX) s = __fma_rn(xi[i], xi[i], s);
-    }
-    s = warp_sum(s);
-    if (lane == 0) {
-      if (bits(s) == 0ull) {
-        e_out[j] = INT_MIN;
-        f_out[j] = 1.0;
-      } else {
-        const double r = __dsqrt_rn(s);
-        const int e = flg(r);
-        e_out[j] = e;
-        f_out[j] = ldexp_rn(r, -e);
-      }
-    }
-  }
-}
-
-__device__ __forceinline__ bool ef_less(int ea, double fa, int eb, double fb)
-{
-  return (ea != eb) ? (ea < eb) : (bits(fa) < bits(fb));
+  for (int j = w; j < M.n; j += W) colnorm_warp<CPLX>(M, j, lane, e_out, f_out);
 }
 
 // rank_j = #{i : sigma_i > sigma_j, or sigma_i == sigma_j and i < j}
 __global__ void rank_kernel(int n, const int *e, const double *f, int *rank, SvdState *st,
                             jsvd_info *info, const SvdState *st32)
 {
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
-    int r = 0;
-    const int ej = e[j];
-    const double fj = f[j];
-    for (int i = 0; i < n; ++i) {
-      const int ei = e[i];
-      const double fi = f[i];
-      const bool gt = ef_less(ej, fj, ei, fi);
-      const bool eq = (ei == ej) && (bits(fi) == bits(fj));
-      r += (gt || (eq && i < j)) ? 1 : 0;
-    }
-    rank[j] = r;
-  }
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
+    rank[j] = rank_of(n, e, f, j);
   if (info && blockIdx.x == 0 && threadIdx.x == 0) {
     jsvd_info out;
     long long rot = 0;
@@ -282,55 +241,28 @@ __global__ void output_kernel(MatView M, const int *e, const double *f, const in
 {
   const int s = st->s;
   const bool bad = st->nonfinite != 0;
-  const double nan = __longlong_as_double(0x7FF8000000000000ll);
   for (int j = blockIdx.y; j < M.n; j += gridDim.y) {
     const int r = rank[j];
     const int ej = e[j];
     const double fj = f[j];
-    const bool zero = (ej == INT_MIN);
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-      if (sigma) sigma[r] = bad ? nan : zero ? 0.0 : ldexp_rn(fj, ej - s);
-      if (sigma_e) sigma_e[r] = bad ? nan : zero ? -__longlong_as_double((long long)kInf) : (double)(ej - s);
-      if (sigma_f) sigma_f[r] = bad ? nan : fj;
-    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) output_sigma(r, ej, fj, s, bad, sigma, sigma_e, sigma_f);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < max(M.m, M.n);
-         i += gridDim.x * blockDim.x) {
-      if (i < M.m) {
-        double ur = 0.0, ui = 0.0;
-        if (bad) {
-          ur = ui = nan;
-        } else if (!zero) {
-          ur = __ddiv_rn(ldexp_rn(M.gr[j * M.ldg + i], -ej), fj);
-          if (CPLX) ui = __ddiv_rn(ldexp_rn(M.gi[j * M.ldg + i], -ej), fj);
-        }
-        if (CPLX) {
-          U[2 * (r * ldu + i)] = ur;
-          U[2 * (r * ldu + i) + 1] = ui;
-        } else {
-          U[r * ldu + i] = ur;
-        }
-      }
-      if (i < M.n) {
-        const double vr = bad ? nan : M.vr[j * M.ldv + i];
-        if (CPLX) {
-          V[2 * (r * ldv + i)] = vr;
-          V[2 * (r * ldv + i) + 1] = bad ? nan : M.vi[j * M.ldv + i];
-        } else {
-          V[r * ldv + i] = vr;
-        }
-      }
-    }
+         i += gridDim.x * blockDim.x)
+      output_elem<CPLX>(M, i, j, r, ej, fj, bad, U, ldu, V, ldv);
   }
 }
 
 // ---------------------------------------------------------------------------
 
 static int g_svd_grid_cap = 0;
+static int g_svd_warps = 0;
 
-int svd_set_grid(int cap)
+int svd_set_grid(int cap, int warps)
 {
   if (cap < 0 || cap > (1 << 20)) return -2;
+  if (warps != 0 && warps != 1 && warps != 2 && warps != 4 && warps != 8) return -3;
   g_svd_grid_cap = cap;
+  g_svd_warps = warps;
   return JSVD_OK;
 }
 
@@ -498,10 +430,18 @@ static int phase_sweeps(const MatViewT<T> &M, SvdState *state, double ups, int S
 {
   const int nt = M.n + (M.n & 1);
   const int Lp = nt / 2;
+  const int sms = sm_count();
+  // warps per block: the most (up to 8) that still leave a chunk of pairs
+  // for every SM, so the step's pairs spread over the whole GPU
+  int W = g_svd_warps;
+  if (W == 0) {
+    W = 1;
+    while (W < 8 && (Lp + 2 * W - 1) / (2 * W) >= sms) W *= 2;
+  }
   int per_sm = 0;
-  JSVD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweeps_kernel<T, CPLX>, 32, 0));
+  JSVD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweeps_kernel<T, CPLX>, 32 * W, 0));
   if (per_sm < 1) return JSVD_E_UNSUPPORTED;
-  int grid = std::min(Lp, per_sm * sm_count());
+  int grid = std::min((Lp + W - 1) / W, per_sm * sms);
   if (g_svd_grid_cap > 0) grid = std::min(grid, g_svd_grid_cap);
   if (grid < 1) grid = 1;
   MatViewT<T> Mk = M;
@@ -509,8 +449,8 @@ static int phase_sweeps(const MatViewT<T> &M, SvdState *state, double ups, int S
   int Sk = S, rk = rexp, pk = permute;
   double upsk = ups;
   void *args[] = {&Mk, &sk, &upsk, &Sk, &rk, &pk};
-  JSVD_CUDA(cudaLaunchCooperativeKernel((const void *)sweeps_kernel<T, CPLX>, dim3(grid), dim3(32),
-                                        args, 0, st));
+  JSVD_CUDA(cudaLaunchCooperativeKernel((const void *)sweeps_kernel<T, CPLX>, dim3(grid),
+                                        dim3(32 * W), args, 0, st));
   return JSVD_OK;
 }
 

@@ -1,0 +1,386 @@
+// svd_batched.cu -- jsvd_svd_batched: one-sided Jacobi SVDs of many matrices
+// of uneven sizes in one persistent launch.
+//
+// Each block takes whole matrices from an atomic queue ordered longest
+// first (by m n^2, the cost of a sweep) and runs every phase of the SVD on
+// one matrix: the max-norm and scaling of A, all sweeps (one warp per pivot
+// pair, __syncthreads between steps, no grid barrier), the final norms,
+// the sort and the output.  The arithmetic is that of jsvd_svd (the same
+// pair step, the same max-norm and rescaling sequence, the same
+// finalisation functions), so a matrix gives the same bits alone through
+// jsvd_svd, in any batch, in any position and with any block shape.
+#include <algorithm>
+#include <climits>
+#include <vector>
+
+#include "common.cuh"
+#include "jsvd_internal.h"
+#include "svd_core.cuh"
+
+namespace jsvd {
+
+struct BatchDesc {
+  const double *A;
+  double *U, *V, *sigma, *sigma_e, *sigma_f;
+  int64_t lda, ldu, ldv;
+  int64_t off;  // byte offset of the matrix's region in the workspace
+  int m, n, mp, np;
+};
+
+struct BatchHdr {
+  int next;   // queue position
+  int count;
+  int fp32;   // reserved
+  int err;
+};
+
+struct BatchLayout {
+  size_t hdr, desc, order, regions, total;
+};
+
+__host__ __device__ __forceinline__ size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// bytes of one matrix's region: G planes, V planes, e, f, rank
+static size_t region_bytes(bool cplx, int64_t m, int64_t n)
+{
+  const int64_t mp = (m + 31) / 32 * 32, np = (n + 31) / 32 * 32;
+  const int pl = cplx ? 2 : 1;
+  size_t o = 0;
+  o = al256(o + sizeof(double) * (size_t)(mp * n) * pl);
+  o = al256(o + sizeof(double) * (size_t)(np * n) * pl);
+  o = al256(o + sizeof(int) * (size_t)n);
+  o = al256(o + sizeof(double) * (size_t)n);
+  o = al256(o + sizeof(int) * (size_t)n);
+  return o;
+}
+
+static BatchLayout batch_layout(int64_t count)
+{
+  BatchLayout L;
+  size_t o = 0;
+  L.hdr = o;
+  o = al256(o + sizeof(BatchHdr));
+  L.desc = o;
+  o = al256(o + sizeof(BatchDesc) * (size_t)count);
+  L.order = o;
+  o = al256(o + sizeof(int) * (size_t)count);
+  L.regions = o;
+  L.total = o;
+  return L;
+}
+
+static int g_batch_warps = 8;
+
+int batch_set_warps(int w)
+{
+  if (w != 1 && w != 2 && w != 4 && w != 8 && w != 16) return -2;
+  g_batch_warps = w;
+  return JSVD_OK;
+}
+
+template <bool CPLX>
+__global__ void __launch_bounds__(512) batched_kernel(const BatchDesc *__restrict__ desc,
+                                                       const int *__restrict__ order,
+                                                       BatchHdr *hdr, char *work, jsvd_info *info,
+                                                       int S, int rexp, int permute)
+{
+  __shared__ int s_idx;
+  __shared__ unsigned long long s_M0;
+  __shared__ unsigned long long s_M[3];
+  __shared__ int s_T;
+  __shared__ int s_s;
+  __shared__ int s_rescales;
+  __shared__ PairSums s_sums[32];
+  __shared__ PairOut s_out[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
+  const int count = hdr->count;
+  for (;;) {
+    if (threadIdx.x == 0) s_idx = atomicAdd(&hdr->next, 1);
+    __syncthreads();
+    const int t = s_idx;
+    if (t >= count) break;
+    const int idx = order[t];
+    const BatchDesc d = desc[idx];
+    MatView M;
+    char *reg = work + d.off;
+    const size_t gbytes = sizeof(double) * (size_t)d.mp * d.n;
+    const size_t vbytes = sizeof(double) * (size_t)d.np * d.n;
+    M.gr = reinterpret_cast<double *>(reg);
+    M.gi = CPLX ? reinterpret_cast<double *>(reg + al256(gbytes)) : nullptr;
+    size_t o = al256(gbytes) * (CPLX ? 2 : 1);
+    M.vr = reinterpret_cast<double *>(reg + o);
+    M.vi = CPLX ? reinterpret_cast<double *>(reg + o + al256(vbytes)) : nullptr;
+    o += al256(vbytes) * (CPLX ? 2 : 1);
+    int *e = reinterpret_cast<int *>(reg + o);
+    o = al256(o + sizeof(int) * (size_t)d.n);
+    double *f = reinterpret_cast<double *>(reg + o);
+    o = al256(o + sizeof(double) * (size_t)d.n);
+    int *rank = reinterpret_cast<int *>(reg + o);
+    M.m = d.m;
+    M.n = d.n;
+    M.mp = d.mp;
+    M.np = d.np;
+    M.ldg = d.mp;
+    M.ldv = d.np;
+
+    // A1: max-norm of A (NaN -> Inf), s_0, G_1 = 2^{s_0} A, V_1 = I
+    if (threadIdx.x == 0) {
+      s_M0 = 0ull;
+      s_T = 0;
+      s_rescales = 0;
+    }
+    __syncthreads();
+    {
+      const int64_t rows = CPLX ? 2 * (int64_t)d.m : d.m, ld = CPLX ? 2 * d.lda : d.lda;
+      unsigned long long mx = 0ull;
+      for (int64_t q = threadIdx.x; q < rows * d.n; q += blockDim.x) {
+        const int64_t j = q / rows, i = q - j * rows;
+        unsigned long long a = abits(d.A[j * ld + i]);
+        a = (a > kInf) ? kInf : a;
+        mx = (a > mx) ? a : mx;
+      }
+      mx = warp_umax(mx);
+      if (lane == 0) atomicMax(&s_M0, mx);
+    }
+    __syncthreads();
+    const unsigned long long m0 = s_M0;
+    const bool bad = m0 >= kInf;
+    const int s0 = (m0 == 0ull || bad) ? 0 : -flg(dbl(m0));
+    for (int64_t q = threadIdx.x; q < (int64_t)d.mp * d.n; q += blockDim.x) {
+      const int j = (int)(q / d.mp), i = (int)(q - (int64_t)j * d.mp);
+      double xr = 0.0, xi = 0.0;
+      if (i < d.m && !bad) {
+        if (CPLX) {
+          xr = ldexp_rn(d.A[2 * (j * d.lda + i)], s0);
+          xi = ldexp_rn(d.A[2 * (j * d.lda + i) + 1], s0);
+        } else {
+          xr = ldexp_rn(d.A[j * d.lda + i], s0);
+        }
+      }
+      M.gr[j * M.ldg + i] = xr;
+      if (CPLX) M.gi[j * M.ldg + i] = xi;
+    }
+    for (int64_t q = threadIdx.x; q < (int64_t)d.np * d.n; q += blockDim.x) {
+      const int j = (int)(q / d.np), i = (int)(q - (int64_t)j * d.np);
+      M.vr[j * M.ldv + i] = (i == j) ? 1.0 : 0.0;
+      if (CPLX) M.vi[j * M.ldv + i] = 0.0;
+    }
+    if (threadIdx.x == 0) {
+      s_s = s0;
+      s_M[0] = (m0 == 0ull || bad) ? 0ull : bits(ldexp_rn(dbl(m0), s0));
+      s_M[1] = s_M[2] = 0ull;
+    }
+    __syncthreads();
+
+    // A2-A8: the sweeps (as sweeps_kernel, with a block barrier per step)
+    int sweeps = 0;
+    bool conv = false;
+    long long rot_total = 0;
+    if (!bad) {
+      const int nt = d.n + (d.n & 1), K = nt - 1, L = nt / 2;
+      const double ups = ldexp_rn(__dsqrt_rn((double)d.m), -53);  // Eq. e:tol
+      if (K < 1) {
+        sweeps = 1;
+        conv = true;
+      }
+      unsigned long long gstep = 0;
+      for (int sweep = 0; sweep < S && !conv; ++sweep) {
+        for (int k = 0; k < K; ++k, ++gstep) {
+          const int cur = (int)(gstep % 3), nxt = (int)((gstep + 1) % 3), old = (int)((gstep + 2) % 3);
+          const double Mcur = dbl(s_M[cur]);
+          const int rk = (bits(Mcur) != 0ull && flg(Mcur) >= rexp) ? -flg(Mcur) : 0;
+          if (threadIdx.x == 0) {
+            s_M[old] = 0ull;
+            atomicMax(&s_M[nxt], bits(rk ? ldexp_rn(Mcur, rk) : Mcur));
+            if (rk) {
+              s_s += rk;
+              s_rescales += 1;
+            }
+          }
+          unsigned long long Mloc = 0ull;
+          int rots = 0;
+          for (int base = 0; base < L; base += 32)
+            step_chunk<double, CPLX>(M, k, nt, base, 32, ups, rk, permute != 0, s_sums, s_out, Mloc,
+                                     rots);
+          Mloc = warp_umax(Mloc);
+          if (lane == 0) {
+            if (Mloc) atomicMax(&s_M[nxt], Mloc);
+            if (rots) atomicAdd(&s_T, rots);
+          }
+          __syncthreads();
+        }
+        const int T = s_T;
+        rot_total += T;
+        sweeps = sweep + 1;
+        conv = (T == 0);
+        __syncthreads();
+        if (threadIdx.x == 0) s_T = 0;
+        __syncthreads();
+      }
+    }
+
+    // A9: norms, order, outputs, info
+    for (int j = warp; j < d.n; j += W) colnorm_warp<CPLX>(M, j, lane, e, f);
+    __syncthreads();
+    for (int j = threadIdx.x; j < d.n; j += blockDim.x) rank[j] = rank_of(d.n, e, f, j);
+    __syncthreads();
+    const int sfin = s_s;
+    const int R = max(d.m, d.n);
+    for (int64_t q = threadIdx.x; q < (int64_t)R * d.n; q += blockDim.x) {
+      const int j = (int)(q / R), i = (int)(q - (int64_t)j * R);
+      const int r = rank[j];
+      if (i == 0) output_sigma(r, e[j], f[j], sfin, bad, d.sigma, d.sigma_e, d.sigma_f);
+      output_elem<CPLX>(M, i, j, r, e[j], f[j], bad, d.U, d.ldu, d.V, d.ldv);
+    }
+    if (info && threadIdx.x == 0) {
+      jsvd_info out;
+      out.status = bad ? JSVD_E_NONFINITE : conv ? 0 : JSVD_NOT_CONVERGED;
+      out.sweeps = sweeps;
+      out.rotations = rot_total;
+      out.rescales = s_rescales;
+      out.sweeps_fp32 = 0;
+      info[idx] = out;
+    }
+    __syncthreads();
+  }
+}
+
+static int batch_check(jsvd_field field, const jsvd_opts *opts, int64_t count, const int64_t *m,
+                       const int64_t *n, int &S, int &rexp, int &permute)
+{
+  if (field != JSVD_REAL && field != JSVD_COMPLEX) return -1;
+  int mode;
+  if (svd_check_opts(opts, S, mode, rexp, permute) || mode != JSVD_FP64) return -2;
+  if (count < 0 || count > (1 << 26)) return -3;
+  if (count > 0 && (!m || !n)) return -4;
+  for (int64_t i = 0; i < count; ++i)
+    if (m[i] < 1 || n[i] < 1 || n[i] > m[i] || m[i] > (1 << 24) || n[i] > (1 << 16)) return -4;
+  return JSVD_OK;
+}
+
+}  // namespace jsvd
+
+using namespace jsvd;
+
+extern "C" int jsvd_svd_batched_workspace_size(jsvd_field field, const jsvd_opts *opts,
+                                               int64_t count, const int64_t *m, const int64_t *n,
+                                               size_t *bytes)
+{
+  int S, rexp, permute;
+  const int rc = batch_check(field, opts, count, m, n, S, rexp, permute);
+  if (rc) return rc;
+  if (!bytes) return -6;
+  const BatchLayout L = batch_layout(count);
+  size_t total = L.regions;
+  for (int64_t i = 0; i < count; ++i) total += region_bytes(field == JSVD_COMPLEX, m[i], n[i]);
+  *bytes = total;
+  return JSVD_OK;
+}
+
+extern "C" int jsvd_svd_batched_prepare(jsvd_field field, const jsvd_opts *opts, int64_t count,
+                                        const int64_t *m, const int64_t *n, const void *const *A,
+                                        const int64_t *lda, void *const *U, const int64_t *ldu,
+                                        double *const *sigma, double *const *sigma_e,
+                                        double *const *sigma_f, void *const *V,
+                                        const int64_t *ldv, void *work, size_t work_bytes,
+                                        void *stream)
+{
+  int S, rexp, permute;
+  const int rc = batch_check(field, opts, count, m, n, S, rexp, permute);
+  if (rc) return rc;
+  if (count > 0 && (!A || !lda || !U || !ldu || !sigma || !V || !ldv)) return -6;
+  if (!work || ((uintptr_t)work & 255)) return -15;
+  size_t need = 0;
+  jsvd_svd_batched_workspace_size(field, opts, count, m, n, &need);
+  if (work_bytes < need) return JSVD_E_WORKSPACE;
+  const bool cplx = field == JSVD_COMPLEX;
+  const uintptr_t al = cplx ? 15 : 7;
+  const BatchLayout L = batch_layout(count);
+  std::vector<BatchDesc> desc((size_t)count);
+  size_t off = L.regions;
+  for (int64_t i = 0; i < count; ++i) {
+    if (!A[i] || ((uintptr_t)A[i] & al) || lda[i] < m[i]) return -6;
+    if (!U[i] || ((uintptr_t)U[i] & al) || ldu[i] < m[i]) return -8;
+    if (!sigma[i]) return -10;
+    if (!V[i] || ((uintptr_t)V[i] & al) || ldv[i] < n[i]) return -13;
+    BatchDesc &d = desc[(size_t)i];
+    d.A = (const double *)A[i];
+    d.U = (double *)U[i];
+    d.V = (double *)V[i];
+    d.sigma = sigma[i];
+    d.sigma_e = sigma_e ? sigma_e[i] : nullptr;
+    d.sigma_f = sigma_f ? sigma_f[i] : nullptr;
+    d.lda = lda[i];
+    d.ldu = ldu[i];
+    d.ldv = ldv[i];
+    d.m = (int)m[i];
+    d.n = (int)n[i];
+    d.mp = (int)((m[i] + 31) / 32 * 32);
+    d.np = (int)((n[i] + 31) / 32 * 32);
+    d.off = (int64_t)off;
+    off += region_bytes(cplx, m[i], n[i]);
+  }
+  // queue order: longest first (m n^2 of a sweep), ties by index; only the
+  // order in which blocks take matrices depends on it, never a result
+  std::vector<int> ord((size_t)count);
+  for (int64_t i = 0; i < count; ++i) ord[(size_t)i] = (int)i;
+  std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) {
+    const double ca = (double)m[a] * (double)n[a] * (double)n[a];
+    const double cb = (double)m[b] * (double)n[b] * (double)n[b];
+    return ca > cb;
+  });
+  BatchHdr h = {0, (int)count, 0, 0};
+  char *w = (char *)work;
+  cudaStream_t st = as_stream(stream);
+  JSVD_CUDA(cudaMemcpyAsync(w + L.hdr, &h, sizeof(h), cudaMemcpyHostToDevice, st));
+  if (count > 0) {
+    JSVD_CUDA(cudaMemcpyAsync(w + L.desc, desc.data(), sizeof(BatchDesc) * desc.size(),
+                              cudaMemcpyHostToDevice, st));
+    JSVD_CUDA(cudaMemcpyAsync(w + L.order, ord.data(), sizeof(int) * ord.size(),
+                              cudaMemcpyHostToDevice, st));
+  }
+  // the host buffers are pageable: the copies have been staged when the
+  // calls return, but keep this call synchronous w.r.t. them to be safe
+  JSVD_CUDA(cudaStreamSynchronize(st));
+  return JSVD_OK;
+}
+
+extern "C" int jsvd_svd_batched_launch(jsvd_field field, const jsvd_opts *opts, int64_t count,
+                                       void *work, jsvd_info *info, void *stream)
+{
+  if (field != JSVD_REAL && field != JSVD_COMPLEX) return -1;
+  int S, mode, rexp, permute;
+  if (svd_check_opts(opts, S, mode, rexp, permute) || mode != JSVD_FP64) return -2;
+  if (count < 0 || count > (1 << 26)) return -3;
+  if (!work || ((uintptr_t)work & 255)) return -4;
+  if (count == 0) return JSVD_OK;
+  const BatchLayout L = batch_layout(count);
+  char *w = (char *)work;
+  cudaStream_t st = as_stream(stream);
+  // rewind the queue (graph-capturable: a memset node)
+  JSVD_CUDA(cudaMemsetAsync(w + L.hdr, 0, sizeof(int), st));
+  const int threads = 32 * g_batch_warps;
+  int per_sm = 0;
+  auto kern = (field == JSVD_COMPLEX) ? batched_kernel<true> : batched_kernel<false>;
+  JSVD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0));
+  if (per_sm < 1) return JSVD_E_UNSUPPORTED;
+  const int grid = (int)std::min<int64_t>(count, (int64_t)per_sm * sm_count());
+  kern<<<grid, threads, 0, st>>>(reinterpret_cast<const BatchDesc *>(w + L.desc),
+                                 reinterpret_cast<const int *>(w + L.order),
+                                 reinterpret_cast<BatchHdr *>(w + L.hdr), w, info, S, rexp, permute);
+  JSVD_CHECK_LAUNCH();
+  return JSVD_OK;
+}
+
+extern "C" int jsvd_svd_batched(jsvd_field field, const jsvd_opts *opts, int64_t count,
+                                const int64_t *m, const int64_t *n, const void *const *A,
+                                const int64_t *lda, void *const *U, const int64_t *ldu,
+                                double *const *sigma, double *const *sigma_e,
+                                double *const *sigma_f, void *const *V, const int64_t *ldv,
+                                void *work, size_t work_bytes, jsvd_info *info, void *stream)
+{
+  const int rc = jsvd_svd_batched_prepare(field, opts, count, m, n, A, lda, U, ldu, sigma, sigma_e,
+                                          sigma_f, V, ldv, work, work_bytes, stream);
+  if (rc) return rc;
+  return jsvd_svd_batched_launch(field, opts, count, work, info, stream);
+}

@@ -13,6 +13,8 @@
 // (Alg. zjrot) to the G and V column pairs, swapping per the permutation
 // bit, and tracks the max-norm of the new G columns (section 3.2, step 4).
 #pragma once
+#include <climits>
+
 #include "evd2.cuh"
 
 namespace jsvd {
@@ -176,15 +178,18 @@ __device__ __forceinline__ PairOut pair_rotation(double spp, double sqq, double 
   return o;
 }
 
-// The fused step for pair (p, q), executed by one full warp, with the
-// columns in precision T (double, or float in the FP32 phase of the mixed
-// SVD).  rk != 0 downscales both columns of G by 2^rk first (section 3.2,
-// step 2; FP64 only); permute applies the column swap P.  Mloc collects
-// magbits() of the transformed G entries (in T's encoding).  Returns
-// whether the pair was rotated (the same in every lane).
+struct PairSums {
+  double pp, qq, qr, qi;  // ||g_p||^2, ||g_q||^2, g_q^* g_p (re, im)
+};
+
+// The three sums of pair (p, q), formed by one full warp with the columns
+// in precision T (double, or float in the FP32 phase of the mixed SVD):
+// lane l accumulates rows l, l+32, ... in ascending order with fma, the lane
+// partials are combined in FP64 by an xor butterfly (the same value in every
+// lane).  rk != 0 downscales both columns of G by 2^rk first (section 3.2,
+// step 2; FP64 only).
 template <typename T, bool CPLX>
-__device__ __forceinline__ bool pair_step(const MatViewT<T> &M, int p, int q, double ups, int rk,
-                                          bool permute, unsigned long long &Mloc)
+__device__ __forceinline__ PairSums pair_sums(const MatViewT<T> &M, int p, int q, int rk)
 {
   // rows per lane per loop trip: their loads are all issued before the
   // arithmetic, which then consumes them in ascending row order, so the
@@ -243,29 +248,36 @@ __device__ __forceinline__ bool pair_step(const MatViewT<T> &M, int p, int q, do
       }
     }
   }
-  // the lane partial sums are combined, and everything after them is
-  // computed, in FP64 whatever the column precision
-  const double dpp = warp_sum((double)spp), dqq = warp_sum((double)sqq);
-  const double dqr = warp_sum((double)sqr), dqi = CPLX ? warp_sum((double)sqi) : 0.0;
-  PairOut o = {};
-  if (lane == 0) {
-    o = pair_rotation<CPLX>(dpp, dqq, dqr, dqi, ups);
-    o.swap = o.swap && permute;
-  }
-  const unsigned full = 0xffffffffu;
-  const int flags = __shfl_sync(full, lane == 0 ? ((o.rot ? 1 : 0) | (o.swap ? 2 : 0)) : 0, 0);
-  const bool rot = flags & 1, swp = (flags >> 1) & 1;
-  if (rot) {
-    const T c = to_t(__shfl_sync(full, o.c, 0), T(0)), C = to_t(__shfl_sync(full, o.C, 0), T(0));
-    const T S = CPLX ? to_t(__shfl_sync(full, o.S, 0), T(0)) : T(0);
-    // Eq. e:transf: x_p' = fma(x_q, e', x_p) c, x_q' = fma(x_p, -conj(e'), x_q) c,
-    // e' = C + iS, on the G rows (tracking the max-norm) and the V rows
+  PairSums r;
+  r.pp = warp_sum((double)spp);
+  r.qq = warp_sum((double)sqq);
+  r.qr = warp_sum((double)sqr);
+  r.qi = CPLX ? warp_sum((double)sqi) : 0.0;
+  return r;
+}
+
+// Eq. e:transf (Alg. zjrot) on the pair's G rows (tracking the max-norm of
+// the new entries in Mloc, as magbits() in T's encoding) and V rows, with the
+// columns swapped if o.swap; a non-rotated pair with o.swap is only swapped.
+// One full warp; o must be the same in every lane.
+template <typename T, bool CPLX>
+__device__ __forceinline__ void pair_apply(const MatViewT<T> &M, int p, int q, const PairOut &o,
+                                           unsigned long long &Mloc)
+{
+  constexpr int U = (sizeof(T) == 4) ? 8 : 4;
+  const int lane = threadIdx.x & 31;
+  const bool swp = o.swap;
+  if (o.rot) {
+    const T c = to_t(o.c, T(0)), C = to_t(o.C, T(0));
+    const T S = CPLX ? to_t(o.S, T(0)) : T(0);
+    // x_p' = fma(x_q, e', x_p) c, x_q' = fma(x_p, -conj(e'), x_q) c, e' = C + iS
     for (int pass = 0; pass < 2; ++pass) {
       const bool onG = (pass == 0);
       const int rows = onG ? M.mp : M.np;
-      T *xpr = onG ? gpr : M.vr + p * M.ldv, *xqr = onG ? gqr : M.vr + q * M.ldv;
-      T *xpi = CPLX ? (onG ? gpi : M.vi + p * M.ldv) : nullptr;
-      T *xqi = CPLX ? (onG ? gqi : M.vi + q * M.ldv) : nullptr;
+      T *xpr = onG ? M.gr + p * M.ldg : M.vr + p * M.ldv;
+      T *xqr = onG ? M.gr + q * M.ldg : M.vr + q * M.ldv;
+      T *xpi = CPLX ? (onG ? M.gi + p * M.ldg : M.vi + p * M.ldv) : nullptr;
+      T *xqi = CPLX ? (onG ? M.gi + q * M.ldg : M.vi + q * M.ldv) : nullptr;
       T *dpr = swp ? xqr : xpr, *dqr = swp ? xpr : xqr;
       T *dpi = swp ? xqi : xpi, *dqi = swp ? xpi : xqi;
       for (int base = lane; base < rows; base += 32 * U) {
@@ -316,9 +328,10 @@ __device__ __forceinline__ bool pair_step(const MatViewT<T> &M, int p, int q, do
     for (int pass = 0; pass < 2; ++pass) {
       const bool onG = (pass == 0);
       const int rows = onG ? M.mp : M.np;
-      T *xpr = onG ? gpr : M.vr + p * M.ldv, *xqr = onG ? gqr : M.vr + q * M.ldv;
-      T *xpi = CPLX ? (onG ? gpi : M.vi + p * M.ldv) : nullptr;
-      T *xqi = CPLX ? (onG ? gqi : M.vi + q * M.ldv) : nullptr;
+      T *xpr = onG ? M.gr + p * M.ldg : M.vr + p * M.ldv;
+      T *xqr = onG ? M.gr + q * M.ldg : M.vr + q * M.ldv;
+      T *xpi = CPLX ? (onG ? M.gi + p * M.ldg : M.vi + p * M.ldv) : nullptr;
+      T *xqi = CPLX ? (onG ? M.gi + q * M.ldg : M.vi + q * M.ldv) : nullptr;
       for (int i = lane; i < rows; i += 32) {
         const T a = ldg2(xpr + i), b = ldg2(xqr + i);
         stg2(xpr + i, b);
@@ -332,7 +345,168 @@ __device__ __forceinline__ bool pair_step(const MatViewT<T> &M, int p, int q, do
     }
   }
   __syncwarp();
-  return rot;
+}
+
+// One chunk of CH <= 32 pivot pairs (l = base .. base + CH - 1) of step k,
+// executed by the whole block (W warps, three block barriers):
+//   1. warps form the sums of the chunk's pairs,
+//   2. one thread per pair turns them into the rotation (Alg. zdpscl's
+//      division, Alg. cvg, Alg. Gram, the EVD) -- the narrow FP64 pipe
+//      charges a masked warp instruction like a full one, so the EVDs of
+//      the chunk share their instructions instead of one lane each,
+//   3. warps apply the rotations.
+// Every pair's arithmetic is the same whatever the chunking.  rots counts
+// (in each warp's lane 0) the rotated pairs, Mloc collects magbits().
+template <typename T, bool CPLX>
+__device__ __forceinline__ void step_chunk(const MatViewT<T> &M, int k, int nt, int base, int CH,
+                                           double ups, int rk, bool permute, PairSums *s_sums,
+                                           PairOut *s_out, unsigned long long &Mloc, int &rots)
+{
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
+  const int L = nt / 2;
+  for (int i = warp; i < CH; i += W) {
+    const int l = base + i;
+    if (l >= L) break;
+    int p, q;
+    pair_of(k, l, nt, p, q);
+    if (q < M.n) {
+      const PairSums sm = pair_sums<T, CPLX>(M, p, q, rk);
+      if (lane == 0) s_sums[i] = sm;
+    } else if (rk) {  // phantom partner: only a pending rescale applies
+      scale_col(M.gr + p * M.ldg, M.mp, rk, lane);
+      if (CPLX) scale_col(M.gi + p * M.ldg, M.mp, rk, lane);
+    }
+  }
+  __syncthreads();
+  if ((int)threadIdx.x < CH) {
+    const int i = threadIdx.x, l = base + i;
+    if (l < L) {
+      int p, q;
+      pair_of(k, l, nt, p, q);
+      if (q < M.n) {
+        const PairSums sm = s_sums[i];
+        PairOut o = pair_rotation<CPLX>(sm.pp, sm.qq, sm.qr, sm.qi, ups);
+        o.swap = o.swap && permute;
+        s_out[i] = o;
+      }
+    }
+  }
+  __syncthreads();
+  for (int i = warp; i < CH; i += W) {
+    const int l = base + i;
+    if (l >= L) break;
+    int p, q;
+    pair_of(k, l, nt, p, q);
+    if (q < M.n) {
+      const PairOut o = s_out[i];
+      pair_apply<T, CPLX>(M, p, q, o, Mloc);
+      if (lane == 0 && o.rot) ++rots;
+    }
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Finalisation pieces (section 4.2.1), shared by the single-matrix and the
+// batched kernels so that both produce the same bits.
+
+// Column j's norm as (e, f) by one warp in the canonical order; a zero
+// column gets e = INT_MIN, f = 1.
+template <bool CPLX>
+__device__ __forceinline__ void colnorm_warp(const MatView &M, int j, int lane, int *e_out,
+                                             double *f_out)
+{
+  const double *xr = M.gr + j * M.ldg, *xi = CPLX ? M.gi + j * M.ldg : nullptr;
+  double s = 0.0;
+  for (int i = lane; i < M.mp; i += 32) {
+    const double a = ldg2(xr + i);
+    s = __fma_rn(a, a, s);
+    if (CPLX) {
+      const double b = ldg2(xi + i);
+      s = __fma_rn(b, b, s);
+    }
+  }
+  s = warp_sum(s);
+  if (lane == 0) {
+    if (bits(s) == 0ull) {
+      e_out[j] = INT_MIN;
+      f_out[j] = 1.0;
+    } else {
+      const double r = __dsqrt_rn(s);
+      const int e = flg(r);
+      e_out[j] = e;
+      f_out[j] = ldexp_rn(r, -e);
+    }
+  }
+}
+
+__device__ __forceinline__ bool ef_less(int ea, double fa, int eb, double fb)
+{
+  return (ea != eb) ? (ea < eb) : (bits(fa) < bits(fb));
+}
+
+// Position of column j after a stable sort by non-increasing sigma:
+// #{i : sigma_i > sigma_j, or sigma_i == sigma_j and i < j}.
+__device__ __forceinline__ int rank_of(int n, const int *e, const double *f, int j)
+{
+  int r = 0;
+  const int ej = e[j];
+  const double fj = f[j];
+  for (int i = 0; i < n; ++i) {
+    const int ei = e[i];
+    const double fi = f[i];
+    const bool gt = ef_less(ej, fj, ei, fi);
+    const bool eq = (ei == ej) && (bits(fi) == bits(fj));
+    r += (gt || (eq && i < j)) ? 1 : 0;
+  }
+  return r;
+}
+
+// One element (row i) of output column j, which goes to position r:
+// U(i, r) = G(i, j) 2^{-e_j} / f_j (i < m), V(i, r) = V_k(i, j) (i < n).
+template <bool CPLX>
+__device__ __forceinline__ void output_elem(const MatView &M, int i, int j, int r, int ej,
+                                            double fj, bool bad, double *U, int64_t ldu,
+                                            double *V, int64_t ldv)
+{
+  const double nan = __longlong_as_double(0x7FF8000000000000ll);
+  const bool zero = (ej == INT_MIN);
+  if (i < M.m) {
+    double ur = 0.0, ui = 0.0;
+    if (bad) {
+      ur = ui = nan;
+    } else if (!zero) {
+      ur = __ddiv_rn(ldexp_rn(ldg2(M.gr + j * M.ldg + i), -ej), fj);
+      if (CPLX) ui = __ddiv_rn(ldexp_rn(ldg2(M.gi + j * M.ldg + i), -ej), fj);
+    }
+    if (CPLX) {
+      U[2 * (r * ldu + i)] = ur;
+      U[2 * (r * ldu + i) + 1] = ui;
+    } else {
+      U[r * ldu + i] = ur;
+    }
+  }
+  if (i < M.n) {
+    const double vr = bad ? nan : ldg2(M.vr + j * M.ldv + i);
+    if (CPLX) {
+      V[2 * (r * ldv + i)] = vr;
+      V[2 * (r * ldv + i) + 1] = bad ? nan : ldg2(M.vi + j * M.ldv + i);
+    } else {
+      V[r * ldv + i] = vr;
+    }
+  }
+}
+
+// sigma_r = 2^{e_j - s} f_j and its (e, f) pair.
+__device__ __forceinline__ void output_sigma(int r, int ej, double fj, int s, bool bad,
+                                             double *sigma, double *sigma_e, double *sigma_f)
+{
+  const double nan = __longlong_as_double(0x7FF8000000000000ll);
+  const bool zero = (ej == INT_MIN);
+  if (sigma) sigma[r] = bad ? nan : zero ? 0.0 : ldexp_rn(fj, ej - s);
+  if (sigma_e)
+    sigma_e[r] = bad ? nan : zero ? -__longlong_as_double((long long)kInf) : (double)(ej - s);
+  if (sigma_f) sigma_f[r] = bad ? nan : fj;
 }
 
 // Device-wide time in ns (for bounded waits).

@@ -174,3 +174,64 @@ def diff_batch(count: int = 4096, m: int = 64, n: int = 32, cond: float = 1e3, k
     w = g.random((count, n))
     C = g.standard_normal((count, m, k))
     return A, w, C
+
+
+# ---------------------------------------------------------------------------
+# device-side generation of the large batches (workloads 4 and 5)
+#
+# Drawing 10,000 Haar-factored matrices with numpy takes over a minute, so
+# the benchmark draws them on the GPU with torch's seeded CUDA generator:
+# for every n, the m x n Gaussians are zero-padded to 2n x n and factored by
+# one batched QR (the zero rows stay zero in Q = Z R^-1, so the first m rows
+# of Q are the Haar factor of the m x n Gaussian).  The draws are
+# reproducible on the same torch build and GPU, not bit-identical to the
+# numpy generators above.
+
+def _haar_batch(torch, gen, k, rows, cols, m_rows, device):
+    Z = torch.randn((k, rows, cols), generator=gen, dtype=torch.float64, device=device)
+    if m_rows is not None:
+        r = torch.arange(rows, device=device).view(1, rows, 1)
+        Z = Z * (r < m_rows.view(k, 1, 1)).to(Z.dtype)
+    Q, R = torch.linalg.qr(Z)
+    d = torch.diagonal(R, dim1=-2, dim2=-1)
+    sg = torch.where(d < 0, -1.0, 1.0).to(Q.dtype)
+    return Q * sg.unsqueeze(1)
+
+
+def uneven_batch_device(count: int = 10000, nmin: int = 16, nmax: int = 256, cond: float = 1e4,
+                        seed_salt: int = 0, device="cuda"):
+    """Workload 4 on the device: (A packed column-major 1-D tensor, m, n)."""
+    import torch
+    m, n = uneven_shapes(count, nmin, nmax, seed_salt)
+    off = np.concatenate([[0], np.cumsum(m * n)[:-1]]) if count else np.zeros(0, np.int64)
+    A = torch.empty(int((m * n).sum()), dtype=torch.float64, device=device)
+    for nv in np.unique(n):
+        idx = np.nonzero(n == nv)[0]
+        gen = torch.Generator(device=device)
+        gen.manual_seed(BASE_SEED + 4 + 7919 * int(nv) + 1000003 * seed_salt)
+        k, nv = len(idx), int(nv)
+        mt = torch.as_tensor(m[idx], device=device)
+        Q1 = _haar_batch(torch, gen, k, 2 * nv, nv, mt, device)
+        Q2 = _haar_batch(torch, gen, k, nv, nv, None, device)
+        s = torch.as_tensor(geometric_sigma(nv, cond), device=device)
+        Ab = (Q1 * s.view(1, 1, nv)) @ Q2.transpose(1, 2)  # (k, 2n, n), zero rows below m
+        for t, i in enumerate(idx):
+            mi = int(m[i])
+            A[int(off[i]):int(off[i]) + mi * nv] = Ab[t, :mi, :].t().reshape(-1)
+    return A, m, n
+
+
+def diff_batch_device(count: int = 4096, m: int = 64, n: int = 32, cond: float = 1e3, k: int = 8,
+                      seed_salt: int = 0, device="cuda"):
+    """Workload 5 on the device: A (count, m, n) row-major tensor, w (count,
+    n), C (count, m, k)."""
+    import torch
+    gen = torch.Generator(device=device)
+    gen.manual_seed(BASE_SEED + 5 + 1000003 * seed_salt)
+    Q1 = _haar_batch(torch, gen, count, m, n, None, device)
+    Q2 = _haar_batch(torch, gen, count, n, n, None, device)
+    s = torch.as_tensor(geometric_sigma(n, cond), device=device)
+    A = (Q1 * s.view(1, 1, n)) @ Q2.transpose(1, 2)
+    w = torch.rand((count, n), generator=gen, dtype=torch.float64, device=device)
+    C = torch.randn((count, m, k), generator=gen, dtype=torch.float64, device=device)
+    return A, w, C

@@ -1,0 +1,166 @@
+"""The batched uneven SVD (jsvd_svd_batched): every matrix gives the same
+bits as jsvd_svd on it alone, whatever the batch, the position in it and
+the block shape; parity with the oracle; the full 10,000-matrix workload
+meets the acceptance bounds on a sample; a captured CUDA graph replays it."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2202_08361_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+EPS = np.finfo(np.float64).eps
+
+
+def tol(n):
+    return 64 * n * EPS
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def mats_mixed(cplx, seed=0):
+    g = np.random.default_rng(seed)
+    shapes = [(1, 1), (7, 1), (9, 2), (33, 17), (64, 64), (100, 37), (65, 33), (40, 40), (130, 70)]
+    out = []
+    for m, n in shapes:
+        A, _ = workloads.svd_geometric(m, n, 1e4, cplx, g)
+        out.append(A)
+    return out
+
+
+def single(A):
+    torch = _torch()
+    import paper_2202_08361_gb300 as J
+    out = J.svd(torch.from_numpy(np.asfortranarray(A)).cuda())
+    torch.cuda.synchronize()
+    return out
+
+
+def same(x, y):
+    torch = _torch()
+    x, y = x.contiguous(), y.contiguous()
+    if x.is_complex():
+        x, y = torch.view_as_real(x), torch.view_as_real(y)
+    return torch.equal(x.view(torch.int64), y.view(torch.int64))
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+def test_batched_equals_single_bitwise(cplx):
+    import paper_2202_08361_gb300 as J
+    mats = mats_mixed(cplx, seed=1 + cplx)
+    B = J.svd_batched(mats)
+    _torch().cuda.synchronize()
+    infos = J.decode_info(B.info)
+    for i, A in enumerate(mats):
+        ref = single(A)
+        U, s, V = B.matrix(i)
+        assert same(U, ref["U"]) and same(V, ref["V"]) and same(s, ref["sigma"]), i
+        assert infos[i] == J.decode_info(ref["info"]), i
+
+
+def test_batch_composition_and_block_shape_invariance():
+    import paper_2202_08361_gb300 as J
+    torch = _torch()
+    mats = mats_mixed(False, seed=5)
+    ref = J.svd_batched(mats)
+    order = list(range(len(mats)))[::-1]
+    rev = J.svd_batched([mats[i] for i in order])
+    try:
+        for w in (1, 4, 16):
+            J.tune_set(J.JSVD_TUNE_BATCH_WARPS, w)
+            other = J.svd_batched(mats + mats[:3])
+            torch.cuda.synchronize()
+            for i in range(len(mats)):
+                for a, b in zip(other.matrix(i), ref.matrix(i)):
+                    assert same(a, b), (w, i)
+    finally:
+        J.tune_set(J.JSVD_TUNE_BATCH_WARPS, 8)
+    for pos, i in enumerate(order):
+        for a, b in zip(rev.matrix(pos), ref.matrix(i)):
+            assert same(a, b), i
+
+
+def test_batched_against_oracle():
+    import paper_2202_08361_gb300 as J
+    mats = mats_mixed(True, seed=9)
+    B = J.svd_batched(mats)
+    _torch().cuda.synchronize()
+    for i, A in enumerate(mats):
+        n = A.shape[1]
+        U, s, V = (t.cpu().numpy() for t in B.matrix(i))
+        o = oracle.vjsvd(A)
+        assert np.abs(s - o["sigma"]).max() <= tol(n) * o["sigma"][0]
+        res = np.linalg.norm(A - (U * s) @ V.conj().T) / max(np.linalg.norm(A), 1e-300)
+        assert res <= tol(n)
+        assert np.abs(U.conj().T @ U - np.eye(n)).max() <= tol(n)
+
+
+def test_batched_edge_cases():
+    import paper_2202_08361_gb300 as J
+    torch = _torch()
+    Z = np.zeros((5, 3))
+    N = workloads.svd_normal(6, 3, seed_salt=2)
+    N[1, 1] = np.nan
+    G = workloads.svd_normal(12, 6, seed_salt=3)
+    B = J.svd_batched([Z, N, G], max_sweeps=1)
+    torch.cuda.synchronize()
+    info = J.decode_info(B.info)
+    assert info[0]["status"] == 0 and torch.all(B.matrix(0)[1] == 0)
+    assert info[1]["status"] == J.JSVD_E_NONFINITE and torch.all(torch.isnan(B.matrix(1)[1]))
+    assert info[2]["status"] == J.JSVD_NOT_CONVERGED and info[2]["sweeps"] == 1
+    E = J.svd_batched([])
+    assert E.count == 0
+
+
+def test_full_workload_10000_uneven():
+    """The 10,000-matrix uneven workload (n ~ U{16..256}, m ~ U{n..2n},
+    condition 1e4): all converge; a sample meets the bounds and matches the
+    oracle; the prescribed spectra are recovered."""
+    import paper_2202_08361_gb300 as J
+    torch = _torch()
+    A, m, n = workloads.uneven_batch_device()
+    B = J.BatchedSVD(A, m, n).launch()
+    torch.cuda.synchronize()
+    info = J.decode_info(B.info)
+    assert all(x["status"] == 0 for x in info)
+    g = np.random.default_rng(11)
+    sample = sorted(set(g.choice(len(m), 12, replace=False).tolist() + [int(np.argmin(m * n))]))
+    for i in sample:
+        mi, ni = int(m[i]), int(n[i])
+        Ai = A[int(B.offA[i]):int(B.offA[i]) + mi * ni].view(ni, mi).t().cpu().numpy()
+        U, s, V = (t.cpu().numpy() for t in B.matrix(i))
+        res = np.linalg.norm(Ai - (U * s) @ V.T) / np.linalg.norm(Ai)
+        assert res <= tol(ni), (i, res)
+        assert np.abs(U.T @ U - np.eye(ni)).max() <= tol(ni)
+        assert np.abs(V.T @ V - np.eye(ni)).max() <= tol(ni)
+        sref = workloads.geometric_sigma(ni, 1e4)
+        assert np.abs(s - sref).max() <= tol(ni) * sref[0]
+        if mi * ni <= 64 * 64:
+            o = oracle.vjsvd(Ai)
+            assert np.abs(s - o["sigma"]).max() <= tol(ni) * o["sigma"][0]
+
+
+def test_cuda_graph_replay():
+    import paper_2202_08361_gb300 as J
+    torch = _torch()
+    mats = mats_mixed(False, seed=21)
+    A, m, n = J.pack_matrices(mats)
+    B = J.BatchedSVD(A, m, n)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        B.launch(s)  # warm-up outside the capture
+    torch.cuda.synchronize()
+    ref = [t.clone() for t in (B.U, B.V, B.sigma)]
+    B.U.zero_()
+    B.sigma.zero_()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        B.launch(s)
+    graph.replay()
+    torch.cuda.synchronize()
+    for a, b in zip((B.U, B.V, B.sigma), ref):
+        assert same(a, b)

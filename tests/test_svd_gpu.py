@@ -157,15 +157,15 @@ def test_bit_identical_across_launch_shapes():
     A, _ = workloads.svd_geometric(96, 70, 1e5, True, np.random.default_rng(3))
     ref = gpu_svd(A)
     try:
-        for cap in (1, 3, 16):
-            J.tune_set(J.JSVD_TUNE_SVD_GRID, cap)
+        for cap, warps in ((1, 1), (3, 2), (16, 8), (0, 4), (5, 0)):
+            J.tune_set(J.JSVD_TUNE_SVD_GRID, cap, warps)
             g = gpu_svd(A)
             for k in ("U", "V", "sigma"):
                 assert np.array_equal(np.ascontiguousarray(g[k]).view(np.uint8),
-                                      np.ascontiguousarray(ref[k]).view(np.uint8)), (cap, k)
+                                      np.ascontiguousarray(ref[k]).view(np.uint8)), (cap, warps, k)
             assert g["info"] == ref["info"]
     finally:
-        J.tune_set(J.JSVD_TUNE_SVD_GRID, 0)
+        J.tune_set(J.JSVD_TUNE_SVD_GRID, 0, 0)
     again = gpu_svd(A)
     assert np.array_equal(np.ascontiguousarray(again["U"]).view(np.uint8),
                           np.ascontiguousarray(ref["U"]).view(np.uint8))
