@@ -46,6 +46,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--evd-log2", type=int, default=24,
                    help="log2 of the matrices per kernel per step (24 = the full workload)")
+    p.add_argument("--no-svd", action="store_true",
+                   help="skip the SVD measurements (C1, C3 plain/mixed, C4, C5)")
     return p.parse_args()
 
 
@@ -126,7 +128,7 @@ def gpu_index(local_rank):
 
 def kernel_source_sha():
     h = hashlib.sha256()
-    for name in ("evd2.cu", "evd2.cuh", "fp64bits.cuh"):
+    for name in ("evd2.cu", "evd2.cuh", "fp64bits.cuh", "fp64soft.cuh"):
         with open(os.path.join(ROOT, "paper_2202_08361_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -159,6 +161,150 @@ def cpu_oracle_evd(r, seed_salt=0):
     oracle.zsjac2(*cx)
     dt = time.perf_counter() - t0
     return dt, oracle.num_threads()
+
+
+
+# ---------------------------------------------------------------------------
+# the SVD workloads (reported beside the EVD headline)
+
+DFMA_FLOPS = 0.99e12  # measured FP64 FMA rate of this GB300 (2 flops per fma), see the design doc
+
+
+def _ev(torch):
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def _svd_flops(m, n, sweeps, rotations, cplx):
+    """FP64 flops of the sweeps (fma = 2): every visited pair forms its sums
+    (3m fma real, 8m complex), every rotated pair transforms m + n rows
+    (2 fma + 2 mul real, 8 fma + 4 mul complex)."""
+    pairs = sweeps * n * (n - 1) // 2
+    if cplx:
+        return pairs * 16 * m + rotations * 20 * (m + n)
+    return pairs * 6 * m + rotations * 6 * (m + n)
+
+
+def svd_bench(torch, J, workloads, dev):
+    import numpy as np
+    out = {}
+    eps = np.finfo(np.float64).eps
+    st = torch.cuda.current_stream(dev)
+
+    def accuracy(A, r):
+        n = A.shape[1]
+        U, s, V = r["U"], r["sigma"], r["V"]
+        I = torch.eye(n, dtype=A.dtype, device=dev)
+        res = (torch.linalg.norm(A - (U * s) @ V.conj().T) / torch.linalg.norm(A)).item()
+        ou = (U.conj().T @ U - I).abs().max().item()
+        ov = (V.conj().T @ V - I).abs().max().item()
+        return {"residual": res, "orth_U": ou, "orth_V": ov, "bound_64neps": 64 * n * eps}
+
+    # C1: real 256 x 128, N(0,1)
+    A1 = torch.from_numpy(workloads.svd_normal()).to(dev)
+    r = J.svd(A1)
+    torch.cuda.synchronize(dev)
+    reps = 20
+    e0, e1 = _ev(torch)
+    e0.record(st)
+    for _ in range(reps):
+        J.svd(A1, out=r)
+    e1.record(st)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / reps
+    info = J.decode_info(r["info"])
+    fl = _svd_flops(256, 128, info["sweeps"], info["rotations"], False)
+    c1 = {"ms_per_svd": ms, "sweeps": info["sweeps"], "rotations": info["rotations"],
+          "fp64_gflops": fl / ms / 1e6, "fp64_frac": fl / (ms * 1e-3) / DFMA_FLOPS}
+    c1.update(accuracy(A1, r))
+    out["C1_real_256x128"] = c1
+
+    # C3: complex 4096 x 2048, cond 1e6, plain FP64 and mixed FP32 -> FP64
+    A3np, s3 = workloads.svd_complex_geometric()
+    A3 = torch.from_numpy(A3np).to(dev)
+    del A3np
+    c3 = {}
+    sig = {}
+    for mode in ("fp64", "mixed"):
+        e0, e1 = _ev(torch)
+        torch.cuda.synchronize(dev)
+        e0.record(st)
+        r = J.svd(A3, mode=mode)
+        e1.record(st)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1)
+        info = J.decode_info(r["info"])
+        d = {"s": ms / 1e3, "sweeps_fp64": info["sweeps"], "sweeps_fp32": info["sweeps_fp32"],
+             "rotations": info["rotations"], "status": info["status"]}
+        d.update(accuracy(A3, r))
+        sig[mode] = r["sigma"].cpu().numpy()
+        d["sigma_err_vs_prescribed"] = float(np.abs(sig[mode] - s3).max() / s3[0])
+        if mode == "fp64":
+            fl = _svd_flops(4096, 2048, info["sweeps"], info["rotations"], True)
+            d["fp64_tflops"] = fl / (ms * 1e-3) / 1e12
+            d["fp64_frac"] = fl / (ms * 1e-3) / DFMA_FLOPS
+        c3[mode] = d
+        del r
+    c3["speedup_mixed_vs_fp64"] = c3["fp64"]["s"] / c3["mixed"]["s"]
+    c3["sigma_mixed_vs_fp64_max_rel"] = float(np.abs(sig["mixed"] - sig["fp64"]).max() / s3[0])
+    out["C3_complex_4096x2048"] = c3
+    del A3
+
+    # C4: 10,000 uneven real matrices, one persistent launch vs a per-matrix loop
+    A4, m4, n4 = workloads.uneven_batch_device(device=dev)
+    B = J.BatchedSVD(A4, m4, n4)
+    e0, e1 = _ev(torch)
+    torch.cuda.synchronize(dev)
+    e0.record(st)
+    B.launch()
+    e1.record(st)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1)
+    infos = J.decode_info(B.info)
+    fl = sum(_svd_flops(int(m4[i]), int(n4[i]), infos[i]["sweeps"], infos[i]["rotations"], False)
+             for i in range(len(m4)))
+    g = np.random.default_rng(0)
+    idx = g.choice(len(m4), 40, replace=False)
+    mats = [A4[int(B.offA[i]):int(B.offA[i] + m4[i] * n4[i])].view(int(n4[i]), int(m4[i])).t()
+            for i in idx]
+    J.svd(mats[0])
+    torch.cuda.synchronize(dev)
+    e2, e3 = _ev(torch)
+    e2.record(st)
+    for M_ in mats:
+        J.svd(M_)
+    e3.record(st)
+    torch.cuda.synchronize(dev)
+    cost = (m4 * n4 * n4).astype(float)
+    loop_s = e2.elapsed_time(e3) / 1e3 * cost.sum() / cost[idx].sum()
+    out["C4_uneven_10000"] = {
+        "s": ms / 1e3, "matrices_per_s": len(m4) / (ms * 1e-3),
+        "converged": int(sum(1 for x in infos if x["status"] == 0)),
+        "sweeps_mean": float(np.mean([x["sweeps"] for x in infos])),
+        "fp64_tflops": fl / (ms * 1e-3) / 1e12, "fp64_frac": fl / (ms * 1e-3) / DFMA_FLOPS,
+        "per_matrix_loop_s_est": loop_s, "speedup_vs_loop": loop_s / (ms / 1e3),
+        "loop_sample": "40 random matrices through jsvd_svd one by one, scaled by m n^2"}
+    del A4, B, mats
+
+    # C5: differentiated batch, 4096 real 64 x 32, loss sum w sigma + <C, U[:, :8]>
+    A5, w5, C5 = workloads.diff_batch_device(device=dev)
+    best = None
+    for _ in range(3):
+        X = A5.clone().requires_grad_(True)
+        torch.cuda.synchronize(dev)
+        e0, e1 = _ev(torch)
+        e2 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        U, S, V = J.svd_diff(X)
+        L = (w5 * S).sum() + (C5 * U[:, :, :8]).sum()
+        e2.record(st)
+        L.backward()
+        e1.record(st)
+        torch.cuda.synchronize(dev)
+        t = (e0.elapsed_time(e2), e0.elapsed_time(e1))
+        best = t if best is None or t[1] < best[1] else best
+    out["C5_diff_4096x64x32"] = {"forward_ms": best[0], "forward_backward_ms": best[1],
+                                 "matrices_per_s": 4096 / (best[1] * 1e-3)}
+    return out
 
 
 def run_reference(args):
@@ -310,6 +456,10 @@ def run_ours(args):
                 "kernel": dom_name, "peak_kind": peak_kind,
                 "algorithmic_bytes_per_launch": dom_bytes, "avg_launch_ms": dom_ms}
 
+    svd = None
+    if rank == 0 and world == 1 and not args.no_svd:
+        svd = svd_bench(torch, J, workloads, dev)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         dt, cores = cpu_oracle_evd(R_EVD)
@@ -330,7 +480,8 @@ def run_ours(args):
                 / peaks["hbm_gbs"],
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
-                "cpu_baseline": cpu, "clocks": clk, "gpu_launches": gpu_launches}
+                "cpu_baseline": cpu, "clocks": clk, "gpu_launches": gpu_launches,
+                "svd": svd}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

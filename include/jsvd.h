@@ -73,6 +73,11 @@ JSVD_API const char *jsvd_last_cuda_error(void);
 /*   JSVD_TUNE_BATCH_WARPS: value = warps per block of the batched SVD
  *     kernel (1, 2, 4, 8 or 16; default 8). */
 #define JSVD_TUNE_BATCH_WARPS 3
+/*   JSVD_TUNE_EVD_ARITH: value = which of the 2x2 EVD's divisions and
+ *     square roots run on the integer pipe instead of the FP64 pipe (0..5;
+ *     default 5: the divisions).  Both are correctly rounded: the results
+ *     are identical. */
+#define JSVD_TUNE_EVD_ARITH 4
 JSVD_API int jsvd_tune_set(int knob, int value, int value2);
 
 /* ------------------------------------------------------------------------
@@ -290,6 +295,15 @@ JSVD_API int jsvd_svd_noalloc(jsvd_field field, const jsvd_opts *opts, int64_t m
 JSVD_API int jsvd_dgemm(int transA, int64_t M, int64_t N, int64_t K, double alpha,
                         const double *A, int64_t lda, const double *B, int64_t ldb, double beta,
                         double *C, int64_t ldc, void *stream);
+
+/* Self-test of the library's integer-pipe binary64 division and square
+ * root against the GPU's IEEE FP64 instructions: n generated operand pairs
+ * (several families: arbitrary bit patterns, subnormals, powers of two,
+ * extremes), from seed; atomically ADDS the number of differing divisions
+ * to mismatches[0] and of square roots to mismatches[1] (DEVICE memory, two
+ * unsigned long long, zeroed by the caller).  Errors: -i, JSVD_E_CUDA. */
+JSVD_API int jsvd_selftest_fp64(int64_t n, uint64_t seed, unsigned long long *mismatches,
+                                void *stream);
 
 /* The parallel pivot ordering the SVD kernels use (section 4.1; the
  * round-robin reading): writes (nt - 1) x (nt / 2) pairs (p, q), p < q, as

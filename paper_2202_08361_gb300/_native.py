@@ -23,6 +23,7 @@ JSVD_COMPLEX = 1
 JSVD_TUNE_EVD_LAUNCH = 1
 JSVD_TUNE_SVD_GRID = 2
 JSVD_TUNE_BATCH_WARPS = 3
+JSVD_TUNE_EVD_ARITH = 4
 
 JSVD_FP64 = 0
 JSVD_MIXED_FP32_FP64 = 1
@@ -110,6 +111,8 @@ def lib():
         L.jsvd_svd_adjoint_batched.restype = ctypes.c_int
         L.jsvd_sign_gauge_batched.argtypes = [_i64, _i64, _i64, _vp, _vp, _vp]
         L.jsvd_sign_gauge_batched.restype = ctypes.c_int
+        L.jsvd_selftest_fp64.argtypes = [_i64, ctypes.c_uint64, _vp, _vp]
+        L.jsvd_selftest_fp64.restype = ctypes.c_int
         L.jsvd_ordering.argtypes = [ctypes.c_int32, _vp, _vp]
         L.jsvd_ordering.restype = ctypes.c_int
         _lib = L

@@ -5,13 +5,16 @@
 // grid-stride kernel sized to the SM count.  Inputs are read once with
 // streaming loads, outputs written with streaming stores; each matrix is
 // independent, so any grid shape and any sub-range give the same bits.
+// The divisions and square roots are split between the FP64 pipe and the
+// integer pipe (correctly rounded either way) so that the two narrow pipes
+// share the work.
 #include "common.cuh"
 #include "evd2.cuh"
 #include "jsvd_internal.h"
 
 namespace jsvd {
 
-template <bool CPLX>
+template <bool CPLX, int MASK>
 __global__ void __launch_bounds__(256) evd2_kernel(const double *__restrict__ a11p,
                                                    const double *__restrict__ a22p,
                                                    const double *__restrict__ a21rp,
@@ -28,9 +31,9 @@ __global__ void __launch_bounds__(256) evd2_kernel(const double *__restrict__ a1
     const double a11 = __ldcs(a11p + i), a22 = __ldcs(a22p + i), a21r = __ldcs(a21rp + i);
     Rot2 r;
     if (CPLX) {
-      r = zsjac2(a11, a22, a21r, __ldcs(a21ip + i));
+      r = zsjac2<MASK>(a11, a22, a21r, __ldcs(a21ip + i));
     } else {
-      r = dsjac2(a11, a22, a21r);
+      r = dsjac2<MASK>(a11, a22, a21r);
     }
     __stcs(cphip + i, r.cphi);
     __stcs(etrp + i, r.etr);
@@ -43,6 +46,48 @@ __global__ void __launch_bounds__(256) evd2_kernel(const double *__restrict__ a1
 
 static int g_evd_block = 256;
 static int g_evd_blocks_per_sm = 8;
+static int g_evd_variant = 5;
+
+// Division/square-root placements (bit k: slot k on the integer pipe; see
+// evd2.cuh).  All give the same bits.
+constexpr int kEvdMasks[] = {
+    0x000,                                  // 0: every division and root on the FP64 pipe
+    0x7FF,                                  // 1: all on the integer pipe
+    0x7FF & ~(1 << 6),                      // 2: lambda2' on the FP64 pipe
+    0x7FF & ~((1 << 5) | (1 << 6)),         // 3: lambda1', lambda2' on the FP64 pipe
+    0x7FF & ~((1 << 4) | (1 << 5) | (1 << 6)),  // 4: and 1/sec
+    0x7FF & ~((1 << 1) | (1 << 3)),         // 5: both square roots on the FP64 pipe
+};
+constexpr int kEvdVariants = (int)(sizeof(kEvdMasks) / sizeof(kEvdMasks[0]));
+
+int evd2_set_variant(int v)
+{
+  if (v < 0 || v >= kEvdVariants) return -2;
+  g_evd_variant = v;
+  return JSVD_OK;
+}
+
+template <bool CPLX, int V>
+static void launch_v(int grid, int block, cudaStream_t st, const jsvd_evd2_streams *s, int64_t n)
+{
+  evd2_kernel<CPLX, kEvdMasks[V]><<<grid, block, 0, st>>>(
+      s->a11, s->a22, s->a21_re, CPLX ? s->a21_im : nullptr, s->cos_phi, s->ea_tan_re,
+      CPLX ? s->ea_tan_im : nullptr, s->lambda1, s->lambda2, s->zeta_p, n);
+}
+
+template <bool CPLX>
+static void launch_any(int v, int grid, int block, cudaStream_t st, const jsvd_evd2_streams *s,
+                       int64_t n)
+{
+  switch (v) {
+    case 0: launch_v<CPLX, 0>(grid, block, st, s, n); break;
+    case 1: launch_v<CPLX, 1>(grid, block, st, s, n); break;
+    case 2: launch_v<CPLX, 2>(grid, block, st, s, n); break;
+    case 3: launch_v<CPLX, 3>(grid, block, st, s, n); break;
+    case 4: launch_v<CPLX, 4>(grid, block, st, s, n); break;
+    default: launch_v<CPLX, 5>(grid, block, st, s, n); break;
+  }
+}
 
 int evd2_set_launch(int block, int blocks_per_sm)
 {
@@ -72,13 +117,9 @@ extern "C" int jsvd_evd2x2_batched(jsvd_field field, const jsvd_evd2_streams *s,
   const int grid = (int)(need < cap ? need : cap);
   cudaStream_t st = as_stream(stream);
   if (cplx)
-    evd2_kernel<true><<<grid, block, 0, st>>>(s->a11, s->a22, s->a21_re, s->a21_im, s->cos_phi,
-                                              s->ea_tan_re, s->ea_tan_im, s->lambda1,
-                                              s->lambda2, s->zeta_p, n);
+    launch_any<true>(g_evd_variant, grid, block, st, s, n);
   else
-    evd2_kernel<false><<<grid, block, 0, st>>>(s->a11, s->a22, s->a21_re, nullptr, s->cos_phi,
-                                               s->ea_tan_re, nullptr, s->lambda1, s->lambda2,
-                                               s->zeta_p, n);
+    launch_any<false>(g_evd_variant, grid, block, st, s, n);
   JSVD_CHECK_LAUNCH();
   return JSVD_OK;
 }

@@ -13,6 +13,7 @@
 // same result for the only NaNs that can arise (0/0).
 #pragma once
 #include "fp64bits.cuh"
+#include "fp64soft.cuh"
 
 namespace jsvd {
 
@@ -39,20 +40,65 @@ struct Rot2 {
   int zeta;      // Eq. e:z exponent
 };
 
+// Where each division and square root runs.  Bit SLOT of MASK set: the
+// integer-pipe routine of fp64soft.cuh; clear: the FP64 pipe's IEEE
+// instruction.  Both are correctly rounded, so every MASK gives the same
+// bits; the choice only balances the two pipes.  Slots:
+//   0 o/|a|   1 sqrt(tan2^2 + 1)   2 tan2/(1 + sqrt)   3 sqrt(sec^2)
+//   4 1/sec   5 lambda1' / sec^2   6 lambda2' / sec^2
+//   7 am/aM   8 sqrt(mM^2 + 1)     9 |Re a21'|/|a21'|  10 Im a21'/|a21'|
+template <int MASK, int SLOT>
+__device__ __forceinline__ double dv(double a, double b)
+{
+  if constexpr (((MASK >> SLOT) & 1) != 0) return soft::div_rn(a, b);
+  else return __ddiv_rn(a, b);
+}
+
+template <int MASK, int SLOT>
+__device__ __forceinline__ double sq(double x)
+{
+  if constexpr (((MASK >> SLOT) & 1) != 0) return soft::sqrt_rn(x);
+  else return __dsqrt_rn(x);
+}
+
 // The rotation part shared by the real and the complex case, from the
 // scaled a11', a22' and |a21'| (section 2.1).
+template <int MASK>
 __device__ __forceinline__ void rot_core(double a11, double a22, double aa21, double &tan1,
                                          double &sec2, double &o, double &cphi)
 {
   o = twice_abs(aa21);                          // o = 2|a21'|, exact
   const double a = __dsub_rn(a11, a22);
-  const double tan2 = clamp_tan2(__ddiv_rn(o, dabs(a)), a);
-  tan1 = __ddiv_rn(tan2, __dadd_rn(1.0, __dsqrt_rn(__fma_rn(tan2, tan2, 1.0))));
+  // Eq. e:tan2; |a| = 0 gives o/|a| = Inf (o > 0) or NaN (o = 0), which the
+  // clamp turns into fl(sqrt nu) or 0 -- selected here without dividing
+  const double aa = dabs(a);
+  const double q = (bits(aa) == 0ull) ? ((bits(o) == 0ull) ? 0.0 : dbl(kInf)) : dv<MASK, 0>(o, aa);
+  const double tan2 = clamp_tan2(q, a);
+  tan1 = dv<MASK, 2>(tan2, __dadd_rn(1.0, sq<MASK, 1>(__fma_rn(tan2, tan2, 1.0))));
   sec2 = __fma_rn(tan1, tan1, 1.0);
-  cphi = __drcp_rn(__dsqrt_rn(sec2));
+  cphi = dv<MASK, 4>(1.0, sq<MASK, 3>(sec2));
+}
+
+// Eq. e:lamsec: lambda1' and lambda2' (scaled).  When both divisions run on
+// the integer pipe they share the prepared divisor sec^2.
+template <int MASK>
+__device__ __forceinline__ void lambdas(Rot2 &r, double a11, double a22, double tan1, double sec2,
+                                        double o)
+{
+  const double n1 = __fma_rn(tan1, __fma_rn(a22, tan1, o), a11);
+  const double n2 = __fma_rn(tan1, __fma_rn(a11, tan1, -o), a22);
+  if constexpr (((MASK >> 5) & 1) != 0 && ((MASK >> 6) & 1) != 0) {
+    const soft::Den D = soft::prepare_den(sec2);
+    r.l1s = soft::div_rn(n1, D);
+    r.l2s = soft::div_rn(n2, D);
+  } else {
+    r.l1s = dv<MASK, 5>(n1, sec2);
+    r.l2s = dv<MASK, 6>(n2, sec2);
+  }
 }
 
 // Real symmetric matrix (Alg. d8jac2).
+template <int MASK>
 __device__ __forceinline__ Rot2 dsjac2(double a11, double a22, double a21)
 {
   Rot2 r;
@@ -62,15 +108,15 @@ __device__ __forceinline__ Rot2 dsjac2(double a11, double a22, double a21)
   a22 = ldexp_rn(a22, r.zeta);
   a21 = ldexp_rn(a21, r.zeta);
   double tan1, sec2, o;
-  rot_core(a11, a22, dabs(a21), tan1, sec2, o, r.cphi);
+  rot_core<MASK>(a11, a22, dabs(a21), tan1, sec2, o, r.cphi);
   r.etr = xor_sign(tan1, a21);
   r.eti = 0.0;
-  r.l1s = __ddiv_rn(__fma_rn(tan1, __fma_rn(a22, tan1, o), a11), sec2);
-  r.l2s = __ddiv_rn(__fma_rn(tan1, __fma_rn(a11, tan1, -o), a22), sec2);
+  lambdas<MASK>(r, a11, a22, tan1, sec2, o);
   return r;
 }
 
 // Complex Hermitian matrix (Listing 1).
+template <int MASK>
 __device__ __forceinline__ Rot2 zsjac2(double a11, double a22, double a21r, double a21i)
 {
   Rot2 r;
@@ -85,18 +131,21 @@ __device__ __forceinline__ Rot2 zsjac2(double a11, double a22, double a21r, doub
   const bool rmin = bits(ar) <= bits(ai);
   const double am = rmin ? ar : ai, aM = rmin ? ai : ar;
   const bool zero = (bits(aM) == 0ull);
-  const double mM = zero ? 0.0 : __ddiv_rn(am, aM);              // fmax(am/aM, 0)
-  const double aa21 = __dmul_rn(__dsqrt_rn(__fma_rn(mM, mM, 1.0)), aM);
-  const double ca = with_sign(zero ? 1.0 : __ddiv_rn(ar, aa21), a21r);  // fmin(., 1)
-  const double sa = zero ? a21i : __ddiv_rn(a21i, aa21);        // / fmax(|a21|, mu)
+  const double mM = zero ? 0.0 : dv<MASK, 7>(am, aM);              // fmax(am/aM, 0)
+  const double aa21 = __dmul_rn(sq<MASK, 8>(__fma_rn(mM, mM, 1.0)), aM);
+  const double ca = with_sign(zero ? 1.0 : dv<MASK, 9>(ar, aa21), a21r);  // fmin(., 1)
+  const double sa = zero ? a21i : dv<MASK, 10>(a21i, aa21);        // / fmax(|a21|, mu)
   double tan1, sec2, o;
-  rot_core(a11, a22, aa21, tan1, sec2, o, r.cphi);
+  rot_core<MASK>(a11, a22, aa21, tan1, sec2, o, r.cphi);
   r.etr = __dmul_rn(ca, tan1);
   r.eti = __dmul_rn(sa, tan1);
-  r.l1s = __ddiv_rn(__fma_rn(tan1, __fma_rn(a22, tan1, o), a11), sec2);
-  r.l2s = __ddiv_rn(__fma_rn(tan1, __fma_rn(a11, tan1, -o), a22), sec2);
+  lambdas<MASK>(r, a11, a22, tan1, sec2, o);
   return r;
 }
+
+// The division placement used inside the SVD kernels, where the FP64 pipe
+// is busy with the column work: everything on the integer pipe.
+constexpr int kMaskAllSoft = 0x7FF;
 
 // p = (lambda1' < lambda2'), as an IEEE comparison (lambda' finite).
 __device__ __forceinline__ int perm_bit(const Rot2 &r) { return ord(r.l1s) < ord(r.l2s); }

@@ -110,8 +110,8 @@ __device__ __forceinline__ double hypot_naive(double x, double y)
   const double ax = dabs(x), ay = dabs(y);
   const bool xm = bits(ax) <= bits(ay);
   const double m = xm ? ax : ay, M = xm ? ay : ax;
-  const double q = (bits(M) == 0ull) ? 0.0 : __ddiv_rn(m, M);
-  return __dmul_rn(__dsqrt_rn(__fma_rn(q, q, 1.0)), M);
+  const double q = (bits(M) == 0ull) ? 0.0 : soft::div_rn(m, M);
+  return __dmul_rn(soft::sqrt_rn(__fma_rn(q, q, 1.0)), M);
 }
 
 // x 2^k for the FP32 phase (never used with k != 0 there: that phase does
@@ -130,8 +130,10 @@ struct PairOut {
   double c, C, S;
 };
 
-// Lane-0 part: from the sums to the rotation (Alg. zdpscl's division,
-// Alg. cvg, Alg. Gram, the EVD).  spp = ||g_p||^2, sqq = ||g_q||^2,
+// From the sums to the rotation (Alg. zdpscl's division, Alg. cvg,
+// Alg. Gram, the EVD); its divisions and square roots run on the integer
+// pipe (fp64soft.cuh, correctly rounded), leaving the FP64 pipe to the
+// column work.  spp = ||g_p||^2, sqq = ||g_q||^2,
 // (sqr, sqi) = g_q^* g_p, all of the current (scaled) G.
 template <bool CPLX>
 __device__ __forceinline__ PairOut pair_rotation(double spp, double sqq, double sqr, double sqi,
@@ -148,17 +150,17 @@ __device__ __forceinline__ PairOut pair_rotation(double spp, double sqq, double 
     return o;
   }
   // (e,f) norms: ||g_j|| = 2^e_j f_j, 1 <= f_j < 2
-  const double rp = __dsqrt_rn(spp), rq = __dsqrt_rn(sqq);
+  const double rp = soft::sqrt_rn(spp), rq = soft::sqrt_rn(sqq);
   const int ep = flg(rp), eq = flg(rq);
   const double fp = ldexp_rn(rp, -ep), fq = ldexp_rn(rq, -eq);
   // a21' = (g_q/2^eq)^* (g_p/2^ep) / (f_q f_p)
   const double d = __dmul_rn(fq, fp);
-  const double zr = __ddiv_rn(ldexp_rn(sqr, -(ep + eq)), d);
-  const double zi = CPLX ? __ddiv_rn(ldexp_rn(sqi, -(ep + eq)), d) : 0.0;
+  const double zr = soft::div_rn(ldexp_rn(sqr, -(ep + eq)), d);
+  const double zi = CPLX ? soft::div_rn(ldexp_rn(sqi, -(ep + eq)), d) : 0.0;
   const double az = CPLX ? hypot_naive(zr, zi) : dabs(zr);
   o.rot = !(ord(az) < ord(ups));
   // Alg. Gram
-  double f12 = __ddiv_rn(fp, fq), f21 = __ddiv_rn(fq, fp);
+  double f12 = soft::div_rn(fp, fq), f21 = soft::div_rn(fq, fp);
   int e12 = ep - eq + flg(f12), e21 = eq - ep + flg(f21);
   f12 = ldexp_rn(f12, -flg(f12));
   f21 = ldexp_rn(f21, -flg(f21));
@@ -167,9 +169,9 @@ __device__ __forceinline__ PairOut pair_rotation(double spp, double sqq, double 
   const double b21r = ldexp_rn(zr, sA);
   Rot2 r;
   if (CPLX) {
-    r = zsjac2(b11, b22, b21r, ldexp_rn(zi, sA));
+    r = zsjac2<kMaskAllSoft>(b11, b22, b21r, ldexp_rn(zi, sA));
   } else {
-    r = dsjac2(b11, b22, b21r);
+    r = dsjac2<kMaskAllSoft>(b11, b22, b21r);
   }
   o.swap = perm_bit(r) != 0;
   o.c = r.cphi;

@@ -1,0 +1,99 @@
+// Host check of the integer-pipe binary64 division and square root
+// (paper_2202_08361_gb300/csrc/fp64soft.cuh) against the host's IEEE
+// arithmetic (SSE2 / AArch64 FP: correctly rounded to nearest even).
+// Usage: soft_fp64_check N seed -> prints "div_bad sqrt_bad" and exits 0.
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+
+#include "fp64soft.cuh"
+
+static uint64_t s_state;
+static uint64_t rnd()
+{
+  // splitmix64
+  uint64_t z = (s_state += 0x9E3779B97F4A7C15ull);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+static double bitsd(uint64_t u)
+{
+  double x;
+  memcpy(&x, &u, 8);
+  return x;
+}
+static uint64_t dbits(double x)
+{
+  uint64_t u;
+  memcpy(&u, &x, 8);
+  return u;
+}
+
+// finite doubles from several families
+static double draw()
+{
+  const uint64_t r = rnd();
+  switch (r & 7) {
+    case 0: {  // any finite bit pattern
+      uint64_t u;
+      do u = rnd(); while (((u >> 52) & 0x7FF) == 0x7FF);
+      return bitsd(u);
+    }
+    case 1:  // subnormal
+      return bitsd((rnd() & 0x000FFFFFFFFFFFFFull) | (rnd() & 0x8000000000000000ull));
+    case 2:  // moderate exponents
+      return ldexp(1.0 + (double)(rnd() >> 11) * 0x1p-53, (int)(rnd() % 200) - 100);
+    case 3:  // powers of two and their neighbours
+      return nextafter(ldexp(1.0, (int)(rnd() % 2090) - 1074), (rnd() & 1) ? INFINITY : 0.0);
+    case 4:  // mantissas with few bits set (exact quotients likely)
+      return ldexp((double)((rnd() % 4096) + 1), (int)(rnd() % 100) - 50);
+    case 5:  // near the top of the range
+      return ldexp(1.0 + (double)(rnd() >> 11) * 0x1p-53, 1000 + (int)(rnd() % 23));
+    case 6:  // near the bottom of the normal range
+      return ldexp(1.0 + (double)(rnd() >> 11) * 0x1p-53, -1022 + (int)(rnd() % 60));
+    default:
+      return (double)(rnd() >> 11) * 0x1p-53 + 1.0;
+  }
+}
+
+int main(int argc, char **argv)
+{
+  const long n = argc > 1 ? atol(argv[1]) : 1000000;
+  s_state = argc > 2 ? strtoull(argv[2], nullptr, 10) : 1;
+  long bad_div = 0, bad_sqrt = 0;
+  for (long i = 0; i < n; ++i) {
+    double a = draw(), b = draw();
+    if (b == 0.0) b = 1.0;
+    // also near-ties: a = q b rounded, for q with a 53-bit mantissa
+    if ((i & 15) == 0) {
+      const double q = ldexp(1.0 + (double)(rnd() >> 11) * 0x1p-53, (int)(rnd() % 40) - 20);
+      a = q * b;
+      if (!std::isfinite(a) || a == 0.0) a = 1.0;
+    }
+    const double ref = a / b;
+    const double got = jsvd::soft::div_rn(a, b);
+    if (dbits(ref) != dbits(got)) {
+      if (bad_div < 5)
+        fprintf(stderr, "div %a / %a: ref %a got %a\n", a, b, ref, got);
+      ++bad_div;
+    }
+    double x = fabs(draw());
+    if ((i & 7) == 0) {  // squares and their neighbours
+      const double s = fabs(draw());
+      x = s * s;
+      if (!std::isfinite(x)) x = 2.0;
+      if (rnd() & 1) x = nextafter(x, (rnd() & 1) ? INFINITY : 0.0);
+    }
+    const double rs = sqrt(x);
+    const double gs = jsvd::soft::sqrt_rn(x);
+    if (dbits(rs) != dbits(gs)) {
+      if (bad_sqrt < 5) fprintf(stderr, "sqrt %a: ref %a got %a\n", x, rs, gs);
+      ++bad_sqrt;
+    }
+  }
+  printf("%ld %ld\n", bad_div, bad_sqrt);
+  return 0;
+}
