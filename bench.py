@@ -338,11 +338,10 @@ def run_ours(args):
     import torch
 
     import paper_2202_08361_gb300 as J
+    from paper_2202_08361_gb300 import dist as D
     from paper_2202_08361_gb300 import workloads
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    world, rank, local_rank = D.rank_env()
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -353,8 +352,8 @@ def run_ours(args):
     stream = torch.cuda.current_stream(dev)
 
     # inputs resident in HBM before the timed region; each rank its own shard
-    host_re = workloads.evd_batch(R_EVD, False, seed_salt=rank)
-    host_cx = workloads.evd_batch(R_EVD, True, seed_salt=rank)
+    host_re = workloads.evd_batch(R_EVD, False, seed_salt=D.evd_seed_salt(rank))
+    host_cx = workloads.evd_batch(R_EVD, True, seed_salt=D.evd_seed_salt(rank))
     d_re = [torch.from_numpy(a).to(dev) for a in host_re]
     d_cx = [torch.from_numpy(a).to(dev) for a in host_cx]
     out_re = J.evd2x2_batched(*d_re)
@@ -399,12 +398,8 @@ def run_ours(args):
     t_cplx = sum(e[1].elapsed_time(e[2]) for e in evs) / K
     gpu_launches = 2 * K
 
-    if dist is not None:
-        t = torch.tensor([ms_total], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    value, _, ms_total = D.aggregate_rate(2 * R_EVD * K, ms_total, dist, dev)
     ms_per_step = ms_total / K
-    value = world * 2 * R_EVD / (ms_per_step * 1e-3)
 
     # end to end through the public API: pinned host -> device, kernels,
     # device -> pinned host, every step
@@ -438,12 +433,7 @@ def run_ours(args):
     e1.record(stream)
     torch.cuda.synchronize(dev)
     barrier()
-    e2e_ms = e0.elapsed_time(e1) / E
-    if dist is not None:
-        t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_value = world * 2 * R_EVD / (e2e_ms * 1e-3)
+    e2e_value, _, e2e_ms = D.aggregate_rate(2 * R_EVD, e0.elapsed_time(e1) / E, dist, dev)
 
     peaks, peak_kind = measured_peaks()
     dom_name, dom_ms, dom_bytes = (("evd2_kernel<complex>", t_cplx, BYTES_CPLX * R_EVD)
