@@ -74,9 +74,10 @@ JSVD_API const char *jsvd_last_cuda_error(void);
  *     kernel (1, 2, 4, 8 or 16; default 8). */
 #define JSVD_TUNE_BATCH_WARPS 3
 /*   JSVD_TUNE_EVD_ARITH: value = which of the 2x2 EVD's divisions and
- *     square roots run on the integer pipe instead of the FP64 pipe (0..5;
- *     default 5: the divisions).  Both are correctly rounded: the results
- *     are identical. */
+ *     square roots run on the integer pipe instead of the FP64 pipe (0..7;
+ *     -1 = the default, 6 for real and 5 for complex matrices); value2 =
+ *     the fields it applies to (0 both, 1 real, 2 complex).  Both pipes
+ *     round correctly: the results are identical. */
 #define JSVD_TUNE_EVD_ARITH 4
 JSVD_API int jsvd_tune_set(int knob, int value, int value2);
 

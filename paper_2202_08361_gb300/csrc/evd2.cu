@@ -7,46 +7,57 @@
 // independent, so any grid shape and any sub-range give the same bits.
 // The divisions and square roots are split between the FP64 pipe and the
 // integer pipe (correctly rounded either way) so that the two narrow pipes
-// share the work.
+// share the work.  (Splitting one launch between warps of two placements was
+// measured slower than either alone: the two code paths double the kernel's
+// instruction footprint, and instruction-fetch stalls grow.)
 #include "common.cuh"
 #include "evd2.cuh"
 #include "jsvd_internal.h"
 
 namespace jsvd {
 
+struct EvdPtrs {
+  const double *a11, *a22, *a21r, *a21i;
+  double *cphi, *etr, *eti, *l1, *l2;
+  int32_t *zp;
+};
+
+// Elements i, i + stride, ... below n, with one division placement.
 template <bool CPLX, int MASK>
-__global__ void __launch_bounds__(256) evd2_kernel(const double *__restrict__ a11p,
-                                                   const double *__restrict__ a22p,
-                                                   const double *__restrict__ a21rp,
-                                                   const double *__restrict__ a21ip,
-                                                   double *__restrict__ cphip,
-                                                   double *__restrict__ etrp,
-                                                   double *__restrict__ etip,
-                                                   double *__restrict__ l1p,
-                                                   double *__restrict__ l2p,
-                                                   int32_t *__restrict__ zpp, int64_t n)
+__device__ __forceinline__ void evd2_range(int64_t i, int64_t stride, int64_t n, const EvdPtrs &p)
 {
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    const double a11 = __ldcs(a11p + i), a22 = __ldcs(a22p + i), a21r = __ldcs(a21rp + i);
+  for (; i < n; i += stride) {
+    const double a11 = __ldcs(p.a11 + i), a22 = __ldcs(p.a22 + i), a21r = __ldcs(p.a21r + i);
     Rot2 r;
     if (CPLX) {
-      r = zsjac2<MASK>(a11, a22, a21r, __ldcs(a21ip + i));
+      r = zsjac2<MASK>(a11, a22, a21r, __ldcs(p.a21i + i));
     } else {
       r = dsjac2<MASK>(a11, a22, a21r);
     }
-    __stcs(cphip + i, r.cphi);
-    __stcs(etrp + i, r.etr);
-    if (CPLX) __stcs(etip + i, r.eti);
-    if (l1p) __stcs(l1p + i, ldexp_rn(r.l1s, -r.zeta));
-    if (l2p) __stcs(l2p + i, ldexp_rn(r.l2s, -r.zeta));
-    if (zpp) __stcs(zpp + i, pack_zp(r));
+    __stcs(p.cphi + i, r.cphi);
+    __stcs(p.etr + i, r.etr);
+    if (CPLX) __stcs(p.eti + i, r.eti);
+    if (p.l1) __stcs(p.l1 + i, ldexp_rn(r.l1s, -r.zeta));
+    if (p.l2) __stcs(p.l2 + i, ldexp_rn(r.l2s, -r.zeta));
+    if (p.zp) __stcs(p.zp + i, pack_zp(r));
   }
+}
+
+// 256-thread blocks, JSVD_EVD_MIN_BLOCKS resident per SM asked of the
+// register allocator: 8 (32 registers) measured fastest for the complex
+// kernel and within noise of the best for the real one.
+#ifndef JSVD_EVD_MIN_BLOCKS
+#define JSVD_EVD_MIN_BLOCKS 8
+#endif
+template <bool CPLX, int MASK>
+__global__ void __launch_bounds__(256, JSVD_EVD_MIN_BLOCKS) evd2_kernel(EvdPtrs p, int64_t n)
+{
+  evd2_range<CPLX, MASK>((int64_t)blockIdx.x * blockDim.x + threadIdx.x,
+                         (int64_t)gridDim.x * blockDim.x, n, p);
 }
 
 static int g_evd_block = 256;
 static int g_evd_blocks_per_sm = 8;
-static int g_evd_variant = 5;
 
 // Division/square-root placements (bit k: slot k on the integer pipe; see
 // evd2.cuh).  All give the same bits.
@@ -56,36 +67,35 @@ constexpr int kEvdMasks[] = {
     0x7FF & ~(1 << 6),                      // 2: lambda2' on the FP64 pipe
     0x7FF & ~((1 << 5) | (1 << 6)),         // 3: lambda1', lambda2' on the FP64 pipe
     0x7FF & ~((1 << 4) | (1 << 5) | (1 << 6)),  // 4: and 1/sec
-    0x7FF & ~((1 << 1) | (1 << 3)),         // 5: both square roots on the FP64 pipe
+    0x7FF & ~((1 << 1) | (1 << 3)),         // 5: both rotation square roots on the FP64 pipe
+    0x7FF & ~(1 << 3),                      // 6: sqrt(sec^2) on the FP64 pipe
+    0x7FF & ~(1 << 1),                      // 7: sqrt(tan2^2 + 1) on the FP64 pipe
 };
-constexpr int kEvdVariants = (int)(sizeof(kEvdMasks) / sizeof(kEvdMasks[0]));
+constexpr int kEvdPlacements = (int)(sizeof(kEvdMasks) / sizeof(kEvdMasks[0]));
 
-int evd2_set_variant(int v)
+// Default placement per field (real, complex), the fastest measured on
+// 2^24 wide-range matrices: the real kernel keeps only sqrt(sec^2) on the
+// FP64 pipe, the complex one both rotation square roots.
+constexpr int kEvdDefault[2] = {6, 5};
+static int g_evd_placement[2] = {kEvdDefault[0], kEvdDefault[1]};
+
+int evd2_set_variant(int v, int fields)
 {
-  if (v < 0 || v >= kEvdVariants) return -2;
-  g_evd_variant = v;
+  if (fields < 0 || fields > 2) return -3;
+  if (v != -1 && (v < 0 || v >= kEvdPlacements)) return -2;
+  for (int f = 0; f < 2; ++f)
+    if (fields == 0 || fields == f + 1) g_evd_placement[f] = (v == -1) ? kEvdDefault[f] : v;
   return JSVD_OK;
 }
 
-template <bool CPLX, int V>
-static void launch_v(int grid, int block, cudaStream_t st, const jsvd_evd2_streams *s, int64_t n)
+template <bool CPLX, int V = 0>
+static void launch_any(int v, int grid, int block, cudaStream_t st, const EvdPtrs &p, int64_t n)
 {
-  evd2_kernel<CPLX, kEvdMasks[V]><<<grid, block, 0, st>>>(
-      s->a11, s->a22, s->a21_re, CPLX ? s->a21_im : nullptr, s->cos_phi, s->ea_tan_re,
-      CPLX ? s->ea_tan_im : nullptr, s->lambda1, s->lambda2, s->zeta_p, n);
-}
-
-template <bool CPLX>
-static void launch_any(int v, int grid, int block, cudaStream_t st, const jsvd_evd2_streams *s,
-                       int64_t n)
-{
-  switch (v) {
-    case 0: launch_v<CPLX, 0>(grid, block, st, s, n); break;
-    case 1: launch_v<CPLX, 1>(grid, block, st, s, n); break;
-    case 2: launch_v<CPLX, 2>(grid, block, st, s, n); break;
-    case 3: launch_v<CPLX, 3>(grid, block, st, s, n); break;
-    case 4: launch_v<CPLX, 4>(grid, block, st, s, n); break;
-    default: launch_v<CPLX, 5>(grid, block, st, s, n); break;
+  if constexpr (V < kEvdPlacements) {
+    if (v == V)
+      evd2_kernel<CPLX, kEvdMasks[V]><<<grid, block, 0, st>>>(p, n);
+    else
+      launch_any<CPLX, V + 1>(v, grid, block, st, p, n);
   }
 }
 
@@ -116,10 +126,12 @@ extern "C" int jsvd_evd2x2_batched(jsvd_field field, const jsvd_evd2_streams *s,
   const int64_t cap = (int64_t)sm_count() * g_evd_blocks_per_sm;
   const int grid = (int)(need < cap ? need : cap);
   cudaStream_t st = as_stream(stream);
+  const EvdPtrs p{s->a11, s->a22, s->a21_re, cplx ? s->a21_im : nullptr, s->cos_phi, s->ea_tan_re,
+                  cplx ? s->ea_tan_im : nullptr, s->lambda1, s->lambda2, s->zeta_p};
   if (cplx)
-    launch_any<true>(g_evd_variant, grid, block, st, s, n);
+    launch_any<true>(g_evd_placement[1], grid, block, st, p, n);
   else
-    launch_any<false>(g_evd_variant, grid, block, st, s, n);
+    launch_any<false>(g_evd_placement[0], grid, block, st, p, n);
   JSVD_CHECK_LAUNCH();
   return JSVD_OK;
 }

@@ -133,8 +133,17 @@ __device__ __forceinline__ Rot2 zsjac2(double a11, double a22, double a21r, doub
   const bool zero = (bits(aM) == 0ull);
   const double mM = zero ? 0.0 : dv<MASK, 7>(am, aM);              // fmax(am/aM, 0)
   const double aa21 = __dmul_rn(sq<MASK, 8>(__fma_rn(mM, mM, 1.0)), aM);
-  const double ca = with_sign(zero ? 1.0 : dv<MASK, 9>(ar, aa21), a21r);  // fmin(., 1)
-  const double sa = zero ? a21i : dv<MASK, 10>(a21i, aa21);        // / fmax(|a21|, mu)
+  double qc, qs;  // |Re a21'| / |a21'| and Im a21' / |a21'|
+  if constexpr (((MASK >> 9) & 1) != 0 && ((MASK >> 10) & 1) != 0) {
+    const soft::Den D = soft::prepare_den(aa21);  // one divisor, prepared once
+    qc = soft::div_rn(ar, D);
+    qs = soft::div_rn(a21i, D);
+  } else {
+    qc = dv<MASK, 9>(ar, aa21);
+    qs = dv<MASK, 10>(a21i, aa21);
+  }
+  const double ca = with_sign(zero ? 1.0 : qc, a21r);  // fmin(., 1)
+  const double sa = zero ? a21i : qs;                  // / fmax(|a21|, mu)
   double tan1, sec2, o;
   rot_core<MASK>(a11, a22, aa21, tan1, sec2, o, r.cphi);
   r.etr = __dmul_rn(ca, tan1);

@@ -4,7 +4,7 @@
 
 namespace jsvd {
 int evd2_set_launch(int block, int blocks_per_sm);
-int evd2_set_variant(int v);
+int evd2_set_variant(int v, int fields);
 int svd_set_grid(int cap, int warps);
 int batch_set_warps(int w);
 }  // namespace jsvd

@@ -62,3 +62,8 @@ def test_argument_errors_need_no_gpu(lib):
     assert L.jsvd_tune_set(99, 0, 0) == -1
     assert L.jsvd_tune_set(1, 100, 8) == -2
     assert L.jsvd_tune_set(1, 256, 0) == -3
+    assert L.jsvd_tune_set(4, 8, 0) == -2           # placements are 0..7
+    assert L.jsvd_tune_set(4, -2, 0) == -2
+    assert L.jsvd_tune_set(4, 1, 3) == -3           # fields: 0, 1 or 2
+    assert L.jsvd_tune_set(4, 1, 2) == 0
+    assert L.jsvd_tune_set(4, -1, 0) == 0           # back to the defaults

@@ -34,26 +34,42 @@ def test_device_against_fp64_pipe():
     assert bad.tolist() == [0, 0]
 
 
+def _check_evd_against_oracle(J, salt, tag):
+    import torch
+    import oracle
+    from paper_2202_08361_gb300 import workloads
+    for cplx in (False, True):
+        streams = workloads.evd_batch(1 << 18, cplx, seed_salt=salt)
+        t = [torch.from_numpy(a).cuda() for a in streams]
+        out = J.evd2x2_batched(t[0], t[1], t[2], t[3] if cplx else None)
+        ref = oracle.zsjac2(*streams) if cplx else oracle.dsjac2(*streams)
+        keys = (["cos_phi", "ea_tan_re", "ea_tan_im", "lambda1", "lambda2", "zeta_p"] if cplx
+                else ["cos_phi", "ea_tan_re", "lambda1", "lambda2", "zeta_p"])
+        for k, r in zip(keys, ref):
+            g = out[k].cpu().numpy()
+            assert np.array_equal(g.view(np.uint8), np.asarray(r).view(np.uint8)), (tag, cplx, k)
+
+
 @pytest.mark.gpu
-@pytest.mark.parametrize("variant", range(6))
+@pytest.mark.parametrize("variant", range(8))
 def test_evd_division_placements_bit_identical(variant):
     """Every placement of the EVD's divisions and roots gives the oracle's
     bits (the placement is a launch knob, not an arithmetic choice)."""
-    import torch
-    import oracle
     import paper_2202_08361_gb300 as J
-    from paper_2202_08361_gb300 import workloads
     try:
         J.tune_set(J.JSVD_TUNE_EVD_ARITH, variant)
-        for cplx in (False, True):
-            streams = workloads.evd_batch(1 << 18, cplx, seed_salt=variant)
-            t = [torch.from_numpy(a).cuda() for a in streams]
-            out = J.evd2x2_batched(t[0], t[1], t[2], t[3] if cplx else None)
-            ref = oracle.zsjac2(*streams) if cplx else oracle.dsjac2(*streams)
-            keys = (["cos_phi", "ea_tan_re", "ea_tan_im", "lambda1", "lambda2", "zeta_p"] if cplx
-                    else ["cos_phi", "ea_tan_re", "lambda1", "lambda2", "zeta_p"])
-            for k, r in zip(keys, ref):
-                g = out[k].cpu().numpy()
-                assert np.array_equal(g.view(np.uint8), np.asarray(r).view(np.uint8)), (variant, k)
+        _check_evd_against_oracle(J, variant, variant)
     finally:
-        J.tune_set(J.JSVD_TUNE_EVD_ARITH, 5)
+        J.tune_set(J.JSVD_TUNE_EVD_ARITH, -1)
+
+
+@pytest.mark.gpu
+def test_evd_per_field_placements_bit_identical():
+    """Different placements for the real and the complex kernel."""
+    import paper_2202_08361_gb300 as J
+    try:
+        J.tune_set(J.JSVD_TUNE_EVD_ARITH, 7, 1)
+        J.tune_set(J.JSVD_TUNE_EVD_ARITH, 1, 2)
+        _check_evd_against_oracle(J, 77, "real 7, complex 1")
+    finally:
+        J.tune_set(J.JSVD_TUNE_EVD_ARITH, -1)
