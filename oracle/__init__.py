@@ -45,8 +45,12 @@ def lib():
         L.orc_pairs.argtypes = [ctypes.c_int, _i32]
         L.orc_pairs.restype = ctypes.c_int
         L.orc_vjsvd.argtypes = [ctypes.c_int64, ctypes.c_int64, _d, _d, ctypes.c_int64, _d, _d,
-                                _d, _d, _d, ctypes.c_int, ctypes.c_int, ctypes.c_int, _i32, _i64]
+                                _d, _d, _d, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                _i32, _i64]
         L.orc_vjsvd.restype = ctypes.c_int
+        L.orc_dpscl.argtypes = [ctypes.c_int64, _d, _d, _d, _d, ctypes.c_int, ctypes.c_double,
+                                ctypes.c_int, ctypes.c_double, ctypes.c_int, _d]
+        L.orc_dpscl.restype = ctypes.c_int
         L.orc_svd_adjoint.argtypes = [ctypes.c_int64, ctypes.c_int64, _d, _d, _d, _d, _d, _d, _d]
         L.orc_svd_adjoint.restype = ctypes.c_int
         L.orc_num_threads.restype = ctypes.c_int
@@ -110,9 +114,10 @@ def pairs(n):
     return tab[: nt - 1] if nt >= 2 else tab[:0]
 
 
-def vjsvd(A, max_sweeps=100, nthreads=0, permute=False):
+def vjsvd(A, max_sweeps=100, nthreads=0, permute=False, compensated=False):
     """One-sided Jacobi SVD of A (m x n, m >= n; real or complex).  permute
-    applies the column swap P of section 2 during the sweeps.
+    applies the column swap P of section 2 during the sweeps; compensated
+    forms the scaled dot-products by Alg. zdpscl' / ddpscl'.
 
     Returns dict(U, sigma, sigma_e, sigma_f, V, status, sweeps, rotations,
     rescales).  sigma is sorted non-increasingly; A ~= U diag(sigma) V^H.
@@ -128,7 +133,8 @@ def vjsvd(A, max_sweeps=100, nthreads=0, permute=False):
     info = np.zeros(4, dtype=np.int32)
     rot = np.zeros(1, dtype=np.int64)
     rc = lib().orc_vjsvd(m, n, _dp(Gr), _dp(Gi), m, _dp(Vr), _dp(Vi), _dp(sig), _dp(se),
-                         _dp(sf), int(max_sweeps), 1 if permute else 0, int(nthreads),
+                         _dp(sf), int(max_sweeps), 1 if permute else 0,
+                         1 if compensated else 0, int(nthreads),
                          info.ctypes.data_as(_i32),
                          rot.ctypes.data_as(_i64))
     if rc < 0:
@@ -138,6 +144,24 @@ def vjsvd(A, max_sweeps=100, nthreads=0, permute=False):
     return dict(U=U, sigma=sig, sigma_e=se, sigma_f=sf,
                 V=V, status=int(info[0]), sweeps=int(info[1]), rotations=int(rot[0]),
                 rescales=int(info[3]))
+
+
+def dpscl(q, p, compensated=False, eq=0, fq=1.0, ep=0, fp=1.0):
+    """z = q^* p / (2^(eq + ep) fq fp) by Alg. zdpscl, or Alg. zdpscl' /
+    ddpscl' (compensated); q, p real or complex vectors of one length.  The
+    default norms make it the dot-product q^* p itself."""
+    q = np.asarray(q)
+    p = np.asarray(p)
+    cplx = np.iscomplexobj(q) or np.iscomplexobj(p)
+    qr, pr = _f64(q.real), _f64(p.real)
+    qi = _f64(q.imag) if cplx else None
+    pi = _f64(p.imag) if cplx else None
+    out = np.zeros(2)
+    rc = lib().orc_dpscl(len(qr), _dp(qr), _dp(qi), _dp(pr), _dp(pi), int(eq), float(fq), int(ep),
+                         float(fp), 1 if compensated else 0, _dp(out))
+    if rc != 0:
+        raise ValueError("orc_dpscl failed with %d" % rc)
+    return complex(out[0], out[1]) if cplx else out[0]
 
 
 def svd_adjoint(U, s, V, Ubar, sbar, Vbar=None):

@@ -18,7 +18,9 @@
  *                            (section 4.3), real or complex (split planes),
  *                            with the rescaling heuristic of section 3.2,
  *                            the scaled dot-products of Alg. zdpscl
- *                            (section 3.3), the convergence test of Eq.
+ *                            (section 3.3) or, optionally, Alg. zdpscl' /
+ *                            ddpscl' (compensated, supplement SM2.2),
+ *                            the convergence test of Eq.
  *                            "e:tol", the scaled Grammians of Alg. Gram
  *                            (section 3.4) and the transformations of
  *                            Eq. "e:transf" / Alg. zjrot (section 3.5).
@@ -239,6 +241,12 @@ ORC_EXPORT int orc_pairs(int n, int32_t *tab)
 /* ------------------------------------------------------------------------
  * One-sided Jacobi SVD (Alg. zvjsvd, section 4.3). */
 
+/* Return codes shared with tests (not with the library). */
+#define ORC_OK 0
+#define ORC_E_ARG (-1)
+#define ORC_E_NONFINITE (-2)
+#define ORC_NOT_CONVERGED 1
+
 /* floor(lg x) for finite x > 0 (the AVX-512 getexp). */
 static int flg(double x)
 {
@@ -311,6 +319,82 @@ static void zdpscl(int64_t m, const double *qr, const double *qi, const double *
   const double d = fq * fp;
   *zr = re / d;
   *zi = im / d;
+}
+
+/* Eq. "e:d2sum" (2Sum): a + b = s + t exactly, s = fl(a + b). */
+static void two_sum(double a, double b, double *s, double *t)
+{
+  const double ss = a + b;
+  double a1 = ss - b;
+  double b1 = ss - a1;
+  a1 = a - a1;
+  b1 = b - b1;
+  *s = ss;
+  *t = a1 + b1;
+}
+
+/* RD(a b), the product rounded toward -infinity.  With p = RN(a b) and its
+ * exact residual r = a b - p (one fma), RD(a b) is p when r >= 0 and the
+ * next double below p otherwise (RN picks RD or RU). */
+static double mul_rd(double a, double b)
+{
+  const double p = a * b;
+  const double r = fma(a, b, -p);
+  return (r < 0.0) ? nextafter(p, -INFINITY) : p;
+}
+
+/* One term x y of a compensated stream (supplement SM2.2, items G, M and
+ * K): c = RD(x y), c' = x y - c >= 0 (one fma), then Kahan's summation with
+ * 2Sum on the value stream (s, t) and on the error stream (s', t'). */
+static void comp_term(double x, double y, double *s, double *t, double *s2, double *t2)
+{
+  const double c = mul_rd(x, y);
+  const double c2 = fma(x, y, -c);
+  two_sum(*s, c + *t, s, t);
+  two_sum(*s2, c2 + *t2, s2, t2);
+}
+
+/* Alg. zdpscl' (complex) and Alg. ddpscl' (real): the scaled dot-product of
+ * Alg. zdpscl with the compensated summation, one stream pair per
+ * component, reduced as s + (t + (s' + t')), then one division by
+ * f_q f_p.  Reading: the imaginary stream accumulates Re g_q Im g_p -
+ * Im g_q Re g_p, the imaginary part of the g_q^* g_p that the algorithm's
+ * output line defines (the printed loop forms its conjugate). */
+static void zdpscl_comp(int64_t m, const double *qr, const double *qi, const double *pr,
+                        const double *pi, int eq, double fq, int ep, double fp, double *zr,
+                        double *zi)
+{
+  double rs = 0.0, rt = 0.0, rs2 = 0.0, rt2 = 0.0;
+  double is = 0.0, it = 0.0, is2 = 0.0, it2 = 0.0;
+  for (int64_t i = 0; i < m; ++i) {
+    const double gqr = ldexp(qr[i], -eq), gpr = ldexp(pr[i], -ep);
+    comp_term(gpr, gqr, &rs, &rt, &rs2, &rt2);
+    if (qi) {
+      const double gqi = ldexp(qi[i], -eq), gpi = ldexp(pi[i], -ep);
+      comp_term(gpi, gqi, &rs, &rt, &rs2, &rt2);
+      comp_term(gpi, gqr, &is, &it, &is2, &it2);
+      comp_term(-gpr, gqi, &is, &it, &is2, &it2);
+    }
+  }
+  const double d = fq * fp;
+  *zr = (rs + (rt + (rs2 + rt2))) / d;
+  *zi = qi ? (is + (it + (is2 + it2))) / d : 0.0;
+}
+
+/* The scaled dot-product alone (for the tests): z = g_q^* g_p / (2^(e_q +
+ * e_p) f_q f_p) by Alg. zdpscl (compensated == 0) or Alg. zdpscl'
+ * (compensated != 0), for given norms (e, f); with e = 0 and f = 1 this is
+ * the dot-product itself.  out[0..1] = (Re, Im). */
+ORC_EXPORT int orc_dpscl(int64_t m, const double *qr, const double *qi, const double *pr,
+                         const double *pi, int eq, double fq, int ep, double fp, int compensated,
+                         double *out)
+{
+  if (m < 1 || !qr || !pr || !out || (!qi) != (!pi)) return ORC_E_ARG;
+  if (compensated)
+    zdpscl_comp(m, qr, qi, pr, pi, eq, fq, ep, fp, &out[0], &out[1]);
+  else
+    zdpscl(m, qr, qi, pr, pi, eq, fq, ep, fp, &out[0], &out[1]);
+  return ORC_OK;
 }
 
 /* Alg. hypot, the naive reproducible |z| used by Alg. cvg. */
@@ -415,11 +499,6 @@ ORC_EXPORT int orc_num_threads(void)
 #endif
 }
 
-/* Return codes shared with tests (not with the library). */
-#define ORC_OK 0
-#define ORC_E_ARG (-1)
-#define ORC_E_NONFINITE (-2)
-#define ORC_NOT_CONVERGED 1
 
 /*
  * orc_vjsvd: Alg. zvjsvd (complex, Gi != NULL) or its real variant dvjsvd.
@@ -430,11 +509,14 @@ ORC_EXPORT int orc_num_threads(void)
  *   out_info[4] = {status, sweeps, rotations (low 31 bits), rescales}.
  *   rotations64 receives the 64-bit rotation count (may be NULL).
  *   permute != 0 applies the column swap P during the sweeps.
+ *   compensated != 0 forms the scaled dot-products by Alg. zdpscl' /
+ *     ddpscl' (supplement SM2.2) instead of Alg. zdpscl.
  * nthreads <= 0 leaves the OpenMP default.
  */
 ORC_EXPORT int orc_vjsvd(int64_t m, int64_t n, double *Gr, double *Gi, int64_t ld, double *Vr,
                          double *Vi, double *sig, double *sig_e, double *sig_f, int max_sweeps,
-                         int permute, int nthreads, int32_t *out_info, int64_t *rotations64)
+                         int permute, int compensated, int nthreads, int32_t *out_info,
+                         int64_t *rotations64)
 {
   if (m < 1 || n < 1 || m < n || ld < m || max_sweeps < 1) return ORC_E_ARG;
 #ifdef _OPENMP
@@ -518,7 +600,10 @@ ORC_EXPORT int orc_vjsvd(int64_t m, int64_t n, double *Gr, double *Gi, int64_t l
             continue;
           }
           double zr, zi;
-          zdpscl(m, gqr, gqi, gpr, gpi, eq, fq, ep, fp, &zr, &zi);
+          if (compensated)
+            zdpscl_comp(m, gqr, gqi, gpr, gpi, eq, fq, ep, fp, &zr, &zi);
+          else
+            zdpscl(m, gqr, gqi, gpr, gpi, eq, fq, ep, fp, &zr, &zi);
           /* Alg. cvg */
           const double az = cplx ? hypot_naive(zr, zi) : fabs(zr);
           const int rot = (ups <= az);
