@@ -79,6 +79,11 @@ JSVD_API const char *jsvd_last_cuda_error(void);
  *     the fields it applies to (0 both, 1 real, 2 complex).  Both pipes
  *     round correctly: the results are identical. */
 #define JSVD_TUNE_EVD_ARITH 4
+/*   JSVD_TUNE_BATCH_SMEM: value = KiB of shared memory per block of the
+ *     batched SVD kernel (0..220; default 0).  A matrix whose G and V
+ *     (padded rows, all planes) fit in it is iterated there instead of in
+ *     its workspace region. */
+#define JSVD_TUNE_BATCH_SMEM 5
 JSVD_API int jsvd_tune_set(int knob, int value, int value2);
 
 /* ------------------------------------------------------------------------
@@ -124,6 +129,23 @@ typedef struct {
 
 JSVD_API int jsvd_evd2x2_batched(jsvd_field field, const jsvd_evd2_streams *s, int64_t n, void *stream);
 
+/* The same batched EVD on HOST streams (same meaning and rules as above,
+ * every pointer in *s a host pointer), with the host-device copies
+ * overlapped with the computation: the batch is cut into chunks that are
+ * copied to `work`, transformed by the kernel of jsvd_evd2x2_batched (same
+ * bits) and copied back, three chunks in flight on internal streams of the
+ * current device.  The call is asynchronous on `stream` like the others:
+ * the outputs are complete once `stream` has reached this point.  For the
+ * copies to overlap (and the call to return early) the host buffers must
+ * be page-locked (cudaHostAlloc / pinned); pageable buffers give the same
+ * results with the copies serialised.  work: DEVICE, 256-byte aligned,
+ * jsvd_evd2x2_host_workspace_size bytes, not used by anything else until
+ * `stream` passes this call.  Errors: as above, -4 work NULL or misaligned,
+ * JSVD_E_WORKSPACE if work_bytes is too small. */
+JSVD_API int jsvd_evd2x2_host_workspace_size(size_t *bytes);
+JSVD_API int jsvd_evd2x2_batched_host(jsvd_field field, const jsvd_evd2_streams *s, int64_t n,
+                                      void *work, size_t work_bytes, void *stream);
+
 /* ------------------------------------------------------------------------
  * One-sided Jacobi SVD (section 4, Alg. zvjsvd; real variant dvjsvd).
  *
@@ -162,6 +184,12 @@ typedef struct {
                           0 selects 256; must be in [1, 480] */
   int32_t permute;     /* 1: apply the column swap P during the sweeps;
                           0 (default): do not */
+  int32_t compensated; /* 1: the pivot pairs' dot-products g_q^* g_p by the
+                          compensated summation of supplement SM2.2
+                          (Alg. zdpscl' / ddpscl': products rounded down
+                          plus their exact errors, each stream summed by
+                          Kahan's method with 2Sum); FP64 sweeps only.
+                          0 (default): plain fma sums (Alg. zdpscl) */
 } jsvd_opts;
 
 /* Per-matrix outcome, written to DEVICE memory by the kernels. */

@@ -9,11 +9,12 @@ import ctypes
 from . import _native
 from ._native import (JSVD_COMPLEX, JSVD_E_CUDA, JSVD_E_NONFINITE, JSVD_E_TIMEOUT,
                       JSVD_E_UNSUPPORTED, JSVD_E_WORKSPACE, JSVD_FP64, JSVD_MIXED_FP32_FP64,
-                      JSVD_NOT_CONVERGED, JSVD_OK, JSVD_REAL, JSVD_TUNE_BATCH_WARPS, JSVD_TUNE_EVD_ARITH,
-                      JSVD_TUNE_EVD_LAUNCH, JSVD_TUNE_SVD_GRID, JsvdError)
+                      JSVD_NOT_CONVERGED, JSVD_OK, JSVD_REAL, JSVD_TUNE_BATCH_SMEM,
+                      JSVD_TUNE_BATCH_WARPS, JSVD_TUNE_EVD_ARITH, JSVD_TUNE_EVD_LAUNCH,
+                      JSVD_TUNE_SVD_GRID, JsvdError)
 
-__all__ = ["evd2x2_batched", "svd", "svd_workspace_size", "ordering", "decode_info", "dgemm",
-           "BatchedSVD", "pack_matrices", "svd_batched", "svd_adjoint_batched",
+__all__ = ["evd2x2_batched", "evd2x2_batched_host", "evd2x2_host_workspace_size", "svd",
+           "svd_workspace_size", "ordering", "decode_info", "dgemm", "BatchedSVD", "pack_matrices", "svd_batched", "svd_adjoint_batched",
            "sign_gauge_batched", "svd_diff", "version", "tune_set", "JsvdError", "JSVD_REAL",
            "JSVD_COMPLEX"]
 
@@ -30,11 +31,11 @@ def _stream_handle(stream):
     return ctypes.c_void_p(stream.cuda_stream)
 
 
-def _vec(t, name, n=None, dtype=None):
+def _vec(t, name, n=None, dtype=None, host=False):
     torch = _torch()
     dtype = dtype or torch.float64
-    if not isinstance(t, torch.Tensor) or not t.is_cuda:
-        raise TypeError("%s must be a CUDA tensor" % name)
+    if not isinstance(t, torch.Tensor) or t.is_cuda == host:
+        raise TypeError("%s must be a %s tensor" % (name, "CPU" if host else "CUDA"))
     if t.dtype != dtype:
         raise TypeError("%s must be %s" % (name, dtype))
     if t.dim() != 1 or not t.is_contiguous():
@@ -92,11 +93,66 @@ def evd2x2_batched(a11, a22, a21_re, a21_im=None, *, out=None, want_lambda=True,
     return out
 
 
+def evd2x2_host_workspace_size():
+    sz = ctypes.c_size_t(0)
+    _native.check(_native.lib().jsvd_evd2x2_host_workspace_size(ctypes.byref(sz)),
+                  "jsvd_evd2x2_host_workspace_size")
+    return sz.value
+
+
+def evd2x2_batched_host(a11, a22, a21_re, a21_im=None, *, out=None, want_lambda=True,
+                        want_zeta_p=True, work=None, device=None, stream=None):
+    """Batched 2x2 Hermitian EVD of HOST streams (jsvd_evd2x2_batched_host):
+    CPU tensors in and out (page-locked for the copies to overlap the
+    kernels), computed on the current CUDA device in pipelined chunks.
+    Returns the output dict (CPU tensors; `out` may supply them, pinned
+    ones are best).  Asynchronous on `stream`: synchronise before reading
+    the outputs.  `work` is a device workspace (uint8, at least
+    evd2x2_host_workspace_size() bytes), allocated if None."""
+    torch = _torch()
+    cplx = a21_im is not None
+    n = a11.numel()
+    s = _native.EvdStreams()
+    s.a11 = _vec(a11, "a11", n, host=True)
+    s.a22 = _vec(a22, "a22", n, host=True)
+    s.a21_re = _vec(a21_re, "a21_re", n, host=True)
+    s.a21_im = _vec(a21_im, "a21_im", n, host=True) if cplx else None
+    if out is None:
+        e = lambda dt=torch.float64: torch.empty(n, dtype=dt).pin_memory()
+        out = {"cos_phi": e(), "ea_tan_re": e()}
+        if cplx:
+            out["ea_tan_im"] = e()
+        if want_lambda:
+            out["lambda1"] = e()
+            out["lambda2"] = e()
+        if want_zeta_p:
+            out["zeta_p"] = e(torch.int32)
+    s.cos_phi = _vec(out["cos_phi"], "cos_phi", n, host=True)
+    s.ea_tan_re = _vec(out["ea_tan_re"], "ea_tan_re", n, host=True)
+    s.ea_tan_im = _vec(out["ea_tan_im"], "ea_tan_im", n, host=True) if cplx else None
+    s.lambda1 = _vec(out["lambda1"], "lambda1", n, host=True) if "lambda1" in out else None
+    s.lambda2 = _vec(out["lambda2"], "lambda2", n, host=True) if "lambda2" in out else None
+    s.zeta_p = (_vec(out["zeta_p"], "zeta_p", n, torch.int32, host=True) if "zeta_p" in out
+                else None)
+    need = evd2x2_host_workspace_size()
+    if work is None:
+        work = torch.empty(need, dtype=torch.uint8,
+                           device=device if device is not None else torch.cuda.current_device())
+    if not work.is_cuda or work.dtype != torch.uint8 or work.numel() < need:
+        raise ValueError("work must be a CUDA uint8 tensor of at least %d bytes" % need)
+    rc = _native.lib().jsvd_evd2x2_batched_host(JSVD_COMPLEX if cplx else JSVD_REAL,
+                                                ctypes.byref(s), n, ctypes.c_void_p(work.data_ptr()),
+                                                work.numel(), _stream_handle(stream))
+    _native.check(rc, "jsvd_evd2x2_batched_host")
+    return out
+
+
 # ---------------------------------------------------------------------------
 # SVD
 
-def _opts(max_sweeps=0, mode=JSVD_FP64, rescale_exp=0, permute=False):
+def _opts(max_sweeps=0, mode=JSVD_FP64, rescale_exp=0, permute=False, compensated=False):
     o = _native.Opts()
+    o.compensated = 1 if compensated else 0
     o.max_sweeps = int(max_sweeps)
     o.mode = int(mode)
     o.rescale_exp = int(rescale_exp)
@@ -148,12 +204,13 @@ def decode_info(info):
     return out[0] if len(out) == 1 else out
 
 
-def svd(A, *, max_sweeps=0, mode="fp64", rescale_exp=0, permute=False, work=None, out=None,
-        stream=None):
+def svd(A, *, max_sweeps=0, mode="fp64", rescale_exp=0, permute=False, compensated=False,
+        work=None, out=None, stream=None):
     """One-sided Jacobi SVD of a CUDA tensor A (m x n, m >= n; float64 or
     complex128), jsvd_svd.  Returns dict(U, sigma, sigma_e, sigma_f, V,
     info); U and V are column-major views, info a 24-byte device tensor
-    (decode_info)."""
+    (decode_info).  compensated forms the pivot pairs' dot-products by the
+    compensated summation (Alg. zdpscl' / ddpscl')."""
     torch = _torch()
     if not isinstance(A, torch.Tensor) or not A.is_cuda or A.dim() != 2:
         raise TypeError("A must be a 2-D CUDA tensor")
@@ -171,7 +228,7 @@ def svd(A, *, max_sweeps=0, mode="fp64", rescale_exp=0, permute=False, work=None
                "info": torch.zeros(_native.INFO_BYTES, dtype=torch.uint8, device=dev)}
     U, ldu = colmajor(out["U"])
     V, ldv = colmajor(out["V"])
-    o = _opts(max_sweeps, _mode(mode), rescale_exp, permute)
+    o = _opts(max_sweeps, _mode(mode), rescale_exp, permute, compensated)
     need = svd_workspace_size(m, n, cplx, mode)
     if work is None:
         work = torch.empty(need, dtype=torch.uint8, device=dev)
@@ -235,7 +292,7 @@ class BatchedSVD:
     launch() enqueues the computation (it may be captured in a CUDA graph and
     replayed)."""
 
-    def __init__(self, A, m, n, *, max_sweeps=0, permute=False, want_ef=True):
+    def __init__(self, A, m, n, *, max_sweeps=0, permute=False, compensated=False, want_ef=True):
         import numpy as np
         torch = _torch()
         self.m = np.asarray(m, dtype=np.int64)
@@ -262,7 +319,7 @@ class BatchedSVD:
         self.sigma_e = torch.empty(ns, dtype=torch.float64, device=dev) if want_ef else None
         self.sigma_f = torch.empty(ns, dtype=torch.float64, device=dev) if want_ef else None
         self.info = torch.zeros(max(self.count, 1) * _native.INFO_BYTES, dtype=torch.uint8, device=dev)
-        self.opts = _opts(max_sweeps, JSVD_FP64, 0, permute)
+        self.opts = _opts(max_sweeps, JSVD_FP64, 0, permute, compensated)
         es = 16 if self.cplx else 8
         cnt = self.count
         P = ctypes.c_void_p * max(cnt, 1)
@@ -321,11 +378,12 @@ def pack_matrices(mats, device="cuda"):
     return flat.to(device), m, n
 
 
-def svd_batched(mats, *, max_sweeps=0, permute=False, stream=None):
+def svd_batched(mats, *, max_sweeps=0, permute=False, compensated=False, stream=None):
     """Batched SVD of a list of matrices (jsvd_svd_batched): returns the
     BatchedSVD after launching it."""
     A, m, n = pack_matrices(mats)
-    return BatchedSVD(A, m, n, max_sweeps=max_sweeps, permute=permute).launch(stream)
+    return BatchedSVD(A, m, n, max_sweeps=max_sweeps, permute=permute,
+                      compensated=compensated).launch(stream)
 
 
 # ---------------------------------------------------------------------------

@@ -24,6 +24,7 @@ JSVD_TUNE_EVD_LAUNCH = 1
 JSVD_TUNE_SVD_GRID = 2
 JSVD_TUNE_BATCH_WARPS = 3
 JSVD_TUNE_EVD_ARITH = 4
+JSVD_TUNE_BATCH_SMEM = 5
 
 JSVD_FP64 = 0
 JSVD_MIXED_FP32_FP64 = 1
@@ -46,7 +47,8 @@ class EvdStreams(ctypes.Structure):
 
 class Opts(ctypes.Structure):
     _fields_ = [("max_sweeps", ctypes.c_int32), ("mode", ctypes.c_int32),
-                ("rescale_exp", ctypes.c_int32), ("permute", ctypes.c_int32)]
+                ("rescale_exp", ctypes.c_int32), ("permute", ctypes.c_int32),
+                ("compensated", ctypes.c_int32)]
 
 
 # jsvd_info as laid out in device memory: int32 status, int32 sweeps,
@@ -80,6 +82,11 @@ def lib():
         L.jsvd_tune_set.restype = ctypes.c_int
         L.jsvd_evd2x2_batched.argtypes = [ctypes.c_int, ctypes.POINTER(EvdStreams), _i64, _vp]
         L.jsvd_evd2x2_batched.restype = ctypes.c_int
+        L.jsvd_evd2x2_host_workspace_size.argtypes = [ctypes.POINTER(ctypes.c_size_t)]
+        L.jsvd_evd2x2_host_workspace_size.restype = ctypes.c_int
+        L.jsvd_evd2x2_batched_host.argtypes = [ctypes.c_int, ctypes.POINTER(EvdStreams), _i64, _vp,
+                                               ctypes.c_size_t, _vp]
+        L.jsvd_evd2x2_batched_host.restype = ctypes.c_int
         _sz = ctypes.c_size_t
         L.jsvd_svd_workspace_size.argtypes = [ctypes.c_int, ctypes.POINTER(Opts), _i64, _i64,
                                               ctypes.POINTER(_sz)]

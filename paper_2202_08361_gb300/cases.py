@@ -3,7 +3,7 @@
     python -m paper_2202_08361_gb300.cases evd   [--log2 23]
     python -m paper_2202_08361_gb300.cases svd   [--m 1024 --n 512 --complex --normal
                                                   --mode fp64|mixed --reps 1]
-    python -m paper_2202_08361_gb300.cases batch [--count 1000]
+    python -m paper_2202_08361_gb300.cases batch [--count 1000] [--shape 64x32]
     python -m paper_2202_08361_gb300.cases diff  [--count 4096]
 
 Each runs the case `--warmup` times and then `--reps` times, synchronising
@@ -32,6 +32,11 @@ def main(argv=None):
                    help="svd: i.i.d. N(0,1) entries (workload 1) instead of a geometric spectrum")
     p.add_argument("--mode", default="fp64", choices=["fp64", "mixed"])
     p.add_argument("--count", type=int, default=1000)
+    p.add_argument("--shape", default=None,
+                   help="batch: every matrix m x n (geometric spectrum, condition 1e3) "
+                        "instead of the uneven shapes")
+    p.add_argument("--warps", type=int, default=0, help="batch: warps per block (0: default)")
+    p.add_argument("--smem", type=int, default=-1, help="batch: shared-memory KiB (-1: default)")
     p.add_argument("--warmup", type=int, default=1)
     p.add_argument("--reps", type=int, default=1)
     a = p.parse_args(argv)
@@ -53,10 +58,21 @@ def main(argv=None):
         run = lambda: J.svd(At, mode=a.mode)
         label = "svd %dx%d %s %s" % (a.m, a.n, "complex" if a.complex else "real", a.mode)
     elif a.case == "batch":
-        A, m, n = workloads.uneven_batch_device(count=a.count, device=dev)
+        import numpy as np
+        if a.shape:
+            mm, nn = (int(x) for x in a.shape.split("x"))
+            A3 = workloads.diff_batch_device(count=a.count, m=mm, n=nn, device=dev)[0]
+            A = A3.transpose(1, 2).contiguous().view(-1)
+            m, n = np.full(a.count, mm), np.full(a.count, nn)
+        else:
+            A, m, n = workloads.uneven_batch_device(count=a.count, device=dev)
+        if a.warps:
+            J.tune_set(J.JSVD_TUNE_BATCH_WARPS, a.warps)
+        if a.smem >= 0:
+            J.tune_set(J.JSVD_TUNE_BATCH_SMEM, a.smem)
         B = J.BatchedSVD(A, m, n)
         run = lambda: B.launch()
-        label = "batched uneven count=%d" % a.count
+        label = "batched %s count=%d" % (a.shape or "uneven", a.count)
     else:
         A, w, C = workloads.diff_batch_device(count=a.count, device=dev)
 

@@ -59,6 +59,7 @@ extern "C" int jsvd_tune_set(int knob, int value, int value2)
     case JSVD_TUNE_EVD_ARITH: return jsvd::evd2_set_variant(value, value2);
     case JSVD_TUNE_SVD_GRID: return jsvd::svd_set_grid(value, value2);
     case JSVD_TUNE_BATCH_WARPS: return jsvd::batch_set_warps(value);
+    case JSVD_TUNE_BATCH_SMEM: return jsvd::batch_set_smem(value);
     default: return -1;
   }
 }

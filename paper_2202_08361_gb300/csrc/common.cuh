@@ -21,6 +21,13 @@ inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s
     if (e_ != cudaSuccess) return ::jsvd::cuda_fail(e_);      \
   } while (0)
 
+// Return an ABI code from a call that produces one, unless it is JSVD_OK.
+#define JSVD_TRY(...)                 \
+  do {                                \
+    const int rc_ = (__VA_ARGS__);    \
+    if (rc_ != JSVD_OK) return rc_;   \
+  } while (0)
+
 #define JSVD_CUDA(call)                                       \
   do {                                                        \
     cudaError_t e_ = (call);                                  \

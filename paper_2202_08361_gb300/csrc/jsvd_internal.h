@@ -7,13 +7,17 @@ int evd2_set_launch(int block, int blocks_per_sm);
 int evd2_set_variant(int v, int fields);
 int svd_set_grid(int cap, int warps);
 int batch_set_warps(int w);
+int batch_set_smem(int kib);
 }  // namespace jsvd
 
 #include <cuda_runtime.h>
 #include <stddef.h>
 
 namespace jsvd {
-int svd_check_opts(const jsvd_opts *o, int &S, int &mode, int &rexp, int &permute);
+// Option bits carried from jsvd_opts to the kernels.
+constexpr int kFlagPermute = 1;  // the column swap P during the sweeps
+constexpr int kFlagComp = 2;     // compensated dot-products (FP64 sweeps)
+int svd_check_opts(const jsvd_opts *o, int &S, int &mode, int &rexp, int &flags);
 size_t svd_fp64_workspace(bool cplx, int64_t m, int64_t n);
 size_t svd_mixed_workspace(bool cplx, int64_t m, int64_t n);
 int dgemm(bool transA, int M, int N, int K, double alpha, const double *A, int64_t lda,
@@ -23,6 +27,6 @@ int zgemm_split(bool conjtransA, int M, int N, int K, double alpha, const double
                 double beta, double *Cr, double *Ci, int64_t ldc, cudaStream_t st);
 int svd_mixed_run(bool cplx, int64_t m, int64_t n, const void *A, int64_t lda, void *U,
                   int64_t ldu, double *sigma, double *sigma_e, double *sigma_f, void *V,
-                  int64_t ldv, char *work, jsvd_info *info, int S, int rexp, int permute,
+                  int64_t ldv, char *work, jsvd_info *info, int S, int rexp, int flags,
                   cudaStream_t st);
 }  // namespace jsvd

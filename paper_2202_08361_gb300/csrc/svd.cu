@@ -141,9 +141,9 @@ __global__ void init_kernel(const double *__restrict__ A, int64_t lda, MatView M
 // chunk's 2x2 EVDs run one per lane), blocks stride over the nt/2 pairs,
 // and a bounded grid barrier separates the steps.  T is the precision of
 // the columns (double; float in the FP32 phase of the mixed SVD).
-template <typename T, bool CPLX>
+template <typename T, bool CPLX, bool COMP>
 __global__ void __launch_bounds__(256) sweeps_kernel(MatViewT<T> M, SvdState *st, double ups,
-                                                     int max_sweeps, int rescale_exp, int permute)
+                                                     int max_sweeps, int rescale_exp, int flags)
 {
   __shared__ PairSums s_sums[32];
   __shared__ PairOut s_out[32];
@@ -178,7 +178,8 @@ __global__ void __launch_bounds__(256) sweeps_kernel(MatViewT<T> M, SvdState *st
       unsigned long long Mloc = 0ull;
       int rots = 0;
       for (int base = blockIdx.x * W; base < L; base += gridDim.x * W)
-        step_chunk<T, CPLX>(M, k, nt, base, W, ups, rk, permute != 0, s_sums, s_out, Mloc, rots);
+        step_chunk<T, CPLX, true, COMP>(M, k, nt, base, W, ups, rk, (flags & kFlagPermute) != 0,
+                                        s_sums, s_out, Mloc, rots);
       Mloc = warp_umax(Mloc);
       if (lane == 0) {
         if (Mloc) atomicMax(&st->Mbuf[nxt], bits(magbits_to_double(Mloc, T(0))));
@@ -277,15 +278,16 @@ __global__ void ordering_kernel(int n, int32_t *tab)
   }
 }
 
-int svd_check_opts(const jsvd_opts *o, int &S, int &mode, int &rexp, int &permute)
+int svd_check_opts(const jsvd_opts *o, int &S, int &mode, int &rexp, int &flags)
 {
   S = 100;
   mode = JSVD_FP64;
   rexp = 256;
-  permute = 0;
+  flags = 0;
   if (!o) return 0;
   if (o->permute != 0 && o->permute != 1) return -1;
-  permute = o->permute;
+  if (o->compensated != 0 && o->compensated != 1) return -1;
+  flags = (o->permute ? kFlagPermute : 0) | (o->compensated ? kFlagComp : 0);
   if (o->max_sweeps > 0) S = o->max_sweeps;
   if (S > kMaxSweepsCap) return -1;
   if (o->mode != JSVD_FP64 && o->mode != JSVD_MIXED_FP32_FP64) return -1;
@@ -424,9 +426,9 @@ static int phase_init(const MatView &M, const double *A, int64_t lda, SvdState *
 }
 
 // A2-A8: every sweep, in one cooperative launch.
-template <typename T, bool CPLX>
-static int phase_sweeps(const MatViewT<T> &M, SvdState *state, double ups, int S, int rexp,
-                        int permute, cudaStream_t st)
+template <typename T, bool CPLX, bool COMP>
+static int launch_sweeps(const MatViewT<T> &M, SvdState *state, double ups, int S, int rexp,
+                         int flags, cudaStream_t st)
 {
   const int nt = M.n + (M.n & 1);
   const int Lp = nt / 2;
@@ -438,20 +440,30 @@ static int phase_sweeps(const MatViewT<T> &M, SvdState *state, double ups, int S
     W = 1;
     while (W < 8 && (Lp + 2 * W - 1) / (2 * W) >= sms) W *= 2;
   }
+  auto kern = sweeps_kernel<T, CPLX, COMP>;
   int per_sm = 0;
-  JSVD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweeps_kernel<T, CPLX>, 32 * W, 0));
+  JSVD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * W, 0));
   if (per_sm < 1) return JSVD_E_UNSUPPORTED;
   int grid = std::min((Lp + W - 1) / W, per_sm * sms);
   if (g_svd_grid_cap > 0) grid = std::min(grid, g_svd_grid_cap);
   if (grid < 1) grid = 1;
   MatViewT<T> Mk = M;
   SvdState *sk = state;
-  int Sk = S, rk = rexp, pk = permute;
+  int Sk = S, rk = rexp, pk = flags;
   double upsk = ups;
   void *args[] = {&Mk, &sk, &upsk, &Sk, &rk, &pk};
-  JSVD_CUDA(cudaLaunchCooperativeKernel((const void *)sweeps_kernel<T, CPLX>, dim3(grid),
-                                        dim3(32 * W), args, 0, st));
+  JSVD_CUDA(cudaLaunchCooperativeKernel((const void *)kern, dim3(grid), dim3(32 * W), args, 0, st));
   return JSVD_OK;
+}
+
+template <typename T, bool CPLX>
+static int phase_sweeps(const MatViewT<T> &M, SvdState *state, double ups, int S, int rexp,
+                        int flags, cudaStream_t st)
+{
+  if constexpr (sizeof(T) == 8) {
+    if (flags & kFlagComp) return launch_sweeps<T, CPLX, true>(M, state, ups, S, rexp, flags, st);
+  }
+  return launch_sweeps<T, CPLX, false>(M, state, ups, S, rexp, flags, st);
 }
 
 // A9: norms, order, U = G 2^{-e_j}/f_j, sigma, V, info.
@@ -475,24 +487,18 @@ static int phase_finish(const MatView &M, int *e, double *f, int *rank, SvdState
   return JSVD_OK;
 }
 
-#define JSVD_TRY(...)                 \
-  do {                                \
-    const int rc_ = (__VA_ARGS__);    \
-    if (rc_ != JSVD_OK) return rc_;   \
-  } while (0)
-
 // The FP64 SVD (Alg. zvjsvd) with V_1 = I.
 template <bool CPLX>
 static int svd_fp64_run(int64_t m, int64_t n, const double *A, int64_t lda, double *U, int64_t ldu,
                         double *sigma, double *sigma_e, double *sigma_f, double *V, int64_t ldv,
-                        char *work, jsvd_info *info, int S, int rexp, int permute,
+                        char *work, jsvd_info *info, int S, int rexp, int flags,
                         cudaStream_t st)
 {
   const SvdLayout L = svd_layout(CPLX, m, n);
   SvdState *state = reinterpret_cast<SvdState *>(work + L.state);
   const MatView M = view_at<double>(work, L.gr, L.gi, L.vr, L.vi, CPLX, L, m, n);
   JSVD_TRY(phase_init<CPLX>(M, A, lda, state, st));
-  JSVD_TRY(phase_sweeps<double, CPLX>(M, state, ldexp(sqrt((double)m), -53), S, rexp, permute, st));
+  JSVD_TRY(phase_sweeps<double, CPLX>(M, state, ldexp(sqrt((double)m), -53), S, rexp, flags, st));
   return phase_finish<CPLX>(M, reinterpret_cast<int *>(work + L.e),
                             reinterpret_cast<double *>(work + L.f),
                             reinterpret_cast<int *>(work + L.rank), state, nullptr, U, ldu, sigma,
@@ -512,7 +518,7 @@ constexpr int kNewtonSchulzSteps = 2;
 template <bool CPLX>
 static int svd_mixed_run_t(int64_t m, int64_t n, const double *A, int64_t lda, double *U,
                            int64_t ldu, double *sigma, double *sigma_e, double *sigma_f, double *V,
-                           int64_t ldv, char *work, jsvd_info *info, int S, int rexp, int permute,
+                           int64_t ldv, char *work, jsvd_info *info, int S, int rexp, int flags,
                            cudaStream_t st)
 {
   const MixedLayout X = mixed_layout(CPLX, m, n);
@@ -534,7 +540,7 @@ static int svd_mixed_run_t(int64_t m, int64_t n, const double *A, int64_t lda, d
   to_fp32_kernel<CPLX><<<grid, 256, 0, st>>>(M0, M32, st64, st32);
   JSVD_CHECK_LAUNCH();
   const double ups32 = ldexp(sqrt((double)m), kMixedTolExp);
-  JSVD_TRY(phase_sweeps<float, CPLX>(M32, st32, ups32, S, 1 << 20, permute, st));
+  JSVD_TRY(phase_sweeps<float, CPLX>(M32, st32, ups32, S, 1 << 20, flags, st));
   // V0 = orth(V32) in FP64 (in M64.v = the FP64 layout's V planes)
   dim3 gv((unsigned)((L.np + 255) / 256), (unsigned)std::min<int64_t>(n, 65535));
   v_to_fp64_kernel<CPLX><<<gv, 256, 0, st>>>(M32, M64.vr, M64.vi, L.ldv);
@@ -578,7 +584,7 @@ static int svd_mixed_run_t(int64_t m, int64_t n, const double *A, int64_t lda, d
       JSVD_CHECK_LAUNCH();
     }
   }
-  JSVD_TRY(phase_sweeps<double, CPLX>(M64, st64, ldexp(sqrt((double)m), -53), S, rexp, permute, st));
+  JSVD_TRY(phase_sweeps<double, CPLX>(M64, st64, ldexp(sqrt((double)m), -53), S, rexp, flags, st));
   return phase_finish<CPLX>(M64, reinterpret_cast<int *>(work + L.e),
                             reinterpret_cast<double *>(work + L.f),
                             reinterpret_cast<int *>(work + L.rank), st64, st32, U, ldu, sigma,
@@ -587,14 +593,14 @@ static int svd_mixed_run_t(int64_t m, int64_t n, const double *A, int64_t lda, d
 
 int svd_mixed_run(bool cplx, int64_t m, int64_t n, const void *A, int64_t lda, void *U,
                   int64_t ldu, double *sigma, double *sigma_e, double *sigma_f, void *V,
-                  int64_t ldv, char *work, jsvd_info *info, int S, int rexp, int permute,
+                  int64_t ldv, char *work, jsvd_info *info, int S, int rexp, int flags,
                   cudaStream_t st)
 {
   if (cplx)
     return svd_mixed_run_t<true>(m, n, (const double *)A, lda, (double *)U, ldu, sigma, sigma_e,
-                                 sigma_f, (double *)V, ldv, work, info, S, rexp, permute, st);
+                                 sigma_f, (double *)V, ldv, work, info, S, rexp, flags, st);
   return svd_mixed_run_t<false>(m, n, (const double *)A, lda, (double *)U, ldu, sigma, sigma_e,
-                                sigma_f, (double *)V, ldv, work, info, S, rexp, permute, st);
+                                sigma_f, (double *)V, ldv, work, info, S, rexp, flags, st);
 }
 
 }  // namespace jsvd
@@ -617,8 +623,8 @@ extern "C" int jsvd_svd_workspace_size(jsvd_field field, const jsvd_opts *opts, 
                                        int64_t n, size_t *bytes)
 {
   if (field != JSVD_REAL && field != JSVD_COMPLEX) return -1;
-  int S, mode, rexp, permute;
-  if (svd_check_opts(opts, S, mode, rexp, permute)) return -2;
+  int S, mode, rexp, flags;
+  if (svd_check_opts(opts, S, mode, rexp, flags)) return -2;
   if (m < 1 || m > (1 << 28)) return -3;
   if (n < 1 || n > m || n > (1 << 20)) return -4;
   if (!bytes) return -5;
@@ -634,8 +640,8 @@ extern "C" int jsvd_svd(jsvd_field field, const jsvd_opts *opts, int64_t m, int6
                         size_t work_bytes, jsvd_info *info, void *stream)
 {
   if (field != JSVD_REAL && field != JSVD_COMPLEX) return -1;
-  int S, mode, rexp, permute;
-  if (svd_check_opts(opts, S, mode, rexp, permute)) return -2;
+  int S, mode, rexp, flags;
+  if (svd_check_opts(opts, S, mode, rexp, flags)) return -2;
   if (m < 1 || m > (1 << 28)) return -3;
   if (n < 1 || n > m || n > (1 << 20)) return -4;
   const bool cplx = field == JSVD_COMPLEX;
@@ -654,10 +660,10 @@ extern "C" int jsvd_svd(jsvd_field field, const jsvd_opts *opts, int64_t m, int6
   cudaStream_t st = as_stream(stream);
   if (mode == JSVD_MIXED_FP32_FP64)
     return svd_mixed_run(cplx, m, n, A, lda, U, ldu, sigma, sigma_e, sigma_f, V, ldv,
-                         (char *)work, info, S, rexp, permute, st);
+                         (char *)work, info, S, rexp, flags, st);
   if (cplx)
     return svd_fp64_run<true>(m, n, (const double *)A, lda, (double *)U, ldu, sigma, sigma_e,
-                              sigma_f, (double *)V, ldv, (char *)work, info, S, rexp, permute, st);
+                              sigma_f, (double *)V, ldv, (char *)work, info, S, rexp, flags, st);
   return svd_fp64_run<false>(m, n, (const double *)A, lda, (double *)U, ldu, sigma, sigma_e,
-                             sigma_f, (double *)V, ldv, (char *)work, info, S, rexp, permute, st);
+                             sigma_f, (double *)V, ldv, (char *)work, info, S, rexp, flags, st);
 }

@@ -5,7 +5,8 @@
 // first (by m n^2, the cost of a sweep) and runs every phase of the SVD on
 // one matrix: the max-norm and scaling of A, all sweeps (one warp per pivot
 // pair, __syncthreads between steps, no grid barrier), the final norms,
-// the sort and the output.  The arithmetic is that of jsvd_svd (the same
+// the sort and the output.  G and V live in shared memory when they fit the
+// launch's budget, else in the matrix's workspace region (L1 and L2).  The arithmetic is that of jsvd_svd (the same
 // pair step, the same max-norm and rescaling sequence, the same
 // finalisation functions), so a matrix gives the same bits alone through
 // jsvd_svd, in any batch, in any position and with any block shape.
@@ -70,6 +71,7 @@ static BatchLayout batch_layout(int64_t count)
 }
 
 static int g_batch_warps = 8;
+static int g_batch_smem_kib = 0;
 
 int batch_set_warps(int w)
 {
@@ -78,12 +80,31 @@ int batch_set_warps(int w)
   return JSVD_OK;
 }
 
-template <bool CPLX>
+// Largest dynamic shared memory a block may take beside the kernel's static
+// arrays (227 KiB per block on sm_103, minus a margin for them).
+constexpr int kBatchSmemMaxKiB = 220;
+
+int batch_set_smem(int kib)
+{
+  if (kib < 0 || kib > kBatchSmemMaxKiB) return -2;
+  g_batch_smem_kib = kib;
+  return JSVD_OK;
+}
+
+// Bytes of shared memory that keep G and V of one matrix (all planes).
+__host__ __device__ __forceinline__ size_t smem_need(bool cplx, int mp, int np, int n)
+{
+  return sizeof(double) * ((size_t)mp + (size_t)np) * (size_t)n * (cplx ? 2 : 1);
+}
+
+template <bool CPLX, bool COMP>
 __global__ void __launch_bounds__(512) batched_kernel(const BatchDesc *__restrict__ desc,
                                                        const int *__restrict__ order,
                                                        BatchHdr *hdr, char *work, jsvd_info *info,
-                                                       int S, int rexp, int permute)
+                                                       int S, int rexp, int flags,
+                                                       size_t smem_cap)
 {
+  extern __shared__ __align__(16) double s_dyn[];
   __shared__ int s_idx;
   __shared__ unsigned long long s_M0;
   __shared__ unsigned long long s_M[3];
@@ -101,16 +122,26 @@ __global__ void __launch_bounds__(512) batched_kernel(const BatchDesc *__restric
     if (t >= count) break;
     const int idx = order[t];
     const BatchDesc d = desc[idx];
-    MatView M;
+    // The block owns the matrix: plain loads and stores (L1 may serve
+    // them), G and V in shared memory when both fit in smem_cap bytes.
+    MatViewT<double, false> M;
     char *reg = work + d.off;
     const size_t gbytes = sizeof(double) * (size_t)d.mp * d.n;
     const size_t vbytes = sizeof(double) * (size_t)d.np * d.n;
-    M.gr = reinterpret_cast<double *>(reg);
-    M.gi = CPLX ? reinterpret_cast<double *>(reg + al256(gbytes)) : nullptr;
-    size_t o = al256(gbytes) * (CPLX ? 2 : 1);
-    M.vr = reinterpret_cast<double *>(reg + o);
-    M.vi = CPLX ? reinterpret_cast<double *>(reg + o + al256(vbytes)) : nullptr;
-    o += al256(vbytes) * (CPLX ? 2 : 1);
+    if (smem_need(CPLX, d.mp, d.np, d.n) <= smem_cap) {
+      const int64_t g = (int64_t)d.mp * d.n, v = (int64_t)d.np * d.n;
+      M.gr = s_dyn;
+      M.gi = CPLX ? s_dyn + g : nullptr;
+      M.vr = s_dyn + (CPLX ? 2 * g : g);
+      M.vi = CPLX ? s_dyn + 2 * g + v : nullptr;
+    } else {
+      M.gr = reinterpret_cast<double *>(reg);
+      M.gi = CPLX ? reinterpret_cast<double *>(reg + al256(gbytes)) : nullptr;
+      const size_t ov = al256(gbytes) * (CPLX ? 2 : 1);
+      M.vr = reinterpret_cast<double *>(reg + ov);
+      M.vi = CPLX ? reinterpret_cast<double *>(reg + ov + al256(vbytes)) : nullptr;
+    }
+    size_t o = (al256(gbytes) + al256(vbytes)) * (CPLX ? 2 : 1);
     int *e = reinterpret_cast<int *>(reg + o);
     o = al256(o + sizeof(int) * (size_t)d.n);
     double *f = reinterpret_cast<double *>(reg + o);
@@ -200,7 +231,8 @@ __global__ void __launch_bounds__(512) batched_kernel(const BatchDesc *__restric
           unsigned long long Mloc = 0ull;
           int rots = 0;
           for (int base = 0; base < L; base += 32)
-            step_chunk<double, CPLX>(M, k, nt, base, 32, ups, rk, permute != 0, s_sums, s_out, Mloc,
+            step_chunk<double, CPLX, false, COMP>(M, k, nt, base, 32, ups, rk,
+                                                  (flags & kFlagPermute) != 0, s_sums, s_out, Mloc,
                                      rots);
           Mloc = warp_umax(Mloc);
           if (lane == 0) {
@@ -246,11 +278,11 @@ __global__ void __launch_bounds__(512) batched_kernel(const BatchDesc *__restric
 }
 
 static int batch_check(jsvd_field field, const jsvd_opts *opts, int64_t count, const int64_t *m,
-                       const int64_t *n, int &S, int &rexp, int &permute)
+                       const int64_t *n, int &S, int &rexp, int &flags)
 {
   if (field != JSVD_REAL && field != JSVD_COMPLEX) return -1;
   int mode;
-  if (svd_check_opts(opts, S, mode, rexp, permute) || mode != JSVD_FP64) return -2;
+  if (svd_check_opts(opts, S, mode, rexp, flags) || mode != JSVD_FP64) return -2;
   if (count < 0 || count > (1 << 26)) return -3;
   if (count > 0 && (!m || !n)) return -4;
   for (int64_t i = 0; i < count; ++i)
@@ -266,8 +298,8 @@ extern "C" int jsvd_svd_batched_workspace_size(jsvd_field field, const jsvd_opts
                                                int64_t count, const int64_t *m, const int64_t *n,
                                                size_t *bytes)
 {
-  int S, rexp, permute;
-  const int rc = batch_check(field, opts, count, m, n, S, rexp, permute);
+  int S, rexp, flags;
+  const int rc = batch_check(field, opts, count, m, n, S, rexp, flags);
   if (rc) return rc;
   if (!bytes) return -6;
   const BatchLayout L = batch_layout(count);
@@ -285,8 +317,8 @@ extern "C" int jsvd_svd_batched_prepare(jsvd_field field, const jsvd_opts *opts,
                                         const int64_t *ldv, void *work, size_t work_bytes,
                                         void *stream)
 {
-  int S, rexp, permute;
-  const int rc = batch_check(field, opts, count, m, n, S, rexp, permute);
+  int S, rexp, flags;
+  const int rc = batch_check(field, opts, count, m, n, S, rexp, flags);
   if (rc) return rc;
   if (count > 0 && (!A || !lda || !U || !ldu || !sigma || !V || !ldv)) return -6;
   if (!work || ((uintptr_t)work & 255)) return -15;
@@ -349,8 +381,8 @@ extern "C" int jsvd_svd_batched_launch(jsvd_field field, const jsvd_opts *opts, 
                                        void *work, jsvd_info *info, void *stream)
 {
   if (field != JSVD_REAL && field != JSVD_COMPLEX) return -1;
-  int S, mode, rexp, permute;
-  if (svd_check_opts(opts, S, mode, rexp, permute) || mode != JSVD_FP64) return -2;
+  int S, mode, rexp, flags;
+  if (svd_check_opts(opts, S, mode, rexp, flags) || mode != JSVD_FP64) return -2;
   if (count < 0 || count > (1 << 26)) return -3;
   if (!work || ((uintptr_t)work & 255)) return -4;
   if (count == 0) return JSVD_OK;
@@ -360,14 +392,27 @@ extern "C" int jsvd_svd_batched_launch(jsvd_field field, const jsvd_opts *opts, 
   // rewind the queue (graph-capturable: a memset node)
   JSVD_CUDA(cudaMemsetAsync(w + L.hdr, 0, sizeof(int), st));
   const int threads = 32 * g_batch_warps;
+  const size_t smem = (size_t)g_batch_smem_kib * 1024;
   int per_sm = 0;
-  auto kern = (field == JSVD_COMPLEX) ? batched_kernel<true> : batched_kernel<false>;
-  JSVD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0));
+  const bool cplx = (field == JSVD_COMPLEX);
+  const bool comp = (flags & kFlagComp) != 0;
+  auto kern = cplx ? (comp ? batched_kernel<true, true> : batched_kernel<true, false>)
+                   : (comp ? batched_kernel<false, true> : batched_kernel<false, false>);
+  // opt in to the dynamic shared memory (static + dynamic may pass the
+  // 48 KiB default even when the budget alone does not)
+  static int attr_set[4] = {-1, -1, -1, -1};
+  const int ki = (cplx ? 2 : 0) + (comp ? 1 : 0);
+  if (smem > 0 && attr_set[ki] != g_batch_smem_kib) {
+    JSVD_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr_set[ki] = g_batch_smem_kib;
+  }
+  JSVD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
   if (per_sm < 1) return JSVD_E_UNSUPPORTED;
   const int grid = (int)std::min<int64_t>(count, (int64_t)per_sm * sm_count());
-  kern<<<grid, threads, 0, st>>>(reinterpret_cast<const BatchDesc *>(w + L.desc),
-                                 reinterpret_cast<const int *>(w + L.order),
-                                 reinterpret_cast<BatchHdr *>(w + L.hdr), w, info, S, rexp, permute);
+  kern<<<grid, threads, smem, st>>>(reinterpret_cast<const BatchDesc *>(w + L.desc),
+                                    reinterpret_cast<const int *>(w + L.order),
+                                    reinterpret_cast<BatchHdr *>(w + L.hdr), w, info, S, rexp,
+                                    flags, smem);
   JSVD_CHECK_LAUNCH();
   return JSVD_OK;
 }

@@ -56,13 +56,28 @@ __device__ __forceinline__ double magbits_to_double(unsigned long long b, float)
 }
 
 // The iteration matrix G (m x n) and V (n x n) in column precision T.
-template <typename T>
+// CG: every access goes through L2 only (ldg2/stg2), for matrices that
+// blocks on several SMs update; otherwise plain loads and stores, for a
+// matrix that one block owns (in global or in shared memory), where the
+// block barriers order the accesses and L1 may serve them.
+template <typename T, bool CG = true>
 struct MatViewT {
   T *gr, *gi;        // G planes (gi == nullptr for real), column j at + j*ldg
   T *vr, *vi;        // V planes, column j at + j*ldv
   int m, n;          // true sizes
   int mp, np;        // rows padded to a multiple of 32 (padding rows are 0)
   int64_t ldg, ldv;
+
+  static __device__ __forceinline__ T ld(const T *p)
+  {
+    if constexpr (CG) return ldg2(p);
+    else return *p;
+  }
+  static __device__ __forceinline__ void st(T *p, T v)
+  {
+    if constexpr (CG) stg2(p, v);
+    else *p = v;
+  }
 };
 using MatView = MatViewT<double>;
 
@@ -119,10 +134,10 @@ __device__ __forceinline__ double hypot_naive(double x, double y)
 __device__ __forceinline__ float ldexp_rn(float x, int k) { return scalbnf(x, k); }
 
 // Scale a column by 2^k in place (rows < mp).
-template <typename T>
-__device__ __forceinline__ void scale_col(T *x, int mp, int k, int lane)
+template <typename T, bool CG>
+__device__ __forceinline__ void scale_col(const MatViewT<T, CG> &M, T *x, int k, int lane)
 {
-  for (int i = lane; i < mp; i += 32) stg2(x + i, ldexp_rn(ldg2(x + i), k));
+  for (int i = lane; i < M.mp; i += 32) M.st(x + i, ldexp_rn(M.ld(x + i), k));
 }
 
 struct PairOut {
@@ -184,15 +199,54 @@ struct PairSums {
   double pp, qq, qr, qi;  // ||g_p||^2, ||g_q||^2, g_q^* g_p (re, im)
 };
 
+// The compensated dot-product of supplement SM2.2 (Alg. zdpscl' /
+// ddpscl'): each term x y enters as c = RD(x y) and c' = x y - c >= 0 (one
+// fma, exact), and each of the two streams is summed by Kahan's method
+// with 2Sum (Eq. e:d2sum) in place of Fast2Sum.
+struct CompSum {
+  double s, t;    // value stream and its carried error
+  double s2, t2;  // error stream and its carried error
+};
+
+// Eq. e:d2sum: a + b = s + t exactly, s = fl(a + b).
+__device__ __forceinline__ void two_sum(double a, double b, double &s, double &t)
+{
+  const double ss = __dadd_rn(a, b);
+  double a1 = __dsub_rn(ss, b);
+  double b1 = __dsub_rn(ss, a1);
+  a1 = __dsub_rn(a, a1);
+  b1 = __dsub_rn(b, b1);
+  s = ss;
+  t = __dadd_rn(a1, b1);
+}
+
+__device__ __forceinline__ void comp_term(double x, double y, CompSum &c)
+{
+  const double p = __dmul_rd(x, y);
+  const double e = __fma_rn(x, y, -p);
+  two_sum(c.s, __dadd_rn(p, c.t), c.s, c.t);
+  two_sum(c.s2, __dadd_rn(e, c.t2), c.s2, c.t2);
+}
+
+// The lanes' streams reduced one by one in the canonical butterfly order,
+// then combined as s + (t + (s' + t')).
+__device__ __forceinline__ double comp_reduce(const CompSum &c)
+{
+  const double S = warp_sum(c.s), T = warp_sum(c.t), S2 = warp_sum(c.s2), T2 = warp_sum(c.t2);
+  return __dadd_rn(S, __dadd_rn(T, __dadd_rn(S2, T2)));
+}
+
 // The three sums of pair (p, q), formed by one full warp with the columns
 // in precision T (double, or float in the FP32 phase of the mixed SVD):
 // lane l accumulates rows l, l+32, ... in ascending order with fma, the lane
 // partials are combined in FP64 by an xor butterfly (the same value in every
 // lane).  rk != 0 downscales both columns of G by 2^rk first (section 3.2,
-// step 2; FP64 only).
-template <typename T, bool CPLX>
-__device__ __forceinline__ PairSums pair_sums(const MatViewT<T> &M, int p, int q, int rk)
+// step 2; FP64 only).  COMP forms g_q^* g_p by the compensated summation
+// (FP64 only); the squared norms stay plain fma sums.
+template <typename T, bool CPLX, bool CG, bool COMP = false>
+__device__ __forceinline__ PairSums pair_sums(const MatViewT<T, CG> &M, int p, int q, int rk)
 {
+  static_assert(!COMP || sizeof(T) == 8, "the compensated sums are FP64 only");
   // rows per lane per loop trip: their loads are all issued before the
   // arithmetic, which then consumes them in ascending row order, so the
   // accumulation order (and the bits) are those of the one-row loop
@@ -201,6 +255,7 @@ __device__ __forceinline__ PairSums pair_sums(const MatViewT<T> &M, int p, int q
   T *gpr = M.gr + p * M.ldg, *gqr = M.gr + q * M.ldg;
   T *gpi = CPLX ? M.gi + p * M.ldg : nullptr, *gqi = CPLX ? M.gi + q * M.ldg : nullptr;
   T spp = T(0), sqq = T(0), sqr = T(0), sqi = T(0);
+  CompSum cr = {0.0, 0.0, 0.0, 0.0}, ci = {0.0, 0.0, 0.0, 0.0};
   for (int base = lane; base < M.mp; base += 32 * U) {
     T xpr[U], xqr[U], xpi[U], xqi[U];
 #pragma unroll
@@ -208,11 +263,11 @@ __device__ __forceinline__ PairSums pair_sums(const MatViewT<T> &M, int p, int q
       const int i = base + 32 * u;  // the same bound for every lane: mp is a multiple of 32
       xpr[u] = xqr[u] = xpi[u] = xqi[u] = T(0);
       if (i < M.mp) {
-        xpr[u] = ldg2(gpr + i);
-        xqr[u] = ldg2(gqr + i);
+        xpr[u] = M.ld(gpr + i);
+        xqr[u] = M.ld(gqr + i);
         if (CPLX) {
-          xpi[u] = ldg2(gpi + i);
-          xqi[u] = ldg2(gqi + i);
+          xpi[u] = M.ld(gpi + i);
+          xqi[u] = M.ld(gqi + i);
         }
       }
     }
@@ -223,13 +278,13 @@ __device__ __forceinline__ PairSums pair_sums(const MatViewT<T> &M, int p, int q
         if (i < M.mp) {
           xpr[u] = ldexp_rn(xpr[u], rk);
           xqr[u] = ldexp_rn(xqr[u], rk);
-          stg2(gpr + i, xpr[u]);
-          stg2(gqr + i, xqr[u]);
+          M.st(gpr + i, xpr[u]);
+          M.st(gqr + i, xqr[u]);
           if (CPLX) {
             xpi[u] = ldexp_rn(xpi[u], rk);
             xqi[u] = ldexp_rn(xqi[u], rk);
-            stg2(gpi + i, xpi[u]);
-            stg2(gqi + i, xqi[u]);
+            M.st(gpi + i, xpi[u]);
+            M.st(gqi + i, xqi[u]);
           }
         }
       }
@@ -239,13 +294,25 @@ __device__ __forceinline__ PairSums pair_sums(const MatViewT<T> &M, int p, int q
       if (base + 32 * u < M.mp) {
         spp = fma_t(xpr[u], xpr[u], spp);
         sqq = fma_t(xqr[u], xqr[u], sqq);
-        sqr = fma_t(xqr[u], xpr[u], sqr);
-        if (CPLX) {
-          spp = fma_t(xpi[u], xpi[u], spp);
-          sqq = fma_t(xqi[u], xqi[u], sqq);
-          sqi = fma_t(xqr[u], xpi[u], sqi);
-          sqr = fma_t(xqi[u], xpi[u], sqr);
-          sqi = fma_t(-xqi[u], xpr[u], sqi);
+        if constexpr (COMP) {
+          // Re: g_p.re g_q.re + g_p.im g_q.im; Im: g_p.im g_q.re - g_p.re g_q.im
+          comp_term(xpr[u], xqr[u], cr);
+          if (CPLX) {
+            spp = fma_t(xpi[u], xpi[u], spp);
+            sqq = fma_t(xqi[u], xqi[u], sqq);
+            comp_term(xpi[u], xqi[u], cr);
+            comp_term(xpi[u], xqr[u], ci);
+            comp_term(-xpr[u], xqi[u], ci);
+          }
+        } else {
+          sqr = fma_t(xqr[u], xpr[u], sqr);
+          if (CPLX) {
+            spp = fma_t(xpi[u], xpi[u], spp);
+            sqq = fma_t(xqi[u], xqi[u], sqq);
+            sqi = fma_t(xqr[u], xpi[u], sqi);
+            sqr = fma_t(xqi[u], xpi[u], sqr);
+            sqi = fma_t(-xqi[u], xpr[u], sqi);
+          }
         }
       }
     }
@@ -253,8 +320,13 @@ __device__ __forceinline__ PairSums pair_sums(const MatViewT<T> &M, int p, int q
   PairSums r;
   r.pp = warp_sum((double)spp);
   r.qq = warp_sum((double)sqq);
-  r.qr = warp_sum((double)sqr);
-  r.qi = CPLX ? warp_sum((double)sqi) : 0.0;
+  if constexpr (COMP) {
+    r.qr = comp_reduce(cr);
+    r.qi = CPLX ? comp_reduce(ci) : 0.0;
+  } else {
+    r.qr = warp_sum((double)sqr);
+    r.qi = CPLX ? warp_sum((double)sqi) : 0.0;
+  }
   return r;
 }
 
@@ -262,8 +334,8 @@ __device__ __forceinline__ PairSums pair_sums(const MatViewT<T> &M, int p, int q
 // the new entries in Mloc, as magbits() in T's encoding) and V rows, with the
 // columns swapped if o.swap; a non-rotated pair with o.swap is only swapped.
 // One full warp; o must be the same in every lane.
-template <typename T, bool CPLX>
-__device__ __forceinline__ void pair_apply(const MatViewT<T> &M, int p, int q, const PairOut &o,
+template <typename T, bool CPLX, bool CG>
+__device__ __forceinline__ void pair_apply(const MatViewT<T, CG> &M, int p, int q, const PairOut &o,
                                            unsigned long long &Mloc)
 {
   constexpr int U = (sizeof(T) == 4) ? 8 : 4;
@@ -289,11 +361,11 @@ __device__ __forceinline__ void pair_apply(const MatViewT<T> &M, int p, int q, c
           const int i = base + 32 * u;
           pr[u] = qr[u] = pi[u] = qi[u] = T(0);
           if (i < rows) {
-            pr[u] = ldg2(xpr + i);
-            qr[u] = ldg2(xqr + i);
+            pr[u] = M.ld(xpr + i);
+            qr[u] = M.ld(xqr + i);
             if (CPLX) {
-              pi[u] = ldg2(xpi + i);
-              qi[u] = ldg2(xqi + i);
+              pi[u] = M.ld(xpi + i);
+              qi[u] = M.ld(xqi + i);
             }
           }
         }
@@ -306,10 +378,10 @@ __device__ __forceinline__ void pair_apply(const MatViewT<T> &M, int p, int q, c
               const T npi = mul_t(fma_t(qr[u], S, fma_t(qi[u], C, pi[u])), c);
               const T nqr = mul_t(fma_t(pr[u], -C, fma_t(-pi[u], S, qr[u])), c);
               const T nqi = mul_t(fma_t(pr[u], S, fma_t(pi[u], -C, qi[u])), c);
-              stg2(dpr + i, npr);
-              stg2(dpi + i, npi);
-              stg2(dqr + i, nqr);
-              stg2(dqi + i, nqi);
+              M.st(dpr + i, npr);
+              M.st(dpi + i, npi);
+              M.st(dqr + i, nqr);
+              M.st(dqi + i, nqi);
               if (onG) {
                 const unsigned long long a =
                     max(max(magbits(npr), magbits(npi)), max(magbits(nqr), magbits(nqi)));
@@ -318,8 +390,8 @@ __device__ __forceinline__ void pair_apply(const MatViewT<T> &M, int p, int q, c
             } else {
               const T npr = mul_t(fma_t(qr[u], C, pr[u]), c);
               const T nqr = mul_t(fma_t(pr[u], -C, qr[u]), c);
-              stg2(dpr + i, npr);
-              stg2(dqr + i, nqr);
+              M.st(dpr + i, npr);
+              M.st(dqr + i, nqr);
               if (onG) Mloc = max(Mloc, max(magbits(npr), magbits(nqr)));
             }
           }
@@ -335,13 +407,13 @@ __device__ __forceinline__ void pair_apply(const MatViewT<T> &M, int p, int q, c
       T *xpi = CPLX ? (onG ? M.gi + p * M.ldg : M.vi + p * M.ldv) : nullptr;
       T *xqi = CPLX ? (onG ? M.gi + q * M.ldg : M.vi + q * M.ldv) : nullptr;
       for (int i = lane; i < rows; i += 32) {
-        const T a = ldg2(xpr + i), b = ldg2(xqr + i);
-        stg2(xpr + i, b);
-        stg2(xqr + i, a);
+        const T a = M.ld(xpr + i), b = M.ld(xqr + i);
+        M.st(xpr + i, b);
+        M.st(xqr + i, a);
         if (CPLX) {
-          const T ai = ldg2(xpi + i), bi = ldg2(xqi + i);
-          stg2(xpi + i, bi);
-          stg2(xqi + i, ai);
+          const T ai = M.ld(xpi + i), bi = M.ld(xqi + i);
+          M.st(xpi + i, bi);
+          M.st(xqi + i, ai);
         }
       }
     }
@@ -359,8 +431,8 @@ __device__ __forceinline__ void pair_apply(const MatViewT<T> &M, int p, int q, c
 //   3. warps apply the rotations.
 // Every pair's arithmetic is the same whatever the chunking.  rots counts
 // (in each warp's lane 0) the rotated pairs, Mloc collects magbits().
-template <typename T, bool CPLX>
-__device__ __forceinline__ void step_chunk(const MatViewT<T> &M, int k, int nt, int base, int CH,
+template <typename T, bool CPLX, bool CG, bool COMP = false>
+__device__ __forceinline__ void step_chunk(const MatViewT<T, CG> &M, int k, int nt, int base, int CH,
                                            double ups, int rk, bool permute, PairSums *s_sums,
                                            PairOut *s_out, unsigned long long &Mloc, int &rots)
 {
@@ -372,11 +444,11 @@ __device__ __forceinline__ void step_chunk(const MatViewT<T> &M, int k, int nt, 
     int p, q;
     pair_of(k, l, nt, p, q);
     if (q < M.n) {
-      const PairSums sm = pair_sums<T, CPLX>(M, p, q, rk);
+      const PairSums sm = pair_sums<T, CPLX, CG, COMP>(M, p, q, rk);
       if (lane == 0) s_sums[i] = sm;
     } else if (rk) {  // phantom partner: only a pending rescale applies
-      scale_col(M.gr + p * M.ldg, M.mp, rk, lane);
-      if (CPLX) scale_col(M.gi + p * M.ldg, M.mp, rk, lane);
+      scale_col(M, M.gr + p * M.ldg, rk, lane);
+      if (CPLX) scale_col(M, M.gi + p * M.ldg, rk, lane);
     }
   }
   __syncthreads();
@@ -414,17 +486,17 @@ __device__ __forceinline__ void step_chunk(const MatViewT<T> &M, int k, int nt, 
 
 // Column j's norm as (e, f) by one warp in the canonical order; a zero
 // column gets e = INT_MIN, f = 1.
-template <bool CPLX>
-__device__ __forceinline__ void colnorm_warp(const MatView &M, int j, int lane, int *e_out,
+template <bool CPLX, bool CG>
+__device__ __forceinline__ void colnorm_warp(const MatViewT<double, CG> &M, int j, int lane, int *e_out,
                                              double *f_out)
 {
   const double *xr = M.gr + j * M.ldg, *xi = CPLX ? M.gi + j * M.ldg : nullptr;
   double s = 0.0;
   for (int i = lane; i < M.mp; i += 32) {
-    const double a = ldg2(xr + i);
+    const double a = M.ld(xr + i);
     s = __fma_rn(a, a, s);
     if (CPLX) {
-      const double b = ldg2(xi + i);
+      const double b = M.ld(xi + i);
       s = __fma_rn(b, b, s);
     }
   }
@@ -466,8 +538,8 @@ __device__ __forceinline__ int rank_of(int n, const int *e, const double *f, int
 
 // One element (row i) of output column j, which goes to position r:
 // U(i, r) = G(i, j) 2^{-e_j} / f_j (i < m), V(i, r) = V_k(i, j) (i < n).
-template <bool CPLX>
-__device__ __forceinline__ void output_elem(const MatView &M, int i, int j, int r, int ej,
+template <bool CPLX, bool CG>
+__device__ __forceinline__ void output_elem(const MatViewT<double, CG> &M, int i, int j, int r, int ej,
                                             double fj, bool bad, double *U, int64_t ldu,
                                             double *V, int64_t ldv)
 {
@@ -478,8 +550,8 @@ __device__ __forceinline__ void output_elem(const MatView &M, int i, int j, int 
     if (bad) {
       ur = ui = nan;
     } else if (!zero) {
-      ur = __ddiv_rn(ldexp_rn(ldg2(M.gr + j * M.ldg + i), -ej), fj);
-      if (CPLX) ui = __ddiv_rn(ldexp_rn(ldg2(M.gi + j * M.ldg + i), -ej), fj);
+      ur = __ddiv_rn(ldexp_rn(M.ld(M.gr + j * M.ldg + i), -ej), fj);
+      if (CPLX) ui = __ddiv_rn(ldexp_rn(M.ld(M.gi + j * M.ldg + i), -ej), fj);
     }
     if (CPLX) {
       U[2 * (r * ldu + i)] = ur;
@@ -489,10 +561,10 @@ __device__ __forceinline__ void output_elem(const MatView &M, int i, int j, int 
     }
   }
   if (i < M.n) {
-    const double vr = bad ? nan : ldg2(M.vr + j * M.ldv + i);
+    const double vr = bad ? nan : M.ld(M.vr + j * M.ldv + i);
     if (CPLX) {
       V[2 * (r * ldv + i)] = vr;
-      V[2 * (r * ldv + i) + 1] = bad ? nan : ldg2(M.vi + j * M.ldv + i);
+      V[2 * (r * ldv + i) + 1] = bad ? nan : M.ld(M.vi + j * M.ldv + i);
     } else {
       V[r * ldv + i] = vr;
     }

@@ -59,6 +59,18 @@ def test_argument_errors_need_no_gpu(lib):
     assert L.jsvd_evd2x2_batched(0, ctypes.byref(s), -1, None) == -3
     assert L.jsvd_evd2x2_batched(1, ctypes.byref(s), 10, None) == -2  # complex needs a21_im
     assert L.jsvd_evd2x2_batched(0, ctypes.byref(s), 0, None) == 0  # n = 0: no-op
+    # the host-buffer EVD checks its arguments before touching the device
+    sz = ctypes.c_size_t(0)
+    assert L.jsvd_evd2x2_host_workspace_size(ctypes.byref(sz)) == 0 and sz.value > 0
+    h = _native.EvdStreams()
+    assert L.jsvd_evd2x2_batched_host(7, ctypes.byref(h), 10, None, 0, None) == -1
+    assert L.jsvd_evd2x2_batched_host(0, None, 10, None, 0, None) == -2
+    assert L.jsvd_evd2x2_batched_host(0, ctypes.byref(h), 10, None, 0, None) == -2
+    assert L.jsvd_evd2x2_batched_host(0, ctypes.byref(h), 0, None, 0, None) == 0
+    h.a11 = h.a22 = h.a21_re = h.cos_phi = h.ea_tan_re = 8
+    assert L.jsvd_evd2x2_batched_host(0, ctypes.byref(h), -1, None, 0, None) == -3
+    assert L.jsvd_evd2x2_batched_host(0, ctypes.byref(h), 10, None, 0, None) == -4
+    assert L.jsvd_evd2x2_batched_host(0, ctypes.byref(h), 10, 256, 0, None) == _native.JSVD_E_WORKSPACE
     assert L.jsvd_tune_set(99, 0, 0) == -1
     assert L.jsvd_tune_set(1, 100, 8) == -2
     assert L.jsvd_tune_set(1, 256, 0) == -3

@@ -62,6 +62,54 @@ def test_batched_equals_single_bitwise(cplx):
         assert infos[i] == J.decode_info(ref["info"]), i
 
 
+@pytest.mark.parametrize("cplx", [False, True])
+def test_batched_compensated_equals_single_bitwise(cplx):
+    """The compensated option in the batched kernel: the bits of jsvd_svd
+    with the same option."""
+    import paper_2202_08361_gb300 as J
+    torch = _torch()
+    mats = mats_mixed(cplx, seed=31 + cplx)
+    B = J.svd_batched(mats, compensated=True)
+    torch.cuda.synchronize()
+    for i, A in enumerate(mats):
+        ref = J.svd(torch.from_numpy(np.asfortranarray(A)).cuda(), compensated=True)
+        torch.cuda.synchronize()
+        U, s, V = B.matrix(i)
+        assert same(U, ref["U"]) and same(V, ref["V"]) and same(s, ref["sigma"]), i
+
+
+@pytest.mark.parametrize("kib", [24, 100, 220])
+def test_shared_memory_path_bitwise(kib):
+    """Matrices whose G and V fit the shared-memory budget are iterated
+    there; the bits do not change, whatever the budget and block shape."""
+    import paper_2202_08361_gb300 as J
+    torch = _torch()
+    mats = mats_mixed(False, seed=5)
+    ref = J.svd_batched(mats)
+    torch.cuda.synchronize()
+    try:
+        for w in (2, 8):
+            J.tune_set(J.JSVD_TUNE_BATCH_WARPS, w)
+            J.tune_set(J.JSVD_TUNE_BATCH_SMEM, kib)
+            other = J.svd_batched(mats)
+            torch.cuda.synchronize()
+            for i in range(len(mats)):
+                for a, b in zip(other.matrix(i), ref.matrix(i)):
+                    assert same(a, b), (kib, w, i)
+        cm = mats_mixed(True, seed=6)
+        J.tune_set(J.JSVD_TUNE_BATCH_SMEM, 0)
+        cref = J.svd_batched(cm)
+        J.tune_set(J.JSVD_TUNE_BATCH_SMEM, kib)
+        cother = J.svd_batched(cm)
+        torch.cuda.synchronize()
+        for i in range(len(cm)):
+            for a, b in zip(cother.matrix(i), cref.matrix(i)):
+                assert same(a, b), (kib, "complex", i)
+    finally:
+        J.tune_set(J.JSVD_TUNE_BATCH_WARPS, 8)
+        J.tune_set(J.JSVD_TUNE_BATCH_SMEM, 0)
+
+
 def test_batch_composition_and_block_shape_invariance():
     import paper_2202_08361_gb300 as J
     torch = _torch()

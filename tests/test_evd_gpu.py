@@ -157,3 +157,44 @@ def test_empty_batch_and_optional_outputs():
     assert set(part) == {"cos_phi", "ea_tan_re"}
     assert torch.equal(part["cos_phi"], full["cos_phi"])
     assert torch.equal(part["ea_tan_re"], full["ea_tan_re"])
+
+
+@pytest.mark.parametrize("complex_", [False, True])
+@pytest.mark.parametrize("n", [5, (1 << 20) + 1, 4 * (1 << 20) + 12345])
+def test_host_pipeline_bit_identical(n, complex_):
+    """jsvd_evd2x2_batched_host (pinned host streams, chunks of 2^20 in three
+    slots): the same bits as the device call, across chunk boundaries, slot
+    reuse and a ragged last chunk; the oracle agrees on a sample."""
+    torch = _torch()
+    import paper_2202_08361_gb300 as J
+    streams = workloads.evd_batch(n, complex_, seed_salt=17)
+    host = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in streams]
+    out = J.evd2x2_batched_host(*host[:3], host[3] if complex_ else None)
+    torch.cuda.synchronize()
+    ref = run_gpu(streams, complex_)
+    for k, v in ref.items():
+        assert np.array_equal(out[k].numpy().view(np.uint8), v.view(np.uint8)), k
+    idx = np.random.default_rng(3).choice(n, min(n, 4096), replace=False)
+    sub = [a[idx] for a in streams]
+    o = oracle.zsjac2(*sub) if complex_ else oracle.dsjac2(*sub)
+    keys = (["cos_phi", "ea_tan_re", "ea_tan_im", "lambda1", "lambda2", "zeta_p"] if complex_
+            else ["cos_phi", "ea_tan_re", "lambda1", "lambda2", "zeta_p"])
+    for k, r in zip(keys, o):
+        assert np.array_equal(out[k].numpy()[idx].view(np.uint8), np.asarray(r).view(np.uint8)), k
+
+
+def test_host_pipeline_pageable_and_optional_outputs():
+    """Pageable host buffers give the same results (copies serialised);
+    lambda and zeta_p may be left out; n = 0 is a no-op."""
+    torch = _torch()
+    import paper_2202_08361_gb300 as J
+    streams = workloads.evd_batch(70000, True, seed_salt=18)
+    host = [torch.from_numpy(np.ascontiguousarray(a)) for a in streams]
+    out = J.evd2x2_batched_host(*host, want_lambda=False, want_zeta_p=False)
+    torch.cuda.synchronize()
+    assert set(out) == {"cos_phi", "ea_tan_re", "ea_tan_im"}
+    ref = run_gpu(streams, True)
+    for k in out:
+        assert np.array_equal(out[k].numpy(), ref[k]), k
+    e = torch.empty(0, dtype=torch.float64)
+    assert J.evd2x2_batched_host(e, e, e)["cos_phi"].numel() == 0

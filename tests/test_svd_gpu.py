@@ -69,6 +69,22 @@ def test_parity_real(m, n):
     check_parity(A, gpu_svd(A), oracle.vjsvd(A))
 
 
+@pytest.mark.parametrize("cplx", [False, True])
+@pytest.mark.parametrize("m,n", [(96, 48), (33, 17), (130, 70)])
+def test_parity_compensated(m, n, cplx):
+    """The compensated dot-products (Alg. zdpscl' / ddpscl', supplement
+    SM2.2) against the oracle's compensated SVD: the acceptance bounds, the
+    same singular values, sweep counts within one."""
+    A, _ = workloads.svd_geometric(m, n, 1e6, cplx, workloads.rng(3, 40 + cplx + m))
+    g = gpu_svd(A, compensated=True)
+    o = oracle.vjsvd(A, compensated=True)
+    check_parity(A, g, o)
+    assert abs(g["info"]["sweeps"] - o["sweeps"]) <= 1
+    # the plain and the compensated GPU runs differ (the option is live)
+    p = gpu_svd(A)
+    assert not np.array_equal(p["sigma"], g["sigma"]) or p["info"] != g["info"]
+
+
 @pytest.mark.parametrize("m,n", [(64, 31), (40, 40)])
 def test_parity_permute(m, n):
     """The column swap P applied during the sweeps (section 2, Alg. zvjsvd
@@ -188,4 +204,7 @@ def test_argument_errors():
     assert L.jsvd_svd(0, None, 8, 4, p, 8, p, 8, s, None, None, p, 4, w.data_ptr(), 16, None, None) == J.JSVD_E_WORKSPACE
     bad = _native.Opts()
     bad.permute = 2
+    assert L.jsvd_svd(0, ctypes.byref(bad), 8, 4, p, 8, p, 8, s, None, None, p, 4, w.data_ptr(), w.numel(), None, None) == -2
+    bad = _native.Opts()
+    bad.compensated = 3
     assert L.jsvd_svd(0, ctypes.byref(bad), 8, 4, p, 8, p, 8, s, None, None, p, 4, w.data_ptr(), w.numel(), None, None) == -2
