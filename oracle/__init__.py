@@ -42,6 +42,11 @@ def lib():
         L.orc_zsjac2.restype = None
         L.orc_zsjac2_scaled.argtypes = [ctypes.c_int64, _d, _d, _d, _d, _d, _d]
         L.orc_zsjac2_scaled.restype = None
+        _f = ctypes.POINTER(ctypes.c_float)
+        L.orc_ssjac2.argtypes = [ctypes.c_int64, _f, _f, _f, _f, _f, _f, _f, _i32]
+        L.orc_ssjac2.restype = None
+        L.orc_csjac2.argtypes = [ctypes.c_int64, _f, _f, _f, _f, _f, _f, _f, _f, _f, _i32]
+        L.orc_csjac2.restype = None
         L.orc_pairs.argtypes = [ctypes.c_int, _i32]
         L.orc_pairs.restype = ctypes.c_int
         L.orc_vjsvd.argtypes = [ctypes.c_int64, ctypes.c_int64, _d, _d, ctypes.c_int64, _d, _d,
@@ -69,6 +74,38 @@ def _dp(a):
 
 def _f64(a):
     return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _f32(a):
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def _fp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+def ssjac2(a11, a22, a21):
+    """Single precision real EVD (binary32 constants of section 2.4):
+    (cos phi, sign(a21) tan phi, lambda1, lambda2, zeta_p)."""
+    a11, a22, a21 = _f32(a11), _f32(a22), _f32(a21)
+    r = a11.size
+    out = [np.empty(r, np.float32) for _ in range(4)]
+    zp = np.empty(r, np.int32)
+    lib().orc_ssjac2(r, _fp(a11), _fp(a22), _fp(a21), *[_fp(o) for o in out],
+                     zp.ctypes.data_as(_i32))
+    return (*out, zp)
+
+
+def csjac2(a11, a22, a21r, a21i):
+    """Single precision complex EVD: (cos phi, cos(alpha) tan phi,
+    sin(alpha) tan phi, lambda1, lambda2, zeta_p)."""
+    a11, a22, a21r, a21i = _f32(a11), _f32(a22), _f32(a21r), _f32(a21i)
+    r = a11.size
+    out = [np.empty(r, np.float32) for _ in range(5)]
+    zp = np.empty(r, np.int32)
+    lib().orc_csjac2(r, _fp(a11), _fp(a22), _fp(a21r), _fp(a21i), *[_fp(o) for o in out],
+                     zp.ctypes.data_as(_i32))
+    return (*out, zp)
 
 
 def dsjac2(a11, a22, a21):

@@ -12,6 +12,8 @@
  *   orc_dsjac2 / orc_zsjac2  batched 2x2 real symmetric / complex Hermitian
  *                            EVD, Alg. d8jac2 (supplement SM2.1) and
  *                            Listing 1 (section 2.3.1), element by element.
+ *   orc_ssjac2 / orc_csjac2  the same in single precision with the
+ *                            binary32 constants of section 2.4.
  *   orc_pairs                the cyclic parallel pivot ordering (round-robin
  *                            reading of section 4.1).
  *   orc_vjsvd                one-sided Jacobi SVD after Alg. zvjsvd
@@ -190,6 +192,103 @@ ORC_EXPORT void orc_zsjac2(int64_t r, const double *a11, const double *a22, cons
   for (int64_t i = 0; i < r; ++i)
     zsjac2_1(a11[i], a22[i], a21r[i], a21i[i], cphi + i, catphi + i, satphi + i,
              lam1 ? lam1 + i : NULL, lam2 ? lam2 + i : NULL, zp ? zp + i : NULL, NULL, NULL);
+}
+
+/* ------------------------------------------------------------------------
+ * Single precision (section 2.4: nu = FLT_MAX, fl(sqrt nu) = 1.844674297E+19,
+ * mu = FLT_TRUE_MIN, eta = FLT_MAX_EXP - 4; every operation in binary32).
+ * Same steps as dsjac2_1 / zsjac2_1. */
+static const float SQRT_NU_F = 1.844674297E+19f;
+
+static int zeta_of_f(float x)
+{
+  int e;
+  (void)frexpf(fmaxf(fabsf(x), FLT_TRUE_MIN), &e);
+  return (FLT_MAX_EXP - 3) - e;
+}
+
+static float xorsignf_(float x, float s)
+{
+  uint32_t a, b;
+  memcpy(&a, &x, 4);
+  memcpy(&b, &s, 4);
+  a ^= (b & 0x80000000u);
+  memcpy(&x, &a, 4);
+  return x;
+}
+
+static void ssjac2_1(float a11, float a22, float a21, float *cphi, float *tphi, float *lam1,
+                     float *lam2, int32_t *zp)
+{
+  const int zeta = imin(imin(zeta_of_f(a11), zeta_of_f(a22)), zeta_of_f(a21));
+  a21 = scalbnf(a21, zeta);
+  a11 = scalbnf(a11, zeta);
+  a22 = scalbnf(a22, zeta);
+  const float aa21 = fabsf(a21);
+  const float o = 2.0f * aa21;
+  const float a = a11 - a22;
+  const float tan2 = copysignf(fminf(fmaxf(o / fabsf(a), 0.0f), SQRT_NU_F), a);
+  const float tan1 = tan2 / (1.0f + sqrtf(fmaf(tan2, tan2, 1.0f)));
+  const float sec2 = fmaf(tan1, tan1, 1.0f);
+  const float sec = sqrtf(sec2);
+  *cphi = 1.0f / sec;
+  *tphi = xorsignf_(tan1, a21);
+  const float l1 = fmaf(tan1, fmaf(a22, tan1, o), a11) / sec2;
+  const float l2 = fmaf(tan1, fmaf(a11, tan1, -o), a22) / sec2;
+  if (lam1) *lam1 = scalbnf(l1, -zeta);
+  if (lam2) *lam2 = scalbnf(l2, -zeta);
+  if (zp) *zp = pack_zp(zeta, l1 < l2);
+}
+
+static void csjac2_1(float a11, float a22, float a21r, float a21i, float *cphi, float *catphi,
+                     float *satphi, float *lam1, float *lam2, int32_t *zp)
+{
+  const int zeta =
+      imin(imin(zeta_of_f(a11), zeta_of_f(a22)), imin(zeta_of_f(a21r), zeta_of_f(a21i)));
+  a21r = scalbnf(a21r, zeta);
+  a21i = scalbnf(a21i, zeta);
+  a11 = scalbnf(a11, zeta);
+  a22 = scalbnf(a22, zeta);
+  const float ar = fabsf(a21r), ai = fabsf(a21i);
+  const float am = fminf(ar, ai), aM = fmaxf(ar, ai);
+  const float mM = fmaxf(am / aM, 0.0f);
+  const float aa21 = sqrtf(fmaf(mM, mM, 1.0f)) * aM;
+  const float calpha = copysignf(fminf(ar / aa21, 1.0f), a21r);
+  const float salpha = a21i / fmaxf(aa21, FLT_TRUE_MIN);
+  const float o = aa21 * 2.0f;
+  const float a = a11 - a22;
+  const float tan2 = copysignf(fminf(fmaxf(o / fabsf(a), 0.0f), SQRT_NU_F), a);
+  const float tan1 = tan2 / (1.0f + sqrtf(fmaf(tan2, tan2, 1.0f)));
+  const float sec2 = fmaf(tan1, tan1, 1.0f);
+  const float sec = sqrtf(sec2);
+  *cphi = 1.0f / sec;
+  *catphi = calpha * tan1;
+  *satphi = salpha * tan1;
+  const float l1 = fmaf(tan1, fmaf(a22, tan1, o), a11) / sec2;
+  const float l2 = fmaf(tan1, fmaf(a11, tan1, -o), a22) / sec2;
+  if (lam1) *lam1 = scalbnf(l1, -zeta);
+  if (lam2) *lam2 = scalbnf(l2, -zeta);
+  if (zp) *zp = pack_zp(zeta, l1 < l2);
+}
+
+/* Batched single precision EVDs (the s/c variants of Alg. dbjac2 / zbjac2). */
+ORC_EXPORT void orc_ssjac2(int64_t r, const float *a11, const float *a22, const float *a21,
+                           float *cphi, float *tphi, float *lam1, float *lam2, int32_t *zp)
+{
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < r; ++i)
+    ssjac2_1(a11[i], a22[i], a21[i], cphi + i, tphi + i, lam1 ? lam1 + i : NULL,
+             lam2 ? lam2 + i : NULL, zp ? zp + i : NULL);
+}
+
+ORC_EXPORT void orc_csjac2(int64_t r, const float *a11, const float *a22, const float *a21r,
+                           const float *a21i, float *cphi, float *catphi, float *satphi,
+                           float *lam1, float *lam2, int32_t *zp)
+{
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < r; ++i)
+    csjac2_1(a11[i], a22[i], a21r[i], a21i[i], cphi + i, catphi + i, satphi + i,
+             lam1 ? lam1 + i : NULL, lam2 ? lam2 + i : NULL, zp ? zp + i : NULL);
 }
 
 /* Scaled eigenvalues lambda' (before backscaling) for the pins. */

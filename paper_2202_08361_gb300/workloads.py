@@ -53,6 +53,26 @@ def evd_batch(r: int, complex_: bool, seed_salt: int = 0):
     return a11, a22, a21r
 
 
+def wide_range_values_f32(g, r, zero_frac=0.01):
+    """The binary32 form of wide_range_values: sign * (1 + k 2^-23) * 2^e,
+    k ~ U{0..2^23-1}, e ~ U{-149..127} (values below 2^-126 rounded to the
+    subnormal grid), each entry exactly 0 with probability zero_frac."""
+    k = g.integers(0, 1 << 23, size=r)
+    e = g.integers(-149, 128, size=r)
+    s = np.where(g.random(r) < 0.5, -1.0, 1.0)
+    v = (s * np.ldexp(1.0 + np.ldexp(k.astype(np.float64), -23), e)).astype(np.float32)
+    v[g.random(r) < zero_frac] = 0.0
+    return v
+
+
+def evd_batch_f32(r: int, complex_: bool, seed_salt: int = 0):
+    """Single precision SoA streams of r Hermitian 2x2 matrices (the binary32
+    counterpart of evd_batch)."""
+    g = rng(2, 20 + seed_salt + (1 if complex_ else 0))
+    cols = [wide_range_values_f32(g, r) for _ in range(4 if complex_ else 3)]
+    return tuple(cols)
+
+
 def evd_prescribed(r: int, complex_: bool, seed_salt: int = 0):
     """Matrices built from prescribed eigenvalues, tan(phi) and cos(alpha)
     as in the paper's EVD test data (Eq. e:2, section 5.1), in FP64 here:
