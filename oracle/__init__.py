@@ -47,6 +47,8 @@ def lib():
         L.orc_ssjac2.restype = None
         L.orc_csjac2.argtypes = [ctypes.c_int64, _f, _f, _f, _f, _f, _f, _f, _f, _f, _i32]
         L.orc_csjac2.restype = None
+        L.orc_rnF.argtypes = [ctypes.c_int64, _d, _d, _d]
+        L.orc_rnF.restype = None
         L.orc_pairs.argtypes = [ctypes.c_int, _i32]
         L.orc_pairs.restype = ctypes.c_int
         L.orc_vjsvd.argtypes = [ctypes.c_int64, ctypes.c_int64, _d, _d, ctypes.c_int64, _d, _d,
@@ -199,6 +201,15 @@ def dpscl(q, p, compensated=False, eq=0, fq=1.0, ep=0, fp=1.0):
     if rc != 0:
         raise ValueError("orc_dpscl failed with %d" % rc)
     return complex(out[0], out[1]) if cplx else out[0]
+
+
+def rnF(x):
+    """||x||_F as (e, f) = 2^e f by Alg. rnF with one lane: e an integral
+    float (-inf for x = 0), f in [1, 2)."""
+    x = _f64(x)
+    e, f = np.zeros(1), np.zeros(1)
+    lib().orc_rnF(x.size, _dp(x), _dp(e), _dp(f))
+    return float(e[0]), float(f[0])
 
 
 def svd_adjoint(U, s, V, Ubar, sbar, Vbar=None):

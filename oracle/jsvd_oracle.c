@@ -26,6 +26,8 @@
  *                            "e:tol", the scaled Grammians of Alg. Gram
  *                            (section 3.4) and the transformations of
  *                            Eq. "e:transf" / Alg. zjrot (section 3.5).
+ *   orc_rnF                  the wide-exponent Frobenius norm of Alg. rnF
+ *                            (supplement SM6) with one lane.
  *   orc_svd_adjoint          thin real SVD adjoint (Townsend 2016), used for
  *                            the differentiated batched SVD.
  *
@@ -386,6 +388,80 @@ static void colnorm(int64_t m, const double *xr, const double *xi, int *e, doubl
   const int er = flg(r);
   *f = ldexp(r, -er);
   *e = E + er;
+}
+
+/* ------------------------------------------------------------------------
+ * Alg. rnF (supplement SM6.2-SM6.3) with one lane (s = 1): the Frobenius
+ * norm of a vector in the wide-exponent representation r = (e, f) = 2^e f,
+ * e an integral double (-inf for zero), f in [1, 2), so that no partial sum
+ * overflows or underflows.  Readings: F(0) = 1 (zero is (-inf, 1) as the
+ * supplement writes it); scalef by -inf gives 0. */
+
+/* getexp: floor(lg|x|) as a double, -inf for 0 (subnormals normalised) */
+static double E_of(double x)
+{
+  if (x == 0.0) return -INFINITY;
+  int e;
+  (void)frexp(x, &e);
+  return (double)(e - 1);
+}
+
+/* getmant to [1, 2): |x| / 2^floor(lg|x|); F(0) = 1 */
+static double F_of(double x)
+{
+  if (x == 0.0) return 1.0;
+  int e;
+  const double m = frexp(fabs(x), &e); /* [0.5, 1) */
+  return 2.0 * m;
+}
+
+/* scalef(f, e) for an integral or infinite double e: f 2^e rounded once */
+static double scalef_d(double f, double e)
+{
+  if (e == -INFINITY) return 0.0;
+  if (e < -4000.0) e = -4000.0;
+  if (e > 4000.0) e = 4000.0;
+  return scalbn(f, (int)e);
+}
+
+/* One step r <- fma(|x|, |x|, r) in (e, f) arithmetic. */
+static void rnf_step(double x, double *e, double *f)
+{
+  /* r' = r with an even (or infinite) exponent */
+  const double lsb = isinf(*e) ? 0.0 : (double)((int64_t)(*e) & 1);
+  const double e1 = *e - lsb;
+  const double f1 = scalef_d(*f, lsb);
+  /* |x| = (E(x), F(x)); x^2 has exponent 2 E(x) or one more */
+  const double ex = E_of(x), fx = F_of(x);
+  const double eh = 2.0 * ex;
+  const double emax = fmax(eh, e1);
+  const double dh = fmax(eh - emax, -INFINITY); /* -inf - -inf = NaN -> -inf */
+  const double d1 = fmax(e1 - emax, -INFINITY);
+  const double fh = scalef_d(fx, dh / 2.0);
+  const double fr = scalef_d(f1, d1);
+  const double fn = fma(fh, fh, fr);
+  *f = F_of(fn);
+  *e = emax + E_of(fn);
+}
+
+/* (e, f) of ||x||^2 -> (e'', f'') of ||x|| (supplement SM6.1). */
+static void ef_sqrt(double e, double f, double *e2, double *f2)
+{
+  double ep = e, fp = f;
+  if (!isinf(e) && ((int64_t)e & 1)) {
+    fp = 2.0 * f;
+    ep = e - 1.0;
+  }
+  *e2 = isinf(ep) ? ep : ep / 2.0;
+  *f2 = sqrt(fp);
+}
+
+/* ||x||_F as (e'', f'') by Alg. rnF with one lane. */
+ORC_EXPORT void orc_rnF(int64_t m, const double *x, double *e_out, double *f_out)
+{
+  double e = -INFINITY, f = 1.0;
+  for (int64_t i = 0; i < m; ++i) rnf_step(x[i], &e, &f);
+  ef_sqrt(e, f, e_out, f_out);
 }
 
 /* (e,f) comparison: x < y for norms */
