@@ -184,6 +184,34 @@ def _svd_flops(m, n, sweeps, rotations, cplx):
     return pairs * 6 * m + rotations * 6 * (m + n)
 
 
+def evd_f32_bench(torch, J, workloads, dev, peaks, reps=50):
+    """The single precision EVD on 2^24 real + 2^24 complex binary32
+    matrices (jsvd_evd2x2_batched_f32): per-kernel CUDA-event times and the
+    HBM fraction (32 / 40 algorithmic bytes per real / complex matrix)."""
+    r = 1 << 24
+    st = torch.cuda.current_stream(dev)
+    res = {}
+    for cplx, name, per in ((False, "real", 32), (True, "complex", 40)):
+        t = [torch.from_numpy(a).to(dev) for a in workloads.evd_batch_f32(r, cplx)]
+        out = J.evd2x2_batched(*t)
+        for _ in range(5):
+            J.evd2x2_batched(*t, out=out)
+        e0, e1 = _ev(torch)
+        torch.cuda.synchronize(dev)
+        e0.record(st)
+        for _ in range(reps):
+            J.evd2x2_batched(*t, out=out)
+        e1.record(st)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / reps
+        gbs = per * r / (ms * 1e-3) / 1e9
+        res[name] = {"ms": ms, "evd_per_s": r / (ms * 1e-3), "gbs": gbs,
+                     "hbm_frac": gbs / peaks["hbm_gbs"], "bytes_per_matrix": per}
+        del t, out
+    res["workload"] = "2^24 real + 2^24 complex binary32 matrices, entries sign*(1+k 2^-23)*2^e, e~U{-149..127}, 1% zeros"
+    return res
+
+
 def svd_bench(torch, J, workloads, dev):
     import numpy as np
     out = {}
@@ -445,6 +473,9 @@ def run_ours(args):
     svd = None
     if rank == 0 and world == 1 and not args.no_svd:
         svd = svd_bench(torch, J, workloads, dev)
+    evd32 = None
+    if rank == 0 and world == 1:
+        evd32 = evd_f32_bench(torch, J, workloads, dev, peaks)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -468,7 +499,7 @@ def run_ours(args):
                         "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
                         "api": "jsvd_evd2x2_batched_host (pinned host streams, pipelined)"},
                 "cpu_baseline": cpu, "clocks": clk, "gpu_launches": gpu_launches,
-                "svd": svd}
+                "evd_fp32": evd32, "svd": svd}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -62,8 +62,9 @@ JSVD_API const char *jsvd_last_cuda_error(void);
 /* Launch-shape knobs.  They are arithmetic-neutral: no setting changes a
  * single result bit, only the speed.  Process-wide; returns -2 or -3 for a
  * value out of range, -1 for an unknown knob.
- *   JSVD_TUNE_EVD_LAUNCH: value = threads per block of the 2x2 EVD kernel
- *     (64, 128 or 256), value2 = resident blocks per SM (1..64). */
+ *   JSVD_TUNE_EVD_LAUNCH: value = threads per block of the 2x2 EVD kernels
+ *     (FP64 and FP32; 64, 128 or 256), value2 = resident blocks per SM
+ *     (1..64). */
 #define JSVD_TUNE_EVD_LAUNCH 1
 /*   JSVD_TUNE_SVD_GRID: value = most blocks of the persistent SVD sweep
  *     kernel (0 = as many as the pair chunks of a step, capped by
@@ -71,7 +72,9 @@ JSVD_API const char *jsvd_last_cuda_error(void);
  *     the number of pairs and SMs). */
 #define JSVD_TUNE_SVD_GRID 2
 /*   JSVD_TUNE_BATCH_WARPS: value = warps per block of the batched SVD
- *     kernel (1, 2, 4, 8 or 16; default 8). */
+ *     kernel (1, 2, 4, 8 or 16), or 0 (the default): chosen when the batch
+ *     is prepared, from its mean n weighted by m n^2 (1 warp for n ~ 32, 16
+ *     for n ~ 256). */
 #define JSVD_TUNE_BATCH_WARPS 3
 /*   JSVD_TUNE_EVD_ARITH: value = which of the 2x2 EVD's divisions and
  *     square roots run on the integer pipe instead of the FP64 pipe (0..7;
@@ -84,6 +87,11 @@ JSVD_API const char *jsvd_last_cuda_error(void);
  *     (padded rows, all planes) fit in it is iterated there instead of in
  *     its workspace region. */
 #define JSVD_TUNE_BATCH_SMEM 5
+/*   JSVD_TUNE_EVD32_DIV: value = 1: the single precision EVD divides and
+ *     takes square roots on operands first scaled into [1, 2) (never the
+ *     IEEE routines' slow path); 0 (default): the IEEE intrinsics directly.
+ *     Both round correctly: the results are identical. */
+#define JSVD_TUNE_EVD32_DIV 6
 JSVD_API int jsvd_tune_set(int knob, int value, int value2);
 
 /* ------------------------------------------------------------------------
@@ -129,6 +137,21 @@ typedef struct {
 
 JSVD_API int jsvd_evd2x2_batched(jsvd_field field, const jsvd_evd2_streams *s, int64_t n, void *stream);
 
+/* The same batched EVD in single precision (section 2.4: the binary32
+ * constants nu = FLT_MAX, fl(sqrt nu) = 1.844674297E+19, mu = FLT_TRUE_MIN,
+ * eta = FLT_MAX_EXP - 4; every operation in binary32, round to nearest).
+ * Streams as above with float in place of double; zeta' in [-273, 3].
+ * Errors as above. */
+typedef struct {
+  const float *a11, *a22, *a21_re, *a21_im;
+  float *cos_phi, *ea_tan_re, *ea_tan_im;
+  float *lambda1, *lambda2;
+  int32_t *zeta_p;
+} jsvd_evd2_streams_f32;
+
+JSVD_API int jsvd_evd2x2_batched_f32(jsvd_field field, const jsvd_evd2_streams_f32 *s, int64_t n,
+                                     void *stream);
+
 /* The same batched EVD on HOST streams (same meaning and rules as above,
  * every pointer in *s a host pointer), with the host-device copies
  * overlapped with the computation: the batch is cut into chunks that are
@@ -145,6 +168,20 @@ JSVD_API int jsvd_evd2x2_batched(jsvd_field field, const jsvd_evd2_streams *s, i
 JSVD_API int jsvd_evd2x2_host_workspace_size(size_t *bytes);
 JSVD_API int jsvd_evd2x2_batched_host(jsvd_field field, const jsvd_evd2_streams *s, int64_t n,
                                       void *work, size_t work_bytes, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Wide-exponent Frobenius norms of the columns of A (supplement SM6,
+ * Alg. rnF): ||a_j|| = 2^e_j f_j with e_j integral (returned as a double,
+ * -inf for a zero column) and f_j in [1, 2), computed without overflow or
+ * underflow of any partial sum (the norm of a column of FLT/DBL_MAX entries
+ * or of subnormals is accurate).  A: m x n column-major, lda >= m; complex
+ * A interleaved (each row adds Re^2 then Im^2).  One warp per column: the
+ * lanes take rows l, l+32, ... in order, then combine in the fixed xor
+ * butterfly, so the bits do not depend on the launch.  e_out, f_out: n
+ * doubles each (device).  Errors: -1 field, -2 m < 0, -3 n < 0, -4 A NULL,
+ * -5 lda, -6 e_out or f_out NULL. */
+JSVD_API int jsvd_colnorm_ef(jsvd_field field, int64_t m, int64_t n, const void *A, int64_t lda,
+                             double *e_out, double *f_out, void *stream);
 
 /* ------------------------------------------------------------------------
  * One-sided Jacobi SVD (section 4, Alg. zvjsvd; real variant dvjsvd).
@@ -180,8 +217,10 @@ JSVD_API int jsvd_evd2x2_batched_host(jsvd_field field, const jsvd_evd2_streams 
 typedef struct {
   int32_t max_sweeps;  /* S; <= 0 selects the default, 100 */
   int32_t mode;        /* JSVD_FP64 or JSVD_MIXED_FP32_FP64 */
-  int32_t rescale_exp; /* rescale G when ||G||_max reaches 2^rescale_exp;
-                          0 selects 256; must be in [1, 480] */
+  int32_t rescale_exp; /* R: G starts with ||G||_max in [2^(R-25), 2^(R-24))
+                          ([1, 2) for R <= 25) and is scaled back there
+                          whenever ||G||_max reaches 2^R (section 3.2);
+                          0 selects 480; must be in [1, 480] */
   int32_t permute;     /* 1: apply the column swap P during the sweeps;
                           0 (default): do not */
   int32_t compensated; /* 1: the pivot pairs' dot-products g_q^* g_p by the
@@ -200,6 +239,10 @@ typedef struct {
   int64_t rotations; /* transformations applied in total */
   int32_t rescales;  /* downscalings of the iteration matrix */
   int32_t sweeps_fp32; /* mixed mode: sweeps of the FP32 phase */
+  int32_t gs_steps;    /* transformations done as the Gram-Schmidt step of
+                          section 3.5.1 (Eq. e:GS: column norms more than
+                          2^1023 fl(eps sqrt m) apart), counted in rotations */
+  int32_t reserved;
 } jsvd_info;
 
 #define JSVD_NOT_CONVERGED 1

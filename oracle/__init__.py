@@ -169,7 +169,7 @@ def vjsvd(A, max_sweeps=100, nthreads=0, permute=False, compensated=False):
     Vr = np.zeros((n, n), order="F")
     Vi = np.zeros((n, n), order="F") if cplx else None
     sig, se, sf = np.empty(n), np.empty(n), np.empty(n)
-    info = np.zeros(4, dtype=np.int32)
+    info = np.zeros(5, dtype=np.int32)
     rot = np.zeros(1, dtype=np.int64)
     rc = lib().orc_vjsvd(m, n, _dp(Gr), _dp(Gi), m, _dp(Vr), _dp(Vi), _dp(sig), _dp(se),
                          _dp(sf), int(max_sweeps), 1 if permute else 0,
@@ -182,7 +182,7 @@ def vjsvd(A, max_sweeps=100, nthreads=0, permute=False, compensated=False):
     V = Vr + 1j * Vi if cplx else Vr
     return dict(U=U, sigma=sig, sigma_e=se, sigma_f=sf,
                 V=V, status=int(info[0]), sweeps=int(info[1]), rotations=int(rot[0]),
-                rescales=int(info[3]))
+                rescales=int(info[3]), gs=int(info[4]))
 
 
 def dpscl(q, p, compensated=False, eq=0, fq=1.0, ep=0, fp=1.0):

@@ -534,7 +534,7 @@ static void comp_term(double x, double y, double *s, double *t, double *s2, doub
  * component, reduced as s + (t + (s' + t')), then one division by
  * f_q f_p.  Reading: the imaginary stream accumulates Re g_q Im g_p -
  * Im g_q Re g_p, the imaginary part of the g_q^* g_p that the algorithm's
- * output line defines (the printed loop forms its conjugate). */
+ * stated output defines (the printed loop forms its conjugate). */
 static void zdpscl_comp(int64_t m, const double *qr, const double *qi, const double *pr,
                         const double *pi, int eq, double fq, int ep, double fp, double *zr,
                         double *zi)
@@ -646,6 +646,39 @@ static double zjrot(int64_t l, double *xpr, double *xpi, double *xqr, double *xq
   return M;
 }
 
+/* Eq. "e:GScond" in (e, f) form: ||x|| > 2^eta^ upsilon ||y||, eta^ =
+ * DBL_MAX_EXP - 1, for ||x|| = 2^ex fx, ||y|| = 2^ey fy. */
+static int gs_cond(int ex, double fx, int ey, double fy, double ups)
+{
+  const int d = ex - ey - (DBL_MAX_EXP - 1);
+  const int dc = (d > 4000) ? 4000 : (d < -4000) ? -4000 : d;
+  return ldexp(fx / fy, dc) > ups;
+}
+
+/* Eq. "e:GS" (Alg. ZGS / DGS): y <- (y / 2^ey - psi x / 2^ex) 2^ey on rows
+ * 0..l-1, psi = (psr, psi_i), in the operation order of Alg. ZGS.  Returns
+ * the max-norm of the new y. */
+static double gsscl(int64_t l, const double *xr, const double *xi, double *yr, double *yi, int ex,
+                    int ey, double psr, double psi_i)
+{
+  double M = 0.0;
+  for (int64_t i = 0; i < l; ++i) {
+    const double x1 = ldexp(xr[i], -ex), y1 = ldexp(yr[i], -ey);
+    if (xi) {
+      const double x2 = ldexp(xi[i], -ex), y2 = ldexp(yi[i], -ey);
+      const double re = fma(-psr, x1, fma(psi_i, x2, y1));
+      const double im = fma(-psr, x2, fma(-psi_i, x1, y2));
+      yr[i] = ldexp(re, ey);
+      yi[i] = ldexp(im, ey);
+      M = fmax(M, fmax(fabs(yr[i]), fabs(yi[i])));
+    } else {
+      yr[i] = ldexp(fma(-psr, x1, y1), ey);
+      M = fmax(M, fabs(yr[i]));
+    }
+  }
+  return M;
+}
+
 static void swap_cols(int64_t l, double *a, double *b)
 {
   for (int64_t i = 0; i < l; ++i) {
@@ -681,7 +714,8 @@ ORC_EXPORT int orc_num_threads(void)
  *     overwritten by U (columns of unit norm, zero columns stay zero).
  *   V (Vr, Vi): n x n, leading dimension n, overwritten by V.
  *   sig, sig_e, sig_f: n singular values, as doubles and as (e, f).
- *   out_info[4] = {status, sweeps, rotations (low 31 bits), rescales}.
+ *   out_info[5] = {status, sweeps, rotations (low 31 bits), rescales,
+ *     Gram-Schmidt transformations (low 31 bits)}.
  *   rotations64 receives the 64-bit rotation count (may be NULL).
  *   permute != 0 applies the column swap P during the sweeps.
  *   compensated != 0 forms the scaled dot-products by Alg. zdpscl' /
@@ -710,7 +744,7 @@ ORC_EXPORT int orc_vjsvd(int64_t m, int64_t n, double *Gr, double *Gi, int64_t l
   double Mt = maxnorm(m, n, Gr, ld);
   if (cplx) Mt = fmax(Mt, maxnorm(m, n, Gi, ld));
   if (!(Mt < INFINITY)) return ORC_E_NONFINITE;
-  int64_t rotations = 0;
+  int64_t rotations = 0, gs_count = 0;
   int rescales = 0, sweeps = 0, status = ORC_OK;
   int s = 0;
   /* floor(lg(nu/(varsigma m))) and friends, Eq. "e:skn" / "e:skr" */
@@ -751,7 +785,7 @@ ORC_EXPORT int orc_vjsvd(int64_t m, int64_t n, double *Gr, double *Gi, int64_t l
         }
         int64_t t = 0;
         double Mstep = 0.0;
-#pragma omp parallel for schedule(static) reduction(+ : t) reduction(max : Mstep)
+#pragma omp parallel for schedule(static) reduction(+ : t, gs_count) reduction(max : Mstep)
         for (int l = 0; l < L; ++l) {
           const int p = tab[2 * ((int64_t)k * L + l)], q = tab[2 * ((int64_t)k * L + l) + 1];
           if (q >= n) continue; /* phantom column */
@@ -792,7 +826,27 @@ ORC_EXPORT int orc_vjsvd(int64_t m, int64_t n, double *Gr, double *Gi, int64_t l
           else
             dsjac2_1(b11, b22, b21r, &c, &Ct, NULL, NULL, &zp, NULL, NULL);
           const int pbit = permute ? (zp & 1) : 0;
-          if (rot) {
+          /* Alg. zvjsvd: when Eq. "e:GScond" holds, Alg. ZGS / DGS replaces
+           * zjrot on G; V still takes the rotation */
+          const int gs_pq = rot && gs_cond(ep, fp, eq, fq, ups);
+          const int gs_qp = rot && !gs_pq && gs_cond(eq, fq, ep, fp, ups);
+          if (rot && (gs_pq || gs_qp)) {
+            double Mp;
+            if (gs_pq) /* g_q against g_p, psi = conj(a21') fq / fp */
+              Mp = gsscl(m, gpr, gpi, gqr, gqi, ep, eq, zr * (fq / fp), -(zi * (fq / fp)));
+            else /* g_p against g_q, psi = a21' fp / fq */
+              Mp = gsscl(m, gqr, gqi, gpr, gpi, eq, ep, zr * (fp / fq), zi * (fp / fq));
+            Mp = fmax(Mp, maxnorm(m, 1, gs_pq ? gpr : gqr, ld));
+            if (cplx) Mp = fmax(Mp, maxnorm(m, 1, gs_pq ? gpi : gqi, ld));
+            if (pbit) {
+              swap_cols(m, gpr, gqr);
+              if (cplx) swap_cols(m, gpi, gqi);
+            }
+            (void)zjrot(n, vpr, vpi, vqr, vqi, c, Ct, St, pbit);
+            Mstep = fmax(Mstep, Mp);
+            ++t;
+            ++gs_count;
+          } else if (rot) {
             const double Mp = zjrot(m, gpr, gpi, gqr, gqi, c, Ct, St, pbit);
             (void)zjrot(n, vpr, vpi, vqr, vqi, c, Ct, St, pbit);
             Mstep = fmax(Mstep, Mp);
@@ -886,6 +940,7 @@ ORC_EXPORT int orc_vjsvd(int64_t m, int64_t n, double *Gr, double *Gi, int64_t l
     out_info[1] = sweeps;
     out_info[2] = (int32_t)(rotations & 0x7fffffff);
     out_info[3] = rescales;
+    out_info[4] = (int32_t)(gs_count & 0x7fffffff);
   }
   if (rotations64) *rotations64 = rotations;
   return status;

@@ -10,11 +10,12 @@ from . import _native
 from ._native import (JSVD_COMPLEX, JSVD_E_CUDA, JSVD_E_NONFINITE, JSVD_E_TIMEOUT,
                       JSVD_E_UNSUPPORTED, JSVD_E_WORKSPACE, JSVD_FP64, JSVD_MIXED_FP32_FP64,
                       JSVD_NOT_CONVERGED, JSVD_OK, JSVD_REAL, JSVD_TUNE_BATCH_SMEM,
+                      JSVD_TUNE_EVD32_DIV,
                       JSVD_TUNE_BATCH_WARPS, JSVD_TUNE_EVD_ARITH, JSVD_TUNE_EVD_LAUNCH,
                       JSVD_TUNE_SVD_GRID, JsvdError)
 
 __all__ = ["evd2x2_batched", "evd2x2_batched_host", "evd2x2_host_workspace_size", "svd",
-           "svd_workspace_size", "ordering", "decode_info", "dgemm", "BatchedSVD", "pack_matrices", "svd_batched", "svd_adjoint_batched",
+           "svd_workspace_size", "colnorm_ef", "ordering", "decode_info", "dgemm", "BatchedSVD", "pack_matrices", "svd_batched", "svd_adjoint_batched",
            "sign_gauge_batched", "svd_diff", "version", "tune_set", "JsvdError", "JSVD_REAL",
            "JSVD_COMPLEX"]
 
@@ -56,7 +57,8 @@ def tune_set(knob, value, value2=0):
 
 def evd2x2_batched(a11, a22, a21_re, a21_im=None, *, out=None, want_lambda=True,
                    want_zeta_p=True, stream=None):
-    """Batched 2x2 Hermitian EVD (jsvd_evd2x2_batched).
+    """Batched 2x2 Hermitian EVD (jsvd_evd2x2_batched, or
+    jsvd_evd2x2_batched_f32 for float32 streams).
 
     Real if a21_im is None.  Returns a dict of CUDA tensors: cos_phi,
     ea_tan_re (REAL: sign(a21) tan(phi)), ea_tan_im (COMPLEX only), lambda1,
@@ -65,14 +67,16 @@ def evd2x2_batched(a11, a22, a21_re, a21_im=None, *, out=None, want_lambda=True,
     torch = _torch()
     cplx = a21_im is not None
     n = a11.numel()
-    s = _native.EvdStreams()
-    s.a11 = _vec(a11, "a11", n)
-    s.a22 = _vec(a22, "a22", n)
-    s.a21_re = _vec(a21_re, "a21_re", n)
-    s.a21_im = _vec(a21_im, "a21_im", n) if cplx else None
+    f32 = isinstance(a11, torch.Tensor) and a11.dtype == torch.float32
+    dt = torch.float32 if f32 else torch.float64
+    s = _native.EvdStreamsF32() if f32 else _native.EvdStreams()
+    s.a11 = _vec(a11, "a11", n, dt)
+    s.a22 = _vec(a22, "a22", n, dt)
+    s.a21_re = _vec(a21_re, "a21_re", n, dt)
+    s.a21_im = _vec(a21_im, "a21_im", n, dt) if cplx else None
     if out is None:
         dev = a11.device
-        e = lambda dt=torch.float64: torch.empty(n, dtype=dt, device=dev)
+        e = lambda t=dt: torch.empty(n, dtype=t, device=dev)
         out = {"cos_phi": e(), "ea_tan_re": e()}
         if cplx:
             out["ea_tan_im"] = e()
@@ -81,15 +85,19 @@ def evd2x2_batched(a11, a22, a21_re, a21_im=None, *, out=None, want_lambda=True,
             out["lambda2"] = e()
         if want_zeta_p:
             out["zeta_p"] = e(torch.int32)
-    s.cos_phi = _vec(out["cos_phi"], "cos_phi", n)
-    s.ea_tan_re = _vec(out["ea_tan_re"], "ea_tan_re", n)
-    s.ea_tan_im = _vec(out["ea_tan_im"], "ea_tan_im", n) if cplx else None
-    s.lambda1 = _vec(out["lambda1"], "lambda1", n) if "lambda1" in out else None
-    s.lambda2 = _vec(out["lambda2"], "lambda2", n) if "lambda2" in out else None
+    s.cos_phi = _vec(out["cos_phi"], "cos_phi", n, dt)
+    s.ea_tan_re = _vec(out["ea_tan_re"], "ea_tan_re", n, dt)
+    s.ea_tan_im = _vec(out["ea_tan_im"], "ea_tan_im", n, dt) if cplx else None
+    s.lambda1 = _vec(out["lambda1"], "lambda1", n, dt) if "lambda1" in out else None
+    s.lambda2 = _vec(out["lambda2"], "lambda2", n, dt) if "lambda2" in out else None
     s.zeta_p = _vec(out["zeta_p"], "zeta_p", n, torch.int32) if "zeta_p" in out else None
-    rc = _native.lib().jsvd_evd2x2_batched(JSVD_COMPLEX if cplx else JSVD_REAL,
-                                           ctypes.byref(s), n, _stream_handle(stream))
-    _native.check(rc, "jsvd_evd2x2_batched")
+    field = JSVD_COMPLEX if cplx else JSVD_REAL
+    L = _native.lib()
+    if f32:
+        rc = L.jsvd_evd2x2_batched_f32(field, ctypes.byref(s), n, _stream_handle(stream))
+    else:
+        rc = L.jsvd_evd2x2_batched(field, ctypes.byref(s), n, _stream_handle(stream))
+    _native.check(rc, "jsvd_evd2x2_batched_f32" if f32 else "jsvd_evd2x2_batched")
     return out
 
 
@@ -147,6 +155,28 @@ def evd2x2_batched_host(a11, a22, a21_re, a21_im=None, *, out=None, want_lambda=
     return out
 
 
+def colnorm_ef(A, stream=None):
+    """Wide-exponent Frobenius norms of the columns of a CUDA matrix
+    (jsvd_colnorm_ef, Alg. rnF): (e, f) float64 tensors with
+    ||a_j|| = 2^e_j f_j, e_j = -inf for a zero column."""
+    torch = _torch()
+    if not isinstance(A, torch.Tensor) or not A.is_cuda or A.dim() != 2:
+        raise TypeError("A must be a 2-D CUDA tensor")
+    cplx = A.dtype == torch.complex128
+    if not cplx and A.dtype != torch.float64:
+        raise TypeError("A must be float64 or complex128")
+    m, n = A.shape
+    Ac, lda = colmajor(A)
+    e = torch.empty(n, dtype=torch.float64, device=A.device)
+    f = torch.empty(n, dtype=torch.float64, device=A.device)
+    rc = _native.lib().jsvd_colnorm_ef(JSVD_COMPLEX if cplx else JSVD_REAL, m, n,
+                                       ctypes.c_void_p(Ac.data_ptr()), lda,
+                                       ctypes.c_void_p(e.data_ptr()),
+                                       ctypes.c_void_p(f.data_ptr()), _stream_handle(stream))
+    _native.check(rc, "jsvd_colnorm_ef")
+    return e, f
+
+
 # ---------------------------------------------------------------------------
 # SVD
 
@@ -193,14 +223,15 @@ def svd_workspace_size(m, n, complex_=False, mode="fp64"):
 
 
 def decode_info(info):
-    """jsvd_info tensor(s) (uint8, 24 bytes each, on any device) -> dict or
+    """jsvd_info tensor(s) (uint8, 32 bytes each, on any device) -> dict or
     list of dicts.  Synchronises with the device if info lives there."""
     import struct
     raw = bytes(info.detach().cpu().numpy().tobytes())
     out = []
     for k in range(len(raw) // _native.INFO_BYTES):
-        st, sw, rot, resc, s32 = struct.unpack_from("<iiqii", raw, k * _native.INFO_BYTES)
-        out.append(dict(status=st, sweeps=sw, rotations=rot, rescales=resc, sweeps_fp32=s32))
+        st, sw, rot, resc, s32, gs, _ = struct.unpack_from("<iiqiiii", raw, k * _native.INFO_BYTES)
+        out.append(dict(status=st, sweeps=sw, rotations=rot, rescales=resc, sweeps_fp32=s32,
+                        gs_steps=gs))
     return out[0] if len(out) == 1 else out
 
 
@@ -208,7 +239,7 @@ def svd(A, *, max_sweeps=0, mode="fp64", rescale_exp=0, permute=False, compensat
         work=None, out=None, stream=None):
     """One-sided Jacobi SVD of a CUDA tensor A (m x n, m >= n; float64 or
     complex128), jsvd_svd.  Returns dict(U, sigma, sigma_e, sigma_f, V,
-    info); U and V are column-major views, info a 24-byte device tensor
+    info); U and V are column-major views, info a 32-byte device tensor
     (decode_info).  compensated forms the pivot pairs' dot-products by the
     compensated summation (Alg. zdpscl' / ddpscl')."""
     torch = _torch()
@@ -288,7 +319,7 @@ class BatchedSVD:
     to back, matrix i column-major with lda = m[i] at element offset
     sum_{j<i} m[j] n[j].  Results: U (packed like A), V (matrix i, n[i] x
     n[i], at sum_{j<i} n[j]^2), sigma (sum_{j<i} n[j]), sigma_e, sigma_f,
-    info (count * 24 bytes).  The constructor runs jsvd_svd_batched_prepare;
+    info (count * 32 bytes).  The constructor runs jsvd_svd_batched_prepare;
     launch() enqueues the computation (it may be captured in a CUDA graph and
     replayed)."""
 
@@ -348,10 +379,28 @@ class BatchedSVD:
             self._lda, self._s, self._se, self._sf, self._V, self._ldv, self.work.data_ptr(),
             self.work.numel(), _stream_handle(None)), "jsvd_svd_batched_prepare")
 
+    warps = None  # warps per block; None: the library's choice for the batch
+
+    def autotune(self, **kw):
+        """Time the candidate warps per block on a sample of this batch
+        (autotune.tune_batched) and launch with the fastest from now on.
+        Returns the {warps: ms} timings (empty when cached)."""
+        from . import autotune
+        self.warps, times = autotune.tune_batched(self.A, self.m, self.n,
+                                                  compensated=bool(self.opts.compensated), **kw)
+        return times
+
     def launch(self, stream=None):
-        rc = _native.lib().jsvd_svd_batched_launch(self.field, ctypes.byref(self.opts), self.count,
-                                                   self.work.data_ptr(), self.info.data_ptr(),
-                                                   _stream_handle(stream))
+        L = _native.lib()
+        if self.warps:
+            tune_set(JSVD_TUNE_BATCH_WARPS, self.warps)
+        try:
+            rc = L.jsvd_svd_batched_launch(self.field, ctypes.byref(self.opts), self.count,
+                                           self.work.data_ptr(), self.info.data_ptr(),
+                                           _stream_handle(stream))
+        finally:
+            if self.warps:
+                tune_set(JSVD_TUNE_BATCH_WARPS, 0)
         _native.check(rc, "jsvd_svd_batched_launch")
         return self
 

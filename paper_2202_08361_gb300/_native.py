@@ -25,6 +25,7 @@ JSVD_TUNE_SVD_GRID = 2
 JSVD_TUNE_BATCH_WARPS = 3
 JSVD_TUNE_EVD_ARITH = 4
 JSVD_TUNE_BATCH_SMEM = 5
+JSVD_TUNE_EVD32_DIV = 6
 
 JSVD_FP64 = 0
 JSVD_MIXED_FP32_FP64 = 1
@@ -45,6 +46,12 @@ class EvdStreams(ctypes.Structure):
                  "lambda1", "lambda2", "zeta_p")]
 
 
+class EvdStreamsF32(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_void_p) for k in ("a11", "a22", "a21_re", "a21_im", "cos_phi",
+                                                "ea_tan_re", "ea_tan_im", "lambda1", "lambda2",
+                                                "zeta_p")]
+
+
 class Opts(ctypes.Structure):
     _fields_ = [("max_sweeps", ctypes.c_int32), ("mode", ctypes.c_int32),
                 ("rescale_exp", ctypes.c_int32), ("permute", ctypes.c_int32),
@@ -52,8 +59,9 @@ class Opts(ctypes.Structure):
 
 
 # jsvd_info as laid out in device memory: int32 status, int32 sweeps,
-# int64 rotations, int32 rescales, int32 sweeps_fp32 (24 bytes)
-INFO_BYTES = 24
+# int64 rotations, int32 rescales, int32 sweeps_fp32, int32 gs_steps,
+# int32 reserved (32 bytes)
+INFO_BYTES = 32
 
 # size of the static scratch of jsvd_svd_noalloc (JSVD_NOALLOC_SCRATCH_BYTES)
 NOALLOC_SCRATCH_BYTES = 16 << 20
@@ -82,6 +90,11 @@ def lib():
         L.jsvd_tune_set.restype = ctypes.c_int
         L.jsvd_evd2x2_batched.argtypes = [ctypes.c_int, ctypes.POINTER(EvdStreams), _i64, _vp]
         L.jsvd_evd2x2_batched.restype = ctypes.c_int
+        L.jsvd_evd2x2_batched_f32.argtypes = [ctypes.c_int, ctypes.POINTER(EvdStreamsF32), _i64,
+                                              _vp]
+        L.jsvd_evd2x2_batched_f32.restype = ctypes.c_int
+        L.jsvd_colnorm_ef.argtypes = [ctypes.c_int, _i64, _i64, _vp, _i64, _vp, _vp, _vp]
+        L.jsvd_colnorm_ef.restype = ctypes.c_int
         L.jsvd_evd2x2_host_workspace_size.argtypes = [ctypes.POINTER(ctypes.c_size_t)]
         L.jsvd_evd2x2_host_workspace_size.restype = ctypes.c_int
         L.jsvd_evd2x2_batched_host.argtypes = [ctypes.c_int, ctypes.POINTER(EvdStreams), _i64, _vp,

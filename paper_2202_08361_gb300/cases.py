@@ -1,6 +1,6 @@
 """Run one named workload once (for profiling and quick checks).
 
-    python -m paper_2202_08361_gb300.cases evd   [--log2 23]
+    python -m paper_2202_08361_gb300.cases evd   [--log2 23] [--f32]
     python -m paper_2202_08361_gb300.cases svd   [--m 1024 --n 512 --complex --normal
                                                   --mode fp64|mixed --reps 1]
     python -m paper_2202_08361_gb300.cases batch [--count 1000] [--shape 64x32]
@@ -25,6 +25,7 @@ def main(argv=None):
     p = argparse.ArgumentParser()
     p.add_argument("case", choices=["evd", "svd", "batch", "diff"])
     p.add_argument("--log2", type=int, default=23)
+    p.add_argument("--f32", action="store_true", help="evd: the binary32 EVD")
     p.add_argument("--m", type=int, default=1024)
     p.add_argument("--n", type=int, default=512)
     p.add_argument("--complex", action="store_true")
@@ -45,10 +46,11 @@ def main(argv=None):
 
     if a.case == "evd":
         r = 1 << a.log2
-        re_ = [torch.from_numpy(x).to(dev) for x in workloads.evd_batch(r, False)]
-        cx = [torch.from_numpy(x).to(dev) for x in workloads.evd_batch(r, True)]
+        gen = workloads.evd_batch_f32 if a.f32 else workloads.evd_batch
+        re_ = [torch.from_numpy(x).to(dev) for x in gen(r, False)]
+        cx = [torch.from_numpy(x).to(dev) for x in gen(r, True)]
         run = lambda: (J.evd2x2_batched(*re_), J.evd2x2_batched(*cx))
-        label = "evd r=2^%d real+complex" % a.log2
+        label = "evd r=2^%d real+complex %s" % (a.log2, "f32" if a.f32 else "f64")
     elif a.case == "svd":
         if a.normal:
             A = workloads.svd_normal(a.m, a.n)
@@ -60,9 +62,11 @@ def main(argv=None):
     elif a.case == "batch":
         import numpy as np
         if a.shape:
+            # drawn on the host (no device linear algebra, so this also runs
+            # under a profiler that hides torch's lazily loaded libraries)
             mm, nn = (int(x) for x in a.shape.split("x"))
-            A3 = workloads.diff_batch_device(count=a.count, m=mm, n=nn, device=dev)[0]
-            A = A3.transpose(1, 2).contiguous().view(-1)
+            A3 = workloads.diff_batch(count=a.count, m=mm, n=nn)[0]  # (count, m, n) column-major
+            A = torch.from_numpy(np.ascontiguousarray(A3.transpose(0, 2, 1))).reshape(-1).to(dev)
             m, n = np.full(a.count, mm), np.full(a.count, nn)
         else:
             A, m, n = workloads.uneven_batch_device(count=a.count, device=dev)

@@ -60,6 +60,7 @@ extern "C" int jsvd_tune_set(int knob, int value, int value2)
     case JSVD_TUNE_SVD_GRID: return jsvd::svd_set_grid(value, value2);
     case JSVD_TUNE_BATCH_WARPS: return jsvd::batch_set_warps(value);
     case JSVD_TUNE_BATCH_SMEM: return jsvd::batch_set_smem(value);
+    case JSVD_TUNE_EVD32_DIV: return jsvd::evd2f_set_fast(value);
     default: return -1;
   }
 }

@@ -99,6 +99,12 @@ static void launch_any(int v, int grid, int block, cudaStream_t st, const EvdPtr
   }
 }
 
+void evd2_get_launch(int &block, int &blocks_per_sm)
+{
+  block = g_evd_block;
+  blocks_per_sm = g_evd_blocks_per_sm;
+}
+
 int evd2_set_launch(int block, int blocks_per_sm)
 {
   if (block != 64 && block != 128 && block != 256) return -2;

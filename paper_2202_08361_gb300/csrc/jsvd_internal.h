@@ -5,9 +5,11 @@
 namespace jsvd {
 int evd2_set_launch(int block, int blocks_per_sm);
 int evd2_set_variant(int v, int fields);
+void evd2_get_launch(int &block, int &blocks_per_sm);
 int svd_set_grid(int cap, int warps);
 int batch_set_warps(int w);
 int batch_set_smem(int kib);
+int evd2f_set_fast(int v);
 }  // namespace jsvd
 
 #include <cuda_runtime.h>

@@ -41,7 +41,8 @@ struct SvdState {
   int rescales;
   int sweeps;
   int converged;
-  int T[kMaxSweepsCap];        // rotations per sweep
+  int T[kMaxSweepsCap];        // transformations per sweep
+  unsigned long long gs;       // Gram-Schmidt steps (Eq. e:GS) in all
 };
 
 struct SvdLayout {
@@ -99,14 +100,16 @@ __global__ void maxnorm_kernel(const double *__restrict__ A, int64_t lda, int64_
   if ((threadIdx.x & 31) == 0) atomicMax(out, mx);
 }
 
-// G_1 = 2^{s_0} A (planes), V_1 = I; s_0 brings ||A||_max into [1, 2).
-// Complex A is interleaved: plane r takes the even doubles, plane i the odd.
+// G_1 = 2^{s_0} A (planes), V_1 = I; s_0 brings ||A||_max into
+// [2^target, 2^(target + 1)).  Complex A is interleaved: plane r takes the
+// even doubles, plane i the odd.
 template <bool CPLX>
-__global__ void init_kernel(const double *__restrict__ A, int64_t lda, MatView M, SvdState *st)
+__global__ void init_kernel(const double *__restrict__ A, int64_t lda, MatView M, SvdState *st,
+                            int target)
 {
   const unsigned long long m0 = st->M0;
   const bool nonfinite = m0 >= kInf;
-  const int s0 = (m0 == 0ull || nonfinite) ? 0 : -flg(dbl(m0));
+  const int s0 = (m0 == 0ull || nonfinite) ? 0 : target - flg(dbl(m0));
   if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
     st->s = s0;
     st->nonfinite = nonfinite ? 1 : 0;
@@ -166,7 +169,8 @@ __global__ void __launch_bounds__(256) sweeps_kernel(MatViewT<T> M, SvdState *st
       const int cur = (int)(gstep % 3), nxt = (int)((gstep + 1) % 3), old = (int)((gstep + 2) % 3);
       const double Mcur = dbl(((volatile unsigned long long *)st->Mbuf)[cur]);
       // section 3.2, step 2: rescale when M~ has grown past 2^rescale_exp
-      const int rk = (bits(Mcur) != 0ull && flg(Mcur) >= rescale_exp) ? -flg(Mcur) : 0;
+      const int rk =
+          (bits(Mcur) != 0ull && flg(Mcur) >= rescale_exp) ? scale_target(rescale_exp) - flg(Mcur) : 0;
       if (blockIdx.x == 0 && threadIdx.x == 0) {
         st->Mbuf[old] = 0ull;
         atomicMax(&st->Mbuf[nxt], bits(rk ? ldexp_rn(Mcur, rk) : Mcur));
@@ -176,14 +180,15 @@ __global__ void __launch_bounds__(256) sweeps_kernel(MatViewT<T> M, SvdState *st
         }
       }
       unsigned long long Mloc = 0ull;
-      int rots = 0;
+      int rots = 0, gsn = 0;
       for (int base = blockIdx.x * W; base < L; base += gridDim.x * W)
         step_chunk<T, CPLX, true, COMP>(M, k, nt, base, W, ups, rk, (flags & kFlagPermute) != 0,
-                                        s_sums, s_out, Mloc, rots);
+                                        s_sums, s_out, Mloc, rots, gsn);
       Mloc = warp_umax(Mloc);
       if (lane == 0) {
         if (Mloc) atomicMax(&st->Mbuf[nxt], bits(magbits_to_double(Mloc, T(0))));
         if (rots) atomicAdd(&st->T[sweep], rots);
+        if (gsn) atomicAdd(&st->gs, (unsigned long long)gsn);
       }
       if (!grid_barrier(&st->bar_count, &st->bar_gen, &st->err, kBarrierLimitNs)) return;
     }
@@ -229,6 +234,8 @@ __global__ void rank_kernel(int n, const int *e, const double *f, int *rank, Svd
     out.rotations = rot;
     out.rescales = st->rescales;
     out.sweeps_fp32 = sw32;
+    out.gs_steps = (int32_t)(st->gs > 0x7fffffffull ? 0x7fffffffull : st->gs);
+    out.reserved = 0;
     *info = out;
   }
 }
@@ -282,7 +289,7 @@ int svd_check_opts(const jsvd_opts *o, int &S, int &mode, int &rexp, int &flags)
 {
   S = 100;
   mode = JSVD_FP64;
-  rexp = 256;
+  rexp = 480;
   flags = 0;
   if (!o) return 0;
   if (o->permute != 0 && o->permute != 1) return -1;
@@ -303,22 +310,24 @@ int svd_check_opts(const jsvd_opts *o, int &S, int &mode, int &rexp, int &flags)
 // ---------------------------------------------------------------------------
 // mixed precision: FP32 copies of the iteration matrix, FP64 conversion
 
-// G32 = fl32(G64) (planes), V32 = I, and the FP32 phase's state.
+// G32 = fl32(2^-target G64) (planes: max-norm back in [1, 2) for the FP32
+// range), V32 = I, and the FP32 phase's state.
 template <bool CPLX>
 __global__ void to_fp32_kernel(MatView M64, MatViewT<float> M32, const SvdState *st64,
-                               SvdState *st32)
+                               SvdState *st32, int target)
 {
   if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
     st32->nonfinite = st64->nonfinite;
-    st32->s = st64->s;
-    st32->Mbuf[0] = st64->Mbuf[0];
+    st32->s = st64->s - target;
+    st32->Mbuf[0] = st64->Mbuf[0] ? bits(ldexp_rn(dbl(st64->Mbuf[0]), -target)) : 0ull;
   }
   for (int j = blockIdx.y; j < M64.n; j += gridDim.y) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < max(M64.mp, M64.np);
          i += gridDim.x * blockDim.x) {
       if (i < M64.mp) {
-        M32.gr[j * M32.ldg + i] = __double2float_rn(M64.gr[j * M64.ldg + i]);
-        if (CPLX) M32.gi[j * M32.ldg + i] = __double2float_rn(M64.gi[j * M64.ldg + i]);
+        M32.gr[j * M32.ldg + i] = __double2float_rn(ldexp_rn(M64.gr[j * M64.ldg + i], -target));
+        if (CPLX)
+          M32.gi[j * M32.ldg + i] = __double2float_rn(ldexp_rn(M64.gi[j * M64.ldg + i], -target));
       }
       if (i < M64.np) {
         M32.vr[j * M32.ldv + i] = (i == j) ? 1.0f : 0.0f;
@@ -407,7 +416,7 @@ static MatViewT<T> view_at(char *work, size_t gr, size_t gi, size_t vr, size_t v
 
 // A1: ||A||_max, G_1 = 2^{s_0} A (planes) in M, V_1 = I.
 template <bool CPLX>
-static int phase_init(const MatView &M, const double *A, int64_t lda, SvdState *state,
+static int phase_init(const MatView &M, const double *A, int64_t lda, SvdState *state, int rexp,
                       cudaStream_t st)
 {
   const int sms = sm_count();
@@ -420,7 +429,7 @@ static int phase_init(const MatView &M, const double *A, int64_t lda, SvdState *
   maxnorm_kernel<<<(int)blocks, 256, 0, st>>>(A, ld, rows, n, &state->M0);
   JSVD_CHECK_LAUNCH();
   dim3 grid((unsigned)((std::max(M.mp, M.np) + 255) / 256), (unsigned)std::min<int64_t>(n, 65535));
-  init_kernel<CPLX><<<grid, 256, 0, st>>>(A, lda, M, state);
+  init_kernel<CPLX><<<grid, 256, 0, st>>>(A, lda, M, state, scale_target(rexp));
   JSVD_CHECK_LAUNCH();
   return JSVD_OK;
 }
@@ -497,7 +506,7 @@ static int svd_fp64_run(int64_t m, int64_t n, const double *A, int64_t lda, doub
   const SvdLayout L = svd_layout(CPLX, m, n);
   SvdState *state = reinterpret_cast<SvdState *>(work + L.state);
   const MatView M = view_at<double>(work, L.gr, L.gi, L.vr, L.vi, CPLX, L, m, n);
-  JSVD_TRY(phase_init<CPLX>(M, A, lda, state, st));
+  JSVD_TRY(phase_init<CPLX>(M, A, lda, state, rexp, st));
   JSVD_TRY(phase_sweeps<double, CPLX>(M, state, ldexp(sqrt((double)m), -53), S, rexp, flags, st));
   return phase_finish<CPLX>(M, reinterpret_cast<int *>(work + L.e),
                             reinterpret_cast<double *>(work + L.f),
@@ -533,11 +542,11 @@ static int svd_mixed_run_t(int64_t m, int64_t n, const double *A, int64_t lda, d
   if (!CPLX) Bi = Xi = nullptr;
 
   // A1 on the FP64 planes: M0.g = 2^{s_0} A
-  JSVD_TRY(phase_init<CPLX>(M0, A, lda, st64, st));
+  JSVD_TRY(phase_init<CPLX>(M0, A, lda, st64, rexp, st));
   // FP32 phase
   JSVD_CUDA(cudaMemsetAsync(st32, 0, sizeof(SvdState), st));
   dim3 grid((unsigned)((std::max(L.mp, L.np) + 255) / 256), (unsigned)std::min<int64_t>(n, 65535));
-  to_fp32_kernel<CPLX><<<grid, 256, 0, st>>>(M0, M32, st64, st32);
+  to_fp32_kernel<CPLX><<<grid, 256, 0, st>>>(M0, M32, st64, st32, scale_target(rexp));
   JSVD_CHECK_LAUNCH();
   const double ups32 = ldexp(sqrt((double)m), kMixedTolExp);
   JSVD_TRY(phase_sweeps<float, CPLX>(M32, st32, ups32, S, 1 << 20, flags, st));

@@ -12,6 +12,8 @@
 // jsvd_svd, in any batch, in any position and with any block shape.
 #include <algorithm>
 #include <climits>
+#include <mutex>
+#include <unordered_map>
 #include <vector>
 
 #include "common.cuh"
@@ -70,14 +72,50 @@ static BatchLayout batch_layout(int64_t count)
   return L;
 }
 
-static int g_batch_warps = 8;
+static int g_batch_warps = 0;  // 0: chosen per prepared batch (batch_auto_warps)
 static int g_batch_smem_kib = 0;
 
 int batch_set_warps(int w)
 {
-  if (w != 1 && w != 2 && w != 4 && w != 8 && w != 16) return -2;
+  if (w != 0 && w != 1 && w != 2 && w != 4 && w != 8 && w != 16) return -2;
   g_batch_warps = w;
   return JSVD_OK;
+}
+
+// Warps per block for a batch: small matrices want many blocks per SM (one
+// warp each hides the pair rotations' latency across matrices), large ones
+// many warps per matrix.  The rule keys on the mean n weighted by the cost
+// of a sweep (m n^2), measured on GB300: 4096 x (64 x 32) is fastest with 1
+// warp, the 10,000 uneven matrices (n up to 256) with 16.
+static int batch_auto_warps(int64_t count, const int64_t *m, const int64_t *n)
+{
+  double w = 0.0, wn = 0.0;
+  for (int64_t i = 0; i < count; ++i) {
+    const double c = (double)m[i] * (double)n[i] * (double)n[i];
+    w += c;
+    wn += c * (double)n[i];
+  }
+  const double navg = (w > 0.0) ? wn / w : 0.0;
+  return navg <= 40.0 ? 1 : navg <= 64.0 ? 2 : navg <= 96.0 ? 4 : navg <= 160.0 ? 8 : 16;
+}
+
+// The automatic choice of each prepared workspace, read by the launch (a
+// host-side table, so the launch needs no device read and stays capturable).
+static std::mutex g_auto_mu;
+static std::unordered_map<const void *, int> g_auto_warps;
+
+static void remember_auto(const void *work, int w)
+{
+  std::lock_guard<std::mutex> lk(g_auto_mu);
+  if (g_auto_warps.size() > 4096) g_auto_warps.clear();
+  g_auto_warps[work] = w;
+}
+
+static int recall_auto(const void *work)
+{
+  std::lock_guard<std::mutex> lk(g_auto_mu);
+  const auto it = g_auto_warps.find(work);
+  return it == g_auto_warps.end() ? 8 : it->second;
 }
 
 // Largest dynamic shared memory a block may take beside the kernel's static
@@ -97,7 +135,157 @@ __host__ __device__ __forceinline__ size_t smem_need(bool cplx, int mp, int np, 
   return sizeof(double) * ((size_t)mp + (size_t)np) * (size_t)n * (cplx ? 2 : 1);
 }
 
-template <bool CPLX, bool COMP>
+// Shared state of a block while it works on one matrix.
+struct BatchShared {
+  int idx;
+  unsigned long long M0;
+  unsigned long long M[3];
+  int T;
+  int s;
+  int rescales;
+  unsigned long long gs;
+  PairSums sums[32];
+  PairOut out[32];
+};
+
+// Every phase of the SVD of one matrix (descriptor d, view M of its G and
+// V, e/f/rank scratch in its region) by the whole block.
+template <bool CPLX, bool COMP, bool CG>
+__device__ __forceinline__ void batch_one(BatchShared &sh, const BatchDesc &d, int idx,
+                                          const MatViewT<double, CG> &M, int *e, double *f,
+                                          int *rank, jsvd_info *info, int S, int rexp, int flags)
+{
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
+  // A1: max-norm of A (NaN -> Inf), s_0, G_1 = 2^{s_0} A, V_1 = I
+  if (threadIdx.x == 0) {
+    sh.M0 = 0ull;
+    sh.T = 0;
+    sh.rescales = 0;
+    sh.gs = 0ull;
+  }
+  __syncthreads();
+  {
+    const int64_t rows = CPLX ? 2 * (int64_t)d.m : d.m, ld = CPLX ? 2 * d.lda : d.lda;
+    unsigned long long mx = 0ull;
+    for (int64_t q = threadIdx.x; q < rows * d.n; q += blockDim.x) {
+      const int64_t j = q / rows, i = q - j * rows;
+      unsigned long long a = abits(d.A[j * ld + i]);
+      a = (a > kInf) ? kInf : a;
+      mx = (a > mx) ? a : mx;
+    }
+    mx = warp_umax(mx);
+    if (lane == 0) atomicMax(&sh.M0, mx);
+  }
+  __syncthreads();
+  const unsigned long long m0 = sh.M0;
+  const bool bad = m0 >= kInf;
+  const int s0 = (m0 == 0ull || bad) ? 0 : scale_target(rexp) - flg(dbl(m0));
+  for (int64_t q = threadIdx.x; q < (int64_t)d.mp * d.n; q += blockDim.x) {
+    const int j = (int)(q / d.mp), i = (int)(q - (int64_t)j * d.mp);
+    double xr = 0.0, xi = 0.0;
+    if (i < d.m && !bad) {
+      if (CPLX) {
+        xr = ldexp_rn(d.A[2 * (j * d.lda + i)], s0);
+        xi = ldexp_rn(d.A[2 * (j * d.lda + i) + 1], s0);
+      } else {
+        xr = ldexp_rn(d.A[j * d.lda + i], s0);
+      }
+    }
+    M.st(M.gr + j * M.ldg + i, xr);
+    if (CPLX) M.st(M.gi + j * M.ldg + i, xi);
+  }
+  for (int64_t q = threadIdx.x; q < (int64_t)d.np * d.n; q += blockDim.x) {
+    const int j = (int)(q / d.np), i = (int)(q - (int64_t)j * d.np);
+    M.st(M.vr + j * M.ldv + i, (i == j) ? 1.0 : 0.0);
+    if (CPLX) M.st(M.vi + j * M.ldv + i, 0.0);
+  }
+  if (threadIdx.x == 0) {
+    sh.s = s0;
+    sh.M[0] = (m0 == 0ull || bad) ? 0ull : bits(ldexp_rn(dbl(m0), s0));
+    sh.M[1] = sh.M[2] = 0ull;
+  }
+  __syncthreads();
+
+  // A2-A8: the sweeps (as sweeps_kernel, with a block barrier per step)
+  int sweeps = 0;
+  bool conv = false;
+  long long rot_total = 0;
+  if (!bad) {
+    const int nt = d.n + (d.n & 1), K = nt - 1, L = nt / 2;
+    const double ups = ldexp_rn(__dsqrt_rn((double)d.m), -53);  // Eq. e:tol
+    if (K < 1) {
+      sweeps = 1;
+      conv = true;
+    }
+    unsigned long long gstep = 0;
+    for (int sweep = 0; sweep < S && !conv; ++sweep) {
+      for (int k = 0; k < K; ++k, ++gstep) {
+        const int cur = (int)(gstep % 3), nxt = (int)((gstep + 1) % 3), old = (int)((gstep + 2) % 3);
+        const double Mcur = dbl(sh.M[cur]);
+        const int rk =
+            (bits(Mcur) != 0ull && flg(Mcur) >= rexp) ? scale_target(rexp) - flg(Mcur) : 0;
+        if (threadIdx.x == 0) {
+          sh.M[old] = 0ull;
+          atomicMax(&sh.M[nxt], bits(rk ? ldexp_rn(Mcur, rk) : Mcur));
+          if (rk) {
+            sh.s += rk;
+            sh.rescales += 1;
+          }
+        }
+        unsigned long long Mloc = 0ull;
+        int rots = 0, gsn = 0;
+        for (int base = 0; base < L; base += 32)
+          step_chunk<double, CPLX, CG, COMP>(M, k, nt, base, 32, ups, rk,
+                                             (flags & kFlagPermute) != 0, sh.sums, sh.out, Mloc,
+                                             rots, gsn);
+        Mloc = warp_umax(Mloc);
+        if (lane == 0) {
+          if (Mloc) atomicMax(&sh.M[nxt], Mloc);
+          if (rots) atomicAdd(&sh.T, rots);
+          if (gsn) atomicAdd(&sh.gs, (unsigned long long)gsn);
+        }
+        __syncthreads();
+      }
+      const int T = sh.T;
+      rot_total += T;
+      sweeps = sweep + 1;
+      conv = (T == 0);
+      __syncthreads();
+      if (threadIdx.x == 0) sh.T = 0;
+      __syncthreads();
+    }
+  }
+
+  // A9: norms, order, outputs, info
+  for (int j = warp; j < d.n; j += W) colnorm_warp<CPLX>(M, j, lane, e, f);
+  __syncthreads();
+  for (int j = threadIdx.x; j < d.n; j += blockDim.x) rank[j] = rank_of(d.n, e, f, j);
+  __syncthreads();
+  const int sfin = sh.s;
+  const int R = max(d.m, d.n);
+  for (int64_t q = threadIdx.x; q < (int64_t)R * d.n; q += blockDim.x) {
+    const int j = (int)(q / R), i = (int)(q - (int64_t)j * R);
+    const int r = rank[j];
+    if (i == 0) output_sigma(r, e[j], f[j], sfin, bad, d.sigma, d.sigma_e, d.sigma_f);
+    output_elem<CPLX>(M, i, j, r, e[j], f[j], bad, d.U, d.ldu, d.V, d.ldv);
+  }
+  if (info && threadIdx.x == 0) {
+    jsvd_info out;
+    out.status = bad ? JSVD_E_NONFINITE : conv ? 0 : JSVD_NOT_CONVERGED;
+    out.sweeps = sweeps;
+    out.rotations = rot_total;
+    out.rescales = sh.rescales;
+    out.sweeps_fp32 = 0;
+    out.gs_steps = (int32_t)(sh.gs > 0x7fffffffull ? 0x7fffffffull : sh.gs);
+    out.reserved = 0;
+    info[idx] = out;
+  }
+}
+
+// One block per matrix at a time; G and V stay in the matrix's region (all
+// accesses through L2, ld/st.cg, which measured faster than L1-cached ones
+// here), or, when SMEM and they fit in smem_cap bytes, in shared memory.
+template <bool CPLX, bool COMP, bool SMEM>
 __global__ void __launch_bounds__(512) batched_kernel(const BatchDesc *__restrict__ desc,
                                                        const int *__restrict__ order,
                                                        BatchHdr *hdr, char *work, jsvd_info *info,
@@ -105,173 +293,54 @@ __global__ void __launch_bounds__(512) batched_kernel(const BatchDesc *__restric
                                                        size_t smem_cap)
 {
   extern __shared__ __align__(16) double s_dyn[];
-  __shared__ int s_idx;
-  __shared__ unsigned long long s_M0;
-  __shared__ unsigned long long s_M[3];
-  __shared__ int s_T;
-  __shared__ int s_s;
-  __shared__ int s_rescales;
-  __shared__ PairSums s_sums[32];
-  __shared__ PairOut s_out[32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
+  __shared__ BatchShared sh;
   const int count = hdr->count;
   for (;;) {
-    if (threadIdx.x == 0) s_idx = atomicAdd(&hdr->next, 1);
+    if (threadIdx.x == 0) sh.idx = atomicAdd(&hdr->next, 1);
     __syncthreads();
-    const int t = s_idx;
+    const int t = sh.idx;
     if (t >= count) break;
     const int idx = order[t];
     const BatchDesc d = desc[idx];
-    // The block owns the matrix: plain loads and stores (L1 may serve
-    // them), G and V in shared memory when both fit in smem_cap bytes.
-    MatViewT<double, false> M;
     char *reg = work + d.off;
     const size_t gbytes = sizeof(double) * (size_t)d.mp * d.n;
     const size_t vbytes = sizeof(double) * (size_t)d.np * d.n;
-    if (smem_need(CPLX, d.mp, d.np, d.n) <= smem_cap) {
-      const int64_t g = (int64_t)d.mp * d.n, v = (int64_t)d.np * d.n;
-      M.gr = s_dyn;
-      M.gi = CPLX ? s_dyn + g : nullptr;
-      M.vr = s_dyn + (CPLX ? 2 * g : g);
-      M.vi = CPLX ? s_dyn + 2 * g + v : nullptr;
-    } else {
-      M.gr = reinterpret_cast<double *>(reg);
-      M.gi = CPLX ? reinterpret_cast<double *>(reg + al256(gbytes)) : nullptr;
-      const size_t ov = al256(gbytes) * (CPLX ? 2 : 1);
-      M.vr = reinterpret_cast<double *>(reg + ov);
-      M.vi = CPLX ? reinterpret_cast<double *>(reg + ov + al256(vbytes)) : nullptr;
-    }
     size_t o = (al256(gbytes) + al256(vbytes)) * (CPLX ? 2 : 1);
     int *e = reinterpret_cast<int *>(reg + o);
     o = al256(o + sizeof(int) * (size_t)d.n);
     double *f = reinterpret_cast<double *>(reg + o);
     o = al256(o + sizeof(double) * (size_t)d.n);
     int *rank = reinterpret_cast<int *>(reg + o);
-    M.m = d.m;
-    M.n = d.n;
-    M.mp = d.mp;
-    M.np = d.np;
-    M.ldg = d.mp;
-    M.ldv = d.np;
-
-    // A1: max-norm of A (NaN -> Inf), s_0, G_1 = 2^{s_0} A, V_1 = I
-    if (threadIdx.x == 0) {
-      s_M0 = 0ull;
-      s_T = 0;
-      s_rescales = 0;
-    }
-    __syncthreads();
-    {
-      const int64_t rows = CPLX ? 2 * (int64_t)d.m : d.m, ld = CPLX ? 2 * d.lda : d.lda;
-      unsigned long long mx = 0ull;
-      for (int64_t q = threadIdx.x; q < rows * d.n; q += blockDim.x) {
-        const int64_t j = q / rows, i = q - j * rows;
-        unsigned long long a = abits(d.A[j * ld + i]);
-        a = (a > kInf) ? kInf : a;
-        mx = (a > mx) ? a : mx;
-      }
-      mx = warp_umax(mx);
-      if (lane == 0) atomicMax(&s_M0, mx);
-    }
-    __syncthreads();
-    const unsigned long long m0 = s_M0;
-    const bool bad = m0 >= kInf;
-    const int s0 = (m0 == 0ull || bad) ? 0 : -flg(dbl(m0));
-    for (int64_t q = threadIdx.x; q < (int64_t)d.mp * d.n; q += blockDim.x) {
-      const int j = (int)(q / d.mp), i = (int)(q - (int64_t)j * d.mp);
-      double xr = 0.0, xi = 0.0;
-      if (i < d.m && !bad) {
-        if (CPLX) {
-          xr = ldexp_rn(d.A[2 * (j * d.lda + i)], s0);
-          xi = ldexp_rn(d.A[2 * (j * d.lda + i) + 1], s0);
-        } else {
-          xr = ldexp_rn(d.A[j * d.lda + i], s0);
-        }
-      }
-      M.gr[j * M.ldg + i] = xr;
-      if (CPLX) M.gi[j * M.ldg + i] = xi;
-    }
-    for (int64_t q = threadIdx.x; q < (int64_t)d.np * d.n; q += blockDim.x) {
-      const int j = (int)(q / d.np), i = (int)(q - (int64_t)j * d.np);
-      M.vr[j * M.ldv + i] = (i == j) ? 1.0 : 0.0;
-      if (CPLX) M.vi[j * M.ldv + i] = 0.0;
-    }
-    if (threadIdx.x == 0) {
-      s_s = s0;
-      s_M[0] = (m0 == 0ull || bad) ? 0ull : bits(ldexp_rn(dbl(m0), s0));
-      s_M[1] = s_M[2] = 0ull;
-    }
-    __syncthreads();
-
-    // A2-A8: the sweeps (as sweeps_kernel, with a block barrier per step)
-    int sweeps = 0;
-    bool conv = false;
-    long long rot_total = 0;
-    if (!bad) {
-      const int nt = d.n + (d.n & 1), K = nt - 1, L = nt / 2;
-      const double ups = ldexp_rn(__dsqrt_rn((double)d.m), -53);  // Eq. e:tol
-      if (K < 1) {
-        sweeps = 1;
-        conv = true;
-      }
-      unsigned long long gstep = 0;
-      for (int sweep = 0; sweep < S && !conv; ++sweep) {
-        for (int k = 0; k < K; ++k, ++gstep) {
-          const int cur = (int)(gstep % 3), nxt = (int)((gstep + 1) % 3), old = (int)((gstep + 2) % 3);
-          const double Mcur = dbl(s_M[cur]);
-          const int rk = (bits(Mcur) != 0ull && flg(Mcur) >= rexp) ? -flg(Mcur) : 0;
-          if (threadIdx.x == 0) {
-            s_M[old] = 0ull;
-            atomicMax(&s_M[nxt], bits(rk ? ldexp_rn(Mcur, rk) : Mcur));
-            if (rk) {
-              s_s += rk;
-              s_rescales += 1;
-            }
-          }
-          unsigned long long Mloc = 0ull;
-          int rots = 0;
-          for (int base = 0; base < L; base += 32)
-            step_chunk<double, CPLX, false, COMP>(M, k, nt, base, 32, ups, rk,
-                                                  (flags & kFlagPermute) != 0, s_sums, s_out, Mloc,
-                                     rots);
-          Mloc = warp_umax(Mloc);
-          if (lane == 0) {
-            if (Mloc) atomicMax(&s_M[nxt], Mloc);
-            if (rots) atomicAdd(&s_T, rots);
-          }
-          __syncthreads();
-        }
-        const int T = s_T;
-        rot_total += T;
-        sweeps = sweep + 1;
-        conv = (T == 0);
-        __syncthreads();
-        if (threadIdx.x == 0) s_T = 0;
-        __syncthreads();
-      }
-    }
-
-    // A9: norms, order, outputs, info
-    for (int j = warp; j < d.n; j += W) colnorm_warp<CPLX>(M, j, lane, e, f);
-    __syncthreads();
-    for (int j = threadIdx.x; j < d.n; j += blockDim.x) rank[j] = rank_of(d.n, e, f, j);
-    __syncthreads();
-    const int sfin = s_s;
-    const int R = max(d.m, d.n);
-    for (int64_t q = threadIdx.x; q < (int64_t)R * d.n; q += blockDim.x) {
-      const int j = (int)(q / R), i = (int)(q - (int64_t)j * R);
-      const int r = rank[j];
-      if (i == 0) output_sigma(r, e[j], f[j], sfin, bad, d.sigma, d.sigma_e, d.sigma_f);
-      output_elem<CPLX>(M, i, j, r, e[j], f[j], bad, d.U, d.ldu, d.V, d.ldv);
-    }
-    if (info && threadIdx.x == 0) {
-      jsvd_info out;
-      out.status = bad ? JSVD_E_NONFINITE : conv ? 0 : JSVD_NOT_CONVERGED;
-      out.sweeps = sweeps;
-      out.rotations = rot_total;
-      out.rescales = s_rescales;
-      out.sweeps_fp32 = 0;
-      info[idx] = out;
+    bool in_smem = false;
+    if constexpr (SMEM) in_smem = smem_need(CPLX, d.mp, d.np, d.n) <= smem_cap;
+    if (in_smem) {
+      const int64_t g = (int64_t)d.mp * d.n, v = (int64_t)d.np * d.n;
+      MatViewT<double, false> M;
+      M.gr = s_dyn;
+      M.gi = CPLX ? s_dyn + g : nullptr;
+      M.vr = s_dyn + (CPLX ? 2 * g : g);
+      M.vi = CPLX ? s_dyn + 2 * g + v : nullptr;
+      M.m = d.m;
+      M.n = d.n;
+      M.mp = d.mp;
+      M.np = d.np;
+      M.ldg = d.mp;
+      M.ldv = d.np;
+      batch_one<CPLX, COMP, false>(sh, d, idx, M, e, f, rank, info, S, rexp, flags);
+    } else {
+      MatViewT<double, true> M;
+      M.gr = reinterpret_cast<double *>(reg);
+      M.gi = CPLX ? reinterpret_cast<double *>(reg + al256(gbytes)) : nullptr;
+      const size_t ov = al256(gbytes) * (CPLX ? 2 : 1);
+      M.vr = reinterpret_cast<double *>(reg + ov);
+      M.vi = CPLX ? reinterpret_cast<double *>(reg + ov + al256(vbytes)) : nullptr;
+      M.m = d.m;
+      M.n = d.n;
+      M.mp = d.mp;
+      M.np = d.np;
+      M.ldg = d.mp;
+      M.ldv = d.np;
+      batch_one<CPLX, COMP, true>(sh, d, idx, M, e, f, rank, info, S, rexp, flags);
     }
     __syncthreads();
   }
@@ -361,6 +430,7 @@ extern "C" int jsvd_svd_batched_prepare(jsvd_field field, const jsvd_opts *opts,
     const double cb = (double)m[b] * (double)n[b] * (double)n[b];
     return ca > cb;
   });
+  remember_auto(work, batch_auto_warps(count, m, n));
   BatchHdr h = {0, (int)count, 0, 0};
   char *w = (char *)work;
   cudaStream_t st = as_stream(stream);
@@ -391,17 +461,22 @@ extern "C" int jsvd_svd_batched_launch(jsvd_field field, const jsvd_opts *opts, 
   cudaStream_t st = as_stream(stream);
   // rewind the queue (graph-capturable: a memset node)
   JSVD_CUDA(cudaMemsetAsync(w + L.hdr, 0, sizeof(int), st));
-  const int threads = 32 * g_batch_warps;
+  const int threads = 32 * (g_batch_warps ? g_batch_warps : recall_auto(work));
   const size_t smem = (size_t)g_batch_smem_kib * 1024;
   int per_sm = 0;
   const bool cplx = (field == JSVD_COMPLEX);
   const bool comp = (flags & kFlagComp) != 0;
-  auto kern = cplx ? (comp ? batched_kernel<true, true> : batched_kernel<true, false>)
-                   : (comp ? batched_kernel<false, true> : batched_kernel<false, false>);
+  using Kern = void (*)(const BatchDesc *, const int *, BatchHdr *, char *, jsvd_info *, int, int,
+                        int, size_t);
+  static const Kern kerns[8] = {batched_kernel<false, false, false>, batched_kernel<false, false, true>,
+                                batched_kernel<false, true, false>,  batched_kernel<false, true, true>,
+                                batched_kernel<true, false, false>,  batched_kernel<true, false, true>,
+                                batched_kernel<true, true, false>,   batched_kernel<true, true, true>};
+  const int ki = (cplx ? 4 : 0) + (comp ? 2 : 0) + (smem > 0 ? 1 : 0);
+  const Kern kern = kerns[ki];
   // opt in to the dynamic shared memory (static + dynamic may pass the
   // 48 KiB default even when the budget alone does not)
-  static int attr_set[4] = {-1, -1, -1, -1};
-  const int ki = (cplx ? 2 : 0) + (comp ? 1 : 0);
+  static int attr_set[8] = {-1, -1, -1, -1, -1, -1, -1, -1};
   if (smem > 0 && attr_set[ki] != g_batch_smem_kib) {
     JSVD_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     attr_set[ki] = g_batch_smem_kib;

@@ -4,8 +4,9 @@
 //
 // The warp reads the pair's columns once for the three sums, reduces them
 // in a canonical order (lane l accumulates rows l, l+32, l+64, ... in
-// ascending order with fma, then an xor butterfly over offsets 16, 8, 4, 2,
-// 1), so the bits never depend on the launch shape.  Lane 0 forms the (e,f)
+// ascending order with fma, then one fixed reduction tree over the lanes for
+// all the sums, warp_sum_slots), so the bits never depend on the launch
+// shape.  Lane 0 forms the (e,f)
 // norms, the scaled dot-product (Alg. zdpscl semantics: power-of-two
 // prescaling, one final division by f_q f_p), the convergence test
 // (Eq. e:tol, Alg. cvg), the scaled Grammian (Alg. Gram) and its 2x2 EVD,
@@ -16,6 +17,7 @@
 #include <climits>
 
 #include "evd2.cuh"
+#include "normef.cuh"
 
 namespace jsvd {
 
@@ -81,6 +83,14 @@ struct MatViewT {
 };
 using MatView = MatViewT<double>;
 
+// The binade the iteration matrix's max-norm is brought to, at the start
+// and by every rescaling (section 3.2), for the rescale bound 2^rexp: 24
+// binades below the bound (no rescaling while the max-norm grows by less
+// than 2^24, about sqrt(m n) at most), 0 for small bounds.  The high scale
+// leaves tiny columns the most room above the subnormal range; the squares
+// of an m x n G below 2^480 cannot overflow for m <= 2^24.
+__host__ __device__ __forceinline__ int scale_target(int rexp) { return rexp > 25 ? rexp - 25 : 0; }
+
 // The round-robin parallel ordering (section 4.1): pair l of step k among
 // nt (even) columns; pairs with q >= n are phantom pairs.
 __device__ __forceinline__ void pair_of(int k, int l, int nt, int &p, int &q)
@@ -104,6 +114,49 @@ __device__ __forceinline__ double warp_sum(double x)
 #pragma unroll
   for (int o = 16; o; o >>= 1) x = __dadd_rn(x, __shfl_xor_sync(0xffffffffu, x, o));
   return x;
+}
+
+// Sums over the warp of N per-lane values (N = 4 or 16) in a fixed tree
+// that spends 6 (N = 4) or 16 (N = 16) FP64 additions per lane instead of
+// the 5 N of one butterfly per value: at the
+// stages with offsets 16, 8, ... the two lanes of a pair split the values
+// still held (the lane with the offset bit clear keeps the lower half) and
+// each adds its partner's copies of the half it keeps; once one value is
+// left the remaining offsets are a plain xor butterfly.  On return lane l
+// holds the total of slot (l >> (5 - lg N)) in v[0]; warp_slot() reads a
+// slot from any lane.  The tree does not depend on the launch.
+template <int N>
+__device__ __forceinline__ double warp_sum_slots(double (&v)[N])
+{
+  static_assert(N == 4 || N == 16, "4 or 16 slots");
+  const int lane = threadIdx.x & 31;
+  int count = N;
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    if (count > 1) {
+      const int half = count / 2;
+      const bool up = (lane & o) != 0;
+#pragma unroll
+      for (int k = 0; k < N / 2; ++k) {
+        if (k < half) {
+          const double keep = up ? v[k + half] : v[k];
+          const double send = up ? v[k] : v[k + half];
+          v[k] = __dadd_rn(keep, __shfl_xor_sync(0xffffffffu, send, o));
+        }
+      }
+      count = half;
+    } else {
+      v[0] = __dadd_rn(v[0], __shfl_xor_sync(0xffffffffu, v[0], o));
+    }
+  }
+  return v[0];
+}
+
+// Slot k of a warp_sum_slots<N> result, broadcast to every lane.
+template <int N>
+__device__ __forceinline__ double warp_slot(double x, int k)
+{
+  return __shfl_sync(0xffffffffu, x, k * (32 / N));
 }
 
 __device__ __forceinline__ unsigned long long warp_umax(unsigned long long x)
@@ -143,6 +196,32 @@ __device__ __forceinline__ void scale_col(const MatViewT<T, CG> &M, T *x, int k,
 struct PairOut {
   bool rot, swap;
   double c, C, S;
+  // Gram-Schmidt step (Eq. e:GS) in place of the rotation on G: gs = 1
+  // orthogonalises g_q against g_p, gs = 2 g_p against g_q; the source
+  // column is scaled by 2^-ex, the target by 2^-ey, psi = psr + i psi_i
+  int gs, ex, ey;
+  double psr, psi;
+};
+
+// Eq. e:GScond in (e, f) form: ||x|| > 2^eta^ upsilon ||y||, eta^ = 1023,
+// with q = fx / fy already formed.
+__device__ __forceinline__ bool gs_cond(int ex, int ey, double q, double ups)
+{
+  int d = ex - ey - 1023;
+  d = d > 4000 ? 4000 : (d < -4000 ? -4000 : d);
+  return bits(ldexp_rn(q, d)) > bits(ups);
+}
+
+// The sums of one pivot pair.  Normally pp = ||g_p||^2, qq = ||g_q||^2 and
+// (qr, qi) = g_q^* g_p of the current G.  When a column's squares underflow
+// (wide): (ep, fp), (eq, fq) are the columns' norms from Alg. rnF and
+// (qr, qi) = (g_q / 2^eq)^* (g_p / 2^ep), the prescaled dot-product of
+// Alg. zdpscl.
+struct PairSums {
+  double pp, qq, qr, qi;
+  double fp, fq;
+  int ep, eq;
+  int wide;
 };
 
 // From the sums to the rotation (Alg. zdpscl's division, Alg. cvg,
@@ -151,31 +230,53 @@ struct PairOut {
 // column work.  spp = ||g_p||^2, sqq = ||g_q||^2,
 // (sqr, sqi) = g_q^* g_p, all of the current (scaled) G.
 template <bool CPLX>
-__device__ __forceinline__ PairOut pair_rotation(double spp, double sqq, double sqr, double sqi,
-                                                 double ups)
+__device__ __forceinline__ PairOut pair_rotation(const PairSums &sm, double ups)
 {
   PairOut o;
   o.c = 1.0;
   o.C = 0.0;
   o.S = 0.0;
-  if (bits(spp) == 0ull || bits(sqq) == 0ull) {
-    // a zero column: never rotated; swapped iff ||g_p|| < ||g_q||
-    o.rot = false;
-    o.swap = bits(spp) < bits(sqq);
-    return o;
+  o.gs = 0;
+  o.ex = o.ey = 0;
+  o.psr = o.psi = 0.0;
+  int ep, eq, shift;
+  double fp, fq;
+  if (sm.wide) {
+    // norms from Alg. rnF; the dot-product is already prescaled
+    if (sm.ep == kNegInfE || sm.eq == kNegInfE) {
+      o.rot = false;
+      o.swap = (sm.ep == kNegInfE) && (sm.eq != kNegInfE);  // ||g_p|| < ||g_q||
+      return o;
+    }
+    ep = sm.ep;
+    eq = sm.eq;
+    fp = sm.fp;
+    fq = sm.fq;
+    shift = 0;
+  } else {
+    if (bits(sm.pp) == 0ull || bits(sm.qq) == 0ull) {
+      // a zero column: never rotated; swapped iff ||g_p|| < ||g_q||
+      o.rot = false;
+      o.swap = bits(sm.pp) < bits(sm.qq);
+      return o;
+    }
+    // (e,f) norms: ||g_j|| = 2^e_j f_j, 1 <= f_j < 2
+    const double rp = soft::sqrt_rn(sm.pp), rq = soft::sqrt_rn(sm.qq);
+    ep = flg(rp);
+    eq = flg(rq);
+    fp = ldexp_rn(rp, -ep);
+    fq = ldexp_rn(rq, -eq);
+    shift = -(ep + eq);
   }
-  // (e,f) norms: ||g_j|| = 2^e_j f_j, 1 <= f_j < 2
-  const double rp = soft::sqrt_rn(spp), rq = soft::sqrt_rn(sqq);
-  const int ep = flg(rp), eq = flg(rq);
-  const double fp = ldexp_rn(rp, -ep), fq = ldexp_rn(rq, -eq);
   // a21' = (g_q/2^eq)^* (g_p/2^ep) / (f_q f_p)
   const double d = __dmul_rn(fq, fp);
-  const double zr = soft::div_rn(ldexp_rn(sqr, -(ep + eq)), d);
-  const double zi = CPLX ? soft::div_rn(ldexp_rn(sqi, -(ep + eq)), d) : 0.0;
+  const double zr = soft::div_rn(ldexp_rn(sm.qr, shift), d);
+  const double zi = CPLX ? soft::div_rn(ldexp_rn(sm.qi, shift), d) : 0.0;
   const double az = CPLX ? hypot_naive(zr, zi) : dabs(zr);
   o.rot = !(ord(az) < ord(ups));
   // Alg. Gram
-  double f12 = soft::div_rn(fp, fq), f21 = soft::div_rn(fq, fp);
+  const double q12 = soft::div_rn(fp, fq), q21 = soft::div_rn(fq, fp);
+  double f12 = q12, f21 = q21;
   int e12 = ep - eq + flg(f12), e21 = eq - ep + flg(f21);
   f12 = ldexp_rn(f12, -flg(f12));
   f21 = ldexp_rn(f21, -flg(f21));
@@ -192,12 +293,27 @@ __device__ __forceinline__ PairOut pair_rotation(double spp, double sqq, double 
   o.c = r.cphi;
   o.C = r.etr;
   o.S = r.eti;
+  // section 3.5.1: for norms this far apart Eq. e:GS replaces the rotation
+  // of G (Alg. zvjsvd checks Eq. e:GScond before zjrot); V still takes the
+  // rotation
+  if (o.rot) {
+    if (gs_cond(ep, eq, q12, ups)) {  // g_q against g_p, psi = conj(a21') fq / fp
+      o.gs = 1;
+      o.ex = ep;
+      o.ey = eq;
+      o.psr = __dmul_rn(zr, q21);
+      o.psi = -__dmul_rn(zi, q21);
+    } else if (gs_cond(eq, ep, q21, ups)) {  // g_p against g_q, psi = a21' fp / fq
+      o.gs = 2;
+      o.ex = eq;
+      o.ey = ep;
+      o.psr = __dmul_rn(zr, q12);
+      o.psi = __dmul_rn(zi, q12);
+    }
+  }
   return o;
 }
 
-struct PairSums {
-  double pp, qq, qr, qi;  // ||g_p||^2, ||g_q||^2, g_q^* g_p (re, im)
-};
 
 // The compensated dot-product of supplement SM2.2 (Alg. zdpscl' /
 // ddpscl'): each term x y enters as c = RD(x y) and c' = x y - c >= 0 (one
@@ -236,11 +352,79 @@ __device__ __forceinline__ double comp_reduce(const CompSum &c)
   return __dadd_rn(S, __dadd_rn(T, __dadd_rn(S2, T2)));
 }
 
+// Bit pattern of 2^-969: a sum of squares below it may contain squares
+// that fell below the normal range (2^-1022) with more than a negligible
+// part of their bits lost.
+constexpr unsigned long long kWideBelow = 0x0360000000000000ull;
+
+// The pair's sums for columns with tiny entries (supplement SM6 and
+// Alg. zdpscl as printed): pass 1 takes the columns' norms with the
+// wide-exponent method of Alg. rnF, pass 2 the dot-product of the columns
+// prescaled by 2^-e_j (in the canonical lane order, compensated if COMP).
+// FP64 columns only.
+template <bool CPLX, bool CG, bool COMP>
+__device__ __noinline__ PairSums pair_sums_wide(const MatViewT<double, CG> &M, int p, int q)
+{
+  const int lane = threadIdx.x & 31;
+  const double *gpr = M.gr + p * M.ldg, *gqr = M.gr + q * M.ldg;
+  const double *gpi = CPLX ? M.gi + p * M.ldg : nullptr, *gqi = CPLX ? M.gi + q * M.ldg : nullptr;
+  EF np = {kNegInfE, 1.0}, nq = {kNegInfE, 1.0};
+  for (int i = lane; i < M.mp; i += 32) {
+    ef_fma_step(M.ld(gpr + i), np);
+    ef_fma_step(M.ld(gqr + i), nq);
+    if (CPLX) {
+      ef_fma_step(M.ld(gpi + i), np);
+      ef_fma_step(M.ld(gqi + i), nq);
+    }
+  }
+  np = ef_sqrt(ef_warp_sum(np));
+  nq = ef_sqrt(ef_warp_sum(nq));
+  PairSums r;
+  r.pp = r.qq = 0.0;
+  r.qr = r.qi = 0.0;
+  r.ep = np.e;
+  r.fp = np.f;
+  r.eq = nq.e;
+  r.fq = nq.f;
+  r.wide = 1;
+  if (np.e == kNegInfE || nq.e == kNegInfE) return r;
+  double sqr = 0.0, sqi = 0.0;
+  CompSum cr = {0.0, 0.0, 0.0, 0.0}, ci = {0.0, 0.0, 0.0, 0.0};
+  for (int i = lane; i < M.mp; i += 32) {
+    const double xpr = ldexp_rn(M.ld(gpr + i), -np.e), xqr = ldexp_rn(M.ld(gqr + i), -nq.e);
+    const double xpi = CPLX ? ldexp_rn(M.ld(gpi + i), -np.e) : 0.0;
+    const double xqi = CPLX ? ldexp_rn(M.ld(gqi + i), -nq.e) : 0.0;
+    if constexpr (COMP) {
+      comp_term(xpr, xqr, cr);
+      if (CPLX) {
+        comp_term(xpi, xqi, cr);
+        comp_term(xpi, xqr, ci);
+        comp_term(-xpr, xqi, ci);
+      }
+    } else {
+      sqr = __fma_rn(xqr, xpr, sqr);
+      if (CPLX) {
+        sqi = __fma_rn(xqr, xpi, sqi);
+        sqr = __fma_rn(xqi, xpi, sqr);
+        sqi = __fma_rn(-xqi, xpr, sqi);
+      }
+    }
+  }
+  if constexpr (COMP) {
+    r.qr = comp_reduce(cr);
+    r.qi = CPLX ? comp_reduce(ci) : 0.0;
+  } else {
+    r.qr = warp_sum(sqr);
+    r.qi = CPLX ? warp_sum(sqi) : 0.0;
+  }
+  return r;
+}
+
 // The three sums of pair (p, q), formed by one full warp with the columns
 // in precision T (double, or float in the FP32 phase of the mixed SVD):
 // lane l accumulates rows l, l+32, ... in ascending order with fma, the lane
-// partials are combined in FP64 by an xor butterfly (the same value in every
-// lane).  rk != 0 downscales both columns of G by 2^rk first (section 3.2,
+// partials are combined in FP64 by warp_sum_slots (the same values end up
+// in every lane).  rk != 0 downscales both columns of G by 2^rk first (section 3.2,
 // step 2; FP64 only).  COMP forms g_q^* g_p by the compensated summation
 // (FP64 only); the squared norms stay plain fma sums.
 template <typename T, bool CPLX, bool CG, bool COMP = false>
@@ -317,17 +501,78 @@ __device__ __forceinline__ PairSums pair_sums(const MatViewT<T, CG> &M, int p, i
       }
     }
   }
+  // the lane partials combined in FP64 by one tree for all the sums
   PairSums r;
-  r.pp = warp_sum((double)spp);
-  r.qq = warp_sum((double)sqq);
   if constexpr (COMP) {
-    r.qr = comp_reduce(cr);
-    r.qi = CPLX ? comp_reduce(ci) : 0.0;
+    double v[16] = {(double)spp, (double)sqq, cr.s, cr.t, cr.s2, cr.t2, ci.s, ci.t,
+                    ci.s2, ci.t2, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    const double x = warp_sum_slots<16>(v);
+    r.pp = warp_slot<16>(x, 0);
+    r.qq = warp_slot<16>(x, 1);
+    // s + (t + (s' + t')) per component
+    r.qr = __dadd_rn(warp_slot<16>(x, 2),
+                     __dadd_rn(warp_slot<16>(x, 3),
+                               __dadd_rn(warp_slot<16>(x, 4), warp_slot<16>(x, 5))));
+    r.qi = CPLX ? __dadd_rn(warp_slot<16>(x, 6),
+                            __dadd_rn(warp_slot<16>(x, 7),
+                                      __dadd_rn(warp_slot<16>(x, 8), warp_slot<16>(x, 9))))
+                : 0.0;
   } else {
-    r.qr = warp_sum((double)sqr);
-    r.qi = CPLX ? warp_sum((double)sqi) : 0.0;
+    double v[4] = {(double)spp, (double)sqq, (double)sqr, (double)sqi};
+    const double x = warp_sum_slots<4>(v);
+    r.pp = warp_slot<4>(x, 0);
+    r.qq = warp_slot<4>(x, 1);
+    r.qr = warp_slot<4>(x, 2);
+    r.qi = CPLX ? warp_slot<4>(x, 3) : 0.0;
+  }
+  r.fp = r.fq = 1.0;
+  r.ep = r.eq = 0;
+  r.wide = 0;
+  if constexpr (sizeof(T) == 8) {
+    // squares below 2^-1022 may have lost bits: a column whose squared norm
+    // is below 2^-969 is redone with the wide-exponent norms (the same
+    // decision in every lane)
+    if (bits(r.pp) < kWideBelow || bits(r.qq) < kWideBelow)
+      r = pair_sums_wide<CPLX, CG, COMP>(M, p, q);
   }
   return r;
+}
+
+// Eq. e:GS (Alg. ZGS / DGS, in their operation order) on G: the target
+// column y <- (y / 2^ey - psi x / 2^ex) 2^ey, the source x unchanged, the
+// pair swapped afterwards if o.swap; Mloc takes the max-norm of both new
+// columns.  One full warp, FP64 columns.
+template <bool CPLX, bool CG>
+__device__ __forceinline__ void gs_apply(const MatViewT<double, CG> &M, int p, int q,
+                                         const PairOut &o, unsigned long long &Mloc)
+{
+  const int lane = threadIdx.x & 31;
+  const int src = (o.gs == 1) ? p : q, dst = (o.gs == 1) ? q : p;
+  double *xr = M.gr + src * M.ldg, *yr = M.gr + dst * M.ldg;
+  double *xi = CPLX ? M.gi + src * M.ldg : nullptr, *yi = CPLX ? M.gi + dst * M.ldg : nullptr;
+  // with the swap the new target lands in the source's place and back
+  double *ox_r = o.swap ? yr : xr, *oy_r = o.swap ? xr : yr;
+  double *ox_i = o.swap ? yi : xi, *oy_i = o.swap ? xi : yi;
+  for (int i = lane; i < M.mp; i += 32) {
+    const double x1 = M.ld(xr + i), y1 = M.ld(yr + i);
+    const double sx1 = ldexp_rn(x1, -o.ex), sy1 = ldexp_rn(y1, -o.ey);
+    if (CPLX) {
+      const double x2 = M.ld(xi + i), y2 = M.ld(yi + i);
+      const double sx2 = ldexp_rn(x2, -o.ex), sy2 = ldexp_rn(y2, -o.ey);
+      const double nr = ldexp_rn(__fma_rn(-o.psr, sx1, __fma_rn(o.psi, sx2, sy1)), o.ey);
+      const double ni = ldexp_rn(__fma_rn(-o.psr, sx2, __fma_rn(-o.psi, sx1, sy2)), o.ey);
+      M.st(ox_r + i, x1);
+      M.st(ox_i + i, x2);
+      M.st(oy_r + i, nr);
+      M.st(oy_i + i, ni);
+      Mloc = max(Mloc, max(max(magbits(x1), magbits(x2)), max(magbits(nr), magbits(ni))));
+    } else {
+      const double nr = ldexp_rn(__fma_rn(-o.psr, sx1, sy1), o.ey);
+      M.st(ox_r + i, x1);
+      M.st(oy_r + i, nr);
+      Mloc = max(Mloc, max(magbits(x1), magbits(nr)));
+    }
+  }
 }
 
 // Eq. e:transf (Alg. zjrot) on the pair's G rows (tracking the max-norm of
@@ -347,6 +592,12 @@ __device__ __forceinline__ void pair_apply(const MatViewT<T, CG> &M, int p, int 
     // x_p' = fma(x_q, e', x_p) c, x_q' = fma(x_p, -conj(e'), x_q) c, e' = C + iS
     for (int pass = 0; pass < 2; ++pass) {
       const bool onG = (pass == 0);
+      if constexpr (sizeof(T) == 8) {
+        if (onG && o.gs) {
+          gs_apply<CPLX, CG>(M, p, q, o, Mloc);
+          continue;
+        }
+      }
       const int rows = onG ? M.mp : M.np;
       T *xpr = onG ? M.gr + p * M.ldg : M.vr + p * M.ldv;
       T *xqr = onG ? M.gr + q * M.ldg : M.vr + q * M.ldv;
@@ -430,11 +681,13 @@ __device__ __forceinline__ void pair_apply(const MatViewT<T, CG> &M, int p, int 
 //      the chunk share their instructions instead of one lane each,
 //   3. warps apply the rotations.
 // Every pair's arithmetic is the same whatever the chunking.  rots counts
-// (in each warp's lane 0) the rotated pairs, Mloc collects magbits().
+// (in each warp's lane 0) the transformed pairs and gsn those of them that
+// took the Gram-Schmidt step; Mloc collects magbits().
 template <typename T, bool CPLX, bool CG, bool COMP = false>
 __device__ __forceinline__ void step_chunk(const MatViewT<T, CG> &M, int k, int nt, int base, int CH,
                                            double ups, int rk, bool permute, PairSums *s_sums,
-                                           PairOut *s_out, unsigned long long &Mloc, int &rots)
+                                           PairOut *s_out, unsigned long long &Mloc, int &rots,
+                                           int &gsn)
 {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
   const int L = nt / 2;
@@ -459,7 +712,7 @@ __device__ __forceinline__ void step_chunk(const MatViewT<T, CG> &M, int k, int 
       pair_of(k, l, nt, p, q);
       if (q < M.n) {
         const PairSums sm = s_sums[i];
-        PairOut o = pair_rotation<CPLX>(sm.pp, sm.qq, sm.qr, sm.qi, ups);
+        PairOut o = pair_rotation<CPLX>(sm, ups);
         o.swap = o.swap && permute;
         s_out[i] = o;
       }
@@ -475,6 +728,7 @@ __device__ __forceinline__ void step_chunk(const MatViewT<T, CG> &M, int k, int 
       const PairOut o = s_out[i];
       pair_apply<T, CPLX>(M, p, q, o, Mloc);
       if (lane == 0 && o.rot) ++rots;
+      if (lane == 0 && o.gs) ++gsn;
     }
   }
   __syncthreads();
@@ -484,8 +738,9 @@ __device__ __forceinline__ void step_chunk(const MatViewT<T, CG> &M, int k, int 
 // Finalisation pieces (section 4.2.1), shared by the single-matrix and the
 // batched kernels so that both produce the same bits.
 
-// Column j's norm as (e, f) by one warp in the canonical order; a zero
-// column gets e = INT_MIN, f = 1.
+// Column j's norm as (e, f) by one warp in the canonical order (the
+// wide-exponent norm when the plain sum of squares is too small to trust);
+// a zero column gets e = INT_MIN, f = 1.
 template <bool CPLX, bool CG>
 __device__ __forceinline__ void colnorm_warp(const MatViewT<double, CG> &M, int j, int lane, int *e_out,
                                              double *f_out)
@@ -501,16 +756,26 @@ __device__ __forceinline__ void colnorm_warp(const MatViewT<double, CG> &M, int 
     }
   }
   s = warp_sum(s);
-  if (lane == 0) {
-    if (bits(s) == 0ull) {
-      e_out[j] = INT_MIN;
-      f_out[j] = 1.0;
-    } else {
-      const double r = __dsqrt_rn(s);
-      const int e = flg(r);
-      e_out[j] = e;
-      f_out[j] = ldexp_rn(r, -e);
+  if (bits(s) < kWideBelow) {
+    // squares may have fallen below the normal range: the wide-exponent
+    // norm (Alg. rnF) instead (kNegInfE == INT_MIN marks a zero column)
+    EF r = {kNegInfE, 1.0};
+    for (int i = lane; i < M.mp; i += 32) {
+      ef_fma_step(M.ld(xr + i), r);
+      if (CPLX) ef_fma_step(M.ld(xi + i), r);
     }
+    r = ef_sqrt(ef_warp_sum(r));
+    if (lane == 0) {
+      e_out[j] = r.e;
+      f_out[j] = r.f;
+    }
+    return;
+  }
+  if (lane == 0) {
+    const double r = __dsqrt_rn(s);
+    const int e = flg(r);
+    e_out[j] = e;
+    f_out[j] = ldexp_rn(r, -e);
   }
 }
 

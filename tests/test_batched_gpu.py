@@ -106,7 +106,7 @@ def test_shared_memory_path_bitwise(kib):
             for a, b in zip(cother.matrix(i), cref.matrix(i)):
                 assert same(a, b), (kib, "complex", i)
     finally:
-        J.tune_set(J.JSVD_TUNE_BATCH_WARPS, 8)
+        J.tune_set(J.JSVD_TUNE_BATCH_WARPS, 0)
         J.tune_set(J.JSVD_TUNE_BATCH_SMEM, 0)
 
 
@@ -126,7 +126,7 @@ def test_batch_composition_and_block_shape_invariance():
                 for a, b in zip(other.matrix(i), ref.matrix(i)):
                     assert same(a, b), (w, i)
     finally:
-        J.tune_set(J.JSVD_TUNE_BATCH_WARPS, 8)
+        J.tune_set(J.JSVD_TUNE_BATCH_WARPS, 0)
     for pos, i in enumerate(order):
         for a, b in zip(rev.matrix(pos), ref.matrix(i)):
             assert same(a, b), i
@@ -211,4 +211,23 @@ def test_cuda_graph_replay():
     graph.replay()
     torch.cuda.synchronize()
     for a, b in zip((B.U, B.V, B.sigma), ref):
+        assert same(a, b)
+
+
+def test_autotune_picks_a_candidate_and_keeps_the_bits(tmp_path, monkeypatch):
+    """The autotuner times the candidates on a sample, caches the winner,
+    and the batch launched with it gives the same bits as the default."""
+    import paper_2202_08361_gb300 as J
+    torch = _torch()
+    monkeypatch.setenv("JSVD_TUNE_CACHE", str(tmp_path / "tune.json"))
+    mats = mats_mixed(False, seed=41) * 3
+    A, m, n = J.pack_matrices(mats)
+    ref = J.BatchedSVD(A, m, n).launch()
+    B = J.BatchedSVD(A, m, n)
+    times = B.autotune(sample=16)
+    assert set(times) == {1, 2, 4, 8, 16} and B.warps in times
+    assert B.autotune(sample=16) == {}  # cached
+    B.launch()
+    torch.cuda.synchronize()
+    for a, b in zip((B.U, B.V, B.sigma), (ref.U, ref.V, ref.sigma)):
         assert same(a, b)

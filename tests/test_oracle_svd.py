@@ -206,3 +206,62 @@ def test_adjoint_sigma_only_textbook():
     sbar = np.arange(1.0, 6.0)
     Abar = oracle.svd_adjoint(r["U"], r["sigma"], r["V"], np.zeros((12, 5)), sbar)
     assert np.allclose(Abar, (r["U"] * sbar) @ r["V"].T, atol=1e-13)
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+def test_graded_columns_relative_accuracy(cplx):
+    """A = Q D, Q with orthonormal columns, D = diag(2^(-50 j)): the singular
+    values are D's entries (down to 2^-750), and one-sided Jacobi gets each
+    to a few eps relatively (its norms never under- or overflow)."""
+    m, n = 40, 16
+    Q = workloads.haar(np.random.default_rng(21 + cplx), m, n, cplx)
+    d = np.ldexp(1.0, -50 * np.arange(n))
+    A = np.asfortranarray(Q * d)
+    r = oracle.vjsvd(A)
+    assert r["status"] == oracle.OK
+    assert np.all(np.abs(r["sigma"] / d - 1) <= 64 * n * EPS64)
+
+
+def gs_test_matrix(cplx=False):
+    """Supplement SM9's 16 x 16 matrix: G_ij = 2^(eta^ - (j-1) - |i-j|) for
+    j <= 8 and 2^(-51 - (j-1) - |i-j|) for j > 8 (one-based), eta^ = 1023;
+    the complex variant multiplies each entry by a fixed unit phase."""
+    n = 16
+    i, j = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    G = np.where(j < 8, np.ldexp(1.0, 1023 - j - abs(i - j)), np.ldexp(1.0, -51 - j - abs(i - j)))
+    if cplx:
+        ph = np.exp(1j * np.random.default_rng(9).uniform(0, 2 * np.pi, (n, n)))
+        G = G * ph
+    return np.asfortranarray(G)
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+def test_gram_schmidt_branch(cplx):
+    """Section 3.5.1 / supplement SM9: the norms of the two column groups
+    differ by ~2^1074 > 2^eta^ upsilon, so the pairs across them take the
+    Gram-Schmidt step (Eq. e:GS) and the method converges.  The large
+    singular values are those of the large block; the small ones those of
+    the small block projected off the large block's span (both from LAPACK
+    on exactly rescaled copies)."""
+    G = gs_test_matrix(cplx)
+    r = oracle.vjsvd(G)
+    assert r["status"] == oracle.OK and r["gs"] > 0
+    U, s, V = r["U"], r["sigma"], r["V"]
+    Gs = G * 2.0 ** -1023  # exact: a power-of-two scaling of normal numbers
+    res = np.linalg.norm(Gs - (U * np.ldexp(s, -1023)) @ V.conj().T) / np.linalg.norm(Gs)
+    assert res <= tol(16)
+    assert np.abs(U.conj().T @ U - np.eye(16)).max() <= tol(16)
+    assert np.abs(V.conj().T @ V - np.eye(16)).max() <= tol(16)
+    big = np.linalg.svd(Gs[:, :8], compute_uv=False)
+    assert np.all(np.abs(np.ldexp(s[:8], -1023) / big - 1) <= tol(16))
+    Q, _ = np.linalg.qr(Gs[:, :8])
+    T = G[:, 8:]
+    small = np.linalg.svd(T - Q @ (Q.conj().T @ T), compute_uv=False)
+    assert np.all(np.abs(s[8:] / small - 1) <= 1e-6)
+
+
+def test_gram_schmidt_not_taken_for_moderate_ranges():
+    """Eq. e:GScond never holds when the column norms differ by less than
+    2^eta^ upsilon: an ordinary matrix takes no Gram-Schmidt step."""
+    A, _ = workloads.svd_geometric(60, 30, 1e12, False, np.random.default_rng(4))
+    assert oracle.vjsvd(A)["gs"] == 0

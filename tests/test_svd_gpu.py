@@ -208,3 +208,36 @@ def test_argument_errors():
     bad = _native.Opts()
     bad.compensated = 3
     assert L.jsvd_svd(0, ctypes.byref(bad), 8, 4, p, 8, p, 8, s, None, None, p, 4, w.data_ptr(), w.numel(), None, None) == -2
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+def test_gram_schmidt_branch_matches_oracle(cplx):
+    """Supplement SM9's 16 x 16 matrix (column norms ~2^1074 apart): the
+    GPU takes Gram-Schmidt steps (Eq. e:GS) as the oracle does, converges,
+    and its singular values match LAPACK on the two blocks (the small ones
+    after projecting off the large block's span); the batched kernel gives
+    the same bits."""
+    import torch
+    import paper_2202_08361_gb300 as J
+    from tests.test_oracle_svd import gs_test_matrix
+    G = gs_test_matrix(cplx)
+    g = gpu_svd(G)
+    o = oracle.vjsvd(G)
+    assert g["info"]["status"] == 0 and g["info"]["gs_steps"] > 0 and o["gs"] > 0
+    s = g["sigma"]
+    U, V = g["U"], g["V"]
+    Gs = G * 2.0 ** -1023
+    assert np.linalg.norm(Gs - (U * np.ldexp(s, -1023)) @ V.conj().T) / np.linalg.norm(Gs) <= tol(16)
+    assert np.abs(U.conj().T @ U - np.eye(16)).max() <= tol(16)
+    assert np.abs(V.conj().T @ V - np.eye(16)).max() <= tol(16)
+    big = np.linalg.svd(Gs[:, :8], compute_uv=False)
+    assert np.all(np.abs(np.ldexp(s[:8], -1023) / big - 1) <= tol(16))
+    Q, _ = np.linalg.qr(Gs[:, :8])
+    T = G[:, 8:]
+    small = np.linalg.svd(T - Q @ (Q.conj().T @ T), compute_uv=False)
+    assert np.all(np.abs(s[8:] / small - 1) <= 1e-6)
+    assert np.all(np.abs(s / o["sigma"] - 1) <= 1e-6)
+    B = J.svd_batched([G])
+    torch.cuda.synchronize()
+    assert np.array_equal(B.matrix(0)[1].cpu().numpy(), s)
+    assert J.decode_info(B.info)["gs_steps"] == g["info"]["gs_steps"]

@@ -27,11 +27,12 @@ def tol(n):
 
 def _outputs(torch, m, n, dtype):
     import paper_2202_08361_gb300 as J
+    from paper_2202_08361_gb300 import _native
     return {"U": J.colmajor_empty(m, n, dtype, "cuda"), "V": J.colmajor_empty(n, n, dtype, "cuda"),
             "sigma": torch.empty(n, dtype=torch.float64, device="cuda"),
             "sigma_e": torch.empty(n, dtype=torch.float64, device="cuda"),
             "sigma_f": torch.empty(n, dtype=torch.float64, device="cuda"),
-            "info": torch.zeros(24, dtype=torch.uint8, device="cuda")}
+            "info": torch.zeros(_native.INFO_BYTES, dtype=torch.uint8, device="cuda")}
 
 
 def noalloc_svd(A):
