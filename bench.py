@@ -246,6 +246,26 @@ def svd_bench(torch, J, workloads, dev):
     c1.update(accuracy(A1, r))
     out["C1_real_256x128"] = c1
 
+    # the same matrix in single precision (jsvd_svd_f32)
+    A1f = A1.float()
+    r = J.svd(A1f)
+    torch.cuda.synchronize(dev)
+    e0, e1 = _ev(torch)
+    e0.record(st)
+    for _ in range(reps):
+        J.svd(A1f, out=r)
+    e1.record(st)
+    torch.cuda.synchronize(dev)
+    info = J.decode_info(r["info"])
+    U, sv, V = r["U"].double(), r["sigma"].double(), r["V"].double()
+    I = torch.eye(128, dtype=torch.float64, device=dev)
+    A1d = A1f.double()
+    out["C1_f32_real_256x128"] = {
+        "ms_per_svd": e0.elapsed_time(e1) / reps, "sweeps": info["sweeps"],
+        "residual": (torch.linalg.norm(A1d - (U * sv) @ V.T) / torch.linalg.norm(A1d)).item(),
+        "orth_U": (U.T @ U - I).abs().max().item(), "orth_V": (V.T @ V - I).abs().max().item(),
+        "bound_64neps32": 64 * 128 * 2.0 ** -23}
+
     # C3: complex 4096 x 2048, cond 1e6, plain FP64 and mixed FP32 -> FP64
     A3np, s3 = workloads.svd_complex_geometric()
     A3 = torch.from_numpy(A3np).to(dev)
@@ -304,8 +324,22 @@ def svd_bench(torch, J, workloads, dev):
     torch.cuda.synchronize(dev)
     cost = (m4 * n4 * n4).astype(float)
     loop_s = e2.elapsed_time(e3) / 1e3 * cost.sum() / cost[idx].sum()
+    # the autotuner's choice (timed on a 400-matrix stratified sample)
+    import time as _time
+    t0 = _time.perf_counter()
+    times = B.autotune(sample=400, use_cache=False)
+    tune_s = _time.perf_counter() - t0
+    e0, e1 = _ev(torch)
+    torch.cuda.synchronize(dev)
+    e0.record(st)
+    B.launch()
+    e1.record(st)
+    torch.cuda.synchronize(dev)
+    ms_tuned = e0.elapsed_time(e1)
     out["C4_uneven_10000"] = {
         "s": ms / 1e3, "matrices_per_s": len(m4) / (ms * 1e-3),
+        "autotuned": {"warps": B.warps, "s": ms_tuned / 1e3, "tuning_s": tune_s,
+                      "sample_ms": {str(k): v for k, v in times.items()}},
         "converged": int(sum(1 for x in infos if x["status"] == 0)),
         "sweeps_mean": float(np.mean([x["sweeps"] for x in infos])),
         "fp64_tflops": fl / (ms * 1e-3) / 1e12, "fp64_frac": fl / (ms * 1e-3) / DFMA_FLOPS,

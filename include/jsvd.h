@@ -73,7 +73,7 @@ JSVD_API const char *jsvd_last_cuda_error(void);
 #define JSVD_TUNE_SVD_GRID 2
 /*   JSVD_TUNE_BATCH_WARPS: value = warps per block of the batched SVD
  *     kernel (1, 2, 4, 8 or 16), or 0 (the default): chosen when the batch
- *     is prepared, from its mean n weighted by m n^2 (1 warp for n ~ 32, 16
+ *     is prepared, from its mean n weighted by m n^2 (1 warp for n ~ 32, 8
  *     for n ~ 256). */
 #define JSVD_TUNE_BATCH_WARPS 3
 /*   JSVD_TUNE_EVD_ARITH: value = which of the 2x2 EVD's divisions and
@@ -261,6 +261,23 @@ JSVD_API int jsvd_svd(jsvd_field field, const jsvd_opts *opts, int64_t m, int64_
                       const void *A, int64_t lda, void *U, int64_t ldu, double *sigma,
                       double *sigma_e, double *sigma_f, void *V, int64_t ldv, void *work,
                       size_t work_bytes, jsvd_info *info, void *stream);
+
+/* The SVD of a single precision matrix (float; complex: interleaved float
+ * pairs): FP32 columns updated by Eq. e:transf, each pivot pair's lane sums
+ * combined in FP64 and its rotation taken from the FP64 2x2 EVD, the final
+ * norms in FP64; converged when no pair has |a21'| >= fl(eps sqrt m),
+ * eps = 2^-24 (Eq. e:tol in single precision).  Outputs in single
+ * precision: U (m x n, ldu >= m), sigma (n floats, non-increasing), V
+ * (n x n, ldv >= n).  opts as for jsvd_svd (mode and rescale_exp are not
+ * used; compensated must be 0).  work: jsvd_svd_f32_workspace_size bytes,
+ * 256-byte aligned.  Errors: -1 field, -2 opts, -3 m, -4 n, -5 A, -6 lda,
+ * -7 U, -8 ldu, -9 sigma, -10 V, -11 ldv, -12 work, JSVD_E_WORKSPACE. */
+JSVD_API int jsvd_svd_f32_workspace_size(jsvd_field field, const jsvd_opts *opts, int64_t m,
+                                         int64_t n, size_t *bytes);
+JSVD_API int jsvd_svd_f32(jsvd_field field, const jsvd_opts *opts, int64_t m, int64_t n,
+                          const void *A, int64_t lda, void *U, int64_t ldu, float *sigma, void *V,
+                          int64_t ldv, void *work, size_t work_bytes, jsvd_info *info,
+                          void *stream);
 
 /* ------------------------------------------------------------------------
  * Batched SVD of many matrices of uneven sizes: the same computation as

@@ -162,9 +162,12 @@ def colnorm_ef(A, stream=None):
     torch = _torch()
     if not isinstance(A, torch.Tensor) or not A.is_cuda or A.dim() != 2:
         raise TypeError("A must be a 2-D CUDA tensor")
+    if A.dtype in (torch.float32, torch.complex64):
+        return _svd_f32(A, max_sweeps=max_sweeps, permute=permute, work=work, out=out,
+                        stream=stream)
     cplx = A.dtype == torch.complex128
     if not cplx and A.dtype != torch.float64:
-        raise TypeError("A must be float64 or complex128")
+        raise TypeError("A must be float64, complex128, float32 or complex64")
     m, n = A.shape
     Ac, lda = colmajor(A)
     e = torch.empty(n, dtype=torch.float64, device=A.device)
@@ -238,16 +241,20 @@ def decode_info(info):
 def svd(A, *, max_sweeps=0, mode="fp64", rescale_exp=0, permute=False, compensated=False,
         work=None, out=None, stream=None):
     """One-sided Jacobi SVD of a CUDA tensor A (m x n, m >= n; float64 or
-    complex128), jsvd_svd.  Returns dict(U, sigma, sigma_e, sigma_f, V,
+    complex128: jsvd_svd; float32 or complex64: jsvd_svd_f32, which returns
+    U, sigma, V in single precision and no sigma_e / sigma_f).  Returns dict(U, sigma, sigma_e, sigma_f, V,
     info); U and V are column-major views, info a 32-byte device tensor
     (decode_info).  compensated forms the pivot pairs' dot-products by the
     compensated summation (Alg. zdpscl' / ddpscl')."""
     torch = _torch()
     if not isinstance(A, torch.Tensor) or not A.is_cuda or A.dim() != 2:
         raise TypeError("A must be a 2-D CUDA tensor")
+    if A.dtype in (torch.float32, torch.complex64):
+        return _svd_f32(A, max_sweeps=max_sweeps, permute=permute, work=work, out=out,
+                        stream=stream)
     cplx = A.dtype == torch.complex128
     if not cplx and A.dtype != torch.float64:
-        raise TypeError("A must be float64 or complex128")
+        raise TypeError("A must be float64, complex128, float32 or complex64")
     m, n = A.shape
     Ac, lda = colmajor(A)
     dev = A.device
@@ -270,6 +277,37 @@ def svd(A, *, max_sweeps=0, mode="fp64", rescale_exp=0, permute=False, compensat
                                 work.data_ptr(), work.numel(), ptr("info"),
                                 _stream_handle(stream))
     _native.check(rc, "jsvd_svd")
+    out["U"], out["V"] = U, V
+    return out
+
+
+def _svd_f32(A, *, max_sweeps=0, permute=False, work=None, out=None, stream=None):
+    """The single precision SVD (jsvd_svd_f32): U, V float32/complex64,
+    sigma float32, info."""
+    torch = _torch()
+    cplx = A.dtype == torch.complex64
+    m, n = A.shape
+    Ac, lda = colmajor(A)
+    dev = A.device
+    if out is None:
+        out = {"U": colmajor_empty(m, n, A.dtype, dev), "V": colmajor_empty(n, n, A.dtype, dev),
+               "sigma": torch.empty(n, dtype=torch.float32, device=dev),
+               "info": torch.zeros(_native.INFO_BYTES, dtype=torch.uint8, device=dev)}
+    U, ldu = colmajor(out["U"])
+    V, ldv = colmajor(out["V"])
+    o = _opts(max_sweeps, JSVD_FP64, 0, permute, False)
+    field = JSVD_COMPLEX if cplx else JSVD_REAL
+    L = _native.lib()
+    sz = ctypes.c_size_t(0)
+    _native.check(L.jsvd_svd_f32_workspace_size(field, ctypes.byref(o), m, n, ctypes.byref(sz)),
+                  "jsvd_svd_f32_workspace_size")
+    if work is None:
+        work = torch.empty(sz.value, dtype=torch.uint8, device=dev)
+    rc = L.jsvd_svd_f32(field, ctypes.byref(o), m, n, Ac.data_ptr(), lda, U.data_ptr(), ldu,
+                        out["sigma"].data_ptr(), V.data_ptr(), ldv, work.data_ptr(), work.numel(),
+                        out["info"].data_ptr() if out.get("info") is not None else None,
+                        _stream_handle(stream))
+    _native.check(rc, "jsvd_svd_f32")
     out["U"], out["V"] = U, V
     return out
 

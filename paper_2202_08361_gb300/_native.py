@@ -108,6 +108,12 @@ def lib():
         L.jsvd_svd.argtypes = [ctypes.c_int, ctypes.POINTER(Opts), _i64, _i64, _vp, _i64, _vp, _i64,
                                _d, _d, _d, _vp, _i64, _vp, _sz, _vp, _vp]
         L.jsvd_svd.restype = ctypes.c_int
+        L.jsvd_svd_f32_workspace_size.argtypes = [ctypes.c_int, ctypes.POINTER(Opts), _i64, _i64,
+                                                  ctypes.POINTER(_sz)]
+        L.jsvd_svd_f32_workspace_size.restype = ctypes.c_int
+        L.jsvd_svd_f32.argtypes = [ctypes.c_int, ctypes.POINTER(Opts), _i64, _i64, _vp, _i64, _vp,
+                                   _i64, _vp, _vp, _i64, _vp, _sz, _vp, _vp]
+        L.jsvd_svd_f32.restype = ctypes.c_int
         L.jsvd_svd_noalloc.argtypes = [ctypes.c_int, ctypes.POINTER(Opts), _i64, _i64, _vp, _i64,
                                        _vp, _i64, _d, _d, _d, _vp, _i64, _vp, _vp]
         L.jsvd_svd_noalloc.restype = ctypes.c_int

@@ -19,42 +19,39 @@ constexpr uint32_t kSqrtNuF = 0x5F7FFFFFu;  // fl(sqrt(FLT_MAX)) = 1.844674297E+
 __device__ __forceinline__ uint32_t fbits(float x) { return __float_as_uint(x); }
 __device__ __forceinline__ float fval(uint32_t u) { return __uint_as_float(u); }
 
-// floor(lg max(|x|, FLT_TRUE_MIN)) (0 -> -149), Eq. e:z's exponent.
+// floor(lg max(|x|, FLT_TRUE_MIN)) (0 -> -149), Eq. e:z's exponent.  Both
+// cases are computed and one is selected, so the lanes of a warp never
+// diverge (wide-range data mixes normal and subnormal values in a warp).
 __device__ __forceinline__ int flgf_sat(float x)
 {
-  uint32_t a = fbits(x) & ~kSignF;
+  const uint32_t a = fbits(x) & ~kSignF;
   const int e = (int)(a >> 23);
-  if (e) return e - 127;
-  a |= (uint32_t)(a == 0u);
-  return (31 - __clz((int)a)) - 149;
+  const int sub = (31 - __clz((int)(a | 1u))) - 149;
+  return e ? e - 127 : sub;
 }
 
-// x * 2^k rounded to nearest-even (scalbnf); x finite, |k| < 1024.
+// x * 2^k rounded to nearest-even (scalbnf); x finite, |k| < 1024.  Branch
+// free, like flgf_sat: the normal, subnormal, overflow and zero results are
+// all formed and selected.
 __device__ __forceinline__ float ldexpf_rn(float x, int k)
 {
   const uint32_t u = fbits(x);
   const uint32_t sign = u & kSignF;
   const uint32_t a = u & ~kSignF;
-  if (a == 0u) return x;
-  int E = (int)(a >> 23);
-  uint32_t sig;
-  if (E) {
-    sig = (a & 0x007FFFFFu) | 0x00800000u;
-  } else {
-    const int lz = __clz((int)a) - 8;
-    sig = a << lz;
-    E = 1 - lz;
-  }
-  const int E2 = E + k;
-  if (E2 >= 255) return fval(sign | kInfF);
-  if (E2 >= 1) return fval(sign | ((((uint32_t)(E2 - 1)) << 23) + sig));
-  const int sh = 1 - E2;
-  if (sh >= 25) return fval(sign);
+  const int E = (int)(a >> 23);
+  const int lz = __clz((int)(a | 1u)) - 8;                 // subnormal normalisation shift
+  const uint32_t sig = E ? ((a & 0x007FFFFFu) | 0x00800000u) : (a << (lz > 0 ? lz : 0));
+  const int E2 = (E ? E : 1 - lz) + k;
+  const uint32_t normal = sign | ((((uint32_t)(E2 - 1)) << 23) + sig);
+  int sh = 1 - E2;                                          // right shift into the subnormal grid
+  sh = sh < 1 ? 1 : (sh > 25 ? 25 : sh);
   uint32_t q = sig >> sh;
   const uint32_t rem = sig & ((1u << sh) - 1u);
   const uint32_t half = 1u << (sh - 1);
   q += (uint32_t)((rem > half) | ((rem == half) & (q & 1u)));
-  return fval(sign | q);
+  uint32_t r = (E2 >= 1) ? normal : (sign | q);
+  r = (E2 >= 255) ? (sign | kInfF) : r;
+  return fval(a == 0u ? u : r);
 }
 
 // a / b, correctly rounded, by the FP32 pipe's fast path.  The operands are

@@ -676,3 +676,275 @@ extern "C" int jsvd_svd(jsvd_field field, const jsvd_opts *opts, int64_t m, int6
   return svd_fp64_run<false>(m, n, (const double *)A, lda, (double *)U, ldu, sigma, sigma_e,
                              sigma_f, (double *)V, ldv, (char *)work, info, S, rexp, flags, st);
 }
+
+// ---------------------------------------------------------------------------
+// The single precision SVD (binary32 data): the sweeps of the FP32 phase
+// (FP32 columns, lane sums combined in FP64, each pair's rotation from the
+// FP64 2x2 EVD), the final norms in FP64 from the FP32 columns, binary32
+// outputs.  Convergence: |a21'| < fl(eps sqrt m) with eps = 2^-24, the
+// binary32 unit roundoff (Eq. e:tol for single precision).
+
+namespace jsvd {
+
+constexpr int kF32TolExp = -24;
+
+struct F32Layout {
+  size_t state, gr, gi, vr, vi, e, f, rank, total;
+  int mp, np;
+};
+
+static F32Layout f32_layout(bool cplx, int64_t m, int64_t n)
+{
+  F32Layout L;
+  L.mp = (int)((m + 31) / 32 * 32);
+  L.np = (int)((n + 31) / 32 * 32);
+  size_t o = 0;
+  L.state = o;
+  o = align256(o + sizeof(SvdState));
+  L.gr = o;
+  o = align256(o + sizeof(float) * (size_t)L.mp * (size_t)n);
+  L.gi = o;
+  if (cplx) o = align256(o + sizeof(float) * (size_t)L.mp * (size_t)n);
+  L.vr = o;
+  o = align256(o + sizeof(float) * (size_t)L.np * (size_t)n);
+  L.vi = o;
+  if (cplx) o = align256(o + sizeof(float) * (size_t)L.np * (size_t)n);
+  L.e = o;
+  o = align256(o + sizeof(int) * (size_t)n);
+  L.f = o;
+  o = align256(o + sizeof(double) * (size_t)n);
+  L.rank = o;
+  o = align256(o + sizeof(int) * (size_t)n);
+  L.total = o;
+  return L;
+}
+
+// max over binary32 entries of |x| (NaN -> Inf), stored as the bits of the
+// same value in binary64 (M0 of the state)
+__global__ void maxnorm32_kernel(const float *__restrict__ A, int64_t lda, int64_t rows,
+                                 int64_t cols, unsigned long long *out)
+{
+  unsigned int mx = 0u;
+  const int64_t total = rows * cols;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = t / rows, i = t - j * rows;
+    unsigned int a = __float_as_uint(A[j * lda + i]) & 0x7FFFFFFFu;
+    a = (a > 0x7F800000u) ? 0x7F800000u : a;
+    mx = (a > mx) ? a : mx;
+  }
+  unsigned long long m64 = (mx >= 0x7F800000u) ? kInf : bits((double)__uint_as_float(mx));
+  m64 = warp_umax(m64);
+  if ((threadIdx.x & 31) == 0) atomicMax(out, m64);
+}
+
+// G32 = fl32(2^s0 A), V32 = I; s0 brings ||A||_max into [2^40, 2^41): high
+// in the binary32 range for the room of tiny entries, low enough that no
+// lane's sum of squares (at most 2^19 rows) overflows.
+constexpr int kF32Target = 40;
+
+template <bool CPLX>
+__global__ void init32_kernel(const float *__restrict__ A, int64_t lda, MatViewT<float> M,
+                              SvdState *st)
+{
+  const unsigned long long m0 = st->M0;
+  const bool nonfinite = m0 >= kInf;
+  const int s0 = (m0 == 0ull || nonfinite) ? 0 : kF32Target - flg(dbl(m0));
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+    st->s = s0;
+    st->nonfinite = nonfinite ? 1 : 0;
+    st->Mbuf[0] = (m0 == 0ull || nonfinite) ? 0ull : bits(ldexp_rn(dbl(m0), s0));
+  }
+  for (int j = blockIdx.y; j < M.n; j += gridDim.y) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < max(M.mp, M.np);
+         i += gridDim.x * blockDim.x) {
+      if (i < M.mp) {
+        float xr = 0.0f, xi = 0.0f;
+        if (i < M.m && !nonfinite) {
+          if (CPLX) {
+            xr = ldexp_rn(A[2 * (j * lda + i)], s0);
+            xi = ldexp_rn(A[2 * (j * lda + i) + 1], s0);
+          } else {
+            xr = ldexp_rn(A[j * lda + i], s0);
+          }
+        }
+        M.gr[j * M.ldg + i] = xr;
+        if (CPLX) M.gi[j * M.ldg + i] = xi;
+      }
+      if (i < M.np) {
+        M.vr[j * M.ldv + i] = (i == j) ? 1.0f : 0.0f;
+        if (CPLX) M.vi[j * M.ldv + i] = 0.0f;
+      }
+    }
+  }
+}
+
+// Final norms: the squares of binary32 entries are exact in binary64 and
+// cannot underflow there; sums in the canonical order.
+template <bool CPLX>
+__global__ void colnorm32_kernel(MatViewT<float> M, int *e_out, double *f_out)
+{
+  const int lane = threadIdx.x & 31;
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int W = (gridDim.x * blockDim.x) >> 5;
+  for (int j = w; j < M.n; j += W) {
+    const float *xr = M.gr + j * M.ldg, *xi = CPLX ? M.gi + j * M.ldg : nullptr;
+    double s = 0.0;
+    for (int i = lane; i < M.mp; i += 32) {
+      const double a = (double)ldg2(xr + i);
+      s = __fma_rn(a, a, s);
+      if (CPLX) {
+        const double b = (double)ldg2(xi + i);
+        s = __fma_rn(b, b, s);
+      }
+    }
+    s = warp_sum(s);
+    if (lane == 0) {
+      if (bits(s) == 0ull) {
+        e_out[j] = INT_MIN;
+        f_out[j] = 1.0;
+      } else {
+        const double r = __dsqrt_rn(s);
+        e_out[j] = flg(r);
+        f_out[j] = ldexp_rn(r, -flg(r));
+      }
+    }
+  }
+}
+
+// U(:, r) = fl32(G32(:, j) 2^-e / f) (one rounding: the binary64 quotient
+// rounded again to binary32 equals the binary32 quotient), V(:, r) = V32,
+// sigma_r = fl32(2^(e - s) f).
+template <bool CPLX>
+__global__ void output32_kernel(MatViewT<float> M, const int *e, const double *f, const int *rank,
+                                const SvdState *st, float *U, int64_t ldu, float *V, int64_t ldv,
+                                float *sigma)
+{
+  const int s = st->s;
+  const bool bad = st->nonfinite != 0;
+  const float nan = __int_as_float(0x7FC00000);
+  for (int j = blockIdx.y; j < M.n; j += gridDim.y) {
+    const int r = rank[j], ej = e[j];
+    const double fj = f[j];
+    const bool zero = (ej == INT_MIN);
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+      sigma[r] = bad ? nan : zero ? 0.0f : __double2float_rn(ldexp_rn(fj, ej - s));
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < max(M.m, M.n);
+         i += gridDim.x * blockDim.x) {
+      if (i < M.m) {
+        float ur = 0.0f, ui = 0.0f;
+        if (bad) {
+          ur = ui = nan;
+        } else if (!zero) {
+          ur = __double2float_rn(__ddiv_rn(ldexp_rn((double)M.gr[j * M.ldg + i], -ej), fj));
+          if (CPLX) ui = __double2float_rn(__ddiv_rn(ldexp_rn((double)M.gi[j * M.ldg + i], -ej), fj));
+        }
+        if (CPLX) {
+          U[2 * (r * ldu + i)] = ur;
+          U[2 * (r * ldu + i) + 1] = ui;
+        } else {
+          U[r * ldu + i] = ur;
+        }
+      }
+      if (i < M.n) {
+        const float vr = bad ? nan : M.vr[j * M.ldv + i];
+        if (CPLX) {
+          V[2 * (r * ldv + i)] = vr;
+          V[2 * (r * ldv + i) + 1] = bad ? nan : M.vi[j * M.ldv + i];
+        } else {
+          V[r * ldv + i] = vr;
+        }
+      }
+    }
+  }
+}
+
+template <bool CPLX>
+static int svd_f32_run(int64_t m, int64_t n, const float *A, int64_t lda, float *U, int64_t ldu,
+                       float *sigma, float *V, int64_t ldv, char *work, jsvd_info *info, int S,
+                       int flags, cudaStream_t st)
+{
+  const F32Layout L = f32_layout(CPLX, m, n);
+  SvdState *state = reinterpret_cast<SvdState *>(work + L.state);
+  MatViewT<float> M;
+  M.gr = reinterpret_cast<float *>(work + L.gr);
+  M.gi = CPLX ? reinterpret_cast<float *>(work + L.gi) : nullptr;
+  M.vr = reinterpret_cast<float *>(work + L.vr);
+  M.vi = CPLX ? reinterpret_cast<float *>(work + L.vi) : nullptr;
+  M.m = (int)m;
+  M.n = (int)n;
+  M.mp = L.mp;
+  M.np = L.np;
+  M.ldg = L.mp;
+  M.ldv = L.np;
+  int *e = reinterpret_cast<int *>(work + L.e);
+  double *f = reinterpret_cast<double *>(work + L.f);
+  int *rank = reinterpret_cast<int *>(work + L.rank);
+  const int sms = sm_count();
+  JSVD_CUDA(cudaMemsetAsync(state, 0, sizeof(SvdState), st));
+  const int64_t rows = CPLX ? 2 * m : m, ld = CPLX ? 2 * lda : lda;
+  int64_t blocks = (rows * n + 255) / 256;
+  if (blocks > (int64_t)sms * 8) blocks = (int64_t)sms * 8;
+  maxnorm32_kernel<<<(int)blocks, 256, 0, st>>>(A, ld, rows, n, &state->M0);
+  JSVD_CHECK_LAUNCH();
+  dim3 grid((unsigned)((std::max(L.mp, L.np) + 255) / 256), (unsigned)std::min<int64_t>(n, 65535));
+  init32_kernel<CPLX><<<grid, 256, 0, st>>>(A, lda, M, state);
+  JSVD_CHECK_LAUNCH();
+  JSVD_TRY(phase_sweeps<float, CPLX>(M, state, ldexp(sqrt((double)m), kF32TolExp), S, 1 << 20,
+                                     flags & kFlagPermute, st));
+  const int nb = (int)std::min<int64_t>((n * 32 + 255) / 256, (int64_t)sms * 8);
+  colnorm32_kernel<CPLX><<<nb, 256, 0, st>>>(M, e, f);
+  JSVD_CHECK_LAUNCH();
+  rank_kernel<<<(int)((n + 127) / 128), 128, 0, st>>>((int)n, e, f, rank, state, info, nullptr);
+  JSVD_CHECK_LAUNCH();
+  dim3 go((unsigned)((std::max<int64_t>(m, n) + 255) / 256), (unsigned)std::min<int64_t>(n, 65535));
+  output32_kernel<CPLX><<<go, 256, 0, st>>>(M, e, f, rank, state, U, ldu, V, ldv, sigma);
+  JSVD_CHECK_LAUNCH();
+  return JSVD_OK;
+}
+
+}  // namespace jsvd
+
+extern "C" int jsvd_svd_f32_workspace_size(jsvd_field field, const jsvd_opts *opts, int64_t m,
+                                           int64_t n, size_t *bytes)
+{
+  using namespace jsvd;
+  if (field != JSVD_REAL && field != JSVD_COMPLEX) return -1;
+  int S, mode, rexp, flags;
+  if (svd_check_opts(opts, S, mode, rexp, flags)) return -2;
+  if (m < 1 || m > (1 << 28)) return -3;
+  if (n < 1 || n > m || n > (1 << 20)) return -4;
+  if (!bytes) return -5;
+  *bytes = f32_layout(field == JSVD_COMPLEX, m, n).total;
+  return JSVD_OK;
+}
+
+extern "C" int jsvd_svd_f32(jsvd_field field, const jsvd_opts *opts, int64_t m, int64_t n,
+                            const void *A, int64_t lda, void *U, int64_t ldu, float *sigma,
+                            void *V, int64_t ldv, void *work, size_t work_bytes, jsvd_info *info,
+                            void *stream)
+{
+  using namespace jsvd;
+  if (field != JSVD_REAL && field != JSVD_COMPLEX) return -1;
+  int S, mode, rexp, flags;
+  if (svd_check_opts(opts, S, mode, rexp, flags) || (flags & kFlagComp)) return -2;
+  if (m < 1 || m > (1 << 28)) return -3;
+  if (n < 1 || n > m || n > (1 << 20)) return -4;
+  const bool cplx = field == JSVD_COMPLEX;
+  const uintptr_t al = cplx ? 7 : 3;
+  if (!A || ((uintptr_t)A & al)) return -5;
+  if (lda < m) return -6;
+  if (!U || ((uintptr_t)U & al)) return -7;
+  if (ldu < m) return -8;
+  if (!sigma) return -9;
+  if (!V || ((uintptr_t)V & al)) return -10;
+  if (ldv < n) return -11;
+  if (!work || ((uintptr_t)work & 255)) return -12;
+  if (work_bytes < f32_layout(cplx, m, n).total) return JSVD_E_WORKSPACE;
+  cudaStream_t st = as_stream(stream);
+  if (cplx)
+    return svd_f32_run<true>(m, n, (const float *)A, lda, (float *)U, ldu, sigma, (float *)V, ldv,
+                             (char *)work, info, S, flags, st);
+  return svd_f32_run<false>(m, n, (const float *)A, lda, (float *)U, ldu, sigma, (float *)V, ldv,
+                            (char *)work, info, S, flags, st);
+}

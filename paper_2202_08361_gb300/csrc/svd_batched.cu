@@ -84,9 +84,9 @@ int batch_set_warps(int w)
 
 // Warps per block for a batch: small matrices want many blocks per SM (one
 // warp each hides the pair rotations' latency across matrices), large ones
-// many warps per matrix.  The rule keys on the mean n weighted by the cost
+// more warps per matrix.  The rule keys on the mean n weighted by the cost
 // of a sweep (m n^2), measured on GB300: 4096 x (64 x 32) is fastest with 1
-// warp, the 10,000 uneven matrices (n up to 256) with 16.
+// warp, the 10,000 uneven matrices (n up to 256) with 8.
 static int batch_auto_warps(int64_t count, const int64_t *m, const int64_t *n)
 {
   double w = 0.0, wn = 0.0;
@@ -96,7 +96,7 @@ static int batch_auto_warps(int64_t count, const int64_t *m, const int64_t *n)
     wn += c * (double)n[i];
   }
   const double navg = (w > 0.0) ? wn / w : 0.0;
-  return navg <= 40.0 ? 1 : navg <= 64.0 ? 2 : navg <= 96.0 ? 4 : navg <= 160.0 ? 8 : 16;
+  return navg <= 40.0 ? 1 : navg <= 64.0 ? 2 : navg <= 96.0 ? 4 : 8;
 }
 
 // The automatic choice of each prepared workspace, read by the launch (a
