@@ -193,6 +193,10 @@ def _opts(max_sweeps=0, mode=JSVD_FP64, rescale_exp=0, permute=False, compensate
     return o
 
 
+def _opts_ref(o):
+    return ctypes.byref(o)
+
+
 def _mode(mode):
     if mode in (JSVD_FP64, "fp64"):
         return JSVD_FP64
@@ -420,12 +424,11 @@ class BatchedSVD:
     warps = None  # warps per block; None: the library's choice for the batch
 
     def autotune(self, **kw):
-        """Time the candidate warps per block on a sample of this batch
-        (autotune.tune_batched) and launch with the fastest from now on.
-        Returns the {warps: ms} timings (empty when cached)."""
+        """Time the candidate warps per block on this batch, a couple of
+        sweeps each (autotune.tune_batched), and launch with the fastest
+        from now on.  Returns the {warps: ms} timings (empty when cached)."""
         from . import autotune
-        self.warps, times = autotune.tune_batched(self.A, self.m, self.n,
-                                                  compensated=bool(self.opts.compensated), **kw)
+        self.warps, times = autotune.tune_batched(self, **kw)
         return times
 
     def launch(self, stream=None):

@@ -1,13 +1,15 @@
 """Launch-shape autotuner for the batched SVD (arithmetic-neutral knobs only:
 no choice here changes a result bit).
 
-tune_batched() times the batched kernel with each candidate number of warps
-per block on a stratified sample of the batch (every k-th matrix in the
-order of cost m n^2, so the sample has the batch's mix of sizes) and
-returns the fastest.  Choices are cached in a JSON file (JSVD_TUNE_CACHE,
-else ~/.cache/jsvd/tune.json) under the device name, the field, the option
-set and a signature of the batch's cost distribution over log2 n.  Without
-tuning, the library's own rule (JSVD_TUNE_BATCH_WARPS = 0) applies.
+tune_batched() times the batched kernel on the whole batch with each
+candidate number of warps per block, every run capped at a couple of
+sweeps (the persistent kernel's occupancy and load balance are those of the
+real run; a subset of the matrices would not fill the GPU the same way),
+and returns the fastest.  Choices are cached in a JSON file
+(JSVD_TUNE_CACHE, else ~/.cache/jsvd/tune.json) under the device name, the
+field, the option set and a signature of the batch's cost distribution over
+log2 n.  Without tuning, the library's own rule (JSVD_TUNE_BATCH_WARPS = 0)
+applies.
 """
 import json
 import os
@@ -54,49 +56,39 @@ def _store(table):
         pass  # a read-only home: the choice is still returned
 
 
-def sample_indices(m, n, size):
-    """Every k-th matrix in the order of decreasing m n^2 (at most `size`)."""
-    m = np.asarray(m, dtype=np.int64)
-    n = np.asarray(n, dtype=np.int64)
-    order = np.argsort(-(m * n * n), kind="stable")
-    k = max(1, int(np.ceil(len(order) / max(size, 1))))
-    return np.sort(order[::k])
-
-
-def tune_batched(A, m, n, *, compensated=False, candidates=CANDIDATES, sample=1024,
-                 use_cache=True, stream=None):
-    """The fastest warps per block for the batch (A packed as for
-    BatchedSVD).  Returns (warps, {warps: ms on the sample}); the timings
-    are empty when the choice came from the cache."""
+def tune_batched(B, *, candidates=CANDIDATES, sweeps=2, use_cache=True, stream=None):
+    """The fastest warps per block for the prepared BatchedSVD B.  Returns
+    (warps, {warps: ms for `sweeps` sweeps}); the timings are empty when the
+    choice came from the cache.  B's outputs are overwritten (a later
+    launch recomputes them)."""
     import torch
 
     import paper_2202_08361_gb300 as J
-    cplx = A.dtype == torch.complex128
-    m = np.asarray(m, dtype=np.int64)
-    n = np.asarray(n, dtype=np.int64)
-    dev = A.device
-    key = "%s|%s" % (torch.cuda.get_device_name(dev), signature(m, n, cplx, compensated))
+    from paper_2202_08361_gb300 import _native
+    key = "%s|%s" % (torch.cuda.get_device_name(B.A.device),
+                     signature(B.m, B.n, B.cplx, bool(B.opts.compensated)))
     table = _load() if use_cache else {}
     if key in table:
         return int(table[key]), {}
-    idx = sample_indices(m, n, sample)
-    off = np.concatenate([[0], np.cumsum(m * n)[:-1]]) if len(m) else np.zeros(0, np.int64)
-    As = torch.cat([A[int(off[i]):int(off[i]) + int(m[i] * n[i])] for i in idx])
-    B = J.BatchedSVD(As, m[idx], n[idx], compensated=compensated)
-    st = stream if stream is not None else torch.cuda.current_stream(dev)
+    st = stream if stream is not None else torch.cuda.current_stream(B.A.device)
+    saved = B.opts.max_sweeps
     times = {}
     try:
+        B.opts.max_sweeps = int(sweeps)
         for w in candidates:
             J.tune_set(J.JSVD_TUNE_BATCH_WARPS, int(w))
-            B.launch(st)
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(st)
-            B.launch(st)
+            rc = _native.lib().jsvd_svd_batched_launch(B.field, J._opts_ref(B.opts), B.count,
+                                                       B.work.data_ptr(), B.info.data_ptr(),
+                                                       J._stream_handle(st))
+            _native.check(rc, "jsvd_svd_batched_launch")
             e1.record(st)
             e1.synchronize()
             times[int(w)] = e0.elapsed_time(e1)
     finally:
+        B.opts.max_sweeps = saved
         J.tune_set(J.JSVD_TUNE_BATCH_WARPS, 0)
     best = min(times, key=times.get)
     if use_cache:
