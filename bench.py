@@ -473,23 +473,13 @@ def run_ours(args):
     h_out_cx = {k: torch.empty_like(v, device="cpu").pin_memory() for k, v in out_cx.items()}
     h2d = sum(t.numel() * t.element_size() for t in h_re + h_cx)
     d2h = sum(t.numel() * t.element_size() for t in list(h_out_re.values()) + list(h_out_cx.values()))
-    # the real and the complex batch on two streams with their own
-    # workspaces, so the second call's chunks follow the first's without
-    # waiting for its pipeline to drain
-    wsz = J.evd2x2_host_workspace_size()
-    work_re = torch.empty(wsz, dtype=torch.uint8, device=dev)
-    work_cx = torch.empty(wsz, dtype=torch.uint8, device=dev)
-    side = torch.cuda.Stream(dev)
-    ev_fork = torch.cuda.Event()
-    ev_join = torch.cuda.Event()
+    work_host = torch.empty(J.evd2x2_host_workspace_size(), dtype=torch.uint8, device=dev)
 
     def e2e_step():
-        ev_fork.record(stream)
-        side.wait_event(ev_fork)
-        J.evd2x2_batched_host(*h_re, out=h_out_re, work=work_re, stream=stream)
-        J.evd2x2_batched_host(*h_cx, out=h_out_cx, work=work_cx, stream=side)
-        ev_join.record(side)
-        stream.wait_event(ev_join)
+        # one stream: two streams sharing the library's pipeline streams
+        # measured slower (12.1 vs 8.8 ms per step)
+        J.evd2x2_batched_host(*h_re, out=h_out_re, work=work_host, stream=stream)
+        J.evd2x2_batched_host(*h_cx, out=h_out_cx, work=work_host, stream=stream)
 
     for _ in range(2):
         e2e_step()

@@ -394,6 +394,17 @@ JSVD_API int jsvd_dgemm(int transA, int64_t M, int64_t N, int64_t K, double alph
 JSVD_API int jsvd_selftest_fp64(int64_t n, uint64_t seed, unsigned long long *mismatches,
                                 void *stream);
 
+/* Failure-detection self-test of the bounded grid barrier the persistent
+ * SVD kernel uses between steps: a cooperative launch of `blocks` blocks
+ * (1 .. number of SMs) takes `rounds` barriers; block `absent` (-1: none)
+ * never arrives, so the others' wait gives up after limit_ns (1e6 .. 5e9)
+ * and they stop.  status (DEVICE, 2 int32): [0] = JSVD_E_TIMEOUT if a wait
+ * gave up, else JSVD_OK; [1] = barriers completed over all blocks.  The
+ * context stays usable.  Errors: -1 blocks, -3 rounds, -4 limit_ns,
+ * -5 status NULL, JSVD_E_CUDA.  Concurrent calls share one state. */
+JSVD_API int jsvd_selftest_barrier(int blocks, int absent, int rounds, int64_t limit_ns,
+                                   int32_t *status, void *stream);
+
 /* The parallel pivot ordering the SVD kernels use (section 4.1; the
  * round-robin reading): writes (nt - 1) x (nt / 2) pairs (p, q), p < q, as
  * int32 [step][pair][2] into the DEVICE buffer tab, nt = n + (n & 1) (a

@@ -47,6 +47,11 @@ def lib():
         L.orc_ssjac2.restype = None
         L.orc_csjac2.argtypes = [ctypes.c_int64, _f, _f, _f, _f, _f, _f, _f, _f, _f, _i32]
         L.orc_csjac2.restype = None
+        L.orc_q_zsjac2.argtypes = [ctypes.c_int64, _d, _d, _d, _d, _d, _d, _d, _d, _d]
+        L.orc_q_zsjac2.restype = None
+        L.orc_q_vjsvd.argtypes = [ctypes.c_int64, ctypes.c_int64, _d, _d, ctypes.c_int64, _d, _d,
+                                  _d, _d, _d, _d, ctypes.c_int, _i32]
+        L.orc_q_vjsvd.restype = ctypes.c_int
         L.orc_rnF.argtypes = [ctypes.c_int64, _d, _d, _d]
         L.orc_rnF.restype = None
         L.orc_pairs.argtypes = [ctypes.c_int, _i32]
@@ -201,6 +206,40 @@ def dpscl(q, p, compensated=False, eq=0, fq=1.0, ep=0, fp=1.0):
     if rc != 0:
         raise ValueError("orc_dpscl failed with %d" % rc)
     return complex(out[0], out[1]) if cplx else out[0]
+
+
+def q_zsjac2(a11, a22, a21r, a21i=None):
+    """The binary128 twin of the 2x2 EVD (Listing 1, binary128 constants):
+    (cos phi, Re e^{ia} tan phi, Im e^{ia} tan phi, lambda1, lambda2), each an
+    (r, 2) array of (hi, lo) doubles with hi + lo the binary128 value."""
+    a11, a22, a21r = _f64(a11), _f64(a22), _f64(a21r)
+    a21i = _f64(a21i) if a21i is not None else None
+    r = a11.size
+    outs = [np.zeros(2 * r) for _ in range(5)]
+    lib().orc_q_zsjac2(r, _dp(a11), _dp(a22), _dp(a21r), _dp(a21i), *[_dp(o) for o in outs])
+    return tuple(o.reshape(r, 2) for o in outs)
+
+
+def q_vjsvd(A, max_sweeps=100):
+    """The binary128 twin of the one-sided Jacobi SVD (Alg. zvjsvd): dict(
+    sigma (n, 2) (hi, lo) pairs, U, V rounded to double, status, sweeps)."""
+    A = np.asarray(A)
+    m, n = A.shape
+    cplx = np.iscomplexobj(A)
+    Ar = np.asfortranarray(A.real, dtype=np.float64)
+    Ai = np.asfortranarray(A.imag, dtype=np.float64) if cplx else None
+    sh, sl = np.zeros(n), np.zeros(n)
+    Ur, Vr = np.zeros((m, n), order="F"), np.zeros((n, n), order="F")
+    Ui = np.zeros((m, n), order="F") if cplx else None
+    Vi = np.zeros((n, n), order="F") if cplx else None
+    sw = np.zeros(1, dtype=np.int32)
+    rc = lib().orc_q_vjsvd(m, n, _dp(Ar), _dp(Ai), m, _dp(sh), _dp(sl), _dp(Ur), _dp(Ui), _dp(Vr),
+                           _dp(Vi), int(max_sweeps), sw.ctypes.data_as(_i32))
+    if rc < 0:
+        raise ValueError("orc_q_vjsvd failed with %d" % rc)
+    U = Ur + 1j * Ui if cplx else Ur
+    V = Vr + 1j * Vi if cplx else Vr
+    return dict(sigma=np.stack([sh, sl], axis=1), U=U, V=V, status=int(rc), sweeps=int(sw[0]))
 
 
 def rnF(x):

@@ -10,6 +10,7 @@ import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "jsvd_oracle.c")
+SRC_Q = os.path.join(HERE, "jsvd_oracle_q.c")  # the binary128 twin
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libjsvd_oracle.so")
 
@@ -18,12 +19,12 @@ def build(force: bool = False) -> str:
     """Compile the oracle shared library if it is missing or stale; return its path."""
     os.makedirs(OUT_DIR, exist_ok=True)
     if (not force and os.path.exists(LIB)
-            and os.path.getmtime(LIB) >= os.path.getmtime(SRC)):
+            and os.path.getmtime(LIB) >= max(os.path.getmtime(SRC), os.path.getmtime(SRC_Q))):
         return LIB
     tmp = LIB + ".tmp.%d" % os.getpid()
     cmd = ["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-fopenmp",
            "-ffp-contract=off", "-fno-fast-math", "-fvisibility=hidden",
-           "-Wall", "-Wextra", "-o", tmp, SRC, "-lm"]
+           "-Wall", "-Wextra", "-o", tmp, SRC, SRC_Q, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, LIB)
     return LIB

@@ -139,6 +139,9 @@ def lib():
         L.jsvd_sign_gauge_batched.restype = ctypes.c_int
         L.jsvd_selftest_fp64.argtypes = [_i64, ctypes.c_uint64, _vp, _vp]
         L.jsvd_selftest_fp64.restype = ctypes.c_int
+        L.jsvd_selftest_barrier.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _i64, _vp,
+                                            _vp]
+        L.jsvd_selftest_barrier.restype = ctypes.c_int
         L.jsvd_ordering.argtypes = [ctypes.c_int32, _vp, _vp]
         L.jsvd_ordering.restype = ctypes.c_int
         _lib = L

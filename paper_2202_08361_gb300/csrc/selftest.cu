@@ -1,12 +1,17 @@
-// selftest.cu -- jsvd_selftest_fp64: the integer-pipe binary64 division and
-// square root (fp64soft.cuh) against the FP64 pipe's IEEE instructions on
-// generated operands, counting mismatching bit patterns.
+// selftest.cu -- self-tests that run on the device:
+//   jsvd_selftest_fp64: the integer-pipe binary64 division and square root
+//     (fp64soft.cuh) against the FP64 pipe's IEEE instructions on generated
+//     operands, counting mismatching bit patterns;
+//   jsvd_selftest_barrier: the bounded grid barrier of the persistent SVD
+//     kernel, with one block that never arrives, so the others' wait runs
+//     out and they report JSVD_E_TIMEOUT (no fault, no trap).
 #include <algorithm>
 
 #include "common.cuh"
 #include "fp64bits.cuh"
 #include "fp64soft.cuh"
 #include "jsvd_internal.h"
+#include "svd_core.cuh"
 
 namespace jsvd {
 
@@ -55,7 +60,69 @@ __global__ void selftest_kernel(int64_t n, uint64_t seed, unsigned long long *ba
   if (bs) atomicAdd(&bad[1], bs);
 }
 
+// Barrier state of the self-test (a library-owned device array: the test
+// needs no allocation; concurrent calls would share it).
+struct BarrierTestState {
+  unsigned int count, gen;
+  int err, arrivals, finished;
+};
+static __device__ BarrierTestState g_bar_test;
+
+// Every block takes `rounds` grid barriers; block `absent` (if in range)
+// returns at once and never arrives.  status[0] = JSVD_E_TIMEOUT when a
+// wait gave up, else JSVD_OK; status[1] = the barriers the blocks completed.
+__global__ void barrier_test_kernel(int absent, int rounds, unsigned long long limit_ns,
+                                    int32_t *status)
+{
+  BarrierTestState *b = &g_bar_test;
+  if ((int)blockIdx.x == absent) return;
+  int done = 0;
+  for (int r = 0; r < rounds; ++r) {
+    if (!grid_barrier(&b->count, &b->gen, &b->err, limit_ns)) break;
+    ++done;
+  }
+  if (threadIdx.x == 0) {
+    atomicAdd(&b->arrivals, done);
+    __threadfence();
+    const int present = (int)gridDim.x - ((absent >= 0 && absent < (int)gridDim.x) ? 1 : 0);
+    if (atomicAdd(&b->finished, 1) == present - 1) {  // the last block out reports
+      __threadfence();
+      status[0] = ((volatile int *)&b->err)[0] ? JSVD_E_TIMEOUT : JSVD_OK;
+      status[1] = atomicAdd(&b->arrivals, 0);
+    }
+  }
+}
+
+__global__ void barrier_test_reset()
+{
+  g_bar_test.count = 0u;
+  g_bar_test.gen = 0u;
+  g_bar_test.err = 0;
+  g_bar_test.arrivals = 0;
+  g_bar_test.finished = 0;
+}
+
 }  // namespace jsvd
+
+extern "C" int jsvd_selftest_barrier(int blocks, int absent, int rounds, int64_t limit_ns,
+                                     int32_t *status, void *stream)
+{
+  using namespace jsvd;
+  if (blocks < 1 || blocks > sm_count()) return -1;
+  if (rounds < 1 || rounds > 1000) return -3;
+  if (limit_ns < 1000000 || limit_ns > 5000000000ll) return -4;  // 1 ms .. 5 s
+  if (!status) return -5;
+  cudaStream_t st = as_stream(stream);
+  barrier_test_reset<<<1, 1, 0, st>>>();
+  JSVD_CHECK_LAUNCH();
+  int a = absent;
+  int rr = rounds;
+  unsigned long long lim = (unsigned long long)limit_ns;
+  void *args[] = {&a, &rr, &lim, &status};
+  JSVD_CUDA(cudaLaunchCooperativeKernel((const void *)barrier_test_kernel, dim3(blocks), dim3(32),
+                                        args, 0, st));
+  return JSVD_OK;
+}
 
 extern "C" int jsvd_selftest_fp64(int64_t n, uint64_t seed, unsigned long long *mismatches,
                                   void *stream)

@@ -82,12 +82,14 @@ int batch_set_warps(int w)
   return JSVD_OK;
 }
 
-// Warps per block for a batch: small matrices want many blocks per SM (one
-// warp each hides the pair rotations' latency across matrices), large ones
-// more warps per matrix.  The rule keys on the mean n weighted by the cost
-// of a sweep (m n^2), measured on GB300: 4096 x (64 x 32) is fastest with 1
-// warp, the 10,000 uneven matrices (n up to 256) with 8.
-static int batch_auto_warps(int64_t count, const int64_t *m, const int64_t *n)
+// Warps per block for a batch.  Two things pull apart: many blocks per SM
+// hide the pair rotations' latency across matrices (a long batch wants
+// small blocks), while a batch that does not fill the GPU wants more warps
+// per matrix (more so the larger n).  The rule weighs the batch's count
+// against the GPU's capacity in one-warp blocks and its mean n, weighted by
+// the cost of a sweep (m n^2).  Measured on GB300 (the best warps): 10,000
+// uneven matrices (n up to 256) 2; 1,250 of them 8; 4096 x (64 x 32) 1.
+static int batch_auto_warps(int64_t count, const int64_t *m, const int64_t *n, int capacity1)
 {
   double w = 0.0, wn = 0.0;
   for (int64_t i = 0; i < count; ++i) {
@@ -96,7 +98,10 @@ static int batch_auto_warps(int64_t count, const int64_t *m, const int64_t *n)
     wn += c * (double)n[i];
   }
   const double navg = (w > 0.0) ? wn / w : 0.0;
-  return navg <= 40.0 ? 1 : navg <= 64.0 ? 2 : navg <= 96.0 ? 4 : 8;
+  const double x = (count > 0) ? (double)capacity1 / (double)count * (navg / 64.0) : 1.0;
+  int warps = 1;
+  while (warps < 8 && x >= 1.5 * warps) warps *= 2;
+  return warps;
 }
 
 // The automatic choice of each prepared workspace, read by the launch (a
@@ -430,7 +435,14 @@ extern "C" int jsvd_svd_batched_prepare(jsvd_field field, const jsvd_opts *opts,
     const double cb = (double)m[b] * (double)n[b] * (double)n[b];
     return ca > cb;
   });
-  remember_auto(work, batch_auto_warps(count, m, n));
+  {
+    // the capacity of the GPU in one-warp blocks of this field's kernel
+    int per_sm = 0;
+    auto k1 = (field == JSVD_COMPLEX) ? batched_kernel<true, false, false>
+                                      : batched_kernel<false, false, false>;
+    JSVD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k1, 32, 0));
+    remember_auto(work, batch_auto_warps(count, m, n, per_sm * sm_count()));
+  }
   BatchHdr h = {0, (int)count, 0, 0};
   char *w = (char *)work;
   cudaStream_t st = as_stream(stream);
