@@ -92,6 +92,12 @@ JSVD_API const char *jsvd_last_cuda_error(void);
  *     IEEE routines' slow path); 0 (default): the IEEE intrinsics directly.
  *     Both round correctly: the results are identical. */
 #define JSVD_TUNE_EVD32_DIV 6
+/*   JSVD_TUNE_EVD_HOST: how jsvd_evd2x2_batched_host moves its data.
+ *     value = 0 (default): directly, the kernel reading and writing the host
+ *     streams, when every stream is page-locked memory mapped for the
+ *     current device, else staged; 1: always staged through the workspace
+ *     in chunks.  The results are identical. */
+#define JSVD_TUNE_EVD_HOST 7
 JSVD_API int jsvd_tune_set(int knob, int value, int value2);
 
 /* ------------------------------------------------------------------------
@@ -153,15 +159,16 @@ JSVD_API int jsvd_evd2x2_batched_f32(jsvd_field field, const jsvd_evd2_streams_f
                                      void *stream);
 
 /* The same batched EVD on HOST streams (same meaning and rules as above,
- * every pointer in *s a host pointer), with the host-device copies
- * overlapped with the computation: the batch is cut into chunks that are
- * copied to `work`, transformed by the kernel of jsvd_evd2x2_batched (same
- * bits) and copied back, three chunks in flight on internal streams of the
- * current device.  The call is asynchronous on `stream` like the others:
- * the outputs are complete once `stream` has reached this point.  For the
- * copies to overlap (and the call to return early) the host buffers must
- * be page-locked (cudaHostAlloc / pinned); pageable buffers give the same
- * results with the copies serialised.  work: DEVICE, 256-byte aligned,
+ * every pointer in *s a host pointer), by the kernel of
+ * jsvd_evd2x2_batched (same bits).  When every stream is page-locked memory
+ * mapped for the current device (cudaHostAlloc, pinned tensors), the
+ * kernel reads and writes the streams in place over the host link, with no
+ * staging.  Otherwise (or with JSVD_TUNE_EVD_HOST = 1) the batch is cut
+ * into chunks that are copied to `work`, transformed and copied back, three
+ * chunks in flight on internal streams of the current device.  The call is
+ * asynchronous on `stream` like the others: the outputs are complete once
+ * `stream` has reached this point.  Pageable buffers give the same results
+ * with the copies serialised.  work: DEVICE, 256-byte aligned,
  * jsvd_evd2x2_host_workspace_size bytes, not used by anything else until
  * `stream` passes this call.  Errors: as above, -4 work NULL or misaligned,
  * JSVD_E_WORKSPACE if work_bytes is too small. */

@@ -10,7 +10,7 @@ from . import _native
 from ._native import (JSVD_COMPLEX, JSVD_E_CUDA, JSVD_E_NONFINITE, JSVD_E_TIMEOUT,
                       JSVD_E_UNSUPPORTED, JSVD_E_WORKSPACE, JSVD_FP64, JSVD_MIXED_FP32_FP64,
                       JSVD_NOT_CONVERGED, JSVD_OK, JSVD_REAL, JSVD_TUNE_BATCH_SMEM,
-                      JSVD_TUNE_EVD32_DIV,
+                      JSVD_TUNE_EVD32_DIV, JSVD_TUNE_EVD_HOST,
                       JSVD_TUNE_BATCH_WARPS, JSVD_TUNE_EVD_ARITH, JSVD_TUNE_EVD_LAUNCH,
                       JSVD_TUNE_SVD_GRID, JsvdError)
 
@@ -111,8 +111,10 @@ def evd2x2_host_workspace_size():
 def evd2x2_batched_host(a11, a22, a21_re, a21_im=None, *, out=None, want_lambda=True,
                         want_zeta_p=True, work=None, device=None, stream=None):
     """Batched 2x2 Hermitian EVD of HOST streams (jsvd_evd2x2_batched_host):
-    CPU tensors in and out (page-locked for the copies to overlap the
-    kernels), computed on the current CUDA device in pipelined chunks.
+    CPU tensors in and out, computed on the current CUDA device.  With every
+    tensor pinned the kernel reads and writes them in place over the host
+    link; otherwise they are staged in pipelined chunks.  Keep the tensors
+    alive until `stream` has passed the call.
     Returns the output dict (CPU tensors; `out` may supply them, pinned
     ones are best).  Asynchronous on `stream`: synchronise before reading
     the outputs.  `work` is a device workspace (uint8, at least

@@ -1,16 +1,24 @@
 // evd2_host.cu -- jsvd_evd2x2_batched_host: the batched 2x2 EVD on host
-// buffers, with the host-device copies overlapped with the kernels.
+// buffers.
 //
-// The batch is cut into chunks.  Chunk c uses workspace slot c mod kSlots
-// and internal stream c mod kSlots: the copies of its input streams to the
-// slot, the EVD kernel on the slot (the same kernel and arithmetic as
-// jsvd_evd2x2_batched), the copies of its output streams back.  With three
-// slots the host-to-device copy of one chunk, the kernel of the next older
-// one and the device-to-host copy of the oldest run at the same time (the
-// two copy directions use separate copy engines).  Events order the
-// internal streams after the work already queued on the caller's stream,
-// and the caller's stream after all chunks, so the call behaves like one
-// asynchronous operation on `stream`.
+// Two ways to move the data, the same kernel and bits either way:
+//
+// Direct (default, when every stream is page-locked memory mapped for the
+// current device): the EVD kernel reads its inputs from the host streams
+// and writes its outputs back to them over the host link; no staging copy,
+// one launch.  On a coherent CPU-GPU node the link then carries exactly the
+// streams' bytes, both directions at once.
+//
+// Staged (pageable or unmapped buffers, or JSVD_TUNE_EVD_HOST = 1): the
+// batch is cut into chunks.  Chunk c uses workspace slot c mod kSlots and
+// internal stream c mod kSlots: the copies of its input streams to the
+// slot, the EVD kernel on the slot, the copies of its output streams back.
+// With three slots the host-to-device copy of one chunk, the kernel of the
+// next older one and the device-to-host copy of the oldest run at the same
+// time (the two copy directions use separate copy engines).  Events order
+// the internal streams after the work already queued on the caller's
+// stream, and the caller's stream after all chunks, so the call behaves
+// like one asynchronous operation on `stream`.
 #include <mutex>
 
 #include "common.cuh"
@@ -19,6 +27,7 @@
 namespace jsvd {
 
 constexpr int kSlots = 3;
+static int g_host_path = 0;  // 0: direct when every stream is mapped; 1: always staged
 constexpr int64_t kChunk = int64_t(1) << 20;  // matrices per chunk
 
 // bytes of one slot: 4 input and 5 output double streams, one int32 stream
@@ -77,6 +86,68 @@ static int copy_out(void *dst, const void *src, size_t bytes, cudaStream_t st)
   return JSVD_OK;
 }
 
+// The address through which the current device reads and writes the host
+// range [p, p + bytes), or nullptr when the range is not page-locked memory
+// mapped for it.  Both ends are checked (a stream is one buffer).
+static void *mapped_address(const void *p, size_t bytes)
+{
+  if (!p || bytes == 0) return nullptr;
+  cudaPointerAttributes a0, a1;
+  const char *last = static_cast<const char *>(p) + (bytes - 1);
+  if (cudaPointerGetAttributes(&a0, p) != cudaSuccess || cudaPointerGetAttributes(&a1, last) != cudaSuccess) {
+    cudaGetLastError();  // an unregistered pointer is an answer here, not an error
+    return nullptr;
+  }
+  if (a0.type != cudaMemoryTypeHost || a1.type != cudaMemoryTypeHost) return nullptr;
+  if (!a0.devicePointer || !a1.devicePointer) return nullptr;
+  // one linear mapping across the range
+  if ((char *)a1.devicePointer - (char *)a0.devicePointer != (ptrdiff_t)(bytes - 1)) return nullptr;
+  return a0.devicePointer;
+}
+
+// Device addresses of all given host streams in *d, true when every one is
+// mapped.
+static bool map_streams(const jsvd_evd2_streams *h, int64_t n, bool cplx, jsvd_evd2_streams *d)
+{
+  const size_t b = (size_t)n * sizeof(double);
+  bool ok = true;
+  auto in = [&](const double *x) -> const double * {
+    if (!x) return nullptr;
+    void *m = mapped_address(x, b);
+    ok = ok && m;
+    return static_cast<const double *>(m);
+  };
+  auto out = [&](double *x) -> double * {
+    if (!x) return nullptr;
+    void *m = mapped_address(x, b);
+    ok = ok && m;
+    return static_cast<double *>(m);
+  };
+  d->a11 = in(h->a11);
+  d->a22 = in(h->a22);
+  d->a21_re = in(h->a21_re);
+  d->a21_im = cplx ? in(h->a21_im) : nullptr;
+  d->cos_phi = out(h->cos_phi);
+  d->ea_tan_re = out(h->ea_tan_re);
+  d->ea_tan_im = cplx ? out(h->ea_tan_im) : nullptr;
+  d->lambda1 = out(h->lambda1);
+  d->lambda2 = out(h->lambda2);
+  d->zeta_p = nullptr;
+  if (h->zeta_p) {
+    void *m = mapped_address(h->zeta_p, (size_t)n * sizeof(int32_t));
+    ok = ok && m;
+    d->zeta_p = static_cast<int32_t *>(m);
+  }
+  return ok;
+}
+
+int evd2_set_host_path(int v)
+{
+  if (v < 0 || v > 1) return -2;
+  g_host_path = v;
+  return JSVD_OK;
+}
+
 }  // namespace jsvd
 
 using namespace jsvd;
@@ -100,6 +171,10 @@ extern "C" int jsvd_evd2x2_batched_host(jsvd_field field, const jsvd_evd2_stream
   if (cplx && (!h->a21_im || !h->ea_tan_im)) return -2;
   if (!work || ((uintptr_t)work & 255)) return -4;
   if (work_bytes < kSlots * slot_bytes(kChunk)) return JSVD_E_WORKSPACE;
+  if (g_host_path == 0) {
+    jsvd_evd2_streams d;
+    if (map_streams(h, n, cplx, &d)) return jsvd_evd2x2_batched(field, &d, n, stream);
+  }
   cudaStream_t ps[kSlots];
   JSVD_TRY(pipe_streams(ps));
   cudaStream_t user = as_stream(stream);

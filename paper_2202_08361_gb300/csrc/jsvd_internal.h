@@ -10,6 +10,7 @@ int svd_set_grid(int cap, int warps);
 int batch_set_warps(int w);
 int batch_set_smem(int kib);
 int evd2f_set_fast(int v);
+int evd2_set_host_path(int v);
 }  // namespace jsvd
 
 #include <cuda_runtime.h>

@@ -79,3 +79,6 @@ def test_argument_errors_need_no_gpu(lib):
     assert L.jsvd_tune_set(4, 1, 3) == -3           # fields: 0, 1 or 2
     assert L.jsvd_tune_set(4, 1, 2) == 0
     assert L.jsvd_tune_set(4, -1, 0) == 0           # back to the defaults
+    assert L.jsvd_tune_set(_native.JSVD_TUNE_EVD_HOST, 2, 0) == -2
+    assert L.jsvd_tune_set(_native.JSVD_TUNE_EVD_HOST, 1, 0) == 0
+    assert L.jsvd_tune_set(_native.JSVD_TUNE_EVD_HOST, 0, 0) == 0

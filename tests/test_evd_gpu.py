@@ -159,18 +159,25 @@ def test_empty_batch_and_optional_outputs():
     assert torch.equal(part["ea_tan_re"], full["ea_tan_re"])
 
 
+@pytest.mark.parametrize("staged", [0, 1])
 @pytest.mark.parametrize("complex_", [False, True])
 @pytest.mark.parametrize("n", [5, (1 << 20) + 1, 4 * (1 << 20) + 12345])
-def test_host_pipeline_bit_identical(n, complex_):
-    """jsvd_evd2x2_batched_host (pinned host streams, chunks of 2^20 in three
-    slots): the same bits as the device call, across chunk boundaries, slot
-    reuse and a ragged last chunk; the oracle agrees on a sample."""
+def test_host_pipeline_bit_identical(n, complex_, staged):
+    """jsvd_evd2x2_batched_host on pinned host streams, the kernel reading
+    and writing them in place (JSVD_TUNE_EVD_HOST = 0) or staged in chunks
+    of 2^20 in three slots (= 1): the same bits as the device call, across
+    chunk boundaries, slot reuse and a ragged last chunk; the oracle agrees
+    on a sample."""
     torch = _torch()
     import paper_2202_08361_gb300 as J
     streams = workloads.evd_batch(n, complex_, seed_salt=17)
     host = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in streams]
-    out = J.evd2x2_batched_host(*host[:3], host[3] if complex_ else None)
-    torch.cuda.synchronize()
+    J.tune_set(J.JSVD_TUNE_EVD_HOST, staged)
+    try:
+        out = J.evd2x2_batched_host(*host[:3], host[3] if complex_ else None)
+        torch.cuda.synchronize()
+    finally:
+        J.tune_set(J.JSVD_TUNE_EVD_HOST, 0)
     ref = run_gpu(streams, complex_)
     for k, v in ref.items():
         assert np.array_equal(out[k].numpy().view(np.uint8), v.view(np.uint8)), k
@@ -198,3 +205,35 @@ def test_host_pipeline_pageable_and_optional_outputs():
         assert np.array_equal(out[k].numpy(), ref[k]), k
     e = torch.empty(0, dtype=torch.float64)
     assert J.evd2x2_batched_host(e, e, e)["cos_phi"].numel() == 0
+
+
+def test_host_mixed_pinned_pageable_and_offset_views():
+    """Pinned inputs with pageable outputs take the staged path; inputs that
+    are views at an offset inside one pinned buffer (and outputs likewise)
+    are mapped and take the direct path; both give the device call's bits."""
+    torch = _torch()
+    import paper_2202_08361_gb300 as J
+    n = 300001
+    streams = workloads.evd_batch(n, True, seed_salt=19)
+    ref = run_gpu(streams, True)
+    pinned = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in streams]
+    out = {k: torch.empty(n, dtype=torch.float64) for k in ("cos_phi", "ea_tan_re", "ea_tan_im",
+                                                            "lambda1", "lambda2")}
+    out["zeta_p"] = torch.empty(n, dtype=torch.int32)
+    r = J.evd2x2_batched_host(*pinned, out=out)
+    torch.cuda.synchronize()
+    for k in ref:
+        assert np.array_equal(r[k].numpy().view(np.uint8), ref[k].view(np.uint8)), k
+    big = torch.empty(4 * n + 7, dtype=torch.float64).pin_memory()
+    views = [big[3 + j * n: 3 + (j + 1) * n] for j in range(4)]
+    for v, a in zip(views, streams):
+        v.copy_(torch.from_numpy(np.ascontiguousarray(a)))
+    obig = torch.empty(5 * n + 1, dtype=torch.float64).pin_memory()
+    out2 = {k: obig[1 + j * n: 1 + (j + 1) * n] for j, k in enumerate(("cos_phi", "ea_tan_re",
+                                                                       "ea_tan_im", "lambda1",
+                                                                       "lambda2"))}
+    out2["zeta_p"] = torch.empty(n, dtype=torch.int32).pin_memory()
+    r2 = J.evd2x2_batched_host(*views, out=out2)
+    torch.cuda.synchronize()
+    for k in ref:
+        assert np.array_equal(r2[k].numpy().view(np.uint8), ref[k].view(np.uint8)), k
