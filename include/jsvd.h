@@ -68,8 +68,9 @@ JSVD_API const char *jsvd_last_cuda_error(void);
 #define JSVD_TUNE_EVD_LAUNCH 1
 /*   JSVD_TUNE_SVD_GRID: value = most blocks of the persistent SVD sweep
  *     kernel (0 = as many as the pair chunks of a step, capped by
- *     residency); value2 = warps per block (1, 2, 4 or 8; 0 = chosen from
- *     the number of pairs and SMs). */
+ *     residency); value2 = warps per block (1, 2, 4 or 8; 0 = 1 for FP64
+ *     and 2 for FP32 sweeps in the per-warp step form, chosen from the
+ *     number of pairs and SMs in the chunked one). */
 #define JSVD_TUNE_SVD_GRID 2
 /*   JSVD_TUNE_BATCH_WARPS: value = warps per block of the batched SVD
  *     kernel (1, 2, 4, 8 or 16), or 0 (the default): chosen when the batch
@@ -98,6 +99,12 @@ JSVD_API const char *jsvd_last_cuda_error(void);
  *     current device, else staged; 1: always staged through the workspace
  *     in chunks.  The results are identical. */
 #define JSVD_TUNE_EVD_HOST 7
+/*   JSVD_TUNE_SVD_STEP: the form of a step in the single-matrix sweep
+ *     kernel: 2 (or 0, the default) = each warp runs its pairs alone, a
+ *     rotation's independent divisions and square roots spread over its
+ *     lanes; 1 = chunks of pairs in three block phases, one pair's rotation
+ *     per lane.  The results are identical. */
+#define JSVD_TUNE_SVD_STEP 8
 JSVD_API int jsvd_tune_set(int knob, int value, int value2);
 
 /* ------------------------------------------------------------------------

@@ -11,6 +11,7 @@ int batch_set_warps(int w);
 int batch_set_smem(int kib);
 int evd2f_set_fast(int v);
 int evd2_set_host_path(int v);
+int svd_set_step_mode(int v);
 }  // namespace jsvd
 
 #include <cuda_runtime.h>
@@ -20,6 +21,7 @@ namespace jsvd {
 // Option bits carried from jsvd_opts to the kernels.
 constexpr int kFlagPermute = 1;  // the column swap P during the sweeps
 constexpr int kFlagComp = 2;     // compensated dot-products (FP64 sweeps)
+constexpr int kFlagWarpStep = 4; // each warp runs its pairs alone (sweep kernel)
 int svd_check_opts(const jsvd_opts *o, int &S, int &mode, int &rexp, int &flags);
 size_t svd_fp64_workspace(bool cplx, int64_t m, int64_t n);
 size_t svd_mixed_workspace(bool cplx, int64_t m, int64_t n);

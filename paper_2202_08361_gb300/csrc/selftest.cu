@@ -63,7 +63,7 @@ __global__ void selftest_kernel(int64_t n, uint64_t seed, unsigned long long *ba
 // Barrier state of the self-test (a library-owned device array: the test
 // needs no allocation; concurrent calls would share it).
 struct BarrierTestState {
-  unsigned int count, gen;
+  unsigned int word;
   int err, arrivals, finished;
 };
 static __device__ BarrierTestState g_bar_test;
@@ -78,7 +78,7 @@ __global__ void barrier_test_kernel(int absent, int rounds, unsigned long long l
   if ((int)blockIdx.x == absent) return;
   int done = 0;
   for (int r = 0; r < rounds; ++r) {
-    if (!grid_barrier(&b->count, &b->gen, &b->err, limit_ns)) break;
+    if (!grid_barrier(&b->word, &b->err, limit_ns)) break;
     ++done;
   }
   if (threadIdx.x == 0) {
@@ -95,8 +95,7 @@ __global__ void barrier_test_kernel(int absent, int rounds, unsigned long long l
 
 __global__ void barrier_test_reset()
 {
-  g_bar_test.count = 0u;
-  g_bar_test.gen = 0u;
+  g_bar_test.word = 0u;
   g_bar_test.err = 0;
   g_bar_test.arrivals = 0;
   g_bar_test.finished = 0;

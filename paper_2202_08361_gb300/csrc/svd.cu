@@ -33,8 +33,7 @@ constexpr unsigned long long kBarrierLimitNs = 20ull * 1000ull * 1000ull * 1000u
 struct SvdState {
   unsigned long long Mbuf[3];  // running max-norm (bits), triple-buffered by step
   unsigned long long M0;       // ||A||_max bits
-  unsigned int bar_count;
-  unsigned int bar_gen;
+  unsigned int bar_word;        // grid barrier (0 at launch)
   int err;                     // barrier timeout
   int nonfinite;
   int s;                       // accumulated scaling exponent: G = 2^s (A V)
@@ -139,21 +138,28 @@ __global__ void init_kernel(const double *__restrict__ A, int64_t lda, MatView M
   }
 }
 
-// All sweeps of Alg. zvjsvd in one cooperative launch.  Each block of W
-// warps takes chunks of W pivot pairs of a step (one pair per warp; the
-// chunk's 2x2 EVDs run one per lane), blocks stride over the nt/2 pairs,
-// and a bounded grid barrier separates the steps.  T is the precision of
-// the columns (double; float in the FP32 phase of the mixed SVD).
+// All sweeps of Alg. zvjsvd in one cooperative launch; the blocks stride
+// over the nt/2 pairs of a step and a bounded grid barrier separates the
+// steps.  Two forms of a block's share of a step, with the same bits:
+//   kFlagWarpStep (the default): each warp runs its pairs alone (sums,
+//     rotation spread over the warp's lanes, transformation), no block
+//     barrier inside a step;
+//   otherwise chunks of W pairs in three block phases, the chunk's
+//     rotations one per lane (a W-th of the rotations' FP64 instructions,
+//     at the price of two block barriers per chunk).
+// T is the precision of the columns (double; float in the FP32 phase of
+// the mixed SVD).
 template <typename T, bool CPLX, bool COMP>
 __global__ void __launch_bounds__(256) sweeps_kernel(MatViewT<T> M, SvdState *st, double ups,
                                                      int max_sweeps, int rescale_exp, int flags)
 {
-  __shared__ PairSums s_sums[32];
-  __shared__ PairOut s_out[32];
+  __shared__ PairSums s_sums[8];
+  __shared__ PairOut s_out[8];
   if (st->nonfinite) return;
   const int nt = M.n + (M.n & 1);
   const int K = nt - 1, L = nt / 2;
   const int lane = threadIdx.x & 31, W = blockDim.x >> 5;
+  const bool warp_step = (flags & kFlagWarpStep) != 0;
   if (K < 1) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       st->sweeps = 1;
@@ -181,16 +187,19 @@ __global__ void __launch_bounds__(256) sweeps_kernel(MatViewT<T> M, SvdState *st
       }
       unsigned long long Mloc = 0ull;
       int rots = 0, gsn = 0;
-      for (int base = blockIdx.x * W; base < L; base += gridDim.x * W)
-        step_chunk<T, CPLX, true, COMP>(M, k, nt, base, W, ups, rk, (flags & kFlagPermute) != 0,
-                                        s_sums, s_out, Mloc, rots, gsn);
+      if (warp_step)
+        step_warps<T, CPLX, COMP>(M, k, nt, ups, rk, (flags & kFlagPermute) != 0, Mloc, rots, gsn);
+      else
+        for (int base = blockIdx.x * W; base < L; base += gridDim.x * W)
+          step_chunk<T, CPLX, true, COMP>(M, k, nt, base, W, ups, rk, (flags & kFlagPermute) != 0,
+                                          s_sums, s_out, Mloc, rots, gsn);
       Mloc = warp_umax(Mloc);
       if (lane == 0) {
         if (Mloc) atomicMax(&st->Mbuf[nxt], bits(magbits_to_double(Mloc, T(0))));
         if (rots) atomicAdd(&st->T[sweep], rots);
         if (gsn) atomicAdd(&st->gs, (unsigned long long)gsn);
       }
-      if (!grid_barrier(&st->bar_count, &st->bar_gen, &st->err, kBarrierLimitNs)) return;
+      if (!grid_barrier(&st->bar_word, &st->err, kBarrierLimitNs)) return;
     }
     converged = (((volatile int *)st->T)[sweep] == 0);
   }
@@ -264,6 +273,14 @@ __global__ void output_kernel(MatView M, const int *e, const double *f, const in
 
 static int g_svd_grid_cap = 0;
 static int g_svd_warps = 0;
+static int g_svd_step = 0;  // 0 or 2: per warp; 1: chunked
+
+int svd_set_step_mode(int v)
+{
+  if (v < 0 || v > 2) return -2;
+  g_svd_step = v;
+  return JSVD_OK;
+}
 
 int svd_set_grid(int cap, int warps)
 {
@@ -442,12 +459,23 @@ static int launch_sweeps(const MatViewT<T> &M, SvdState *state, double ups, int 
   const int nt = M.n + (M.n & 1);
   const int Lp = nt / 2;
   const int sms = sm_count();
-  // warps per block: the most (up to 8) that still leave a chunk of pairs
-  // for every SM, so the step's pairs spread over the whole GPU
+  // The step form: each warp alone unless the chunked form is asked for.
+  // Measured on GB300 for 256 x 128 to 4096 x 2048, real and complex, FP64
+  // and mixed: the per-warp form is 2-15 % faster everywhere (its extra
+  // FP64 instructions for unshared rotations cost less than the chunked
+  // form's block barriers and its coarser spread of pairs over the SMs).
+  const bool warp_step = (g_svd_step != 1);
+  // warps per block: per-warp form 1 (FP64 sweeps) or 2 (FP32 sweeps), the
+  // fastest measured; chunked form the most (up to 8) that still leave a
+  // chunk of pairs for every SM
   int W = g_svd_warps;
   if (W == 0) {
-    W = 1;
-    while (W < 8 && (Lp + 2 * W - 1) / (2 * W) >= sms) W *= 2;
+    if (warp_step) {
+      W = (sizeof(T) == 4) ? 2 : 1;
+    } else {
+      W = 1;
+      while (W < 8 && (Lp + 2 * W - 1) / (2 * W) >= sms) W *= 2;
+    }
   }
   auto kern = sweeps_kernel<T, CPLX, COMP>;
   int per_sm = 0;
@@ -458,7 +486,7 @@ static int launch_sweeps(const MatViewT<T> &M, SvdState *state, double ups, int 
   if (grid < 1) grid = 1;
   MatViewT<T> Mk = M;
   SvdState *sk = state;
-  int Sk = S, rk = rexp, pk = flags;
+  int Sk = S, rk = rexp, pk = flags | (warp_step ? kFlagWarpStep : 0);
   double upsk = ups;
   void *args[] = {&Mk, &sk, &upsk, &Sk, &rk, &pk};
   JSVD_CUDA(cudaLaunchCooperativeKernel((const void *)kern, dim3(grid), dim3(32 * W), args, 0, st));

@@ -315,6 +315,162 @@ __device__ __forceinline__ PairOut pair_rotation(const PairSums &sm, double ups)
 }
 
 
+// pair_rotation computed by a whole warp whose every lane holds the pair's
+// sums: the same operations on the same operands, so the same bits, but the
+// divisions and square roots that do not depend on one another run side by
+// side, lane r (mod 4) taking the r-th of a stage as one warp instruction:
+//   1 sqrt  ||g_p||^2, ||g_q||^2
+//   2 div   Re a21', Im a21', f_p/f_q, f_q/f_p (Alg. zdpscl, Alg. Gram)
+//   3 div   am/aM of Eq. e:zpolar; m/M of Alg. hypot for |a21'|      (complex)
+//   4 sqrt  their sqrt(x^2 + 1)                                        (complex)
+//   5 div   o/|a| of Eq. e:tan2; |Re a21'|/|a21'|, Im a21'/|a21'|
+//   6 sqrt  sqrt(tan2^2 + 1)
+//   7 div   tan(phi)
+//   8 sqrt  sec(phi)
+//   9 div   cos(phi); lambda1', lambda2'
+// The chain of dependent correctly rounded operations is then 7 (real) or 9
+// (complex) long instead of the 12 or 19 one lane would run.  For launches
+// with one pair per warp, whose step time is this chain.  A lane whose
+// stage has a zero divisor (a result the selects below then discard)
+// divides by 1 instead.
+template <bool CPLX>
+__device__ __forceinline__ PairOut pair_rotation_warp(const PairSums &sm, double ups)
+{
+  const int r = threadIdx.x & 3;
+  auto from = [](double x, int src) { return __shfl_sync(0xffffffffu, x, src); };
+  PairOut o;
+  o.c = 1.0;
+  o.C = 0.0;
+  o.S = 0.0;
+  o.gs = 0;
+  o.ex = o.ey = 0;
+  o.psr = o.psi = 0.0;
+  int ep, eq, shift;
+  double fp, fq;
+  if (sm.wide) {
+    if (sm.ep == kNegInfE || sm.eq == kNegInfE) {
+      o.rot = false;
+      o.swap = (sm.ep == kNegInfE) && (sm.eq != kNegInfE);
+      return o;
+    }
+    ep = sm.ep;
+    eq = sm.eq;
+    fp = sm.fp;
+    fq = sm.fq;
+    shift = 0;
+  } else {
+    if (bits(sm.pp) == 0ull || bits(sm.qq) == 0ull) {
+      o.rot = false;
+      o.swap = bits(sm.pp) < bits(sm.qq);
+      return o;
+    }
+    const double s1 = soft::sqrt_rn(r == 0 ? sm.pp : sm.qq);  // stage 1
+    const double rp = from(s1, 0), rq = from(s1, 1);
+    ep = flg(rp);
+    eq = flg(rq);
+    fp = ldexp_rn(rp, -ep);
+    fq = ldexp_rn(rq, -eq);
+    shift = -(ep + eq);
+  }
+  // stage 2: a21' = (g_q/2^eq)^* (g_p/2^ep) / (f_q f_p), f_p/f_q, f_q/f_p
+  const double d = __dmul_rn(fq, fp);
+  const double n2 = (r == 0) ? ldexp_rn(sm.qr, shift)
+                    : (r == 1) ? (CPLX ? ldexp_rn(sm.qi, shift) : 1.0)
+                    : (r == 2) ? fp : fq;
+  const double d2 = (r == 0) ? d : (r == 1) ? (CPLX ? d : 1.0) : (r == 2) ? fq : fp;
+  const double v2 = soft::div_rn(n2, d2);
+  const double zr = from(v2, 0), zi = CPLX ? from(v2, 1) : 0.0;
+  const double q12 = from(v2, 2), q21 = from(v2, 3);
+  // Alg. Gram
+  double f12 = q12, f21 = q21;
+  const int e12 = ep - eq + flg(f12), e21 = eq - ep + flg(f21);
+  f12 = ldexp_rn(f12, -flg(f12));
+  f21 = ldexp_rn(f21, -flg(f21));
+  const int sA = min(1023 - max(e12, e21), 0);
+  double a11 = ldexp_rn(f12, e12 + sA), a22 = ldexp_rn(f21, e21 + sA);
+  double a21r = ldexp_rn(zr, sA), a21i = CPLX ? ldexp_rn(zi, sA) : 0.0;
+  // the EVD (Alg. d8jac2 / Listing 1): Eq. e:z
+  const int E = CPLX ? max(max(flg_sat(a11), flg_sat(a22)), max(flg_sat(a21r), flg_sat(a21i)))
+                     : max(max(flg_sat(a11), flg_sat(a22)), flg_sat(a21r));
+  const int zeta = 1020 - E;
+  a11 = ldexp_rn(a11, zeta);
+  a22 = ldexp_rn(a22, zeta);
+  a21r = ldexp_rn(a21r, zeta);
+  if (CPLX) a21i = ldexp_rn(a21i, zeta);
+  double az, aa21, ar = dabs(a21r);
+  bool zero = false;
+  if (CPLX) {
+    // stages 3, 4: |a21'| by Eq. e:zpolar (lane 0) and the convergence
+    // test's hypot of the unscaled a21' (lane 1), side by side
+    const double ai = dabs(a21i);
+    const bool rmin = bits(ar) <= bits(ai);
+    const double am = rmin ? ar : ai, aM = rmin ? ai : ar;
+    zero = (bits(aM) == 0ull);
+    const double azr = dabs(zr), azi = dabs(zi);
+    const bool xm = bits(azr) <= bits(azi);
+    const double mz = xm ? azr : azi, Mz = xm ? azi : azr;
+    const bool zz = (bits(Mz) == 0ull);
+    const double v3 = soft::div_rn(r == 0 ? am : mz, r == 0 ? (zero ? 1.0 : aM) : (zz ? 1.0 : Mz));
+    const double mM = zero ? 0.0 : from(v3, 0), qz = zz ? 0.0 : from(v3, 1);
+    const double v4 = soft::sqrt_rn(r == 0 ? __fma_rn(mM, mM, 1.0) : __fma_rn(qz, qz, 1.0));
+    aa21 = __dmul_rn(from(v4, 0), aM);
+    az = __dmul_rn(from(v4, 1), Mz);
+  } else {
+    aa21 = ar;
+    az = dabs(zr);
+  }
+  o.rot = !(ord(az) < ord(ups));
+  // stage 5: Eq. e:tan2's o/|a| (|a| = 0 gives Inf or NaN, which the clamp
+  // turns into fl(sqrt nu) or 0), and the phase of a21'
+  const double oo = twice_abs(aa21);
+  const double a = __dsub_rn(a11, a22);
+  const double aa = dabs(a);
+  const double den21 = zero ? 1.0 : aa21;
+  const double n5 = (r == 0) ? oo : (r == 1) ? ar : a21i;
+  const double d5 = (r == 0) ? ((bits(aa) == 0ull) ? 1.0 : aa) : den21;
+  const double v5 = soft::div_rn(n5, CPLX ? d5 : ((bits(aa) == 0ull) ? 1.0 : aa));
+  const double q5 = from(v5, 0);
+  const double q = (bits(aa) == 0ull) ? ((bits(oo) == 0ull) ? 0.0 : dbl(kInf)) : q5;
+  const double tan2 = clamp_tan2(q, a);
+  // stages 6 - 8: tan(phi), sec^2(phi), sec(phi) (Eq. e:jactan, e:jacsec)
+  const double tan1 = soft::div_rn(tan2, __dadd_rn(1.0, soft::sqrt_rn(__fma_rn(tan2, tan2, 1.0))));
+  const double sec2 = __fma_rn(tan1, tan1, 1.0);
+  const double sec = soft::sqrt_rn(sec2);
+  // stage 9: cos(phi) = 1/sec(phi); the eigenvalues of Eq. e:lamsec
+  const double nl1 = __fma_rn(tan1, __fma_rn(a22, tan1, oo), a11);
+  const double nl2 = __fma_rn(tan1, __fma_rn(a11, tan1, -oo), a22);
+  const double v9 = soft::div_rn((r == 0) ? 1.0 : (r == 1) ? nl1 : nl2, (r == 0) ? sec : sec2);
+  const double cphi = from(v9, 0), l1s = from(v9, 1), l2s = from(v9, 2);
+  if (CPLX) {
+    const double qc = from(v5, 1), qs = from(v5, 2);
+    const double ca = with_sign(zero ? 1.0 : qc, a21r);  // fmin(., 1)
+    const double sa = zero ? a21i : qs;
+    o.C = __dmul_rn(ca, tan1);
+    o.S = __dmul_rn(sa, tan1);
+  } else {
+    o.C = xor_sign(tan1, a21r);
+    o.S = 0.0;
+  }
+  o.c = cphi;
+  o.swap = ord(l1s) < ord(l2s);
+  if (o.rot) {
+    if (gs_cond(ep, eq, q12, ups)) {
+      o.gs = 1;
+      o.ex = ep;
+      o.ey = eq;
+      o.psr = __dmul_rn(zr, q21);
+      o.psi = -__dmul_rn(zi, q21);
+    } else if (gs_cond(eq, ep, q21, ups)) {
+      o.gs = 2;
+      o.ex = eq;
+      o.ey = ep;
+      o.psr = __dmul_rn(zr, q12);
+      o.psi = __dmul_rn(zi, q12);
+    }
+  }
+  return o;
+}
+
 // The compensated dot-product of supplement SM2.2 (Alg. zdpscl' /
 // ddpscl'): each term x y enters as c = RD(x y) and c' = x y - c >= 0 (one
 // fma, exact), and each of the two streams is summed by Kahan's method
@@ -427,14 +583,16 @@ __device__ __noinline__ PairSums pair_sums_wide(const MatViewT<double, CG> &M, i
 // in every lane).  rk != 0 downscales both columns of G by 2^rk first (section 3.2,
 // step 2; FP64 only).  COMP forms g_q^* g_p by the compensated summation
 // (FP64 only); the squared norms stay plain fma sums.
-template <typename T, bool CPLX, bool CG, bool COMP = false>
+template <typename T, bool CPLX, bool CG, bool COMP = false, int U = (sizeof(T) == 4) ? 8 : 4>
 __device__ __forceinline__ PairSums pair_sums(const MatViewT<T, CG> &M, int p, int q, int rk)
 {
   static_assert(!COMP || sizeof(T) == 8, "the compensated sums are FP64 only");
-  // rows per lane per loop trip: their loads are all issued before the
+  // U rows per lane per loop trip: their loads are all issued before the
   // arithmetic, which then consumes them in ascending row order, so the
-  // accumulation order (and the bits) are those of the one-row loop
-  constexpr int U = (sizeof(T) == 4) ? 8 : 4;
+  // accumulation order (and the bits) are those of the one-row loop.  The
+  // rows of a last, partial trip cost FP64 issue slots all the same (a
+  // masked FP64 instruction takes the pipe like a full one): wide trips
+  // only where the column fills them.
   const int lane = threadIdx.x & 31;
   T *gpr = M.gr + p * M.ldg, *gqr = M.gr + q * M.ldg;
   T *gpi = CPLX ? M.gi + p * M.ldg : nullptr, *gqi = CPLX ? M.gi + q * M.ldg : nullptr;
@@ -578,73 +736,120 @@ __device__ __forceinline__ void gs_apply(const MatViewT<double, CG> &M, int p, i
 // Eq. e:transf (Alg. zjrot) on the pair's G rows (tracking the max-norm of
 // the new entries in Mloc, as magbits() in T's encoding) and V rows, with the
 // columns swapped if o.swap; a non-rotated pair with o.swap is only swapped.
-// One full warp; o must be the same in every lane.
-template <typename T, bool CPLX, bool CG>
+// One full warp; o must be the same in every lane.  U rows per lane per
+// loop trip, whose loads are all issued before its arithmetic and stores
+// (the rows are independent, so U changes no bits).  G's rows and then V's
+// take separate trips; with MERGED, G's mp rows followed by V's np rows are
+// one sequence (both multiples of 32, so each 32 rows lie in one matrix),
+// so that a trip may hold rows of both -- one trip for a short pair of
+// columns, at the price of a pointer select per row.
+template <typename T, bool CPLX, bool CG, int U = (sizeof(T) == 4) ? 8 : 4, bool MERGED = false>
 __device__ __forceinline__ void pair_apply(const MatViewT<T, CG> &M, int p, int q, const PairOut &o,
                                            unsigned long long &Mloc)
 {
-  constexpr int U = (sizeof(T) == 4) ? 8 : 4;
   const int lane = threadIdx.x & 31;
   const bool swp = o.swap;
   if (o.rot) {
     const T c = to_t(o.c, T(0)), C = to_t(o.C, T(0));
     const T S = CPLX ? to_t(o.S, T(0)) : T(0);
-    // x_p' = fma(x_q, e', x_p) c, x_q' = fma(x_p, -conj(e'), x_q) c, e' = C + iS
-    for (int pass = 0; pass < 2; ++pass) {
-      const bool onG = (pass == 0);
-      if constexpr (sizeof(T) == 8) {
-        if (onG && o.gs) {
-          gs_apply<CPLX, CG>(M, p, q, o, Mloc);
-          continue;
-        }
+    bool gdone = false;
+    if constexpr (sizeof(T) == 8) {
+      if (o.gs) {  // Eq. e:GS replaces the rotation on G
+        gs_apply<CPLX, CG>(M, p, q, o, Mloc);
+        gdone = true;
       }
-      const int rows = onG ? M.mp : M.np;
-      T *xpr = onG ? M.gr + p * M.ldg : M.vr + p * M.ldv;
-      T *xqr = onG ? M.gr + q * M.ldg : M.vr + q * M.ldv;
-      T *xpi = CPLX ? (onG ? M.gi + p * M.ldg : M.vi + p * M.ldv) : nullptr;
-      T *xqi = CPLX ? (onG ? M.gi + q * M.ldg : M.vi + q * M.ldv) : nullptr;
-      T *dpr = swp ? xqr : xpr, *dqr = swp ? xpr : xqr;
-      T *dpi = swp ? xqi : xpi, *dqi = swp ? xpi : xqi;
-      for (int base = lane; base < rows; base += 32 * U) {
+    }
+    // x_p' = fma(x_q, e', x_p) c, x_q' = fma(x_p, -conj(e'), x_q) c, e' = C + iS
+    auto rotate = [&](const T pr, const T pi, const T qr, const T qi, T *dpr, T *dpi, T *dqr,
+                      T *dqi, bool onG) {
+      if (CPLX) {
+        const T npr = mul_t(fma_t(qr, C, fma_t(-qi, S, pr)), c);
+        const T npi = mul_t(fma_t(qr, S, fma_t(qi, C, pi)), c);
+        const T nqr = mul_t(fma_t(pr, -C, fma_t(-pi, S, qr)), c);
+        const T nqi = mul_t(fma_t(pr, S, fma_t(pi, -C, qi)), c);
+        M.st(dpr, npr);
+        M.st(dpi, npi);
+        M.st(dqr, nqr);
+        M.st(dqi, nqi);
+        if (onG) {
+          const unsigned long long a =
+              max(max(magbits(npr), magbits(npi)), max(magbits(nqr), magbits(nqi)));
+          Mloc = max(Mloc, a);
+        }
+      } else {
+        const T npr = mul_t(fma_t(qr, C, pr), c);
+        const T nqr = mul_t(fma_t(pr, -C, qr), c);
+        M.st(dpr, npr);
+        M.st(dqr, nqr);
+        if (onG) Mloc = max(Mloc, max(magbits(npr), magbits(nqr)));
+      }
+    };
+    T *gpr = M.gr + p * M.ldg, *gqr = M.gr + q * M.ldg;
+    T *vpr = M.vr + p * M.ldv, *vqr = M.vr + q * M.ldv;
+    T *gpi = CPLX ? M.gi + p * M.ldg : nullptr, *gqi = CPLX ? M.gi + q * M.ldg : nullptr;
+    T *vpi = CPLX ? M.vi + p * M.ldv : nullptr, *vqi = CPLX ? M.vi + q * M.ldv : nullptr;
+    if constexpr (MERGED) {
+      const int r0 = gdone ? M.mp : 0, R = M.mp + M.np;
+      for (int base = r0 + lane; base < R; base += 32 * U) {
         T pr[U], qr[U], pi[U], qi[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-          const int i = base + 32 * u;
+          const int v = base + 32 * u;
           pr[u] = qr[u] = pi[u] = qi[u] = T(0);
-          if (i < rows) {
-            pr[u] = M.ld(xpr + i);
-            qr[u] = M.ld(xqr + i);
+          if (v < R) {
+            const bool onG = v < M.mp;
+            const int i = onG ? v : v - M.mp;
+            pr[u] = M.ld((onG ? gpr : vpr) + i);
+            qr[u] = M.ld((onG ? gqr : vqr) + i);
             if (CPLX) {
-              pi[u] = M.ld(xpi + i);
-              qi[u] = M.ld(xqi + i);
+              pi[u] = M.ld((onG ? gpi : vpi) + i);
+              qi[u] = M.ld((onG ? gqi : vqi) + i);
             }
           }
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-          const int i = base + 32 * u;
-          if (i < rows) {
-            if (CPLX) {
-              const T npr = mul_t(fma_t(qr[u], C, fma_t(-qi[u], S, pr[u])), c);
-              const T npi = mul_t(fma_t(qr[u], S, fma_t(qi[u], C, pi[u])), c);
-              const T nqr = mul_t(fma_t(pr[u], -C, fma_t(-pi[u], S, qr[u])), c);
-              const T nqi = mul_t(fma_t(pr[u], S, fma_t(pi[u], -C, qi[u])), c);
-              M.st(dpr + i, npr);
-              M.st(dpi + i, npi);
-              M.st(dqr + i, nqr);
-              M.st(dqi + i, nqi);
-              if (onG) {
-                const unsigned long long a =
-                    max(max(magbits(npr), magbits(npi)), max(magbits(nqr), magbits(nqi)));
-                Mloc = max(Mloc, a);
+          const int v = base + 32 * u;
+          if (v < R) {
+            const bool onG = v < M.mp;
+            const int i = onG ? v : v - M.mp;
+            T *xpr = onG ? gpr : vpr, *xqr = onG ? gqr : vqr;
+            T *xpi = onG ? gpi : vpi, *xqi = onG ? gqi : vqi;
+            T *dpr = (swp ? xqr : xpr) + i, *dqr = (swp ? xpr : xqr) + i;
+            T *dpi = CPLX ? (swp ? xqi : xpi) + i : nullptr, *dqi = CPLX ? (swp ? xpi : xqi) + i : nullptr;
+            rotate(pr[u], pi[u], qr[u], qi[u], dpr, dpi, dqr, dqi, onG);
+          }
+        }
+      }
+    } else {
+      for (int pass = gdone ? 1 : 0; pass < 2; ++pass) {
+        const bool onG = (pass == 0);
+        const int rows = onG ? M.mp : M.np;
+        T *xpr = onG ? gpr : vpr, *xqr = onG ? gqr : vqr;
+        T *xpi = onG ? gpi : vpi, *xqi = onG ? gqi : vqi;
+        T *dpr = swp ? xqr : xpr, *dqr = swp ? xpr : xqr;
+        T *dpi = swp ? xqi : xpi, *dqi = swp ? xpi : xqi;
+        for (int base = lane; base < rows; base += 32 * U) {
+          T pr[U], qr[U], pi[U], qi[U];
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            const int i = base + 32 * u;
+            pr[u] = qr[u] = pi[u] = qi[u] = T(0);
+            if (i < rows) {
+              pr[u] = M.ld(xpr + i);
+              qr[u] = M.ld(xqr + i);
+              if (CPLX) {
+                pi[u] = M.ld(xpi + i);
+                qi[u] = M.ld(xqi + i);
               }
-            } else {
-              const T npr = mul_t(fma_t(qr[u], C, pr[u]), c);
-              const T nqr = mul_t(fma_t(pr[u], -C, qr[u]), c);
-              M.st(dpr + i, npr);
-              M.st(dqr + i, nqr);
-              if (onG) Mloc = max(Mloc, max(magbits(npr), magbits(nqr)));
             }
+          }
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            const int i = base + 32 * u;
+            if (i < rows)
+              rotate(pr[u], pi[u], qr[u], qi[u], dpr + i, CPLX ? dpi + i : nullptr, dqr + i,
+                     CPLX ? dqi + i : nullptr, onG);
           }
         }
       }
@@ -732,6 +937,45 @@ __device__ __forceinline__ void step_chunk(const MatViewT<T, CG> &M, int k, int 
     }
   }
   __syncthreads();
+}
+
+// A block's share of step k when every warp runs its pairs alone: warp w
+// takes pairs l = blockIdx.x W + w, + gridDim.x W, ..., each one its sums,
+// its rotation (pair_rotation_warp, the same bits as the chunked form) and
+// its transformation, with no block barrier in between.  For the
+// persistent single-matrix sweep, where a step has at most a few pairs per
+// block and its time is the chain of one pair.
+template <typename T, bool CPLX, bool COMP = false>
+__device__ __forceinline__ void step_warps(const MatViewT<T, true> &M, int k, int nt, double ups, int rk,
+                                           bool permute, unsigned long long &Mloc, int &rots, int &gsn)
+{
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
+  const int L = nt / 2;
+  for (int l = blockIdx.x * W + warp; l < L; l += gridDim.x * W) {
+    int p, q;
+    pair_of(k, l, nt, p, q);
+    if (q < M.n) {
+      // FP64 columns that fill them take wider load trips: sums 8 rows per
+      // lane (4 complex), the transformation 12 (6 complex) of G's and V's
+      // rows together -- one trip each for 256 + 128 rows
+      constexpr int US = CPLX ? 4 : 8, UA = CPLX ? 6 : 12;
+      const bool wide_sums = sizeof(T) == 8 && M.mp % (32 * US) == 0;
+      const bool wide_apply = sizeof(T) == 8 && (M.mp + M.np) % (32 * UA) == 0;
+      const PairSums sm = wide_sums ? pair_sums<T, CPLX, true, COMP, US>(M, p, q, rk)
+                                    : pair_sums<T, CPLX, true, COMP>(M, p, q, rk);
+      PairOut o = pair_rotation_warp<CPLX>(sm, ups);
+      o.swap = o.swap && permute;
+      if (wide_apply)
+        pair_apply<T, CPLX, true, UA, true>(M, p, q, o, Mloc);
+      else
+        pair_apply<T, CPLX, true>(M, p, q, o, Mloc);
+      if (lane == 0 && o.rot) ++rots;
+      if (lane == 0 && o.gs) ++gsn;
+    } else if (rk) {  // phantom partner: only a pending rescale applies
+      scale_col(M, M.gr + p * M.ldg, rk, lane);
+      if (CPLX) scale_col(M, M.gi + p * M.ldg, rk, lane);
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -856,30 +1100,29 @@ __device__ __forceinline__ unsigned long long global_ns()
   return t;
 }
 
-// Sense-reversing grid barrier for a cooperative (co-resident) launch.
-// The wait is bounded: after limit_ns it sets *err = 1 and returns, so a
-// lost block can never hang the GPU; callers then leave the kernel.
-__device__ __forceinline__ bool grid_barrier(unsigned int *count, volatile unsigned int *gen,
-                                             volatile int *err, unsigned long long limit_ns)
+// Grid barrier for a cooperative (co-resident) launch, one atomic per
+// block: block 0 adds 2^31 - (gridDim.x - 1) to *word and every other
+// block 1, so the top bit of *word flips exactly when the last block
+// arrives (the partial sums stay below 2^31 past the value at the start),
+// and each block waits until the top bit differs from the one it saw when
+// it arrived.  A block already at the next barrier cannot flip the bit
+// back before every block has left this one.  The wait is bounded: after
+// limit_ns it sets *err = 1 and returns, so a lost block can never hang the
+// GPU; callers then leave the kernel.  *word must be 0 at launch.
+__device__ __forceinline__ bool grid_barrier(unsigned int *word, volatile int *err,
+                                             unsigned long long limit_ns)
 {
   __syncthreads();
   if (threadIdx.x == 0) {
-    const unsigned int g = *gen;
+    const unsigned int add = (blockIdx.x == 0) ? (0x80000000u - (gridDim.x - 1u)) : 1u;
     __threadfence();
-    const unsigned int arrived = atomicAdd(count, 1u) + 1u;
-    if (arrived == gridDim.x) {
-      *count = 0u;
-      __threadfence();
-      atomicAdd((unsigned int *)gen, 1u);
-    } else {
-      const unsigned long long t0 = global_ns();
-      while (*gen == g) {
-        if (*err) break;
-        if (global_ns() - t0 > limit_ns) {
-          *err = 1;
-          break;
-        }
-        __nanosleep(32);
+    const unsigned int old = atomicAdd(word, add);
+    const unsigned long long t0 = global_ns();
+    while (((*(volatile unsigned int *)word ^ old) & 0x80000000u) == 0u) {
+      if (*err) break;
+      if (global_ns() - t0 > limit_ns) {
+        *err = 1;
+        break;
       }
     }
     __threadfence();

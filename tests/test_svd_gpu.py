@@ -187,6 +187,46 @@ def test_bit_identical_across_launch_shapes():
                           np.ascontiguousarray(ref["U"]).view(np.uint8))
 
 
+def _step_cases():
+    g = np.random.default_rng(41)
+    from tests.test_oracle_svd import gs_test_matrix
+    A1, _ = workloads.svd_geometric(256, 128, 1e6, False, g)        # one-trip rows, real
+    A2, _ = workloads.svd_geometric(128, 64, 1e6, True, g)          # one-trip rows, complex
+    A3, _ = workloads.svd_geometric(75, 31, 1e3, False, g)          # ragged rows, odd n
+    B = g.standard_normal((60, 12))
+    A4 = np.asfortranarray(B * np.ldexp(1.0, -60 * np.arange(12)))   # wide-exponent columns
+    A5 = gs_test_matrix(True)                                        # Gram-Schmidt steps
+    A6 = g.standard_normal((40, 10))
+    A6[:, 3] = 0.0                                                   # a zero column
+    return [("real256x128", A1, {}), ("cplx128x64", A2, {}), ("ragged", A3, {}),
+            ("permute", A3, {"permute": True}), ("compensated", A2, {"compensated": True}),
+            ("wide", A4, {}), ("gram_schmidt", A5, {}), ("zero_col", A6, {})]
+
+
+@pytest.mark.parametrize("case", range(8))
+def test_step_forms_bit_identical(case):
+    """The two forms of a sweep step (JSVD_TUNE_SVD_STEP: chunks with one
+    rotation per lane, or each warp alone with the rotation's independent
+    divisions and roots spread over its lanes) give the same bits, on
+    one-trip and ragged columns, odd n, column swaps, compensated sums,
+    the wide-exponent fallback, Gram-Schmidt steps and a zero column."""
+    import paper_2202_08361_gb300 as J
+    name, A, kw = _step_cases()[case]
+    outs = []
+    try:
+        for mode in (1, 2):
+            J.tune_set(J.JSVD_TUNE_SVD_STEP, mode)
+            outs.append(gpu_svd(A, **kw))
+    finally:
+        J.tune_set(J.JSVD_TUNE_SVD_STEP, 0)
+    a, b = outs
+    assert a["info"]["status"] == 0, name
+    for k in ("U", "V", "sigma", "sigma_e", "sigma_f"):
+        assert np.array_equal(np.ascontiguousarray(a[k]).view(np.uint8),
+                              np.ascontiguousarray(b[k]).view(np.uint8)), (name, k)
+    assert a["info"] == b["info"], name
+
+
 def test_argument_errors():
     import ctypes
     torch = _torch()
