@@ -32,6 +32,7 @@ def main(argv=None):
     p.add_argument("--normal", action="store_true",
                    help="svd: i.i.d. N(0,1) entries (workload 1) instead of a geometric spectrum")
     p.add_argument("--mode", default="fp64", choices=["fp64", "mixed"])
+    p.add_argument("--max-sweeps", type=int, default=0, help="svd: sweep cap (0: the default)")
     p.add_argument("--count", type=int, default=1000)
     p.add_argument("--shape", default=None,
                    help="batch: every matrix m x n (geometric spectrum, condition 1e3) "
@@ -57,7 +58,7 @@ def main(argv=None):
         else:
             A, _ = workloads.svd_geometric(a.m, a.n, 1e6, a.complex, workloads.rng(3, 7))
         At = torch.from_numpy(A).to(dev)
-        run = lambda: J.svd(At, mode=a.mode)
+        run = lambda: J.svd(At, mode=a.mode, max_sweeps=a.max_sweeps)
         label = "svd %dx%d %s %s" % (a.m, a.n, "complex" if a.complex else "real", a.mode)
     elif a.case == "batch":
         import numpy as np

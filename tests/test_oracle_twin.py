@@ -97,6 +97,38 @@ def test_fp64_oracle_svd_against_twin(cplx, shape):
             assert cu >= 1 - tol / gaps[j] * sq[0] / sq[j] and cv >= 1 - tol / gaps[j] * sq[0] / sq[j], j
 
 
+@pytest.mark.parametrize("complex_", [False, True])
+def test_fp32_evd_within_prop_bounds_of_twin(complex_):
+    """The binary32 EVD (the constants of section 2.4) against the binary128
+    twin on binary32 inputs spread over 2^-40 .. 2^40: Prop. p:s2 with
+    eps = 2^-24 (the bounds hold for any precision with at least 23
+    fraction bits while nothing underflows)."""
+    g = np.random.default_rng(29 + complex_)
+    r = 1500
+    e = lambda: g.integers(-40, 40, r)
+    f = lambda: np.float32(np.ldexp(g.standard_normal(r), e()))
+    a11, a22, a21r = f(), f(), f()
+    a21i = f() if complex_ else np.zeros(r, np.float32)
+    E32 = 2.0 ** -24
+    if complex_:
+        c, ct, st, l1, l2, _ = oracle.csjac2(a11, a22, a21r, a21i)
+    else:
+        c, ct, l1, l2, _ = oracle.ssjac2(a11, a22, a21r)
+        st = np.zeros_like(c)
+    qc, qtr, qti, _, _ = oracle.q_zsjac2(a11.astype(float), a22.astype(float), a21r.astype(float),
+                                         a21i.astype(float))
+    cos_b = (14.000006 if complex_ else 8.000002) * E32
+    tan_b = (11.500004 if complex_ else 5.500001) * E32
+    et_b = (1 + 4.000001 * E32) * (1 + tan_b) * (1 + E32) - 1
+    for i in range(r):
+        rc = hl(qc[i])
+        assert abs(D(float(c[i])) - rc) <= D(cos_b) * rc, i
+        rr, ri = hl(qtr[i]), hl(qti[i])
+        mag = (rr * rr + ri * ri).sqrt()
+        err = ((D(float(ct[i])) - rr) ** 2 + (D(float(st[i])) - ri) ** 2).sqrt()
+        assert err <= D(et_b) * mag + D(2.0 ** -149), i
+
+
 def test_graded_relative_accuracy_against_twin():
     """A column-graded matrix B D: the FP64 oracle's small singular values
     relatively accurate against the twin (one-sided Jacobi's relative

@@ -88,3 +88,17 @@ def test_scaled_inputs_and_zero():
         assert np.array_equal(g["U"], base["U"])
     z = gpu_svd32(np.zeros((9, 4), np.float32, order="F"))
     assert np.all(z["sigma"] == 0) and z["info"]["status"] == 0
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+def test_sigma_against_binary128_twin(cplx):
+    """The single precision SVD's singular values against the binary128
+    twin's on the same binary32 matrix: within 64 n eps32 sigma_max."""
+    A, _ = workloads.svd_geometric(96, 40, 1e3, cplx, np.random.default_rng(71 + cplx))
+    A = A.astype(np.complex64 if cplx else np.float32)
+    g = gpu_svd32(A)
+    t = oracle.q_vjsvd(A.astype(np.complex128 if cplx else np.float64))
+    assert t["status"] == 0
+    sq = t["sigma"][:, 0]
+    assert np.abs(g["sigma"].astype(float) - sq).max() <= tol(40) * sq[0]
+
