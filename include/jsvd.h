@@ -189,9 +189,11 @@ JSVD_API int jsvd_evd2x2_batched_host(jsvd_field field, const jsvd_evd2_streams 
  * -inf for a zero column) and f_j in [1, 2), computed without overflow or
  * underflow of any partial sum (the norm of a column of FLT/DBL_MAX entries
  * or of subnormals is accurate).  A: m x n column-major, lda >= m; complex
- * A interleaved (each row adds Re^2 then Im^2).  One warp per column: the
- * lanes take rows l, l+32, ... in order, then combine in the fixed xor
- * butterfly, so the bits do not depend on the launch.  e_out, f_out: n
+ * A interleaved (each row adds Re^2 then Im^2).  The order of the sums is
+ * fixed by m: L = 32 lanes for m <= 8192, else 1024; lane t adds rows t,
+ * t+L, ... in order, and the lanes are combined by the xor butterfly within
+ * each group of 32 and then (L = 1024) over the 32 groups, so the bits do
+ * not depend on the launch.  e_out, f_out: n
  * doubles each (device).  Errors: -1 field, -2 m < 0, -3 n < 0, -4 A NULL,
  * -5 lda, -6 e_out or f_out NULL. */
 JSVD_API int jsvd_colnorm_ef(jsvd_field field, int64_t m, int64_t n, const void *A, int64_t lda,

@@ -164,12 +164,9 @@ def colnorm_ef(A, stream=None):
     torch = _torch()
     if not isinstance(A, torch.Tensor) or not A.is_cuda or A.dim() != 2:
         raise TypeError("A must be a 2-D CUDA tensor")
-    if A.dtype in (torch.float32, torch.complex64):
-        return _svd_f32(A, max_sweeps=max_sweeps, permute=permute, work=work, out=out,
-                        stream=stream)
     cplx = A.dtype == torch.complex128
     if not cplx and A.dtype != torch.float64:
-        raise TypeError("A must be float64, complex128, float32 or complex64")
+        raise TypeError("A must be float64 or complex128")
     m, n = A.shape
     Ac, lda = colmajor(A)
     e = torch.empty(n, dtype=torch.float64, device=A.device)

@@ -255,3 +255,17 @@ def diff_batch_device(count: int = 4096, m: int = 64, n: int = 32, cond: float =
     w = torch.rand((count, n), generator=gen, dtype=torch.float64, device=device)
     C = torch.randn((count, m, k), generator=gen, dtype=torch.float64, device=device)
     return A, w, C
+
+
+def gram_schmidt_matrix(complex_: bool = False) -> np.ndarray:
+    """The 16 x 16 matrix of supplement SM9 (one-based i, j):
+    G_ij = 2^(1023 - (j - 1) - |i - j|) for j <= 8 and
+    2^(-51 - (j - 1) - |i - j|) for j > 8; the complex variant multiplies
+    each entry by a fixed unit phase (seed 9)."""
+    n = 16
+    i, j = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    G = np.where(j < 8, np.ldexp(1.0, 1023 - j - abs(i - j)), np.ldexp(1.0, -51 - j - abs(i - j)))
+    if complex_:
+        G = G * np.exp(1j * np.random.default_rng(9).uniform(0, 2 * np.pi, (n, n)))
+    return np.asfortranarray(G)
+

@@ -50,6 +50,43 @@ def test_norms_against_oracle(cplx):
     assert e[3] == -np.inf and f[3] == 1.0
 
 
+@pytest.mark.parametrize("cplx", [False, True])
+def test_long_columns_1024_lanes(cplx):
+    """Columns longer than 8192 rows take 1024 lanes: against the oracle's
+    one-lane rnF (the error bound of a sum of m squares), exact cases, the
+    same bits on every call, and exact power-of-two scale invariance; a
+    column of 8192 rows and one of 8193 bracket the switch."""
+    g = np.random.default_rng(6 + cplx)
+    m, n = 20011, 9
+    A = g.standard_normal((m, n)) * np.exp2(g.integers(-900, 900, (m, n)))
+    if cplx:
+        A = A + 1j * g.standard_normal((m, n)) * np.exp2(g.integers(-900, 900, (m, n)))
+    A[:, 2] = 0.0
+    A[:, 4] = NU
+    A[:, 6] = 0.0
+    A[m - 1, 6] = -3.0 * MU
+    e, f = gpu_norms(A)
+    e2, f2 = gpu_norms(A)
+    assert np.array_equal(e, e2) and np.array_equal(f, f2)
+    for j in range(n):
+        col = A[:, j]
+        x = np.column_stack([col.real, col.imag]).ravel() if cplx else col
+        eo, fo = oracle.rnF(x)
+        assert rel_diff(e[j], f[j], eo, fo) <= (2 * m + 4) * U, j
+    assert e[2] == -np.inf and f[2] == 1.0
+    assert (e[6], f[6]) == (-1073.0, 1.5)
+    B = np.ldexp(g.integers(-(1 << 20), 1 << 20, (m, 3)).astype(float), -20)
+    e0, f0 = gpu_norms(B)
+    e1, f1 = gpu_norms(np.ldexp(B, -1030))
+    assert np.array_equal(e1, e0 - 1030) and np.array_equal(f1, f0)
+    for rows in (8192, 8193):
+        C = g.standard_normal((rows, 2))
+        ec, fc = gpu_norms(C)
+        for j in range(2):
+            eo, fo = oracle.rnF(C[:, j])
+            assert rel_diff(ec[j], fc[j], eo, fo) <= (rows + 4) * U
+
+
 def test_exact_cases_and_scale_invariance():
     A = np.zeros((70, 4))
     A[:, 0] = NU
@@ -108,3 +145,15 @@ def test_svd_graded_against_oracle(cplx):
     assert np.all(np.abs(s / o["sigma"] - 1) <= 1e-11), s / o["sigma"] - 1
     assert torch.equal(bt.matrix(0)[1].contiguous().view(torch.int64),
                        out["sigma"].contiguous().view(torch.int64))
+
+
+def test_binding_rejects_other_dtypes():
+    """jsvd_colnorm_ef is binary64 only: the binding refuses float32,
+    complex64 and integer matrices, and host tensors."""
+    import torch
+    import paper_2202_08361_gb300 as J
+    for dt in (torch.float32, torch.complex64, torch.int64):
+        with pytest.raises(TypeError):
+            J.colnorm_ef(torch.zeros(8, 3, dtype=dt, device="cuda"))
+    with pytest.raises(TypeError):
+        J.colnorm_ef(torch.zeros(8, 3, dtype=torch.float64))

@@ -223,16 +223,8 @@ def test_graded_columns_relative_accuracy(cplx):
 
 
 def gs_test_matrix(cplx=False):
-    """Supplement SM9's 16 x 16 matrix: G_ij = 2^(eta^ - (j-1) - |i-j|) for
-    j <= 8 and 2^(-51 - (j-1) - |i-j|) for j > 8 (one-based), eta^ = 1023;
-    the complex variant multiplies each entry by a fixed unit phase."""
-    n = 16
-    i, j = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
-    G = np.where(j < 8, np.ldexp(1.0, 1023 - j - abs(i - j)), np.ldexp(1.0, -51 - j - abs(i - j)))
-    if cplx:
-        ph = np.exp(1j * np.random.default_rng(9).uniform(0, 2 * np.pi, (n, n)))
-        G = G * ph
-    return np.asfortranarray(G)
+    """Supplement SM9's 16 x 16 matrix (workloads.gram_schmidt_matrix)."""
+    return workloads.gram_schmidt_matrix(cplx)
 
 
 @pytest.mark.parametrize("cplx", [False, True])
