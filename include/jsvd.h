@@ -88,10 +88,11 @@ JSVD_API const char *jsvd_last_cuda_error(void);
  *     (padded rows, all planes) fit in it is iterated there instead of in
  *     its workspace region. */
 #define JSVD_TUNE_BATCH_SMEM 5
-/*   JSVD_TUNE_EVD32_DIV: value = 1: the single precision EVD divides and
- *     takes square roots on operands first scaled into [1, 2) (never the
- *     IEEE routines' slow path); 0 (default): the IEEE intrinsics directly.
- *     Both round correctly: the results are identical. */
+/*   JSVD_TUNE_EVD32_DIV: value = 1: the single precision EVD divides by a
+ *     branch-free routine (operands scaled into [1, 2), the quotient's
+ *     exponent rebuilt, subnormal results rounded with the exact
+ *     remainder); 0 (default): the IEEE division directly.  Both round
+ *     correctly: the results are identical. */
 #define JSVD_TUNE_EVD32_DIV 6
 /*   JSVD_TUNE_EVD_HOST: how jsvd_evd2x2_batched_host moves its data.
  *     value = 0 (default): directly, the kernel reading and writing the host
@@ -407,6 +408,16 @@ JSVD_API int jsvd_dgemm(int transA, int64_t M, int64_t N, int64_t K, double alph
  * extremes), from seed; atomically ADDS the number of differing divisions
  * to mismatches[0] and of square roots to mismatches[1] (DEVICE memory, two
  * unsigned long long, zeroed by the caller).  Errors: -i, JSVD_E_CUDA. */
+/* Self-test of the branch-free binary32 division of the single precision
+ * EVD (JSVD_TUNE_EVD32_DIV = 1) against the GPU's IEEE FP32 division: n
+ * generated operand pairs (arbitrary bit patterns, subnormals, powers of
+ * two, extremes, zeros), from seed; atomically ADDS the number of results
+ * whose bits differ (two NaNs count as equal) to *mismatches (DEVICE, one
+ * unsigned long long, zeroed by the caller).  Errors: -1 n < 0,
+ * -3 mismatches NULL, JSVD_E_CUDA. */
+JSVD_API int jsvd_selftest_fp32div(int64_t n, uint64_t seed, unsigned long long *mismatches,
+                                   void *stream);
+
 JSVD_API int jsvd_selftest_fp64(int64_t n, uint64_t seed, unsigned long long *mismatches,
                                 void *stream);
 

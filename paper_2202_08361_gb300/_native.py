@@ -141,6 +141,8 @@ def lib():
         L.jsvd_sign_gauge_batched.restype = ctypes.c_int
         L.jsvd_selftest_fp64.argtypes = [_i64, ctypes.c_uint64, _vp, _vp]
         L.jsvd_selftest_fp64.restype = ctypes.c_int
+        L.jsvd_selftest_fp32div.argtypes = [_i64, ctypes.c_uint64, _vp, _vp]
+        L.jsvd_selftest_fp32div.restype = ctypes.c_int
         L.jsvd_selftest_barrier.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _i64, _vp,
                                             _vp]
         L.jsvd_selftest_barrier.restype = ctypes.c_int

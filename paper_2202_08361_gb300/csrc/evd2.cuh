@@ -31,6 +31,15 @@ __device__ __forceinline__ double clamp_tan2(double q, double a)
   return dbl(qb | (bits(a) & kSign));
 }
 
+// floor(lg max(|x|, |y|, |w|, |v|, DBL_TRUE_MIN)) of Eq. e:z: the larger
+// magnitude has the larger bit pattern, so one exponent extraction serves
+// all four.
+__device__ __forceinline__ int flg_max(double x, double y, double w, double v)
+{
+  const uint64_t m = max(max(bits(x) & ~kSign, bits(y) & ~kSign), max(bits(w) & ~kSign, bits(v) & ~kSign));
+  return flg_sat(dbl(m));
+}
+
 struct Rot2 {
   double cphi;   // cos(phi)
   double etr;    // Re(e^{i alpha} tan(phi)) (real: sign(a21) tan(phi))
@@ -102,8 +111,7 @@ template <int MASK>
 __device__ __forceinline__ Rot2 dsjac2(double a11, double a22, double a21)
 {
   Rot2 r;
-  const int E = max(max(flg_sat(a11), flg_sat(a22)), flg_sat(a21));
-  r.zeta = 1020 - E;  // eta - floor(lg max|a_ij|), eta = 1020
+  r.zeta = 1020 - flg_max(a11, a22, a21, 0.0);  // eta - floor(lg max|a_ij|), eta = 1020
   a11 = ldexp_rn(a11, r.zeta);
   a22 = ldexp_rn(a22, r.zeta);
   a21 = ldexp_rn(a21, r.zeta);
@@ -120,8 +128,7 @@ template <int MASK>
 __device__ __forceinline__ Rot2 zsjac2(double a11, double a22, double a21r, double a21i)
 {
   Rot2 r;
-  const int E = max(max(flg_sat(a11), flg_sat(a22)), max(flg_sat(a21r), flg_sat(a21i)));
-  r.zeta = 1020 - E;
+  r.zeta = 1020 - flg_max(a11, a22, a21r, a21i);
   a11 = ldexp_rn(a11, r.zeta);
   a22 = ldexp_rn(a22, r.zeta);
   a21r = ldexp_rn(a21r, r.zeta);

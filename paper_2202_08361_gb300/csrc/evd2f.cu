@@ -48,9 +48,10 @@ __global__ void __launch_bounds__(256) evd2f_kernel(jsvd_evd2_streams_f32 p, int
   }
 }
 
-// Division and square root: 1 = the scaled fast path (div_fast, sqrt_fast),
-// 0 = the IEEE intrinsics as they are (default: measured faster, 0.32 vs
-// 0.60 ms for 2^24 real matrices).  Same bits either way.
+// Division: 1 = the branch-free division (div_fast), 0 = the IEEE
+// intrinsic as it is (default: measured faster on wide-range batches, 0.32
+// vs 0.37 ms for 2^24 real matrices and 0.49 vs 0.62 ms complex, although
+// some lanes of a warp take its slow path).  Same bits either way.
 static int g_evd32_fast = 0;
 
 int evd2f_set_fast(int v)

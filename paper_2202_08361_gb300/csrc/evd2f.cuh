@@ -54,53 +54,82 @@ __device__ __forceinline__ float ldexpf_rn(float x, int k)
   return fval(a == 0u ? u : r);
 }
 
-// a / b, correctly rounded, by the FP32 pipe's fast path.  The operands are
-// brought into [1, 2) by exact power-of-two scalings (exponent-field
-// rewrites; subnormals are normalised), so the IEEE division's slow path
-// (taken near the ends of the exponent range) is never needed; the
-// quotient in (1/2, 2) is scaled back by an exponent add, exact in the
-// normal range and infinity above it.  A quotient below the normal range
-// would be rounded twice that way, so it is redone directly, as are zero,
-// infinite and NaN operands.
-__device__ __forceinline__ float mant12(float x, int &e)
+// x 2^z for the prescaling of Eq. e:z, z = eta - floor(lg max|a_ij|) in
+// [-3, 273], by three multiplications by powers of two on the FP32 pipe:
+// 2^min(z, 127), then the rest of z in at most two factors >= 1.  Only the
+// first can round (z < 0, a result below the normal range: one rounding,
+// as ldexpf_rn); every later one scales up a value that stays below
+// 2^125, which is exact.
+__device__ __forceinline__ float scale_zeta(float x, int z)
 {
-  const uint32_t a = fbits(x) & ~kSignF;
-  if (a >= 0x00800000u) {
-    e = (int)(a >> 23) - 127;
-    return fval((fbits(x) & 0x807FFFFFu) | 0x3F800000u);
-  }
-  const int lz = __clz((int)a) - 8;  // subnormal: shift the leading bit into place
-  e = -126 - lz;
-  return fval((fbits(x) & kSignF) | 0x3F800000u | ((a << lz) & 0x007FFFFFu));
+  const int z1 = min(z, 127), z2 = min(max(z - 127, 0), 127), z3 = max(z - 254, 0);
+  const float p1 = fval((uint32_t)(z1 + 127) << 23);
+  const float p2 = fval((uint32_t)(z2 + 127) << 23);
+  const float p3 = fval((uint32_t)(z3 + 127) << 23);
+  return __fmul_rn(__fmul_rn(__fmul_rn(x, p1), p2), p3);
 }
 
+// floor(lg max(|x|, |y|, |w|, |v|, FLT_TRUE_MIN)): the larger magnitude has
+// the larger bit pattern, so one exponent extraction serves all.
+__device__ __forceinline__ int flgf_max(float x, float y, float w, float v)
+{
+  const uint32_t m = max(max(fbits(x) & ~kSignF, fbits(y) & ~kSignF),
+                         max(fbits(w) & ~kSignF, fbits(v) & ~kSignF));
+  return flgf_sat(fval(m));
+}
+
+// The significand of |x| (bits a, a != 0) scaled into [1, 2) and its
+// exponent: x = m 2^e exactly; subnormals are normalised.  Both forms are
+// computed and one selected, so the lanes of a warp never diverge.
+__device__ __forceinline__ float norm12(uint32_t a, int &e)
+{
+  const int E = (int)(a >> 23);
+  const int p = 31 - __clz((int)(a | 1u));                 // top set bit of a subnormal
+  const uint32_t msub = (a << ((23 - p) & 31)) & 0x007FFFFFu;
+  e = E ? E - 127 : p - 149;
+  return fval(0x3F800000u | (E ? (a & 0x007FFFFFu) : msub));
+}
+
+// a / b, correctly rounded (to nearest-even), for finite a and b (b = 0
+// gives IEEE's Inf or NaN), without a data-dependent branch: the operands are scaled into
+// [1, 2) (exactly), their quotient q in (1/2, 2) is taken by the IEEE
+// division (which never needs its slow path there) together with the exact
+// remainder r = a' - q b' (one fma), and the result is rebuilt from q's
+// significand and the exponent difference.  A result below the normal range
+// is rounded once more on the subnormal grid: the bits of q shifted out
+// decide, except when they are exactly half an ulp of that grid, where q
+// sits on the midpoint itself and the sign of r tells on which side of it
+// the exact quotient lies (r = 0: a tie, to even).  The midpoint is a
+// 24-bit number, so q (the correctly rounded quotient) is below, on or above
+// it exactly when the exact quotient is.
 __device__ __forceinline__ float div_fast(float a, float b)
 {
-  const uint32_t ua = fbits(a) & ~kSignF, ub = fbits(b) & ~kSignF;
-  if (ua == 0u || ub == 0u || ua >= kInfF || ub >= kInfF) return __fdiv_rn(a, b);
+  const uint32_t ua = fbits(a), ub = fbits(b);
+  const uint32_t sign = (ua ^ ub) & kSignF;
+  const uint32_t xa = ua & ~kSignF, xb = ub & ~kSignF;
   int ea, eb;
-  const float q = __fdiv_rn(mant12(a, ea), mant12(b, eb));  // |q| in (1/2, 2)
-  const int k = ea - eb;
-  const int eq = (int)((fbits(q) >> 23) & 0xFFu) + k;  // biased exponent of the result
-  if (eq <= 0) return __fdiv_rn(a, b);
-  if (eq >= 255) return fval((fbits(q) & kSignF) | kInfF);
-  return fval(fbits(q) + ((uint32_t)k << 23));
-}
-
-// sqrt(x), correctly rounded, x >= 0 finite: x = m 2^(2j), m in [1, 4)
-// (exact), sqrt(m) in [1, 2) by the fast path, then 2^j added exactly.
-__device__ __forceinline__ float sqrt_fast(float x)
-{
-  const uint32_t a = fbits(x) & ~kSignF;
-  if (a == 0u || a >= kInfF) return __fsqrt_rn(x);
-  int e;
-  float m = mant12(x, e);
-  if (e & 1) {  // make the exponent even: m in [2, 4)
-    m = fval(fbits(m) + 0x00800000u);
-    e -= 1;
-  }
-  const float r = __fsqrt_rn(m);
-  return fval(fbits(r) + ((uint32_t)(e / 2) << 23));
+  const float ma = norm12(xa, ea), mb = norm12(xb, eb);
+  const float q = __fdiv_rn(ma, mb);
+  const float r = __fmaf_rn(-q, mb, ma);  // exact
+  const uint32_t uq = fbits(q);
+  const int E = ea - eb + (int)(uq >> 23) - 127;           // exponent of the result
+  const uint32_t sig = (uq & 0x007FFFFFu) | 0x00800000u;  // q's 24-bit significand
+  const uint32_t normal = (((uint32_t)(E + 127)) << 23) | (sig & 0x007FFFFFu);
+  int sh = -126 - E;                                      // right shift onto the grid 2^-149
+  sh = sh < 1 ? 1 : (sh > 25 ? 25 : sh);
+  uint32_t qs = sig >> sh;
+  const uint32_t lost = sig & ((1u << sh) - 1u), half = 1u << (sh - 1);
+  const uint32_t rb = fbits(r);
+  const bool r_pos = (rb & ~kSignF) != 0u && !(rb & kSignF);
+  const bool r_zero = (rb & ~kSignF) == 0u;
+  qs += (uint32_t)((lost > half) | ((lost == half) & (r_pos | (r_zero & ((qs & 1u) != 0u)))));
+  uint32_t res = (E >= -126) ? normal : qs;
+  res = (E > 127) ? kInfF : res;
+  res = (xa == 0u) ? 0u : res;
+  // a zero divisor gives what IEEE division gives (the EVD's clamps rely on
+  // it): Inf, or NaN for 0/0
+  res = (xb == 0u) ? ((xa == 0u) ? 0x7FC00000u : kInfF) : res;
+  return fval(sign | res);
 }
 
 template <bool FAST>
@@ -110,11 +139,12 @@ __device__ __forceinline__ float fdiv(float a, float b)
   else return __fdiv_rn(a, b);
 }
 
+// The EVD's square roots all take operands in [1, fl(sqrt nu)^2 + 1]
+// (x^2 + 1, sec^2), where the IEEE routine never leaves its fast path.
 template <bool FAST>
 __device__ __forceinline__ float fsqrt(float x)
 {
-  if constexpr (FAST) return sqrt_fast(x);
-  else return __fsqrt_rn(x);
+  return __fsqrt_rn(x);
 }
 
 struct Rot2f {
@@ -150,10 +180,10 @@ template <bool FAST>
 __device__ __forceinline__ Rot2f ssjac2(float a11, float a22, float a21)
 {
   Rot2f r;
-  r.zeta = 124 - max(max(flgf_sat(a11), flgf_sat(a22)), flgf_sat(a21));
-  a11 = ldexpf_rn(a11, r.zeta);
-  a22 = ldexpf_rn(a22, r.zeta);
-  a21 = ldexpf_rn(a21, r.zeta);
+  r.zeta = 124 - flgf_max(a11, a22, a21, 0.0f);
+  a11 = scale_zeta(a11, r.zeta);
+  a22 = scale_zeta(a22, r.zeta);
+  a21 = scale_zeta(a21, r.zeta);
   float tan1, sec2, o;
   rot_core_f<FAST>(a11, a22, fabsf(a21), tan1, sec2, o, r.cphi);
   r.etr = fval(fbits(tan1) ^ (fbits(a21) & kSignF));
@@ -167,11 +197,11 @@ template <bool FAST>
 __device__ __forceinline__ Rot2f csjac2(float a11, float a22, float a21r, float a21i)
 {
   Rot2f r;
-  r.zeta = 124 - max(max(flgf_sat(a11), flgf_sat(a22)), max(flgf_sat(a21r), flgf_sat(a21i)));
-  a11 = ldexpf_rn(a11, r.zeta);
-  a22 = ldexpf_rn(a22, r.zeta);
-  a21r = ldexpf_rn(a21r, r.zeta);
-  a21i = ldexpf_rn(a21i, r.zeta);
+  r.zeta = 124 - flgf_max(a11, a22, a21r, a21i);
+  a11 = scale_zeta(a11, r.zeta);
+  a22 = scale_zeta(a22, r.zeta);
+  a21r = scale_zeta(a21r, r.zeta);
+  a21i = scale_zeta(a21i, r.zeta);
   const float ar = fabsf(a21r), ai = fabsf(a21i);
   const float am = fminf(ar, ai), aM = fmaxf(ar, ai);
   const float mM = fmaxf(fdiv<FAST>(am, aM), 0.0f);  // 0/0 -> 0

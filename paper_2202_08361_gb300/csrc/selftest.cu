@@ -2,12 +2,15 @@
 //   jsvd_selftest_fp64: the integer-pipe binary64 division and square root
 //     (fp64soft.cuh) against the FP64 pipe's IEEE instructions on generated
 //     operands, counting mismatching bit patterns;
+//   jsvd_selftest_fp32div: the branch-free binary32 division of the single
+//     precision EVD (evd2f.cuh) against the FP32 pipe's IEEE division;
 //   jsvd_selftest_barrier: the bounded grid barrier of the persistent SVD
 //     kernel, with one block that never arrives, so the others' wait runs
 //     out and they report JSVD_E_TIMEOUT (no fault, no trap).
 #include <algorithm>
 
 #include "common.cuh"
+#include "evd2f.cuh"
 #include "fp64bits.cuh"
 #include "fp64soft.cuh"
 #include "jsvd_internal.h"
@@ -120,6 +123,55 @@ extern "C" int jsvd_selftest_barrier(int blocks, int absent, int rounds, int64_t
   void *args[] = {&a, &rr, &lim, &status};
   JSVD_CUDA(cudaLaunchCooperativeKernel((const void *)barrier_test_kernel, dim3(blocks), dim3(32),
                                         args, 0, st));
+  return JSVD_OK;
+}
+
+namespace jsvd {
+
+// a finite float from one of several families (any bit pattern, subnormals,
+// powers of two, short significands, near the top, near the normal range's
+// bottom, zero, near one)
+__device__ __forceinline__ float family32(uint64_t r, uint64_t r2)
+{
+  const uint32_t u = (uint32_t)r2;
+  switch (r & 7) {
+    case 0: return fval(((u >> 23) & 0xFF) == 0xFF ? (u & ~(1u << 30)) : u);
+    case 1: return fval(u & 0x807FFFFFu);
+    case 2: return fval((u & 0x80000000u) | ((((u >> 8) % 254u) + 1u) << 23));
+    case 3: return ldexpf_rn((float)((u % 4096u) + 1u), (int)((u >> 16) % 265u) - 160);  // < 2^117
+    case 4: return fval((u & 0x80000000u) | ((uint32_t)(250u + (u >> 24) % 5u) << 23) | (u & 0x7FFFFFu));
+    case 5: return fval((u & 0x80000000u) | ((uint32_t)(1u + (u >> 24) % 6u) << 23) | (u & 0x7FFFFFu));
+    case 6: return (u & 1u) ? 0.0f : -0.0f;
+    default: return fval(0x3F800000u | (u & 0x7FFFFFu));
+  }
+}
+
+__global__ void selftest32_kernel(int64_t n, uint64_t seed, unsigned long long *bad)
+{
+  unsigned long long bd = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t k = seed + 4 * (uint64_t)i;
+    const float a = family32(splitmix(k), splitmix(k + 1));
+    const float b = family32(splitmix(k + 2), splitmix(k + 3));
+    const float x = __fdiv_rn(a, b), y = div_fast(a, b);
+    const bool both_nan = (x != x) && (y != y);
+    if (!both_nan && fbits(x) != fbits(y)) ++bd;
+  }
+  if (bd) atomicAdd(bad, bd);
+}
+
+}  // namespace jsvd
+
+extern "C" int jsvd_selftest_fp32div(int64_t n, uint64_t seed, unsigned long long *mismatches,
+                                     void *stream)
+{
+  if (n < 0) return -1;
+  if (!mismatches) return -3;
+  if (n == 0) return JSVD_OK;
+  const int blocks = (int)std::min<int64_t>((n + 255) / 256, (int64_t)jsvd::sm_count() * 8);
+  jsvd::selftest32_kernel<<<blocks, 256, 0, jsvd::as_stream(stream)>>>(n, seed, mismatches);
+  JSVD_CHECK_LAUNCH();
   return JSVD_OK;
 }
 

@@ -390,9 +390,7 @@ __device__ __forceinline__ PairOut pair_rotation_warp(const PairSums &sm, double
   double a11 = ldexp_rn(f12, e12 + sA), a22 = ldexp_rn(f21, e21 + sA);
   double a21r = ldexp_rn(zr, sA), a21i = CPLX ? ldexp_rn(zi, sA) : 0.0;
   // the EVD (Alg. d8jac2 / Listing 1): Eq. e:z
-  const int E = CPLX ? max(max(flg_sat(a11), flg_sat(a22)), max(flg_sat(a21r), flg_sat(a21i)))
-                     : max(max(flg_sat(a11), flg_sat(a22)), flg_sat(a21r));
-  const int zeta = 1020 - E;
+  const int zeta = 1020 - flg_max(a11, a22, a21r, a21i);  // a21i = 0 when real
   a11 = ldexp_rn(a11, zeta);
   a22 = ldexp_rn(a22, zeta);
   a21r = ldexp_rn(a21r, zeta);

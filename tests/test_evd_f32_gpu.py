@@ -32,14 +32,36 @@ def check(streams, complex_):
         assert bad.size == 0, (k, bad[:5], [s[bad[0]] for s in streams])
 
 
+@pytest.fixture(params=[0, 1], ids=["ieee_div", "branch_free_div"])
+def div_mode(request):
+    """Both divisions of the single precision EVD (JSVD_TUNE_EVD32_DIV)."""
+    import paper_2202_08361_gb300 as J
+    J.tune_set(J.JSVD_TUNE_EVD32_DIV, request.param)
+    yield request.param
+    J.tune_set(J.JSVD_TUNE_EVD32_DIV, 0)
+
+
 @pytest.mark.parametrize("complex_", [False, True])
 @pytest.mark.parametrize("n", [1, 7, 1000, 65537, (1 << 20) + 13])
-def test_parity_wide_range(n, complex_):
+def test_parity_wide_range(n, complex_, div_mode):
     check(workloads.evd_batch_f32(n, complex_, seed_salt=n % 97), complex_)
 
 
+def test_branch_free_division_against_ieee():
+    """The branch-free binary32 division against the IEEE division on 2^30
+    operand pairs of every kind (subnormal quotients and operands, overflow,
+    zeros, zero divisors)."""
+    import torch
+    from paper_2202_08361_gb300 import _native
+    bad = torch.zeros(1, dtype=torch.int64, device="cuda")
+    for seed in (0, 1 << 40):
+        assert _native.lib().jsvd_selftest_fp32div(1 << 29, seed, bad.data_ptr(), None) == 0
+    torch.cuda.synchronize()
+    assert bad.item() == 0
+
+
 @pytest.mark.parametrize("complex_", [False, True])
-def test_parity_special_cases(complex_):
+def test_parity_special_cases(complex_, div_mode):
     fmax = np.finfo(np.float32).max
     tiny = np.float32(2.0 ** -149)
     vals = np.array([0.0, -0.0, 1.0, -1.0, tiny, -tiny, fmax, -fmax, fmax / 8, 2.0 ** -126,
