@@ -88,11 +88,15 @@ JSVD_API const char *jsvd_last_cuda_error(void);
  *     (padded rows, all planes) fit in it is iterated there instead of in
  *     its workspace region. */
 #define JSVD_TUNE_BATCH_SMEM 5
-/*   JSVD_TUNE_EVD32_DIV: value = 1: the single precision EVD divides by a
+/*   JSVD_TUNE_EVD32_DIV: which divisions of the single precision EVD use a
  *     branch-free routine (operands scaled into [1, 2), the quotient's
- *     exponent rebuilt, subnormal results rounded with the exact
- *     remainder); 0 (default): the IEEE division directly.  Both round
- *     correctly: the results are identical. */
+ *     exponent rebuilt, subnormal results rounded with the exact remainder)
+ *     instead of the IEEE division: value = a placement 0..7 (0 none, 1 all,
+ *     2 o/|a|, tan(phi) and the phase quotients of a21', 3 - 7 subsets of
+ *     these; -1 = the defaults, 2 for real and 7 -- the phase quotients only --
+ *     for complex matrices); value2 = the fields it
+ *     applies to (0 both, 1 real, 2 complex).  All round correctly: the
+ *     results are identical. */
 #define JSVD_TUNE_EVD32_DIV 6
 /*   JSVD_TUNE_EVD_HOST: how jsvd_evd2x2_batched_host moves its data.
  *     value = 0 (default): directly, the kernel reading and writing the host

@@ -60,7 +60,7 @@ extern "C" int jsvd_tune_set(int knob, int value, int value2)
     case JSVD_TUNE_SVD_GRID: return jsvd::svd_set_grid(value, value2);
     case JSVD_TUNE_BATCH_WARPS: return jsvd::batch_set_warps(value);
     case JSVD_TUNE_BATCH_SMEM: return jsvd::batch_set_smem(value);
-    case JSVD_TUNE_EVD32_DIV: return jsvd::evd2f_set_fast(value);
+    case JSVD_TUNE_EVD32_DIV: return jsvd::evd2f_set_fast(value, value2);
     case JSVD_TUNE_EVD_HOST: return jsvd::evd2_set_host_path(value);
     case JSVD_TUNE_SVD_STEP: return jsvd::svd_set_step_mode(value);
     default: return -1;

@@ -2,9 +2,10 @@
 // single precision.
 //
 // Same layout and structure as the FP64 kernel (one thread per matrix over
-// structure-of-arrays streams, grid-stride, streaming loads and stores).
-// On GB300 the FP32 pipe is wide, so this kernel is bound by HBM: each
-// thread keeps kUnroll matrices in flight to cover the memory latency.
+// structure-of-arrays streams, grid-stride, streaming loads and stores);
+// each thread keeps kUnroll matrices in flight to cover the memory latency.
+// On wide-range data the kernel is bound by instruction issue: the
+// exponent work and the divisions whose quotients leave the normal range.
 #include "common.cuh"
 #include "evd2f.cuh"
 #include "jsvd_internal.h"
@@ -13,7 +14,7 @@ namespace jsvd {
 
 constexpr int kUnroll = 4;
 
-template <bool CPLX, bool FAST>
+template <bool CPLX, int DM>
 __global__ void __launch_bounds__(256) evd2f_kernel(jsvd_evd2_streams_f32 p, int64_t n)
 {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -35,8 +36,8 @@ __global__ void __launch_bounds__(256) evd2f_kernel(jsvd_evd2_streams_f32 p, int
     for (int u = 0; u < kUnroll; ++u) {
       const int64_t i = i0 + u * stride;
       if (i < n) {
-        const Rot2f r = CPLX ? csjac2<FAST>(a11[u], a22[u], ar[u], ai[u])
-                             : ssjac2<FAST>(a11[u], a22[u], ar[u]);
+        const Rot2f r = CPLX ? csjac2<DM>(a11[u], a22[u], ar[u], ai[u])
+                             : ssjac2<DM>(a11[u], a22[u], ar[u]);
         __stcs(p.cos_phi + i, r.cphi);
         __stcs(p.ea_tan_re + i, r.etr);
         if (CPLX) __stcs(p.ea_tan_im + i, r.eti);
@@ -48,17 +49,46 @@ __global__ void __launch_bounds__(256) evd2f_kernel(jsvd_evd2_streams_f32 p, int
   }
 }
 
-// Division: 1 = the branch-free division (div_fast), 0 = the IEEE
-// intrinsic as it is (default: measured faster on wide-range batches, 0.32
-// vs 0.37 ms for 2^24 real matrices and 0.49 vs 0.62 ms complex, although
-// some lanes of a warp take its slow path).  Same bits either way.
-static int g_evd32_fast = 0;
+// Division placements (fdiv's DM: bit k set = site k by the branch-free
+// division); all give the same bits.
+constexpr int kEvd32Masks[] = {
+    0x00,  // 0: the IEEE division everywhere
+    0xFF,  // 1: the branch-free division everywhere
+    0xE3,  // 2: o/|a|, tan(phi), the three phase quotients
+    0xE1,  // 3: o/|a| and the three phase quotients
+    0x21,  // 4: o/|a| and am/aM
+    0xC1,  // 5: o/|a|, |Re a21'|/|a21'|, Im a21'/|a21'|
+    0x01,  // 6: o/|a| only
+    0xE0,  // 7: the three phase quotients only
+};
+constexpr int kEvd32Placements = (int)(sizeof(kEvd32Masks) / sizeof(kEvd32Masks[0]));
+// real, complex: the fastest measured on wide-range 2^24 batches (ms per
+// launch for placements 0..7 -- real: .265 .307 .231 .253 .253 .253 .253
+// .264; complex: .425 .514 .418 .405 .397 .432 .422 .394)
+constexpr int kEvd32Default[2] = {2, 7};
+static int g_evd32_placement[2] = {kEvd32Default[0], kEvd32Default[1]};
 
-int evd2f_set_fast(int v)
+// v = -1 restores the defaults; fields: 0 both, 1 real, 2 complex.
+int evd2f_set_fast(int v, int fields)
 {
-  if (v != 0 && v != 1) return -2;
-  g_evd32_fast = v;
+  if (v < -1 || v >= kEvd32Placements) return -2;
+  if (fields < 0 || fields > 2) return -3;
+  for (int c = 0; c < 2; ++c)
+    if (fields == 0 || fields == c + 1) g_evd32_placement[c] = (v < 0) ? kEvd32Default[c] : v;
   return JSVD_OK;
+}
+
+template <bool CPLX, int I>
+static void launch_f32(int placement, int grid, int block, cudaStream_t st,
+                       const jsvd_evd2_streams_f32 &s, int64_t n)
+{
+  if constexpr (I < kEvd32Placements) {
+    if (placement == I) {
+      evd2f_kernel<CPLX, kEvd32Masks[I]><<<grid, block, 0, st>>>(s, n);
+      return;
+    }
+    launch_f32<CPLX, I + 1>(placement, grid, block, st, s, n);
+  }
 }
 
 }  // namespace jsvd
@@ -80,17 +110,10 @@ extern "C" int jsvd_evd2x2_batched_f32(jsvd_field field, const jsvd_evd2_streams
   const int64_t cap = (int64_t)sm_count() * per_sm;
   const int grid = (int)(need < cap ? need : cap);
   cudaStream_t st = as_stream(stream);
-  if (g_evd32_fast) {
-    if (cplx)
-      evd2f_kernel<true, true><<<grid, block, 0, st>>>(*s, n);
-    else
-      evd2f_kernel<false, true><<<grid, block, 0, st>>>(*s, n);
-  } else {
-    if (cplx)
-      evd2f_kernel<true, false><<<grid, block, 0, st>>>(*s, n);
-    else
-      evd2f_kernel<false, false><<<grid, block, 0, st>>>(*s, n);
-  }
+  if (cplx)
+    launch_f32<true, 0>(g_evd32_placement[1], grid, block, st, *s, n);
+  else
+    launch_f32<false, 0>(g_evd32_placement[0], grid, block, st, *s, n);
   JSVD_CHECK_LAUNCH();
   return JSVD_OK;
 }

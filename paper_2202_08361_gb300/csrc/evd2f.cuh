@@ -132,20 +132,24 @@ __device__ __forceinline__ float div_fast(float a, float b)
   return fval(sign | res);
 }
 
-template <bool FAST>
+// Which division each site takes: bit SITE of DM set, the branch-free
+// div_fast; clear, the IEEE division.  Sites:
+//   0 o/|a|   1 tan(phi)   2 1/sec(phi)   3 lambda1'   4 lambda2'
+//   5 am/aM   6 |Re a21'|/|a21'|   7 Im a21'/|a21'|
+// On wide-range data the quotients of sites 0, 1, 5, 6 and 7 leave the
+// normal range in 4 - 30 % of the lanes, so that nearly every warp would run
+// the IEEE slow path there; those of 2 - 4 almost never.  Both round
+// correctly, so DM changes no bit.
+template <int DM, int SITE>
 __device__ __forceinline__ float fdiv(float a, float b)
 {
-  if constexpr (FAST) return div_fast(a, b);
+  if constexpr (((DM >> SITE) & 1) != 0) return div_fast(a, b);
   else return __fdiv_rn(a, b);
 }
 
 // The EVD's square roots all take operands in [1, fl(sqrt nu)^2 + 1]
 // (x^2 + 1, sec^2), where the IEEE routine never leaves its fast path.
-template <bool FAST>
-__device__ __forceinline__ float fsqrt(float x)
-{
-  return __fsqrt_rn(x);
-}
+__device__ __forceinline__ float fsqrt(float x) { return __fsqrt_rn(x); }
 
 struct Rot2f {
   float cphi, etr, eti, l1s, l2s;
@@ -153,30 +157,30 @@ struct Rot2f {
 };
 
 // Section 2.1 from the scaled a11', a22' and |a21'|.
-template <bool FAST>
+template <int DM>
 __device__ __forceinline__ void rot_core_f(float a11, float a22, float aa21, float &tan1,
                                           float &sec2, float &o, float &cphi)
 {
   o = __fmul_rn(aa21, 2.0f);  // exact
   const float a = __fsub_rn(a11, a22);
   // Eq. e:tan2: min(max(o/|a|, 0), fl(sqrt nu)) with the sign of a (0/0 -> 0)
-  const float q = fmaxf(fdiv<FAST>(o, fabsf(a)), 0.0f);
+  const float q = fmaxf(fdiv<DM, 0>(o, fabsf(a)), 0.0f);
   const float tan2 = copysignf(fminf(q, fval(kSqrtNuF)), a);
-  tan1 = fdiv<FAST>(tan2, __fadd_rn(1.0f, fsqrt<FAST>(__fmaf_rn(tan2, tan2, 1.0f))));
+  tan1 = fdiv<DM, 1>(tan2, __fadd_rn(1.0f, fsqrt(__fmaf_rn(tan2, tan2, 1.0f))));
   sec2 = __fmaf_rn(tan1, tan1, 1.0f);
-  cphi = fdiv<FAST>(1.0f, fsqrt<FAST>(sec2));
+  cphi = fdiv<DM, 2>(1.0f, fsqrt(sec2));
 }
 
-template <bool FAST>
+template <int DM>
 __device__ __forceinline__ void lambdas_f(Rot2f &r, float a11, float a22, float tan1, float sec2,
                                           float o)
 {
-  r.l1s = fdiv<FAST>(__fmaf_rn(tan1, __fmaf_rn(a22, tan1, o), a11), sec2);
-  r.l2s = fdiv<FAST>(__fmaf_rn(tan1, __fmaf_rn(a11, tan1, -o), a22), sec2);
+  r.l1s = fdiv<DM, 3>(__fmaf_rn(tan1, __fmaf_rn(a22, tan1, o), a11), sec2);
+  r.l2s = fdiv<DM, 4>(__fmaf_rn(tan1, __fmaf_rn(a11, tan1, -o), a22), sec2);
 }
 
 // Real symmetric (Alg. d8jac2 in binary32).
-template <bool FAST>
+template <int DM>
 __device__ __forceinline__ Rot2f ssjac2(float a11, float a22, float a21)
 {
   Rot2f r;
@@ -185,15 +189,15 @@ __device__ __forceinline__ Rot2f ssjac2(float a11, float a22, float a21)
   a22 = scale_zeta(a22, r.zeta);
   a21 = scale_zeta(a21, r.zeta);
   float tan1, sec2, o;
-  rot_core_f<FAST>(a11, a22, fabsf(a21), tan1, sec2, o, r.cphi);
+  rot_core_f<DM>(a11, a22, fabsf(a21), tan1, sec2, o, r.cphi);
   r.etr = fval(fbits(tan1) ^ (fbits(a21) & kSignF));
   r.eti = 0.0f;
-  lambdas_f<FAST>(r, a11, a22, tan1, sec2, o);
+  lambdas_f<DM>(r, a11, a22, tan1, sec2, o);
   return r;
 }
 
 // Complex Hermitian (Listing 1 in binary32).
-template <bool FAST>
+template <int DM>
 __device__ __forceinline__ Rot2f csjac2(float a11, float a22, float a21r, float a21i)
 {
   Rot2f r;
@@ -204,15 +208,15 @@ __device__ __forceinline__ Rot2f csjac2(float a11, float a22, float a21r, float 
   a21i = scale_zeta(a21i, r.zeta);
   const float ar = fabsf(a21r), ai = fabsf(a21i);
   const float am = fminf(ar, ai), aM = fmaxf(ar, ai);
-  const float mM = fmaxf(fdiv<FAST>(am, aM), 0.0f);  // 0/0 -> 0
-  const float aa21 = __fmul_rn(fsqrt<FAST>(__fmaf_rn(mM, mM, 1.0f)), aM);
-  const float ca = copysignf(fminf(fdiv<FAST>(ar, aa21), 1.0f), a21r);
-  const float sa = fdiv<FAST>(a21i, fmaxf(aa21, fval(1u)));  // fval(1) = FLT_TRUE_MIN
+  const float mM = fmaxf(fdiv<DM, 5>(am, aM), 0.0f);  // 0/0 -> 0
+  const float aa21 = __fmul_rn(fsqrt(__fmaf_rn(mM, mM, 1.0f)), aM);
+  const float ca = copysignf(fminf(fdiv<DM, 6>(ar, aa21), 1.0f), a21r);
+  const float sa = fdiv<DM, 7>(a21i, fmaxf(aa21, fval(1u)));  // fval(1) = FLT_TRUE_MIN
   float tan1, sec2, o;
-  rot_core_f<FAST>(a11, a22, aa21, tan1, sec2, o, r.cphi);
+  rot_core_f<DM>(a11, a22, aa21, tan1, sec2, o, r.cphi);
   r.etr = __fmul_rn(ca, tan1);
   r.eti = __fmul_rn(sa, tan1);
-  lambdas_f<FAST>(r, a11, a22, tan1, sec2, o);
+  lambdas_f<DM>(r, a11, a22, tan1, sec2, o);
   return r;
 }
 

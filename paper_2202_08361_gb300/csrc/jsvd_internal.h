@@ -9,7 +9,7 @@ void evd2_get_launch(int &block, int &blocks_per_sm);
 int svd_set_grid(int cap, int warps);
 int batch_set_warps(int w);
 int batch_set_smem(int kib);
-int evd2f_set_fast(int v);
+int evd2f_set_fast(int v, int fields);
 int evd2_set_host_path(int v);
 int svd_set_step_mode(int v);
 }  // namespace jsvd

@@ -212,6 +212,31 @@ __device__ __forceinline__ bool gs_cond(int ex, int ey, double q, double ups)
   return bits(ldexp_rn(q, d)) > bits(ups);
 }
 
+// Section 3.5.1: for a pair to be rotated whose norms are this far apart,
+// Eq. e:GS replaces the rotation of G (Alg. zvjsvd checks Eq. e:GScond
+// before zjrot); V still takes the rotation.  gs = 1 orthogonalises g_q
+// against g_p (psi = conj(a21') f_q / f_p), gs = 2 g_p against g_q
+// (psi = a21' f_p / f_q).
+__device__ __forceinline__ void gs_select(PairOut &o, int ep, int eq, double q12, double q21,
+                                          double zr, double zi, double ups)
+{
+  if (!o.rot) return;
+  if (gs_cond(ep, eq, q12, ups)) {
+    o.gs = 1;
+    o.ex = ep;
+    o.ey = eq;
+    o.psr = __dmul_rn(zr, q21);
+    o.psi = -__dmul_rn(zi, q21);
+  } else if (gs_cond(eq, ep, q21, ups)) {
+    o.gs = 2;
+    o.ex = eq;
+    o.ey = ep;
+    o.psr = __dmul_rn(zr, q12);
+    o.psi = __dmul_rn(zi, q12);
+  }
+}
+
+
 // The sums of one pivot pair.  Normally pp = ||g_p||^2, qq = ||g_q||^2 and
 // (qr, qi) = g_q^* g_p of the current G.  When a column's squares underflow
 // (wide): (ep, fp), (eq, fq) are the columns' norms from Alg. rnF and
@@ -293,24 +318,7 @@ __device__ __forceinline__ PairOut pair_rotation(const PairSums &sm, double ups)
   o.c = r.cphi;
   o.C = r.etr;
   o.S = r.eti;
-  // section 3.5.1: for norms this far apart Eq. e:GS replaces the rotation
-  // of G (Alg. zvjsvd checks Eq. e:GScond before zjrot); V still takes the
-  // rotation
-  if (o.rot) {
-    if (gs_cond(ep, eq, q12, ups)) {  // g_q against g_p, psi = conj(a21') fq / fp
-      o.gs = 1;
-      o.ex = ep;
-      o.ey = eq;
-      o.psr = __dmul_rn(zr, q21);
-      o.psi = -__dmul_rn(zi, q21);
-    } else if (gs_cond(eq, ep, q21, ups)) {  // g_p against g_q, psi = a21' fp / fq
-      o.gs = 2;
-      o.ex = eq;
-      o.ey = ep;
-      o.psr = __dmul_rn(zr, q12);
-      o.psi = __dmul_rn(zi, q12);
-    }
-  }
+  gs_select(o, ep, eq, q12, q21, zr, zi, ups);
   return o;
 }
 
@@ -451,21 +459,7 @@ __device__ __forceinline__ PairOut pair_rotation_warp(const PairSums &sm, double
   }
   o.c = cphi;
   o.swap = ord(l1s) < ord(l2s);
-  if (o.rot) {
-    if (gs_cond(ep, eq, q12, ups)) {
-      o.gs = 1;
-      o.ex = ep;
-      o.ey = eq;
-      o.psr = __dmul_rn(zr, q21);
-      o.psi = -__dmul_rn(zi, q21);
-    } else if (gs_cond(eq, ep, q21, ups)) {
-      o.gs = 2;
-      o.ex = eq;
-      o.ey = ep;
-      o.psr = __dmul_rn(zr, q12);
-      o.psi = __dmul_rn(zi, q12);
-    }
-  }
+  gs_select(o, ep, eq, q12, q21, zr, zi, ups);
   return o;
 }
 

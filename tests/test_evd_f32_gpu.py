@@ -32,13 +32,15 @@ def check(streams, complex_):
         assert bad.size == 0, (k, bad[:5], [s[bad[0]] for s in streams])
 
 
-@pytest.fixture(params=[0, 1], ids=["ieee_div", "branch_free_div"])
+@pytest.fixture(params=[0, 1, 2, 4, 7], ids=lambda v: "div_placement_%d" % v)
 def div_mode(request):
-    """Both divisions of the single precision EVD (JSVD_TUNE_EVD32_DIV)."""
+    """Placements of the single precision EVD's divisions between the IEEE
+    and the branch-free routine (JSVD_TUNE_EVD32_DIV): none, all, the
+    default, two subsets."""
     import paper_2202_08361_gb300 as J
     J.tune_set(J.JSVD_TUNE_EVD32_DIV, request.param)
     yield request.param
-    J.tune_set(J.JSVD_TUNE_EVD32_DIV, 0)
+    J.tune_set(J.JSVD_TUNE_EVD32_DIV, -1)
 
 
 @pytest.mark.parametrize("complex_", [False, True])
