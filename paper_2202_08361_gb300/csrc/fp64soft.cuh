@@ -7,8 +7,8 @@
 // inputs and outputs) from 64-bit integer arithmetic:
 //
 //   division a/b: mantissas n/d with n/d in [1, 2); a fixed-point
-//     reciprocal y ~ 2^115/d from an FP32 seed refined by two Newton steps
-//     y <- y + y (2^115 - d y)/2^115; the quotient Q = floor(n 2^55 / d)
+//     reciprocal y ~ 2^115/d from an FP32 seed refined by one third-order
+//     step y <- y (1 + eps + eps^2), eps = (2^115 - d y)/2^115; the quotient Q = floor(n 2^55 / d)
 //     from Q ~ n y / 2^60 corrected with the exact remainder
 //     R = n 2^55 - Q d (which fits in 64 bits), then rounded from Q's low
 //     bits and R != 0 (Newton-Raphson division with an exact remainder
@@ -16,7 +16,8 @@
 //     done here in fixed point);
 //   square root of x: t = mantissa in [1, 4) with an even exponent; a
 //     fixed-point inverse square root z ~ 2^63/sqrt(t) from an FP32 seed and
-//     two Newton steps z <- z + z (1 - t z^2)/2; S = floor(sqrt(t) 2^55)
+//     one third-order step z <- z (1 + delta/2 + 3 delta^2/8), delta =
+//     1 - t z^2; S = floor(sqrt(t) 2^55)
 //     from S ~ t z corrected with the exact remainder t 2^110 - S^2, then
 //     rounded likewise.
 //
@@ -145,22 +146,25 @@ SOFT_FN uint64_t recip_seed(uint64_t d)
   return m << (E - 150 + 63 + 0);  // r 2^63 = m 2^(E - 150 + 63)
 }
 
-// y ~ 2^115/d refined to a few units by two fixed-point Newton steps.
+// y ~ 2^115/d refined to a few units by one third-order step
+// y <- y (1 + eps + eps^2), eps = (2^115 - d y) / 2^115: the seed's
+// |eps| < 2^-22 leaves eps^3 < 2^-66, below the fixed-point truncations
+// (a few units of y's last bit), as two Newton steps would, with one long
+// multiplication fewer.
 SOFT_FN uint64_t recip115(uint64_t d)
 {
-  uint64_t y = recip_seed(d);
-#pragma unroll
-  for (int it = 0; it < 2; ++it) {
-    // e = 2^115 - d y  (|e| < 2^96), as e / 2^52 in a signed 64-bit word
-    const uint64_t lo = d * y, hi = mulhi(d, y);  // d y < 2^116
-    const uint64_t elo = 0ull - lo;
-    const int64_t ehi = (int64_t)((1ull << 51) - hi - (lo != 0ull ? 1ull : 0ull));
-    const int64_t e52 = (int64_t)(((uint64_t)ehi << 12) | (elo >> 52));
-    // y += y e / 2^115 = y (e / 2^52) / 2^63
-    const int64_t t = mulhi_s(y, e52);  // y e52 / 2^64
-    y = y + (uint64_t)(t * 2);
-  }
-  return y;
+  const uint64_t y = recip_seed(d);
+  // e = 2^115 - d y  (|e| < 2^94), as e52 = e / 2^52 = eps 2^63 in a signed word
+  const uint64_t lo = d * y, hi = mulhi(d, y);  // d y < 2^116
+  const uint64_t elo = 0ull - lo;
+  const int64_t ehi = (int64_t)((1ull << 51) - hi - (lo != 0ull ? 1ull : 0ull));
+  const int64_t e52 = (int64_t)(((uint64_t)ehi << 12) | (elo >> 52));
+  // eps^2 2^63 = e52^2 / 2^63: with a = |e52| 2^21 (< 2^64), a^2 / 2^64 = e52^2 / 2^22
+  const uint64_t a = (uint64_t)(e52 < 0 ? -e52 : e52) << 21;
+  const int64_t e2 = (int64_t)(mulhi(a, a) >> 41);
+  // y += y (eps + eps^2) = y (e52 + e2) / 2^63
+  const int64_t t = mulhi_s(y, e52 + e2);  // y (e52 + e2) / 2^64
+  return y + (uint64_t)(t * 2);
 }
 
 // A divisor prepared once for several quotients: its mantissa d, exponent
@@ -257,13 +261,19 @@ SOFT_FN double sqrt_rn(double x)
   const uint64_t mt = odd ? (m << 1) : m;  // < 2^54
   const int eh = (odd ? e - 1 : e) / 2;    // exact: e - odd is even
   uint64_t z = rsqrt_seed(m, odd);
-#pragma unroll
-  for (int it = 0; it < 2; ++it) {
+  {
+    // one third-order step z <- z (1 + delta/2 + 3 delta^2/8), delta =
+    // 1 - t z^2 / 2^126 (|delta| < 2^-21 from the seed; the step leaves
+    // about delta^3 / 3 < 2^-64, below the truncations).
     // t z^2 / 2^126 ~ 1: wh = z^2 / 2^64, p = t wh / 4 = mt wh / 2^54
     const uint64_t wh = mulhi(z, z);
-    const uint64_t p = mulhi(mt << 10, wh);        // mt 2^10 wh / 2^64 = mt wh / 2^54
-    const int64_t e60 = (int64_t)((1ull << 60) - p);  // 2^60 (1 - t z^2 / 2^126)
-    const int64_t t = mulhi_s(z, e60 * 8);            // z e60 / 2^61
+    const uint64_t p = mulhi(mt << 10, wh);           // mt 2^10 wh / 2^64 = mt wh / 2^54
+    const int64_t e60 = (int64_t)((1ull << 60) - p);  // delta 2^60
+    // 3 delta^2 2^58 = 3 e60^2 / 2^62: with a = |e60| 2^24 (< 2^64), a^2 / 2^64 = e60^2 / 2^16
+    const uint64_t a = (uint64_t)(e60 < 0 ? -e60 : e60) << 24;
+    const int64_t q = (int64_t)(3ull * (mulhi(a, a) >> 46));
+    // z += z (delta/2 + 3 delta^2/8) = z (e60 + q) / 2^61
+    const int64_t t = mulhi_s(z, (e60 + q) * 8);      // z (e60 + q) / 2^61
     z = z + (uint64_t)t;
   }
   // S ~ sqrt(t) 2^55 = t z / 2^8 = mt z / 2^60
