@@ -4,9 +4,9 @@
 //   1. maxnorm_kernel   M~_0 = ||A||_max (NaN -> Inf), section 3.2
 //   2. init_kernel      G_1 = 2^{s_0} A split into planes, V_1 = I
 //   3. sweeps_kernel    persistent cooperative kernel: every sweep, every
-//                       step, one warp per pivot pair (svd_core.cuh), a
-//                       bounded grid barrier between steps, stop on a
-//                       rotation-free sweep
+//                       step, one warp per pivot pair (svd_core.cuh: sums,
+//                       rotation, transformation), a bounded grid barrier
+//                       between steps, stop on a rotation-free sweep
 //   4. colnorm_kernel   final (e,f) norms of the columns
 //   5. rank_kernel      stable non-increasing order of sigma, info
 //   6. output_kernel    U = G 2^{-e_j} / f_j, V, sigma, merged planes
@@ -14,9 +14,12 @@
 // Scaling (section 3.2, adapted): the paper keeps ||G||_max below
 // nu/(varsigma m) so that an xNRM2-style norm cannot overflow.  Here the
 // three sums of a pair are formed in one pass as plain sums of squares and
-// products, which is safe while the entries stay near 1 (the safe region of
-// supplement SM3): G_1 is scaled to max-norm in [1, 2) and downscaled back
-// to that range whenever the tracked max-norm M~ reaches 2^rescale_exp.
+// products, which is safe while the entries stay below 2^rescale_exp (the
+// safe region of supplement SM3; 2^480 by default): G_1 is scaled to a
+// max-norm in [2^(R-25), 2^(R-24)), R = rescale_exp, and scaled back there
+// whenever the tracked max-norm M~ reaches 2^R.  The high binade leaves tiny
+// columns the most room above the subnormal range; columns whose squares
+// still fall below it take the wide-exponent norms (Alg. rnF).
 #include <algorithm>
 #include <climits>
 
@@ -160,6 +163,11 @@ __global__ void __launch_bounds__(256) sweeps_kernel(MatViewT<T> M, SvdState *st
   const int K = nt - 1, L = nt / 2;
   const int lane = threadIdx.x & 31, W = blockDim.x >> 5;
   const bool warp_step = (flags & kFlagWarpStep) != 0;
+  // V's transformation held over to the next step (DeferredV) when every
+  // warp has at most one pair per step and V's rows take one trip
+  const bool defer = warp_step && (int64_t)gridDim.x * W >= L &&
+                     M.np <= 32 * DeferredV<T, CPLX>::kRows;
+  DeferredV<T, CPLX> dv;
   if (K < 1) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       st->sweeps = 1;
@@ -188,7 +196,8 @@ __global__ void __launch_bounds__(256) sweeps_kernel(MatViewT<T> M, SvdState *st
       unsigned long long Mloc = 0ull;
       int rots = 0, gsn = 0;
       if (warp_step)
-        step_warps<T, CPLX, COMP>(M, k, nt, ups, rk, (flags & kFlagPermute) != 0, Mloc, rots, gsn);
+        step_warps<T, CPLX, COMP>(M, k, nt, ups, rk, (flags & kFlagPermute) != 0, Mloc, rots, gsn,
+                                  defer, dv);
       else
         for (int base = blockIdx.x * W; base < L; base += gridDim.x * W)
           step_chunk<T, CPLX, true, COMP>(M, k, nt, base, W, ups, rk, (flags & kFlagPermute) != 0,
@@ -202,6 +211,10 @@ __global__ void __launch_bounds__(256) sweeps_kernel(MatViewT<T> M, SvdState *st
       if (!grid_barrier(&st->bar_word, &st->err, kBarrierLimitNs)) return;
     }
     converged = (((volatile int *)st->T)[sweep] == 0);
+  }
+  if (defer && dv.p >= 0) {  // the last step's V
+    dv.load(M);
+    dv.apply(M);
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     st->sweeps = sweep;

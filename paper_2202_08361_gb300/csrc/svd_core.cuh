@@ -725,6 +725,24 @@ __device__ __forceinline__ void gs_apply(const MatViewT<double, CG> &M, int p, i
   }
 }
 
+// One row of Eq. e:transf: x_p' = fma(x_q, e', x_p) c, x_q' = fma(x_p,
+// -conj(e'), x_q) c, e' = C + iS (real: S = 0).
+template <typename T, bool CPLX>
+__device__ __forceinline__ void rotate_row(T pr, T pi, T qr, T qi, T c, T C, T S, T &npr, T &npi,
+                                           T &nqr, T &nqi)
+{
+  if (CPLX) {
+    npr = mul_t(fma_t(qr, C, fma_t(-qi, S, pr)), c);
+    npi = mul_t(fma_t(qr, S, fma_t(qi, C, pi)), c);
+    nqr = mul_t(fma_t(pr, -C, fma_t(-pi, S, qr)), c);
+    nqi = mul_t(fma_t(pr, S, fma_t(pi, -C, qi)), c);
+  } else {
+    npr = mul_t(fma_t(qr, C, pr), c);
+    nqr = mul_t(fma_t(pr, -C, qr), c);
+    npi = nqi = T(0);
+  }
+}
+
 // Eq. e:transf (Alg. zjrot) on the pair's G rows (tracking the max-norm of
 // the new entries in Mloc, as magbits() in T's encoding) and V rows, with the
 // columns swapped if o.swap; a non-rotated pair with o.swap is only swapped.
@@ -734,8 +752,10 @@ __device__ __forceinline__ void gs_apply(const MatViewT<double, CG> &M, int p, i
 // take separate trips; with MERGED, G's mp rows followed by V's np rows are
 // one sequence (both multiples of 32, so each 32 rows lie in one matrix),
 // so that a trip may hold rows of both -- one trip for a short pair of
-// columns, at the price of a pointer select per row.
-template <typename T, bool CPLX, bool CG, int U = (sizeof(T) == 4) ? 8 : 4, bool MERGED = false>
+// columns, at the price of a pointer select per row.  G_ONLY leaves V to the
+// caller (DeferredV).
+template <typename T, bool CPLX, bool CG, int U = (sizeof(T) == 4) ? 8 : 4, bool MERGED = false,
+          bool G_ONLY = false>
 __device__ __forceinline__ void pair_apply(const MatViewT<T, CG> &M, int p, int q, const PairOut &o,
                                            unsigned long long &Mloc)
 {
@@ -754,14 +774,12 @@ __device__ __forceinline__ void pair_apply(const MatViewT<T, CG> &M, int p, int 
     // x_p' = fma(x_q, e', x_p) c, x_q' = fma(x_p, -conj(e'), x_q) c, e' = C + iS
     auto rotate = [&](const T pr, const T pi, const T qr, const T qi, T *dpr, T *dpi, T *dqr,
                       T *dqi, bool onG) {
+      T npr, npi, nqr, nqi;
+      rotate_row<T, CPLX>(pr, pi, qr, qi, c, C, S, npr, npi, nqr, nqi);
+      M.st(dpr, npr);
+      M.st(dqr, nqr);
       if (CPLX) {
-        const T npr = mul_t(fma_t(qr, C, fma_t(-qi, S, pr)), c);
-        const T npi = mul_t(fma_t(qr, S, fma_t(qi, C, pi)), c);
-        const T nqr = mul_t(fma_t(pr, -C, fma_t(-pi, S, qr)), c);
-        const T nqi = mul_t(fma_t(pr, S, fma_t(pi, -C, qi)), c);
-        M.st(dpr, npr);
         M.st(dpi, npi);
-        M.st(dqr, nqr);
         M.st(dqi, nqi);
         if (onG) {
           const unsigned long long a =
@@ -769,10 +787,6 @@ __device__ __forceinline__ void pair_apply(const MatViewT<T, CG> &M, int p, int 
           Mloc = max(Mloc, a);
         }
       } else {
-        const T npr = mul_t(fma_t(qr, C, pr), c);
-        const T nqr = mul_t(fma_t(pr, -C, qr), c);
-        M.st(dpr, npr);
-        M.st(dqr, nqr);
         if (onG) Mloc = max(Mloc, max(magbits(npr), magbits(nqr)));
       }
     };
@@ -781,7 +795,7 @@ __device__ __forceinline__ void pair_apply(const MatViewT<T, CG> &M, int p, int 
     T *gpi = CPLX ? M.gi + p * M.ldg : nullptr, *gqi = CPLX ? M.gi + q * M.ldg : nullptr;
     T *vpi = CPLX ? M.vi + p * M.ldv : nullptr, *vqi = CPLX ? M.vi + q * M.ldv : nullptr;
     if constexpr (MERGED) {
-      const int r0 = gdone ? M.mp : 0, R = M.mp + M.np;
+      const int r0 = gdone ? M.mp : 0, R = G_ONLY ? M.mp : M.mp + M.np;
       for (int base = r0 + lane; base < R; base += 32 * U) {
         T pr[U], qr[U], pi[U], qi[U];
 #pragma unroll
@@ -814,7 +828,7 @@ __device__ __forceinline__ void pair_apply(const MatViewT<T, CG> &M, int p, int 
         }
       }
     } else {
-      for (int pass = gdone ? 1 : 0; pass < 2; ++pass) {
+      for (int pass = gdone ? 1 : 0; pass < (G_ONLY ? 1 : 2); ++pass) {
         const bool onG = (pass == 0);
         const int rows = onG ? M.mp : M.np;
         T *xpr = onG ? gpr : vpr, *xqr = onG ? gqr : vqr;
@@ -847,7 +861,7 @@ __device__ __forceinline__ void pair_apply(const MatViewT<T, CG> &M, int p, int 
       }
     }
   } else if (swp) {
-    for (int pass = 0; pass < 2; ++pass) {
+    for (int pass = 0; pass < (G_ONLY ? 1 : 2); ++pass) {
       const bool onG = (pass == 0);
       const int rows = onG ? M.mp : M.np;
       T *xpr = onG ? M.gr + p * M.ldg : M.vr + p * M.ldv;
@@ -931,6 +945,69 @@ __device__ __forceinline__ void step_chunk(const MatViewT<T, CG> &M, int k, int 
   __syncthreads();
 }
 
+// A pair's transformation of V held over to the next step.  The sweep
+// never reads V but to transform it, and V's columns p and q are not
+// touched by any other pair before the next step's barrier, so applying
+// step k's rotation to them during step k + 1 keeps every column's updates
+// in their order and gives the same bits.  The rows (np <= 32 kRows per
+// lane: one trip) are loaded before the next rotation's chain of dependent
+// operations and transformed after it, so their L2 round trip is hidden
+// behind that chain and the step's critical path keeps only G's rows.
+template <typename T, bool CPLX>
+struct DeferredV {
+  static constexpr int kRows = 4;
+  int p = -1, q = -1;  // the pending pair (p < 0: none)
+  PairOut o;
+  T pr[kRows], qr[kRows], pi[kRows], qi[kRows];
+
+  __device__ __forceinline__ void load(const MatViewT<T, true> &M)
+  {
+    const int lane = threadIdx.x & 31;
+    const T *xp = M.vr + p * M.ldv, *xq = M.vr + q * M.ldv;
+    const T *xpi = CPLX ? M.vi + p * M.ldv : nullptr, *xqi = CPLX ? M.vi + q * M.ldv : nullptr;
+#pragma unroll
+    for (int u = 0; u < kRows; ++u) {
+      const int i = lane + 32 * u;
+      pr[u] = qr[u] = pi[u] = qi[u] = T(0);
+      if (i < M.np) {
+        pr[u] = M.ld(xp + i);
+        qr[u] = M.ld(xq + i);
+        if (CPLX) {
+          pi[u] = M.ld(xpi + i);
+          qi[u] = M.ld(xqi + i);
+        }
+      }
+    }
+  }
+
+  // the transformation (or the swap alone) of the loaded rows, as
+  // pair_apply's V pass would do it
+  __device__ __forceinline__ void apply(const MatViewT<T, true> &M)
+  {
+    const int lane = threadIdx.x & 31;
+    T *xp = M.vr + p * M.ldv, *xq = M.vr + q * M.ldv;
+    T *xpi = CPLX ? M.vi + p * M.ldv : nullptr, *xqi = CPLX ? M.vi + q * M.ldv : nullptr;
+    T *dp = o.swap ? xq : xp, *dq = o.swap ? xp : xq;
+    T *dpi = o.swap ? xqi : xpi, *dqi = o.swap ? xpi : xqi;
+    const T c = to_t(o.c, T(0)), C = to_t(o.C, T(0)), S = CPLX ? to_t(o.S, T(0)) : T(0);
+#pragma unroll
+    for (int u = 0; u < kRows; ++u) {
+      const int i = lane + 32 * u;
+      if (i < M.np) {
+        T npr = pr[u], npi = pi[u], nqr = qr[u], nqi = qi[u];
+        if (o.rot) rotate_row<T, CPLX>(pr[u], pi[u], qr[u], qi[u], c, C, S, npr, npi, nqr, nqi);
+        M.st(dp + i, npr);
+        M.st(dq + i, nqr);
+        if (CPLX) {
+          M.st(dpi + i, npi);
+          M.st(dqi + i, nqi);
+        }
+      }
+    }
+    p = q = -1;
+  }
+};
+
 // A block's share of step k when every warp runs its pairs alone: warp w
 // takes pairs l = blockIdx.x W + w, + gridDim.x W, ..., each one its sums,
 // its rotation (pair_rotation_warp, the same bits as the chunked form) and
@@ -939,7 +1016,8 @@ __device__ __forceinline__ void step_chunk(const MatViewT<T, CG> &M, int k, int 
 // block and its time is the chain of one pair.
 template <typename T, bool CPLX, bool COMP = false>
 __device__ __forceinline__ void step_warps(const MatViewT<T, true> &M, int k, int nt, double ups, int rk,
-                                           bool permute, unsigned long long &Mloc, int &rots, int &gsn)
+                                           bool permute, unsigned long long &Mloc, int &rots, int &gsn,
+                                           bool defer, DeferredV<T, CPLX> &dv)
 {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
   const int L = nt / 2;
@@ -955,17 +1033,36 @@ __device__ __forceinline__ void step_warps(const MatViewT<T, true> &M, int k, in
       const bool wide_apply = sizeof(T) == 8 && (M.mp + M.np) % (32 * UA) == 0;
       const PairSums sm = wide_sums ? pair_sums<T, CPLX, true, COMP, US>(M, p, q, rk)
                                     : pair_sums<T, CPLX, true, COMP>(M, p, q, rk);
+      if (defer && dv.p >= 0) dv.load(M);  // the last step's V rows, in flight during the rotation
       PairOut o = pair_rotation_warp<CPLX>(sm, ups);
       o.swap = o.swap && permute;
-      if (wide_apply)
+      if (defer) {
+        if (dv.p >= 0) dv.apply(M);
+        if (wide_sums)
+          pair_apply<T, CPLX, true, US, false, true>(M, p, q, o, Mloc);
+        else
+          pair_apply<T, CPLX, true, (sizeof(T) == 4) ? 8 : 4, false, true>(M, p, q, o, Mloc);
+        if (o.rot || o.swap) {
+          dv.p = p;
+          dv.q = q;
+          dv.o = o;
+        }
+      } else if (wide_apply) {
         pair_apply<T, CPLX, true, UA, true>(M, p, q, o, Mloc);
-      else
+      } else {
         pair_apply<T, CPLX, true>(M, p, q, o, Mloc);
+      }
       if (lane == 0 && o.rot) ++rots;
       if (lane == 0 && o.gs) ++gsn;
-    } else if (rk) {  // phantom partner: only a pending rescale applies
-      scale_col(M, M.gr + p * M.ldg, rk, lane);
-      if (CPLX) scale_col(M, M.gi + p * M.ldg, rk, lane);
+    } else {
+      if (defer && dv.p >= 0) {  // no pair of its own this step: settle the last one's V
+        dv.load(M);
+        dv.apply(M);
+      }
+      if (rk) {  // phantom partner: only a pending rescale applies
+        scale_col(M, M.gr + p * M.ldg, rk, lane);
+        if (CPLX) scale_col(M, M.gi + p * M.ldg, rk, lane);
+      }
     }
   }
 }
