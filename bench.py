@@ -134,6 +134,20 @@ def kernel_source_sha():
     return h.hexdigest()[:16]
 
 
+def recorded_pipes(kernel):
+    """FP64-pipe, integer-ALU and issue utilisation of the kernel from the
+    committed ncu summary, if it was taken on the current kernel source;
+    else None."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "evd2_traffic.json")) as f:
+            rec = json.load(f)
+    except Exception:
+        return None
+    if rec.get("source_sha") != kernel_source_sha():
+        return None
+    return rec.get("pipes_active", {}).get(kernel)
+
+
 def recorded_traffic(kernel):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
     on the current kernel source; else None."""
@@ -582,6 +596,7 @@ def run_ours(args):
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
                 "kernel": dom_name, "peak_kind": peak_kind,
+                "pipes_active": recorded_pipes(dom_name),
                 "algorithmic_bytes_per_launch": dom_bytes, "avg_launch_ms": dom_ms}
 
     svd = None
