@@ -203,21 +203,17 @@ SOFT_FN double div_rn(double a, const Den &D)
   // Q ~ n 2^55 / d = n y / 2^60
   const uint64_t hi = mulhi(n, y), lo = n * y;
   uint64_t Q = (hi << 4) | (lo >> 60);
-  // exact remainder R = n 2^55 - Q d (|R| < 2^63), then at most a few fixes
+  // exact remainder R = n 2^55 - Q d (|R| < 2^63), then one fix either way:
+  // y is within a few units of 2^115/d (relative 2^-60), so n y / 2^60 is
+  // within 0.05 of n 2^55 / d < 2^56 and Q is off by at most one
   int64_t R = (int64_t)((n << 55) - Q * d);
-#pragma unroll
-  for (int k = 0; k < 2; ++k) {
-    if (R < 0) {
-      Q -= 1;
-      R += (int64_t)d;
-    }
+  if (R < 0) {
+    Q -= 1;
+    R += (int64_t)d;
   }
-#pragma unroll
-  for (int k = 0; k < 2; ++k) {
-    if (R >= (int64_t)d) {
-      Q += 1;
-      R -= (int64_t)d;
-    }
+  if (R >= (int64_t)d) {
+    Q += 1;
+    R -= (int64_t)d;
   }
   return round_pack(sign, Q, R != 0, e);
 }
@@ -278,21 +274,17 @@ SOFT_FN double sqrt_rn(double x)
   }
   // S ~ sqrt(t) 2^55 = t z / 2^8 = mt z / 2^60
   uint64_t S = mulhi(mt << 4, z);
-  // exact remainder R = mt 2^58 - S^2 (|R| < 2^58), then fixes
+  // exact remainder R = mt 2^58 - S^2 (|R| < 2^58), then one fix either way:
+  // z is within a few units of 2^63/sqrt(t) (relative 2^-61), so S is off by
+  // at most one
   int64_t R = (int64_t)((mt << 58) - S * S);
-#pragma unroll
-  for (int k = 0; k < 2; ++k) {
-    if (R < 0) {
-      R += (int64_t)(2 * S - 1);
-      S -= 1;
-    }
+  if (R < 0) {
+    R += (int64_t)(2 * S - 1);
+    S -= 1;
   }
-#pragma unroll
-  for (int k = 0; k < 2; ++k) {
-    if (R > (int64_t)(2 * S)) {
-      R -= (int64_t)(2 * S + 1);
-      S += 1;
-    }
+  if (R > (int64_t)(2 * S)) {
+    R -= (int64_t)(2 * S + 1);
+    S += 1;
   }
   // sqrt(x) = sqrt(t) 2^eh = (S + frac) 2^(eh - 55)
   return round_pack(ux & kSgn, S, R != 0, eh);
