@@ -79,7 +79,7 @@ JSVD_API const char *jsvd_last_cuda_error(void);
 #define JSVD_TUNE_BATCH_WARPS 3
 /*   JSVD_TUNE_EVD_ARITH: value = which of the 2x2 EVD's divisions and
  *     square roots run on the integer pipe instead of the FP64 pipe (0..7;
- *     -1 = the default, 6 for real and 5 for complex matrices); value2 =
+ *     -1 = the default, 7 for both fields); value2 =
  *     the fields it applies to (0 both, 1 real, 2 complex).  Both pipes
  *     round correctly: the results are identical. */
 #define JSVD_TUNE_EVD_ARITH 4

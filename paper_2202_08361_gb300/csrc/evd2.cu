@@ -74,9 +74,11 @@ constexpr int kEvdMasks[] = {
 constexpr int kEvdPlacements = (int)(sizeof(kEvdMasks) / sizeof(kEvdMasks[0]));
 
 // Default placement per field (real, complex), the fastest measured on
-// 2^24 wide-range matrices: the real kernel keeps only sqrt(sec^2) on the
-// FP64 pipe, the complex one both rotation square roots.
-constexpr int kEvdDefault[2] = {6, 5};
+// 2^24 wide-range matrices: only sqrt(tan2^2 + 1) on the FP64 pipe, every
+// other division and square root on the integer pipe (ms per launch for
+// placements 0..7 -- real: 3.65 .922 1.26 1.86 1.96 1.10 .915 .896;
+// complex: 6.13 1.41 1.65 2.18 2.28 1.44 1.37 1.36).
+constexpr int kEvdDefault[2] = {7, 7};
 static int g_evd_placement[2] = {kEvdDefault[0], kEvdDefault[1]};
 
 int evd2_set_variant(int v, int fields)
