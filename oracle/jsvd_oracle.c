@@ -34,7 +34,7 @@
  * Compile with -ffp-contract=off: every fused multiply-add below is an
  * explicit fma() call, exactly where the paper writes one.
  *
- * Readings of the paper where it is silent (also listed in the design doc):
+ * Readings of the paper where it is silent:
  *   - zeta of an all-zero 2x2 matrix follows Listing 1 (frexp of the
  *     smallest subnormal), so zeta is a finite int in [-3, 2094];
  *   - the packed (zeta' << 1) | p is formed by an unsigned shift;
