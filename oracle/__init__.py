@@ -34,7 +34,9 @@ _i64 = ctypes.POINTER(ctypes.c_int64)
 def lib():
     global _lib
     if _lib is None:
-        path = _build.build()
+        # ORC_LIB: a library built by build.build_mutant, for the tests that
+        # check that the pins catch a planted mistake (run in a subprocess)
+        path = os.environ.get("ORC_LIB") or _build.build()
         L = ctypes.CDLL(path)
         L.orc_dsjac2.argtypes = [ctypes.c_int64, _d, _d, _d, _d, _d, _d, _d, _i32]
         L.orc_dsjac2.restype = None

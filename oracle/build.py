@@ -30,5 +30,17 @@ def build(force: bool = False) -> str:
     return LIB
 
 
+def build_mutant(k: int, out_dir: str) -> str:
+    """The oracle with planted mistake number k (ORC_MUTANT = k, see MUT in
+    jsvd_oracle.c) in out_dir, for the tests that check the pins catch it."""
+    os.makedirs(out_dir, exist_ok=True)
+    lib = os.path.join(out_dir, "libjsvd_oracle_m%d.so" % k)
+    cmd = ["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-fopenmp",
+           "-ffp-contract=off", "-fno-fast-math", "-fvisibility=hidden",
+           "-DORC_MUTANT=%d" % k, "-o", lib, SRC, SRC_Q, "-lm"]
+    subprocess.run(cmd, check=True)
+    return lib
+
+
 if __name__ == "__main__":
     print(build(force="--force" in sys.argv))

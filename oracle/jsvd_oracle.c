@@ -67,6 +67,15 @@
 
 #define ORC_EXPORT __attribute__((visibility("default")))
 
+/* Mutation points for the tests that check the pins (tests/
+ * test_oracle_mutants.py): compiled with -DORC_MUTANT=k (k > 0), MUT(k, ...)
+ * takes its second expression, a planted mistake; by default (0) every
+ * MUT is its first expression and the code is the plain oracle. */
+#ifndef ORC_MUTANT
+#define ORC_MUTANT 0
+#endif
+#define MUT(k, good, bad) ((ORC_MUTANT == (k)) ? (bad) : (good))
+
 /* fl(sqrt(nu)) from Eq. (2.4 "e:tan2"), as printed in Listing 1. */
 static const double SQRT_NU = 1.34078079299425956E+154;
 
@@ -89,7 +98,7 @@ static int zeta_of(double x)
 {
   int e;
   (void)frexp(fmax(fabs(x), DBL_TRUE_MIN), &e);
-  return (DBL_MAX_EXP - 3) - e;
+  return MUT(5, (DBL_MAX_EXP - 3), (DBL_MAX_EXP - 2)) - e;
 }
 
 static int imin(int a, int b) { return (a <= b) ? a : b; }
@@ -124,10 +133,10 @@ static void dsjac2_1(double a11, double a22, double a21, double *cphi, double *t
   /* Eq. "e:jacsec" */
   const double sec2 = fma(tan1, tan1, 1.0);
   const double sec = sqrt(sec2);
-  *cphi = 1.0 / sec;
-  *tphi = xorsign(tan1, a21);
+  *cphi = MUT(2, 1.0 / sec, 1.0 / sec2);
+  *tphi = MUT(3, xorsign(tan1, a21), tan1);
   /* Eq. "e:lamsec" */
-  const double l1 = fma(tan1, fma(a22, tan1, o), a11) / sec2;
+  const double l1 = fma(tan1, fma(MUT(1, a22, a11), tan1, o), a11) / sec2;
   const double l2 = fma(tan1, fma(a11, tan1, -o), a22) / sec2;
   if (lam1) *lam1 = scalbn(l1, -zeta);
   if (lam2) *lam2 = scalbn(l2, -zeta);
@@ -154,7 +163,7 @@ static void zsjac2_1(double a11, double a22, double a21r, double a21i, double *c
   const double mM = fmax(am / aM, 0.0);
   const double aa21 = sqrt(fma(mM, mM, 1.0)) * aM;
   const double calpha = copysign(fmin(ar / aa21, 1.0), a21r);
-  const double salpha = a21i / fmax(aa21, DBL_TRUE_MIN);
+  const double salpha = MUT(4, a21i, -a21i) / fmax(aa21, DBL_TRUE_MIN);
   /* the Jacobi rotation, section 2.1 */
   const double o = aa21 * 2.0;
   const double a = a11 - a22;
@@ -233,7 +242,7 @@ static void ssjac2_1(float a11, float a22, float a21, float *cphi, float *tphi, 
   const float tan1 = tan2 / (1.0f + sqrtf(fmaf(tan2, tan2, 1.0f)));
   const float sec2 = fmaf(tan1, tan1, 1.0f);
   const float sec = sqrtf(sec2);
-  *cphi = 1.0f / sec;
+  *cphi = MUT(13, 1.0f / sec, 1.0f / sec2);
   *tphi = xorsignf_(tan1, a21);
   const float l1 = fmaf(tan1, fmaf(a22, tan1, o), a11) / sec2;
   const float l2 = fmaf(tan1, fmaf(a11, tan1, -o), a22) / sec2;
@@ -328,7 +337,7 @@ ORC_EXPORT int orc_pairs(int n, int32_t *tab)
         q = nt - 1;
       } else {
         const int a = (k + l) % K;
-        const int b = ((k - l) % K + K) % K;
+        const int b = ((k - l + MUT(8, 0, 1)) % K + K) % K;
         p = (a < b) ? a : b;
         q = (a < b) ? b : a;
       }
@@ -439,7 +448,7 @@ static void rnf_step(double x, double *e, double *f)
   const double d1 = fmax(e1 - emax, -INFINITY);
   const double fh = scalef_d(fx, dh / 2.0);
   const double fr = scalef_d(f1, d1);
-  const double fn = fma(fh, fh, fr);
+  const double fn = fma(fh, MUT(14, fh, fr), fr);
   *f = F_of(fn);
   *e = emax + E_of(fn);
 }
@@ -449,7 +458,7 @@ static void ef_sqrt(double e, double f, double *e2, double *f2)
 {
   double ep = e, fp = f;
   if (!isinf(e) && ((int64_t)e & 1)) {
-    fp = 2.0 * f;
+    fp = MUT(9, 2.0 * f, f);
     ep = e - 1.0;
   }
   *e2 = isinf(ep) ? ep : ep / 2.0;
@@ -486,7 +495,7 @@ static void zdpscl(int64_t m, const double *qr, const double *qi, const double *
       re = fma(gqr, gpr, re);
       im = fma(gqr, gpi, im);
       re = fma(gqi, gpi, re);
-      im = fma(-gqi, gpr, im);
+      im = fma(MUT(6, -gqi, gqi), gpr, im);
     }
   } else {
     for (int64_t i = 0; i < m; ++i) re = fma(ldexp(qr[i], -eq), ldexp(pr[i], -ep), re);
@@ -552,7 +561,7 @@ static void zdpscl_comp(int64_t m, const double *qr, const double *qi, const dou
     }
   }
   const double d = fq * fp;
-  *zr = (rs + (rt + (rs2 + rt2))) / d;
+  *zr = MUT(10, (rs + (rt + (rs2 + rt2))), (rs + (rs2 + rt2))) / d;
   *zi = qi ? (is + (it + (is2 + it2))) / d : 0.0;
 }
 
@@ -623,7 +632,7 @@ static double zjrot(int64_t l, double *xpr, double *xpi, double *xqr, double *xq
     } else {
       const double pr = xpr[i], qr = xqr[i];
       npr = fma(qr, C, pr) * c;
-      nqr = fma(pr, -C, qr) * c;
+      nqr = fma(pr, MUT(7, -C, C), qr) * c;
     }
     M = fmax(M, fmax(fabs(npr), fabs(nqr)));
     if (xpi) M = fmax(M, fmax(fabs(npi), fabs(nqi)));
@@ -672,7 +681,7 @@ static double gsscl(int64_t l, const double *xr, const double *xi, double *yr, d
       yi[i] = ldexp(im, ey);
       M = fmax(M, fmax(fabs(yr[i]), fabs(yi[i])));
     } else {
-      yr[i] = ldexp(fma(-psr, x1, y1), ey);
+      yr[i] = ldexp(fma(MUT(11, -psr, psr), x1, y1), ey);
       M = fmax(M, fabs(yr[i]));
     }
   }
@@ -983,7 +992,7 @@ ORC_EXPORT int orc_svd_adjoint(int64_t m, int64_t n, const double *U, const doub
     for (int64_t j = 0; j < n; ++j) {
       double v = 0.0;
       if (i != j) {
-        const double F = 1.0 / (s[j] * s[j] - s[i] * s[i]);
+        const double F = MUT(12, 1.0 / (s[j] * s[j] - s[i] * s[i]), 1.0 / (s[i] * s[i] - s[j] * s[j]));
         v = F * (J[i + j * n] - J[j + i * n]) * s[j] + s[i] * F * (Kv[i + j * n] - Kv[j + i * n]);
       } else {
         v = sbar ? sbar[i] : 0.0;
