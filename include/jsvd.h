@@ -68,9 +68,9 @@ JSVD_API const char *jsvd_last_cuda_error(void);
 #define JSVD_TUNE_EVD_LAUNCH 1
 /*   JSVD_TUNE_SVD_GRID: value = most blocks of the persistent SVD sweep
  *     kernel (0 = as many as the pair chunks of a step, capped by
- *     residency); value2 = warps per block (1, 2, 4 or 8; 0 = 1 for FP64
- *     and 2 for FP32 sweeps in the per-warp step form, chosen from the
- *     number of pairs and SMs in the chunked one). */
+ *     residency); value2 = warps per block (1, 2, 4 or 8; 0 = 2 in the
+ *     per-warp step form, or 1 for FP64 sweeps with more pairs per step than
+ *     SMs; chosen from the number of pairs and SMs in the chunked one). */
 #define JSVD_TUNE_SVD_GRID 2
 /*   JSVD_TUNE_BATCH_WARPS: value = warps per block of the batched SVD
  *     kernel (1, 2, 4, 8 or 16), or 0 (the default): chosen when the batch

@@ -478,13 +478,14 @@ static int launch_sweeps(const MatViewT<T> &M, SvdState *state, double ups, int 
   // FP64 instructions for unshared rotations cost less than the chunked
   // form's block barriers and its coarser spread of pairs over the SMs).
   const bool warp_step = (g_svd_step != 1);
-  // warps per block: per-warp form 1 (FP64 sweeps) or 2 (FP32 sweeps), the
-  // fastest measured; chunked form the most (up to 8) that still leave a
-  // chunk of pairs for every SM
+  // warps per block: per-warp form 2, or 1 for FP64 sweeps with more pairs
+  // per step than SMs (measured: real 256 x 128 14.56 vs 14.75 ms with 2;
+  // complex 4096 x 2048 15.9 vs 16.4 s with 1); chunked form the most (up
+  // to 8) that still leave a chunk of pairs for every SM
   int W = g_svd_warps;
   if (W == 0) {
     if (warp_step) {
-      W = (sizeof(T) == 4) ? 2 : 1;
+      W = (sizeof(T) == 4 || Lp <= sms) ? 2 : 1;
     } else {
       W = 1;
       while (W < 8 && (Lp + 2 * W - 1) / (2 * W) >= sms) W *= 2;
