@@ -557,7 +557,7 @@ static void zdpscl_comp(int64_t m, const double *qr, const double *qi, const dou
       const double gqi = ldexp(qi[i], -eq), gpi = ldexp(pi[i], -ep);
       comp_term(gpi, gqi, &rs, &rt, &rs2, &rt2);
       comp_term(gpi, gqr, &is, &it, &is2, &it2);
-      comp_term(-gpr, gqi, &is, &it, &is2, &it2);
+      comp_term(MUT(17, -gpr, gpr), gqi, &is, &it, &is2, &it2);
     }
   }
   const double d = fq * fp;
@@ -607,7 +607,7 @@ static void gram(double a21r, double a21i, int e1, double f1, int e2, double f2,
   e12 += sA;
   e21 += sA;
   *a11 = ldexp(f12, e12);
-  *a22 = ldexp(f21, e21);
+  *a22 = ldexp(MUT(15, f21, f12), e21);
   *b21r = ldexp(a21r, sA);
   *b21i = ldexp(a21i, sA);
 }

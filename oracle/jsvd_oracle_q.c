@@ -30,6 +30,13 @@
 
 #define ORC_EXPORT __attribute__((visibility("default")))
 
+/* Mutation points for the pin tests (see jsvd_oracle.c): -DORC_MUTANT=k
+ * plants mistake k; by default the plain twin. */
+#ifndef ORC_MUTANT
+#define ORC_MUTANT 0
+#endif
+#define MUT(k, good, bad) ((ORC_MUTANT == (k)) ? (bad) : (good))
+
 typedef _Float128 q;
 
 /* from jsvd_oracle.c: the round-robin ordering table */
@@ -74,7 +81,7 @@ static void zsjac2_q(q a11, q a22, q a21r, q a21i, q *cphi, q *ctr, q *cti, q *l
   const q o = aa21 * 2;
   const q a = a11 - a22;
   const q tan2 = copysignf128(fminf128(fmaxf128(o / fabsf128(a), 0), SQRT_NU), a);
-  const q tan1 = tan2 / (1 + sqrtf128(fmaf128(tan2, tan2, 1)));
+  const q tan1 = tan2 / (MUT(16, 1, 2) + sqrtf128(fmaf128(tan2, tan2, 1)));
   const q sec2 = fmaf128(tan1, tan1, 1);
   *cphi = 1 / sqrtf128(sec2);
   *ctr = ca * tan1;

@@ -43,6 +43,12 @@ MUTANTS = {
           "tests/test_oracle_evd_fp32.py::test_prop_2_1_rotation_bounds"),
     14: ("fma(fh, fr, fr) in the (e, f) step of SM6.2",
           "tests/test_oracle_rnf.py"),
+    15: ("the scaled Grammian's a22 built from f_p/f_q (Alg. Gram)",
+          "tests/test_oracle_svd.py::test_svd_real_geometric"),
+    16: ("tan(phi) = tan(2phi) / (2 + sqrt(...)) in the binary128 twin",
+          "tests/test_oracle_twin.py::test_twin_evd_against_exact"),
+    17: ("the compensated imaginary stream with the wrong sign (reading R19)",
+          "tests/test_oracle_compensated.py"),
 }
 
 
