@@ -177,6 +177,19 @@ def cpu_oracle_evd(r, seed_salt=0):
     return dt, oracle.num_threads()
 
 
+def cpu_oracle_svd(A):
+    """Time the oracle's SVD (as it stands, OpenMP over the pairs of a step)
+    on the host matrix A once; (ms, threads, sweeps)."""
+    os.environ.setdefault("OMP_PROC_BIND", "spread")
+    os.environ.setdefault("OMP_PLACES", "cores")
+    os.environ.setdefault("OMP_DYNAMIC", "false")
+    import oracle
+    t0 = time.perf_counter()
+    r = oracle.vjsvd(A)
+    dt = time.perf_counter() - t0
+    return 1e3 * dt, oracle.num_threads(), int(r["sweeps"])
+
+
 
 # ---------------------------------------------------------------------------
 # the SVD workloads (reported beside the EVD headline)
@@ -258,6 +271,9 @@ def svd_bench(torch, J, workloads, dev):
     c1 = {"ms_per_svd": ms, "sweeps": info["sweeps"], "rotations": info["rotations"],
           "fp64_gflops": fl / ms / 1e6, "fp64_frac": fl / (ms * 1e-3) / DFMA_FLOPS}
     c1.update(accuracy(A1, r))
+    ms_o, thr_o, sw_o = cpu_oracle_svd(workloads.svd_normal())
+    c1["cpu_oracle"] = {"ms_per_svd": ms_o, "threads": thr_o, "sweeps": sw_o,
+                        "kind": "oracle", "sample": "the same matrix, once"}
     out["C1_real_256x128"] = c1
 
     # the same matrix in single precision (jsvd_svd_f32)
