@@ -271,9 +271,12 @@ def svd_bench(torch, J, workloads, dev):
     c1 = {"ms_per_svd": ms, "sweeps": info["sweeps"], "rotations": info["rotations"],
           "fp64_gflops": fl / ms / 1e6, "fp64_frac": fl / (ms * 1e-3) / DFMA_FLOPS}
     c1.update(accuracy(A1, r))
-    ms_o, thr_o, sw_o = cpu_oracle_svd(workloads.svd_normal())
-    c1["cpu_oracle"] = {"ms_per_svd": ms_o, "threads": thr_o, "sweeps": sw_o,
-                        "kind": "oracle", "sample": "the same matrix, once"}
+    try:
+        ms_o, thr_o, sw_o = cpu_oracle_svd(workloads.svd_normal())
+        c1["cpu_oracle"] = {"ms_per_svd": ms_o, "threads": thr_o, "sweeps": sw_o,
+                            "kind": "oracle", "sample": "the same matrix, once"}
+    except Exception as exc:  # host-side context only: the GPU figures stand without it
+        c1["cpu_oracle"] = {"error": repr(exc)}
     out["C1_real_256x128"] = c1
 
     # the same matrix in single precision (jsvd_svd_f32)
