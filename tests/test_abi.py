@@ -87,3 +87,29 @@ def test_argument_errors_need_no_gpu(lib):
     assert L.jsvd_tune_set(_native.JSVD_TUNE_EVD32_DIV, -1, 0) == 0
     assert L.jsvd_tune_set(_native.JSVD_TUNE_SVD_STEP, 3, 0) == -2
     assert L.jsvd_tune_set(_native.JSVD_TUNE_SVD_STEP, 0, 0) == 0
+
+
+def test_plain_c_user_compiles_and_runs(tmp_path):
+    """include/jsvd.h is a C header: a C99 program compiled with -pedantic
+    -Werror links libjsvd.so and gets the documented answers from the
+    host-side entry points (no GPU needed)."""
+    import subprocess
+    from paper_2202_08361_gb300 import build
+    lib = build.build()
+    exe = str(tmp_path / "c_abi_user")
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic",
+                    "-I" + os.path.join(ROOT, "include"),
+                    os.path.join(ROOT, "tests", "native", "c_abi_user.c"), "-o", exe,
+                    lib, "-Wl,-rpath," + os.path.dirname(lib)], check=True)
+    out = dict(line.split(" ", 1) for line in
+               subprocess.run([exe], check=True, capture_output=True, text=True).stdout.splitlines())
+    rc, size = out["svd_ws"].split()
+    assert rc == "0" and int(size) > 4096 * 2048 * 16
+    assert out["svd_ws_bad_n"] == "-4"
+    assert out["svd_ws_bad_opts"] == "-2"
+    assert out["host_ws"].split()[0] == "0" and int(out["host_ws"].split()[1]) > 0
+    assert out["evd_missing_stream"] == "-2"
+    assert out["evd_empty"] == "0"
+    assert out["tune_bad"] == "-2" and out["tune_ok"] == "0"
+    assert "workspace" in out["message"]
+
