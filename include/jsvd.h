@@ -50,10 +50,10 @@ extern "C" {
 
 typedef enum { JSVD_REAL = 0, JSVD_COMPLEX = 1 } jsvd_field;
 
-/* Library version as 10000*major + 100*minor + patch. */
+/* Library version as 10000*major + 100*minor + patch; never fails. */
 JSVD_API int jsvd_version(void);
 
-/* Static description of a return code (never NULL). */
+/* Static description of a return code (never NULL; any int is accepted). */
 JSVD_API const char *jsvd_strerror(int code);
 
 /* Text of the last CUDA error this host thread saw (after JSVD_E_CUDA). */
@@ -110,6 +110,9 @@ JSVD_API const char *jsvd_last_cuda_error(void);
  *     lanes; 1 = chunks of pairs in three block phases, one pair's rotation
  *     per lane.  The results are identical. */
 #define JSVD_TUNE_SVD_STEP 8
+/* Sets one of the knobs above for the whole process (not thread-safe with
+ * respect to launches running concurrently on other host threads).
+ * Errors: -1 unknown knob, -2 value out of range, -3 value2 out of range. */
 JSVD_API int jsvd_tune_set(int knob, int value, int value2);
 
 /* ------------------------------------------------------------------------
