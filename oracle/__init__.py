@@ -6,8 +6,8 @@ CPU-baseline leg may import this package; the library under
 paper_2202_08361_gb300/ never does.
 
 Functions:
-  dsjac2 / zsjac2     batched 2x2 EVD (Alg. d8jac2 / Listing 1)
-  zsjac2_scaled       the scaled eigenvalues lambda' of Listing 1
+  dsjac2 / zsjac2     batched 2x2 EVD (section 2, Alg. d8jac2 / z8jac2)
+  zsjac2_scaled       the scaled eigenvalues lambda' (Eq. e:lamsec)
   pairs               the round-robin parallel ordering (section 4.1 reading)
   vjsvd               one-sided Jacobi SVD after Alg. zvjsvd (section 4.3)
   svd_adjoint         thin real SVD adjoint (Townsend 2016)
@@ -60,7 +60,7 @@ def lib():
         L.orc_pairs.restype = ctypes.c_int
         L.orc_vjsvd.argtypes = [ctypes.c_int64, ctypes.c_int64, _d, _d, ctypes.c_int64, _d, _d,
                                 _d, _d, _d, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
-                                _i32, _i64]
+                                ctypes.c_int, _i32, _i64]
         L.orc_vjsvd.restype = ctypes.c_int
         L.orc_dpscl.argtypes = [ctypes.c_int64, _d, _d, _d, _d, ctypes.c_int, ctypes.c_double,
                                 ctypes.c_int, ctypes.c_double, ctypes.c_int, _d]
@@ -130,7 +130,7 @@ def dsjac2(a11, a22, a21):
 
 
 def zsjac2(a11, a22, a21r, a21i):
-    """Complex Hermitian 2x2 EVD (Listing 1): returns (cos_phi,
+    """Complex Hermitian 2x2 EVD (section 2, Alg. z8jac2): returns (cos_phi,
     cos_alpha tan_phi, sin_alpha tan_phi, lambda1, lambda2, zeta_p)."""
     a11, a22, a21r, a21i = _f64(a11), _f64(a22), _f64(a21r), _f64(a21i)
     r = a11.size
@@ -142,7 +142,7 @@ def zsjac2(a11, a22, a21r, a21i):
 
 
 def zsjac2_scaled(a11, a22, a21r, a21i):
-    """The scaled eigenvalues (lambda1', lambda2') of Listing 1."""
+    """The scaled eigenvalues (lambda1', lambda2') of Eq. e:lamsec."""
     a11, a22, a21r, a21i = _f64(a11), _f64(a22), _f64(a21r), _f64(a21i)
     r = a11.size
     l1, l2 = np.empty(r), np.empty(r)
@@ -160,10 +160,12 @@ def pairs(n):
     return tab[: nt - 1] if nt >= 2 else tab[:0]
 
 
-def vjsvd(A, max_sweeps=100, nthreads=0, permute=False, compensated=False):
+def vjsvd(A, max_sweeps=100, nthreads=0, permute=False, compensated=False, skr_shift=0):
     """One-sided Jacobi SVD of A (m x n, m >= n; real or complex).  permute
     applies the column swap P of section 2 during the sweeps; compensated
-    forms the scaled dot-products by Alg. zdpscl' / ddpscl'.
+    forms the scaled dot-products by Alg. zdpscl' / ddpscl'; skr_shift > 0
+    lowers the per-step rescaling threshold of section 3.2 (Eq. e:skr) by
+    2^skr_shift, so that the rescaling branch runs (results unchanged).
 
     Returns dict(U, sigma, sigma_e, sigma_f, V, status, sweeps, rotations,
     rescales).  sigma is sorted non-increasingly; A ~= U diag(sigma) V^H.
@@ -180,7 +182,7 @@ def vjsvd(A, max_sweeps=100, nthreads=0, permute=False, compensated=False):
     rot = np.zeros(1, dtype=np.int64)
     rc = lib().orc_vjsvd(m, n, _dp(Gr), _dp(Gi), m, _dp(Vr), _dp(Vi), _dp(sig), _dp(se),
                          _dp(sf), int(max_sweeps), 1 if permute else 0,
-                         1 if compensated else 0, int(nthreads),
+                         1 if compensated else 0, int(skr_shift), int(nthreads),
                          info.ctypes.data_as(_i32),
                          rot.ctypes.data_as(_i64))
     if rc < 0:
@@ -211,7 +213,7 @@ def dpscl(q, p, compensated=False, eq=0, fq=1.0, ep=0, fp=1.0):
 
 
 def q_zsjac2(a11, a22, a21r, a21i=None):
-    """The binary128 twin of the 2x2 EVD (Listing 1, binary128 constants):
+    """The binary128 twin of the 2x2 EVD (section 2, binary128 constants):
     (cos phi, Re e^{ia} tan phi, Im e^{ia} tan phi, lambda1, lambda2), each an
     (r, 2) array of (hi, lo) doubles with hi + lo the binary128 value."""
     a11, a22, a21r = _f64(a11), _f64(a22), _f64(a21r)

@@ -10,15 +10,19 @@
  *
  * Contents (each function cites the passage it follows):
  *   orc_dsjac2 / orc_zsjac2  batched 2x2 real symmetric / complex Hermitian
- *                            EVD, Alg. d8jac2 (supplement SM2.1) and
- *                            Listing 1 (section 2.3.1), element by element.
+ *                            EVD, restated from the equations of section 2
+ *                            (Eq. "e:z", "e:zpolar", "e:tan2", "e:jactan",
+ *                            "e:jacsec", "e:lamsec"), one matrix at a time,
+ *                            with the rounded operations of Alg. d8jac2 /
+ *                            z8jac2 in their order.
  *   orc_ssjac2 / orc_csjac2  the same in single precision with the
  *                            binary32 constants of section 2.4.
  *   orc_pairs                the cyclic parallel pivot ordering (round-robin
  *                            reading of section 4.1).
  *   orc_vjsvd                one-sided Jacobi SVD after Alg. zvjsvd
  *                            (section 4.3), real or complex (split planes),
- *                            with the rescaling heuristic of section 3.2,
+ *                            with the rescaling heuristic of section 3.2
+ *                            (its threshold lowerable for the tests),
  *                            the scaled dot-products of Alg. zdpscl
  *                            (section 3.3) or, optionally, Alg. zdpscl' /
  *                            ddpscl' (compensated, supplement SM2.2),
@@ -35,12 +39,12 @@
  * explicit fma() call, exactly where the paper writes one.
  *
  * Readings of the paper where it is silent:
- *   - zeta of an all-zero 2x2 matrix follows Listing 1 (frexp of the
+ *   - zeta of an all-zero 2x2 matrix follows section 2.3.1 (frexp of the
  *     smallest subnormal), so zeta is a finite int in [-3, 2094];
  *   - the packed (zeta' << 1) | p is formed by an unsigned shift;
  *   - the column swap P of section 2 (Alg. zvjsvd: U P) is optional, as
- *     section 2 makes it ("if the orthogonalized pivot columns are also to
- *     be ordered"): with permute != 0 the EVD is computed for every pivot
+ *     section 2 needs it only when the transformed pivot columns must also
+ *     come out sorted by norm: with permute != 0 the EVD is computed for every pivot
  *     pair, a rotated pair is transformed by U P and a pair that is not
  *     rotated is swapped iff its EVD says lambda1' < lambda2'; with
  *     permute == 0 (the default) no column moves during the sweeps -- with
@@ -76,11 +80,42 @@
 #endif
 #define MUT(k, good, bad) ((ORC_MUTANT == (k)) ? (bad) : (good))
 
-/* fl(sqrt(nu)) from Eq. (2.4 "e:tan2"), as printed in Listing 1. */
-static const double SQRT_NU = 1.34078079299425956E+154;
+/* ------------------------------------------------------------------------
+ * The 2x2 Hermitian EVD of section 2, restated from its equations:
+ *   Eq. "e:z"       the power-of-two scaling A' = 2^zeta A;
+ *   Eq. "e:zpolar"  the polar form |a21| e^{i alpha} of a21 (complex), with
+ *                   |a21| from Alg. hypot (Eq. "e:hypot");
+ *   Eq. "e:tan2", "e:jactan", "e:jacsec", "e:lamsec"   the rotation and
+ *                   the eigenvalues of section 2.1.
+ * Every rounded operation below is one the equations write, in their
+ * order, so the results are those of Alg. d8jac2 / z8jac2 lane by lane. */
 
-/* x with its sign bit XOR-ed with the sign bit of s (the AVX-512 `xor`
- * sign transfer of Alg. d8jac2). */
+/* floor(lg x) for finite x > 0 (the AVX-512 getexp; subnormals too). */
+static int flg(double x)
+{
+  int e;
+  (void)frexp(x, &e);
+  return e - 1;
+}
+
+static int imin(int a, int b) { return (a <= b) ? a : b; }
+
+/* nu, the largest finite value, and mu-check, the smallest positive
+ * subnormal (section 2.2). */
+#define NU DBL_MAX
+#define MU_CHECK DBL_TRUE_MIN
+
+/* zeta_x of Eq. "e:z": eta - floor(lg|x|) with eta = floor(lg(nu/8)) =
+ * 1020.  lg 0 is read as lg mu-check (the serial scaling of section 2.3.1),
+ * so an all-zero matrix gets the finite zeta = 1020 + 1074 = 2094. */
+static int zeta_elem(double x)
+{
+  const int eta = flg(NU / 8.0) + MUT(5, 0, 1);
+  return eta - flg(fmax(fabs(x), MU_CHECK));
+}
+
+/* x sign(s), sign(+-0) = +-1: the sign bit of s XOR-ed into x, exact (the
+ * sign transfer Alg. d8jac2 applies to tan(phi)). */
 static double xorsign(double x, double s)
 {
   uint64_t a, b;
@@ -91,17 +126,100 @@ static double xorsign(double x, double s)
   return x;
 }
 
-/* One element of Eq. "e:z" as Listing 1 computes it: eta' - frexp exponent
- * of max(|x|, smallest subnormal), eta' = DBL_MAX_EXP - 3 = 1021.  This is
- * eta - floor(lg|x|) with eta = 1020, and 2094 for x = 0. */
-static int zeta_of(double x)
+/* Alg. hypot: sqrt(x^2 + y^2) = M sqrt(q^2 + 1), q = m / M, m and M the
+ * smaller and larger of |x|, |y| (Eq. "e:hypot"); fmax(., 0) turns the
+ * 0/0 of x = y = 0 into q = 0.  Also the |z| of Alg. cvg. */
+static double hypot_naive(double x, double y)
 {
-  int e;
-  (void)frexp(fmax(fabs(x), DBL_TRUE_MIN), &e);
-  return MUT(5, (DBL_MAX_EXP - 3), (DBL_MAX_EXP - 2)) - e;
+  const double ax = fabs(x), ay = fabs(y);
+  const double m = fmin(ax, ay), M = fmax(ax, ay);
+  const double q = fmax(m / M, 0.0);
+  return sqrt(fma(q, q, 1.0)) * M;
 }
 
-static int imin(int a, int b) { return (a <= b) ? a : b; }
+/* Section 2.1 for an already scaled matrix: only |a21| enters. */
+struct jacrot {
+  double tan_phi;  /* tan(phi) >= 0 iff a11 - a22 >= 0            */
+  double sec2_phi; /* sec^2(phi)                                   */
+  double cos_phi;  /* 1 / sec(phi)                                 */
+  double lam1, lam2; /* the eigenvalues lambda' of the scaled matrix */
+};
+
+static void jacobi_rotation(double a11, double a22, double abs_a21, struct jacrot *J)
+{
+  /* Eq. "e:tan2": tan(2phi) = min(fmax(2|a21| / |a|, 0), fl(sqrt nu)) sign a
+   * with a = a11 - a22.  2|a21| is exact; fmax sends 0/0 to 0, so the min
+   * never sees a NaN; the sign of a is copied in, an exact multiply by +-1. */
+  const double two_abs_a21 = 2.0 * abs_a21;
+  const double a = a11 - a22;
+  const double tan_2phi = copysign(fmin(fmax(two_abs_a21 / fabs(a), 0.0), sqrt(NU)), a);
+  /* Eq. "e:jactan" */
+  const double t = tan_2phi / (1.0 + sqrt(fma(tan_2phi, tan_2phi, 1.0)));
+  /* Eq. "e:jacsec": sec^2 = fma(tan, tan, 1), sec = sqrt(sec^2), cos = 1/sec */
+  const double sec2 = fma(t, t, 1.0);
+  J->tan_phi = t;
+  J->sec2_phi = sec2;
+  J->cos_phi = MUT(2, 1.0 / sqrt(sec2), 1.0 / sec2);
+  /* Eq. "e:lamsec": lambda_1 = ((a22 tan + 2|a21|) tan + a11) / sec^2,
+   *                 lambda_2 = ((a11 tan - 2|a21|) tan + a22) / sec^2 */
+  J->lam1 = fma(fma(MUT(1, a22, a11), t, two_abs_a21), t, a11) / sec2;
+  J->lam2 = fma(fma(a11, t, -two_abs_a21), t, a22) / sec2;
+}
+
+/* What one EVD returns (section 2.3): cos(phi), e^{i alpha} tan(phi), the
+ * backscaled eigenvalues lambda = 2^-zeta lambda', the scaled lambda', zeta
+ * and the permutation bit p = (lambda1' < lambda2'). */
+struct evd2 {
+  double cos_phi, eatan_re, eatan_im;
+  double lam1, lam2, lam1s, lam2s;
+  int zeta, p;
+};
+
+static void evd2_finish(const struct jacrot *J, int zeta, struct evd2 *o)
+{
+  o->cos_phi = J->cos_phi;
+  o->lam1s = J->lam1;
+  o->lam2s = J->lam2;
+  o->lam1 = scalbn(J->lam1, -zeta);
+  o->lam2 = scalbn(J->lam2, -zeta);
+  o->zeta = zeta;
+  o->p = (J->lam1 < J->lam2);
+}
+
+/* Real symmetric EVD (Alg. d8jac2, one lane): e^{i alpha} = sign a21. */
+static void evd2_real(double a11, double a22, double a21, struct evd2 *o)
+{
+  const int zeta = imin(imin(zeta_elem(a11), zeta_elem(a22)), zeta_elem(a21));
+  a11 = scalbn(a11, zeta);
+  a22 = scalbn(a22, zeta);
+  a21 = scalbn(a21, zeta);
+  struct jacrot J;
+  jacobi_rotation(a11, a22, fabs(a21), &J);
+  o->eatan_re = MUT(3, xorsign(J.tan_phi, a21), J.tan_phi);
+  o->eatan_im = 0.0;
+  evd2_finish(&J, zeta, o);
+}
+
+/* Complex Hermitian EVD (Alg. z8jac2, one lane). */
+static void evd2_complex(double a11, double a22, double a21r, double a21i, struct evd2 *o)
+{
+  const int zeta = imin(imin(zeta_elem(a11), zeta_elem(a22)),
+                        imin(zeta_elem(a21r), zeta_elem(a21i)));
+  a11 = scalbn(a11, zeta);
+  a22 = scalbn(a22, zeta);
+  a21r = scalbn(a21r, zeta);
+  a21i = scalbn(a21i, zeta);
+  /* Eq. "e:zpolar": cos(alpha) = fmin(|Re a21| / |a21|, 1) sign(Re a21),
+   * sin(alpha) = Im a21 / max(|a21|, mu-check) */
+  const double abs_a21 = hypot_naive(a21r, a21i);
+  const double cos_alpha = copysign(fmin(fabs(a21r) / abs_a21, 1.0), a21r);
+  const double sin_alpha = MUT(4, a21i, -a21i) / fmax(abs_a21, MU_CHECK);
+  struct jacrot J;
+  jacobi_rotation(a11, a22, abs_a21, &J);
+  o->eatan_re = cos_alpha * J.tan_phi;
+  o->eatan_im = sin_alpha * J.tan_phi;
+  evd2_finish(&J, zeta, o);
+}
 
 /* Pack (zeta' << 1) | p, zeta' = -zeta, through an unsigned shift (a
  * negative int may not be left-shifted in C). */
@@ -111,111 +229,74 @@ static int32_t pack_zp(int zeta, int p)
   return (int32_t)(u | (uint32_t)(p != 0));
 }
 
-/* Real symmetric 2x2 EVD, Alg. d8jac2 with s = 1 (supplement SM2.1).
- * Outputs cos(phi), sign(a21)*tan(phi), the backscaled eigenvalues, the
- * packed (zeta', p).  lam1s/lam2s receive the scaled lambda' (may be NULL). */
-static void dsjac2_1(double a11, double a22, double a21, double *cphi, double *tphi,
-                     double *lam1, double *lam2, int32_t *zp, double *lam1s, double *lam2s)
-{
-  /* Eq. "e:z": the power-of-two scaling exponent, then A' = 2^zeta A. */
-  const int zeta = imin(imin(zeta_of(a11), zeta_of(a22)), zeta_of(a21));
-  a21 = scalbn(a21, zeta);
-  a11 = scalbn(a11, zeta);
-  a22 = scalbn(a22, zeta);
-  /* "polar form" of a real a21: |a21| and sign(a21) */
-  const double aa21 = fabs(a21);
-  /* Eq. "e:tan2" */
-  const double o = 2.0 * aa21; /* exact doubling (scalef by 1) */
-  const double a = a11 - a22;
-  const double tan2 = copysign(fmin(fmax(o / fabs(a), 0.0), SQRT_NU), a);
-  /* Eq. "e:jactan" */
-  const double tan1 = tan2 / (1.0 + sqrt(fma(tan2, tan2, 1.0)));
-  /* Eq. "e:jacsec" */
-  const double sec2 = fma(tan1, tan1, 1.0);
-  const double sec = sqrt(sec2);
-  *cphi = MUT(2, 1.0 / sec, 1.0 / sec2);
-  *tphi = MUT(3, xorsign(tan1, a21), tan1);
-  /* Eq. "e:lamsec" */
-  const double l1 = fma(tan1, fma(MUT(1, a22, a11), tan1, o), a11) / sec2;
-  const double l2 = fma(tan1, fma(a11, tan1, -o), a22) / sec2;
-  if (lam1) *lam1 = scalbn(l1, -zeta);
-  if (lam2) *lam2 = scalbn(l2, -zeta);
-  if (lam1s) *lam1s = l1;
-  if (lam2s) *lam2s = l2;
-  if (zp) *zp = pack_zp(zeta, l1 < l2);
-}
-
-/* Complex Hermitian 2x2 EVD, Listing 1 (section 2.3.1).  Outputs
- * cos(phi), cos(alpha)tan(phi), sin(alpha)tan(phi), lambda1, lambda2 and
- * the packed (zeta', p). */
-static void zsjac2_1(double a11, double a22, double a21r, double a21i, double *cphi,
-                     double *catphi, double *satphi, double *lam1, double *lam2,
-                     int32_t *zp, double *lam1s, double *lam2s)
-{
-  const int zeta = imin(imin(zeta_of(a11), zeta_of(a22)), imin(zeta_of(a21r), zeta_of(a21i)));
-  a21r = scalbn(a21r, zeta);
-  a21i = scalbn(a21i, zeta);
-  a11 = scalbn(a11, zeta);
-  a22 = scalbn(a22, zeta);
-  /* polar form of a21', Eq. "e:zpolar" with the naive hypot of Alg. hypot */
-  const double ar = fabs(a21r), ai = fabs(a21i);
-  const double am = fmin(ar, ai), aM = fmax(ar, ai);
-  const double mM = fmax(am / aM, 0.0);
-  const double aa21 = sqrt(fma(mM, mM, 1.0)) * aM;
-  const double calpha = copysign(fmin(ar / aa21, 1.0), a21r);
-  const double salpha = MUT(4, a21i, -a21i) / fmax(aa21, DBL_TRUE_MIN);
-  /* the Jacobi rotation, section 2.1 */
-  const double o = aa21 * 2.0;
-  const double a = a11 - a22;
-  const double tan2 = copysign(fmin(fmax(o / fabs(a), 0.0), SQRT_NU), a);
-  const double tan1 = tan2 / (1.0 + sqrt(fma(tan2, tan2, 1.0)));
-  const double sec2 = fma(tan1, tan1, 1.0);
-  const double sec = sqrt(sec2);
-  *cphi = 1.0 / sec;
-  *catphi = calpha * tan1;
-  *satphi = salpha * tan1;
-  const double l1 = fma(tan1, fma(a22, tan1, o), a11) / sec2;
-  const double l2 = fma(tan1, fma(a11, tan1, -o), a22) / sec2;
-  if (lam1) *lam1 = scalbn(l1, -zeta);
-  if (lam2) *lam2 = scalbn(l2, -zeta);
-  if (lam1s) *lam1s = l1;
-  if (lam2s) *lam2s = l2;
-  if (zp) *zp = pack_zp(zeta, l1 < l2);
-}
-
-/* Batched real EVD (Alg. dbjac2); any pointer except the inputs, cphi and
- * tphi may be NULL. */
+/* Batched real EVD (Alg. dbjac2): outputs cos(phi), sign(a21) tan(phi),
+ * lambda1, lambda2 and the packed (zeta', p); lam1, lam2, zp may be NULL. */
 ORC_EXPORT void orc_dsjac2(int64_t r, const double *a11, const double *a22, const double *a21,
                            double *cphi, double *tphi, double *lam1, double *lam2, int32_t *zp)
 {
 #pragma omp parallel for schedule(static)
-  for (int64_t i = 0; i < r; ++i)
-    dsjac2_1(a11[i], a22[i], a21[i], cphi + i, tphi + i, lam1 ? lam1 + i : NULL,
-             lam2 ? lam2 + i : NULL, zp ? zp + i : NULL, NULL, NULL);
+  for (int64_t i = 0; i < r; ++i) {
+    struct evd2 o;
+    evd2_real(a11[i], a22[i], a21[i], &o);
+    cphi[i] = o.cos_phi;
+    tphi[i] = o.eatan_re;
+    if (lam1) lam1[i] = o.lam1;
+    if (lam2) lam2[i] = o.lam2;
+    if (zp) zp[i] = pack_zp(o.zeta, o.p);
+  }
 }
 
-/* Batched complex EVD (Alg. zbjac2). */
+/* Batched complex EVD (Alg. zbjac2): outputs cos(phi), cos(alpha) tan(phi),
+ * sin(alpha) tan(phi), lambda1, lambda2 and the packed (zeta', p). */
 ORC_EXPORT void orc_zsjac2(int64_t r, const double *a11, const double *a22, const double *a21r,
                            const double *a21i, double *cphi, double *catphi, double *satphi,
                            double *lam1, double *lam2, int32_t *zp)
 {
 #pragma omp parallel for schedule(static)
-  for (int64_t i = 0; i < r; ++i)
-    zsjac2_1(a11[i], a22[i], a21r[i], a21i[i], cphi + i, catphi + i, satphi + i,
-             lam1 ? lam1 + i : NULL, lam2 ? lam2 + i : NULL, zp ? zp + i : NULL, NULL, NULL);
+  for (int64_t i = 0; i < r; ++i) {
+    struct evd2 o;
+    evd2_complex(a11[i], a22[i], a21r[i], a21i[i], &o);
+    cphi[i] = o.cos_phi;
+    catphi[i] = o.eatan_re;
+    satphi[i] = o.eatan_im;
+    if (lam1) lam1[i] = o.lam1;
+    if (lam2) lam2[i] = o.lam2;
+    if (zp) zp[i] = pack_zp(o.zeta, o.p);
+  }
+}
+
+/* The scaled eigenvalues lambda' (before backscaling) of the complex EVD,
+ * for the pins. */
+ORC_EXPORT void orc_zsjac2_scaled(int64_t r, const double *a11, const double *a22,
+                                  const double *a21r, const double *a21i, double *lam1s,
+                                  double *lam2s)
+{
+  for (int64_t i = 0; i < r; ++i) {
+    struct evd2 o;
+    evd2_complex(a11[i], a22[i], a21r[i], a21i[i], &o);
+    lam1s[i] = o.lam1s;
+    lam2s[i] = o.lam2s;
+  }
 }
 
 /* ------------------------------------------------------------------------
- * Single precision (section 2.4: nu = FLT_MAX, fl(sqrt nu) = 1.844674297E+19,
- * mu = FLT_TRUE_MIN, eta = FLT_MAX_EXP - 4; every operation in binary32).
- * Same steps as dsjac2_1 / zsjac2_1. */
-static const float SQRT_NU_F = 1.844674297E+19f;
+ * The same EVD in single precision (section 2.4): nu = FLT_MAX, mu-check =
+ * FLT_TRUE_MIN, eta = floor(lg(nu/8)) = 124, every operation in binary32.
+ * The steps are those of the binary64 functions above. */
+#define NU_F FLT_MAX
+#define MU_CHECK_F FLT_TRUE_MIN
 
-static int zeta_of_f(float x)
+static int flgf(float x)
 {
   int e;
-  (void)frexpf(fmaxf(fabsf(x), FLT_TRUE_MIN), &e);
-  return (FLT_MAX_EXP - 3) - e;
+  (void)frexpf(x, &e);
+  return e - 1;
+}
+
+static int zeta_elem_f(float x)
+{
+  const int eta = flgf(NU_F / 8.0f);
+  return eta - flgf(fmaxf(fabsf(x), MU_CHECK_F));
 }
 
 static float xorsignf_(float x, float s)
@@ -228,68 +309,48 @@ static float xorsignf_(float x, float s)
   return x;
 }
 
-static void ssjac2_1(float a11, float a22, float a21, float *cphi, float *tphi, float *lam1,
-                     float *lam2, int32_t *zp)
+static float hypot_naive_f(float x, float y)
 {
-  const int zeta = imin(imin(zeta_of_f(a11), zeta_of_f(a22)), zeta_of_f(a21));
-  a21 = scalbnf(a21, zeta);
-  a11 = scalbnf(a11, zeta);
-  a22 = scalbnf(a22, zeta);
-  const float aa21 = fabsf(a21);
-  const float o = 2.0f * aa21;
-  const float a = a11 - a22;
-  const float tan2 = copysignf(fminf(fmaxf(o / fabsf(a), 0.0f), SQRT_NU_F), a);
-  const float tan1 = tan2 / (1.0f + sqrtf(fmaf(tan2, tan2, 1.0f)));
-  const float sec2 = fmaf(tan1, tan1, 1.0f);
-  const float sec = sqrtf(sec2);
-  *cphi = MUT(13, 1.0f / sec, 1.0f / sec2);
-  *tphi = xorsignf_(tan1, a21);
-  const float l1 = fmaf(tan1, fmaf(a22, tan1, o), a11) / sec2;
-  const float l2 = fmaf(tan1, fmaf(a11, tan1, -o), a22) / sec2;
-  if (lam1) *lam1 = scalbnf(l1, -zeta);
-  if (lam2) *lam2 = scalbnf(l2, -zeta);
-  if (zp) *zp = pack_zp(zeta, l1 < l2);
+  const float ax = fabsf(x), ay = fabsf(y);
+  const float m = fminf(ax, ay), M = fmaxf(ax, ay);
+  const float q = fmaxf(m / M, 0.0f);
+  return sqrtf(fmaf(q, q, 1.0f)) * M;
 }
 
-static void csjac2_1(float a11, float a22, float a21r, float a21i, float *cphi, float *catphi,
-                     float *satphi, float *lam1, float *lam2, int32_t *zp)
+struct jacrot_f {
+  float tan_phi, sec2_phi, cos_phi, lam1, lam2;
+};
+
+static void jacobi_rotation_f(float a11, float a22, float abs_a21, struct jacrot_f *J)
 {
-  const int zeta =
-      imin(imin(zeta_of_f(a11), zeta_of_f(a22)), imin(zeta_of_f(a21r), zeta_of_f(a21i)));
-  a21r = scalbnf(a21r, zeta);
-  a21i = scalbnf(a21i, zeta);
-  a11 = scalbnf(a11, zeta);
-  a22 = scalbnf(a22, zeta);
-  const float ar = fabsf(a21r), ai = fabsf(a21i);
-  const float am = fminf(ar, ai), aM = fmaxf(ar, ai);
-  const float mM = fmaxf(am / aM, 0.0f);
-  const float aa21 = sqrtf(fmaf(mM, mM, 1.0f)) * aM;
-  const float calpha = copysignf(fminf(ar / aa21, 1.0f), a21r);
-  const float salpha = a21i / fmaxf(aa21, FLT_TRUE_MIN);
-  const float o = aa21 * 2.0f;
+  const float two_abs_a21 = 2.0f * abs_a21;                                /* Eq. "e:tan2" */
   const float a = a11 - a22;
-  const float tan2 = copysignf(fminf(fmaxf(o / fabsf(a), 0.0f), SQRT_NU_F), a);
-  const float tan1 = tan2 / (1.0f + sqrtf(fmaf(tan2, tan2, 1.0f)));
-  const float sec2 = fmaf(tan1, tan1, 1.0f);
-  const float sec = sqrtf(sec2);
-  *cphi = 1.0f / sec;
-  *catphi = calpha * tan1;
-  *satphi = salpha * tan1;
-  const float l1 = fmaf(tan1, fmaf(a22, tan1, o), a11) / sec2;
-  const float l2 = fmaf(tan1, fmaf(a11, tan1, -o), a22) / sec2;
-  if (lam1) *lam1 = scalbnf(l1, -zeta);
-  if (lam2) *lam2 = scalbnf(l2, -zeta);
-  if (zp) *zp = pack_zp(zeta, l1 < l2);
+  const float tan_2phi = copysignf(fminf(fmaxf(two_abs_a21 / fabsf(a), 0.0f), sqrtf(NU_F)), a);
+  const float t = tan_2phi / (1.0f + sqrtf(fmaf(tan_2phi, tan_2phi, 1.0f))); /* "e:jactan" */
+  const float sec2 = fmaf(t, t, 1.0f);                                       /* "e:jacsec" */
+  J->tan_phi = t;
+  J->sec2_phi = sec2;
+  J->cos_phi = MUT(13, 1.0f / sqrtf(sec2), 1.0f / sec2);
+  J->lam1 = fmaf(fmaf(a22, t, two_abs_a21), t, a11) / sec2;                   /* "e:lamsec" */
+  J->lam2 = fmaf(fmaf(a11, t, -two_abs_a21), t, a22) / sec2;
 }
 
-/* Batched single precision EVDs (the s/c variants of Alg. dbjac2 / zbjac2). */
 ORC_EXPORT void orc_ssjac2(int64_t r, const float *a11, const float *a22, const float *a21,
                            float *cphi, float *tphi, float *lam1, float *lam2, int32_t *zp)
 {
 #pragma omp parallel for schedule(static)
-  for (int64_t i = 0; i < r; ++i)
-    ssjac2_1(a11[i], a22[i], a21[i], cphi + i, tphi + i, lam1 ? lam1 + i : NULL,
-             lam2 ? lam2 + i : NULL, zp ? zp + i : NULL);
+  for (int64_t i = 0; i < r; ++i) {
+    const int zeta = imin(imin(zeta_elem_f(a11[i]), zeta_elem_f(a22[i])), zeta_elem_f(a21[i]));
+    const float b11 = scalbnf(a11[i], zeta), b22 = scalbnf(a22[i], zeta);
+    const float b21 = scalbnf(a21[i], zeta);
+    struct jacrot_f J;
+    jacobi_rotation_f(b11, b22, fabsf(b21), &J);
+    cphi[i] = J.cos_phi;
+    tphi[i] = xorsignf_(J.tan_phi, b21);
+    if (lam1) lam1[i] = scalbnf(J.lam1, -zeta);
+    if (lam2) lam2[i] = scalbnf(J.lam2, -zeta);
+    if (zp) zp[i] = pack_zp(zeta, J.lam1 < J.lam2);
+  }
 }
 
 ORC_EXPORT void orc_csjac2(int64_t r, const float *a11, const float *a22, const float *a21r,
@@ -297,20 +358,22 @@ ORC_EXPORT void orc_csjac2(int64_t r, const float *a11, const float *a22, const 
                            float *lam1, float *lam2, int32_t *zp)
 {
 #pragma omp parallel for schedule(static)
-  for (int64_t i = 0; i < r; ++i)
-    csjac2_1(a11[i], a22[i], a21r[i], a21i[i], cphi + i, catphi + i, satphi + i,
-             lam1 ? lam1 + i : NULL, lam2 ? lam2 + i : NULL, zp ? zp + i : NULL);
-}
-
-/* Scaled eigenvalues lambda' (before backscaling) for the pins. */
-ORC_EXPORT void orc_zsjac2_scaled(int64_t r, const double *a11, const double *a22,
-                                  const double *a21r, const double *a21i, double *lam1s,
-                                  double *lam2s)
-{
   for (int64_t i = 0; i < r; ++i) {
-    double c, ct, st;
-    zsjac2_1(a11[i], a22[i], a21r[i], a21i[i], &c, &ct, &st, NULL, NULL, NULL, lam1s + i,
-             lam2s + i);
+    const int zeta = imin(imin(zeta_elem_f(a11[i]), zeta_elem_f(a22[i])),
+                          imin(zeta_elem_f(a21r[i]), zeta_elem_f(a21i[i])));
+    const float b11 = scalbnf(a11[i], zeta), b22 = scalbnf(a22[i], zeta);
+    const float br = scalbnf(a21r[i], zeta), bi = scalbnf(a21i[i], zeta);
+    const float abs_a21 = hypot_naive_f(br, bi);                               /* "e:zpolar" */
+    const float cos_alpha = copysignf(fminf(fabsf(br) / abs_a21, 1.0f), br);
+    const float sin_alpha = bi / fmaxf(abs_a21, MU_CHECK_F);
+    struct jacrot_f J;
+    jacobi_rotation_f(b11, b22, abs_a21, &J);
+    cphi[i] = J.cos_phi;
+    catphi[i] = cos_alpha * J.tan_phi;
+    satphi[i] = sin_alpha * J.tan_phi;
+    if (lam1) lam1[i] = scalbnf(J.lam1, -zeta);
+    if (lam2) lam2[i] = scalbnf(J.lam2, -zeta);
+    if (zp) zp[i] = pack_zp(zeta, J.lam1 < J.lam2);
   }
 }
 
@@ -357,13 +420,6 @@ ORC_EXPORT int orc_pairs(int n, int32_t *tab)
 #define ORC_E_NONFINITE (-2)
 #define ORC_NOT_CONVERGED 1
 
-/* floor(lg x) for finite x > 0 (the AVX-512 getexp). */
-static int flg(double x)
-{
-  int e;
-  (void)frexp(x, &e);
-  return e - 1;
-}
 
 /* The Frobenius norm of a column (one or two planes, length m) as (e, f):
  * ||x|| = 2^e f, 1 <= f < 2; zero is (INT_MIN, 1) (section 3.2, the (e,f)
@@ -581,16 +637,6 @@ ORC_EXPORT int orc_dpscl(int64_t m, const double *qr, const double *qi, const do
   return ORC_OK;
 }
 
-/* Alg. hypot, the naive reproducible |z| used by Alg. cvg. */
-static double hypot_naive(double x, double y)
-{
-  x = fabs(x);
-  y = fabs(y);
-  const double m = fmin(x, y), M = fmax(x, y);
-  const double q = fmax(m / M, 0.0);
-  return sqrt(fma(q, q, 1.0)) * M;
-}
-
 /* Alg. Gram: the non-overflowing scaled Grammian A'' from a21' and the
  * (e,f) norms of g_p (1) and g_q (2). */
 static void gram(double a21r, double a21i, int e1, double f1, int e2, double f2, double *a11,
@@ -729,14 +775,21 @@ ORC_EXPORT int orc_num_threads(void)
  *   permute != 0 applies the column swap P during the sweeps.
  *   compensated != 0 forms the scaled dot-products by Alg. zdpscl' /
  *     ddpscl' (supplement SM2.2) instead of Alg. zdpscl.
+ *   skr_shift >= 0 lowers the threshold of the per-step rescaling test of
+ *     section 3.2 by 2^skr_shift: step k downscales G (by 2^{s_[k]}, Eq.
+ *     "e:skn") when s_(k) - skr_shift < 0 (Eq. "e:skr").  0 is the paper's
+ *     test, which the initial scaling keeps from firing unless the max-norm
+ *     grows by about 2m; a positive shift makes the branch run on ordinary
+ *     inputs, so that the tests can pin it.  Power-of-two scaling is exact,
+ *     so without underflow the results do not depend on the shift.
  * nthreads <= 0 leaves the OpenMP default.
  */
 ORC_EXPORT int orc_vjsvd(int64_t m, int64_t n, double *Gr, double *Gi, int64_t ld, double *Vr,
                          double *Vi, double *sig, double *sig_e, double *sig_f, int max_sweeps,
-                         int permute, int compensated, int nthreads, int32_t *out_info,
-                         int64_t *rotations64)
+                         int permute, int compensated, int skr_shift, int nthreads,
+                         int32_t *out_info, int64_t *rotations64)
 {
-  if (m < 1 || n < 1 || m < n || ld < m || max_sweeps < 1) return ORC_E_ARG;
+  if (m < 1 || n < 1 || m < n || ld < m || max_sweeps < 1 || skr_shift < 0) return ORC_E_ARG;
 #ifdef _OPENMP
   if (nthreads > 0) omp_set_num_threads(nthreads);
 #else
@@ -779,17 +832,19 @@ ORC_EXPORT int orc_vjsvd(int64_t m, int64_t n, double *Gr, double *Gi, int64_t l
     for (int C = 0; C < max_sweeps && !converged; ++C) {
       int64_t T = 0;
       for (int k = 0; k < K; ++k) {
-        /* step 2 of the heuristic: s_(k) < 0 => downscale by 2^{s_[k]} */
+        /* steps 2-4 of the heuristic: s_(k) < 0 (Eq. "e:skr") => G is
+         * downscaled by 2^{s_[k]} (Eq. "e:skn"), M~ with it, and s_[k] is
+         * added to the running scale exponent s */
         const int sk_r = lg_skr - flg(Mt) - (cplx ? 1 : 0);
-        if (sk_r < 0) {
+        if (sk_r - skr_shift < 0) {
           const int sk_n = lg_skn - flg(Mt) - 1;
           for (int64_t j = 0; j < n; ++j)
             for (int64_t i = 0; i < m; ++i) {
-              Gr[i + j * ld] = ldexp(Gr[i + j * ld], sk_n);
-              if (cplx) Gi[i + j * ld] = ldexp(Gi[i + j * ld], sk_n);
+              Gr[i + j * ld] = ldexp(Gr[i + j * ld], MUT(19, sk_n, -sk_n));
+              if (cplx) Gi[i + j * ld] = ldexp(Gi[i + j * ld], MUT(19, sk_n, -sk_n));
             }
           Mt = ldexp(Mt, sk_n);
-          s += sk_n;
+          s += MUT(18, sk_n, 0);
           ++rescales;
         }
         int64_t t = 0;
@@ -828,13 +883,13 @@ ORC_EXPORT int orc_vjsvd(int64_t m, int64_t n, double *Gr, double *Gi, int64_t l
           /* Alg. Gram, then the EVD (Alg. zbjac2 / dbjac2) */
           double b11, b22, b21r, b21i;
           gram(zr, zi, ep, fp, eq, fq, &b11, &b22, &b21r, &b21i);
-          double c, Ct, St = 0.0;
-          int32_t zp;
+          struct evd2 ev;
           if (cplx)
-            zsjac2_1(b11, b22, b21r, b21i, &c, &Ct, &St, NULL, NULL, &zp, NULL, NULL);
+            evd2_complex(b11, b22, b21r, b21i, &ev);
           else
-            dsjac2_1(b11, b22, b21r, &c, &Ct, NULL, NULL, &zp, NULL, NULL);
-          const int pbit = permute ? (zp & 1) : 0;
+            evd2_real(b11, b22, b21r, &ev);
+          const double c = ev.cos_phi, Ct = ev.eatan_re, St = ev.eatan_im;
+          const int pbit = permute ? ev.p : 0;
           /* Alg. zvjsvd: when Eq. "e:GScond" holds, Alg. ZGS / DGS replaces
            * zjrot on G; V still takes the rotation */
           const int gs_pq = rot && gs_cond(ep, fp, eq, fq, ups);

@@ -5,10 +5,11 @@
  * FP64 oracle in IEEE binary128 (_Float128 with glibc's f128 functions), so
  * that the tests can measure the FP64 oracle against results carrying 60
  * more bits:
- *   orc_q_zsjac2  the 2x2 Hermitian EVD of Listing 1 with the binary128
- *                 constants the paper prescribes for other formats (section
- *                 2.4: nu = FLT128_MAX, fl(sqrt nu), mu = FLT128_TRUE_MIN,
- *                 eta = FLT128_MAX_EXP - 4);
+ *   orc_q_zsjac2  the 2x2 Hermitian EVD of section 2 (the equations the
+ *                 FP64 oracle restates) with the binary128 constants the
+ *                 paper prescribes for other formats (section 2.4: nu =
+ *                 FLT128_MAX, fl(sqrt nu), mu = FLT128_TRUE_MIN, eta =
+ *                 floor(lg(nu/8)) = FLT128_MAX_EXP - 4);
  *   orc_q_vjsvd   the one-sided Jacobi SVD of Alg. zvjsvd: the same
  *                 round-robin ordering, the scaled dot-products of Alg.
  *                 zdpscl, the test of Eq. "e:tol" with eps = 2^-113, the
@@ -49,45 +50,65 @@ static void split(q x, double *hi, double *lo)
   *lo = (double)(x - (q)h);
 }
 
-/* Eq. "e:z" element with the binary128 constants: eta' - frexp exponent of
- * max(|x|, smallest subnormal), eta' = FLT128_MAX_EXP - 3. */
-static int zeta_of_q(q x)
+/* floor(lg x) for finite x > 0. */
+static int flg_q(q x)
 {
   int e;
-  const q tiny = FLT128_TRUE_MIN;
-  (void)frexpf128(fmaxf128(fabsf128(x), tiny), &e);
-  return (FLT128_MAX_EXP - 3) - e;
+  (void)frexpf128(x, &e);
+  return e - 1;
 }
 
 static int imin_q(int a, int b) { return a <= b ? a : b; }
 
-/* Listing 1 in binary128: cos(phi), e^{i alpha} tan(phi), the scaled
+/* zeta_x of Eq. "e:z" with the binary128 constants of section 2.4:
+ * eta - floor(lg max(|x|, mu-check)), eta = floor(lg(nu/8)), nu =
+ * FLT128_MAX, mu-check = FLT128_TRUE_MIN. */
+static int zeta_elem_q(q x)
+{
+  const int eta = flg_q(FLT128_MAX / 8);
+  return eta - flg_q(fmaxf128(fabsf128(x), FLT128_TRUE_MIN));
+}
+
+/* Alg. hypot in binary128 (Eq. "e:hypot"). */
+static q hypot_naive_q(q x, q y)
+{
+  const q ax = fabsf128(x), ay = fabsf128(y);
+  const q m = fminf128(ax, ay), M = fmaxf128(ax, ay);
+  const q ratio = fmaxf128(m / M, 0);
+  return sqrtf128(fmaf128(ratio, ratio, 1)) * M;
+}
+
+/* The EVD of section 2 in binary128: the scaling of Eq. "e:z", the polar
+ * form of Eq. "e:zpolar", then Eq. "e:tan2", "e:jactan", "e:jacsec" and
+ * "e:lamsec".  Returns cos(phi), e^{i alpha} tan(phi), the scaled
  * eigenvalues lambda' and zeta. */
 static void zsjac2_q(q a11, q a22, q a21r, q a21i, q *cphi, q *ctr, q *cti, q *l1, q *l2, int *zeta)
 {
-  const q SQRT_NU = sqrtf128(FLT128_MAX);
-  const int z = imin_q(imin_q(zeta_of_q(a11), zeta_of_q(a22)),
-                       imin_q(zeta_of_q(a21r), zeta_of_q(a21i)));
+  const int z = imin_q(imin_q(zeta_elem_q(a11), zeta_elem_q(a22)),
+                       imin_q(zeta_elem_q(a21r), zeta_elem_q(a21i)));
   a11 = ldexpf128(a11, z);
   a22 = ldexpf128(a22, z);
   a21r = ldexpf128(a21r, z);
   a21i = ldexpf128(a21i, z);
-  const q ar = fabsf128(a21r), ai = fabsf128(a21i);
-  const q am = fminf128(ar, ai), aM = fmaxf128(ar, ai);
-  const q mM = fmaxf128(am / aM, 0);
-  const q aa21 = sqrtf128(fmaf128(mM, mM, 1)) * aM;
-  const q ca = copysignf128(fminf128(ar / aa21, 1), a21r);
-  const q sa = a21i / fmaxf128(aa21, FLT128_TRUE_MIN);
-  const q o = aa21 * 2;
+  /* Eq. "e:zpolar" */
+  const q abs_a21 = hypot_naive_q(a21r, a21i);
+  const q cos_alpha = copysignf128(fminf128(fabsf128(a21r) / abs_a21, 1), a21r);
+  const q sin_alpha = a21i / fmaxf128(abs_a21, FLT128_TRUE_MIN);
+  /* Eq. "e:tan2" */
+  const q two_abs_a21 = 2 * abs_a21;
   const q a = a11 - a22;
-  const q tan2 = copysignf128(fminf128(fmaxf128(o / fabsf128(a), 0), SQRT_NU), a);
-  const q tan1 = tan2 / (MUT(16, 1, 2) + sqrtf128(fmaf128(tan2, tan2, 1)));
-  const q sec2 = fmaf128(tan1, tan1, 1);
+  const q tan_2phi =
+      copysignf128(fminf128(fmaxf128(two_abs_a21 / fabsf128(a), 0), sqrtf128(FLT128_MAX)), a);
+  /* Eq. "e:jactan" */
+  const q t = tan_2phi / (MUT(16, 1, 2) + sqrtf128(fmaf128(tan_2phi, tan_2phi, 1)));
+  /* Eq. "e:jacsec" */
+  const q sec2 = fmaf128(t, t, 1);
   *cphi = 1 / sqrtf128(sec2);
-  *ctr = ca * tan1;
-  *cti = sa * tan1;
-  *l1 = fmaf128(tan1, fmaf128(a22, tan1, o), a11) / sec2;
-  *l2 = fmaf128(tan1, fmaf128(a11, tan1, -o), a22) / sec2;
+  *ctr = cos_alpha * t;
+  *cti = sin_alpha * t;
+  /* Eq. "e:lamsec" */
+  *l1 = fmaf128(fmaf128(a22, t, two_abs_a21), t, a11) / sec2;
+  *l2 = fmaf128(fmaf128(a11, t, -two_abs_a21), t, a22) / sec2;
   *zeta = z;
 }
 

@@ -49,6 +49,10 @@ MUTANTS = {
           "tests/test_oracle_twin.py::test_twin_evd_against_exact"),
     17: ("the compensated imaginary stream with the wrong sign (reading R19)",
           "tests/test_oracle_compensated.py"),
+    18: ("the rescaling of section 3.2 without its update s += s_[k]",
+          "tests/test_oracle_svd.py::test_rescale_branch_is_exact"),
+    19: ("the rescaling of section 3.2 scales G by 2^-s_[k] (wrong sign)",
+          "tests/test_oracle_svd.py::test_rescale_branch_is_exact"),
 }
 
 

@@ -257,3 +257,36 @@ def test_gram_schmidt_not_taken_for_moderate_ranges():
     2^eta^ upsilon: an ordinary matrix takes no Gram-Schmidt step."""
     A, _ = workloads.svd_geometric(60, 30, 1e12, False, np.random.default_rng(4))
     assert oracle.vjsvd(A)["gs"] == 0
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+def test_rescale_branch_is_exact(cplx):
+    """The per-step rescaling of section 3.2 (steps 2-4: the test of Eq.
+    e:skr, the downscaling by 2^{s_[k]} of Eq. e:skn, the running exponent
+    s).  Its threshold is lowered (skr_shift) so that the branch runs on a
+    matrix whose max-norm grows during the sweeps: nearly parallel columns,
+    whose norm Jacobi gathers into one column (growth about sqrt(n)).
+    Power-of-two scaling is exact here (no entry comes near the subnormal
+    range), so every output must equal, bit for bit, that of the run that
+    never rescales; a dropped or wrong-signed exponent update changes sigma
+    by a power of two."""
+    rng = np.random.default_rng(77 + cplx)
+    m, n = 48, 24
+    A = np.ones((m, n)) + 0.01 * rng.standard_normal((m, n))
+    if cplx:
+        A = A * np.exp(0.3j) + 0.01j * rng.standard_normal((m, n))
+    ref = oracle.vjsvd(A)
+    assert ref["status"] == oracle.OK and ref["rescales"] == 0
+    check_svd(A, ref)
+    fired = []
+    for shift in (4, 8, 12, 40):
+        r = oracle.vjsvd(A, skr_shift=shift)
+        fired.append(r["rescales"])
+        for k in ("sigma", "sigma_e", "sigma_f", "U", "V"):
+            assert np.array_equal(np.ascontiguousarray(r[k]).view(np.uint8),
+                                  np.ascontiguousarray(ref[k]).view(np.uint8)), (shift, k)
+        assert (r["sweeps"], r["rotations"], r["status"]) == (
+            ref["sweeps"], ref["rotations"], ref["status"])
+    # the branch ran: a few times once the max-norm doubled, and at every
+    # step when the threshold lies below the initial max-norm
+    assert fired[-1] >= ref["sweeps"] * (n - 1) and max(fired[:-1]) > 0, fired
