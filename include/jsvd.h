@@ -280,7 +280,9 @@ JSVD_API int jsvd_svd_workspace_size(jsvd_field field, const jsvd_opts *opts, in
  * (m x n, ldu >= m), sigma (n), V (n x n, ldv >= n) are written; sigma_e,
  * sigma_f (n doubles each) and info may be NULL.  work must be 256-byte
  * aligned and hold jsvd_svd_workspace_size bytes; its contents on entry do
- * not matter.  Errors: -i for argument i, JSVD_E_WORKSPACE, JSVD_E_CUDA. */
+ * not matter.  Errors: -i for argument i, JSVD_E_WORKSPACE,
+ * JSVD_E_UNSUPPORTED (the sweep kernel cannot be made resident: zero blocks
+ * per SM), JSVD_E_CUDA (also when the device's SM count cannot be read). */
 JSVD_API int jsvd_svd(jsvd_field field, const jsvd_opts *opts, int64_t m, int64_t n,
                       const void *A, int64_t lda, void *U, int64_t ldu, double *sigma,
                       double *sigma_e, double *sigma_f, void *V, int64_t ldv, void *work,
@@ -295,7 +297,8 @@ JSVD_API int jsvd_svd(jsvd_field field, const jsvd_opts *opts, int64_t m, int64_
  * (n x n, ldv >= n).  opts as for jsvd_svd (mode and rescale_exp are not
  * used; compensated must be 0).  work: jsvd_svd_f32_workspace_size bytes,
  * 256-byte aligned.  Errors: -1 field, -2 opts, -3 m, -4 n, -5 A, -6 lda,
- * -7 U, -8 ldu, -9 sigma, -10 V, -11 ldv, -12 work, JSVD_E_WORKSPACE. */
+ * -7 U, -8 ldu, -9 sigma, -10 V, -11 ldv, -12 work, JSVD_E_WORKSPACE,
+ * JSVD_E_UNSUPPORTED, JSVD_E_CUDA. */
 JSVD_API int jsvd_svd_f32_workspace_size(jsvd_field field, const jsvd_opts *opts, int64_t m,
                                          int64_t n, size_t *bytes);
 JSVD_API int jsvd_svd_f32(jsvd_field field, const jsvd_opts *opts, int64_t m, int64_t n,
@@ -375,15 +378,20 @@ JSVD_API int jsvd_sign_gauge_batched(int64_t count, int64_t m, int64_t n, double
  * It takes no workspace and allocates nothing (no cudaMalloc, cudaFree or
  * allocating library call).  Its scratch is one static device array of
  * JSVD_NOALLOC_SCRATCH_BYTES (16 MiB) inside the library, which every GPU
- * that loads the library keeps until the process exits.  A problem whose
- * jsvd_svd_workspace_size exceeds that is rejected with JSVD_E_WORKSPACE
- * (e.g. real 2048 x 512 and complex 512 x 512 fit; real 1024 x 1024 does
- * not).
+ * that loads the library keeps until the process exits.  A problem fits
+ * when jsvd_svd_workspace_size, called with the same field and opts, is at
+ * most that; otherwise it is rejected with JSVD_E_WORKSPACE.  The mixed
+ * mode needs more scratch than plain FP64.  Examples: in JSVD_FP64 real
+ * 2048 x 512 and complex 512 x 512 fit, real 1024 x 1024 does not; in
+ * JSVD_MIXED_FP32_FP64 real 512 x 512 and complex 384 x 384 fit, real
+ * 1024 x 512 and complex 512 x 512 do not.
  *
- * The first call on a device looks up the array's device address there
- * (cudaGetSymbolAddress, which may load the library's device code on that
- * device); make that first call before any stream capture.  All calls share
- * the one array and it keeps the last call's contents: each call clears the
+ * Every call looks up the array's device address in the current context
+ * (cudaGetSymbolAddress, a host-side query; the first call in a context may
+ * load the library's device code there, so make it before any stream
+ * capture).  The address is not cached, so calls stay correct after
+ * cudaDeviceReset or a change of the current context.  All calls share the
+ * one array and it keeps the last call's contents: each call clears the
  * state that must start at zero, but calls whose work overlaps on the GPU
  * (different streams, or different host threads) race on it and give wrong
  * results -- serialise them.
@@ -391,7 +399,9 @@ JSVD_API int jsvd_sign_gauge_batched(int64_t count, int64_t m, int64_t n, double
  * Arguments and results as jsvd_svd, without work/work_bytes; A, U, sigma,
  * V (and the optional sigma_e, sigma_f, info) remain the caller's device
  * buffers.  Errors: -i for argument i (1..13), JSVD_E_WORKSPACE when the
- * problem does not fit the scratch, JSVD_E_CUDA. */
+ * problem does not fit the scratch, JSVD_E_UNSUPPORTED when the sweep
+ * kernel cannot be made resident on the device (an occupancy of zero
+ * blocks per SM), JSVD_E_CUDA. */
 #define JSVD_NOALLOC_SCRATCH_BYTES (16u << 20)
 JSVD_API int jsvd_svd_noalloc(jsvd_field field, const jsvd_opts *opts, int64_t m, int64_t n,
                               const void *A, int64_t lda, void *U, int64_t ldu, double *sigma,

@@ -160,7 +160,8 @@ extern "C" int jsvd_svd_adjoint_batched(int64_t count, int64_t m, int64_t n, con
   int per_sm = 0;
   JSVD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adjoint_kernel, 256, smem));
   if (per_sm < 1) return JSVD_E_UNSUPPORTED;
-  const int grid = (int)std::min<int64_t>(count, (int64_t)per_sm * sm_count());
+  JSVD_SMS(sms);
+  const int grid = (int)std::min<int64_t>(count, (int64_t)per_sm * sms);
   adjoint_kernel<<<grid, 256, smem, as_stream(stream)>>>((int)count, (int)m, (int)n, U, s, V, Ubar,
                                                          sbar, Vbar, Abar);
   JSVD_CHECK_LAUNCH();
@@ -177,7 +178,8 @@ extern "C" int jsvd_sign_gauge_batched(int64_t count, int64_t m, int64_t n, doub
   if (!U) return -4;
   if (!V) return -5;
   const int64_t warps = count * n;
-  const int blocks = (int)std::min<int64_t>((warps * 32 + 255) / 256, (int64_t)sm_count() * 16);
+  JSVD_SMS(sms);
+  const int blocks = (int)std::min<int64_t>((warps * 32 + 255) / 256, (int64_t)sms * 16);
   sign_gauge_kernel<<<blocks, 256, 0, as_stream(stream)>>>((int)count, (int)m, (int)n, U, V);
   JSVD_CHECK_LAUNCH();
   return JSVD_OK;

@@ -14,20 +14,29 @@ int cuda_fail(cudaError_t e)
   return JSVD_E_CUDA;
 }
 
-int sm_count()
+int sm_count(int *out)
 {
   static std::mutex mu;
   static int cache[64] = {0};
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+  JSVD_CUDA(cudaGetDevice(&dev));
+  if (dev < 0) return cuda_fail(cudaErrorInvalidDevice);
+  if (dev >= 64) {  // beyond the cache: ask every time
+    int v = 0;
+    JSVD_CUDA(cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev));
+    if (v <= 0) return cuda_fail(cudaErrorInvalidValue);
+    *out = v;
+    return JSVD_OK;
+  }
   std::lock_guard<std::mutex> lock(mu);
   if (!cache[dev]) {
     int v = 0;
-    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0)
-      v = 152;
+    JSVD_CUDA(cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev));
+    if (v <= 0) return cuda_fail(cudaErrorInvalidValue);
     cache[dev] = v;
   }
-  return cache[dev];
+  *out = cache[dev];
+  return JSVD_OK;
 }
 
 }  // namespace jsvd

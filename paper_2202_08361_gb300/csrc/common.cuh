@@ -7,8 +7,9 @@
 
 namespace jsvd {
 
-// Number of SMs of the current device (cached per device).
-int sm_count();
+// Number of SMs of the current device (cached per device) in *out:
+// JSVD_OK, or JSVD_E_CUDA when the device or its attribute cannot be read.
+int sm_count(int *out);
 
 // Map a CUDA error to the ABI code (JSVD_E_CUDA), remembering the text.
 int cuda_fail(cudaError_t e);
@@ -27,6 +28,12 @@ inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s
     const int rc_ = (__VA_ARGS__);    \
     if (rc_ != JSVD_OK) return rc_;   \
   } while (0)
+
+// Declare `var` and set it to the current device's SM count, or return
+// the error.
+#define JSVD_SMS(var)  \
+  int var = 0;         \
+  JSVD_TRY(::jsvd::sm_count(&var))
 
 #define JSVD_CUDA(call)                                       \
   do {                                                        \

@@ -131,7 +131,8 @@ extern "C" int jsvd_evd2x2_batched(jsvd_field field, const jsvd_evd2_streams *s,
   if (cplx && (!s->a21_im || !s->ea_tan_im)) return -2;
   const int block = g_evd_block;
   const int64_t need = (n + block - 1) / block;
-  const int64_t cap = (int64_t)sm_count() * g_evd_blocks_per_sm;
+  JSVD_SMS(sms);
+  const int64_t cap = (int64_t)sms * g_evd_blocks_per_sm;
   const int grid = (int)(need < cap ? need : cap);
   cudaStream_t st = as_stream(stream);
   const EvdPtrs p{s->a11, s->a22, s->a21_re, cplx ? s->a21_im : nullptr, s->cos_phi, s->ea_tan_re,

@@ -107,7 +107,8 @@ extern "C" int jsvd_evd2x2_batched_f32(jsvd_field field, const jsvd_evd2_streams
   int block, per_sm;
   evd2_get_launch(block, per_sm);
   const int64_t need = (n + (int64_t)block * kUnroll - 1) / ((int64_t)block * kUnroll);
-  const int64_t cap = (int64_t)sm_count() * per_sm;
+  JSVD_SMS(sms);
+  const int64_t cap = (int64_t)sms * per_sm;
   const int grid = (int)(need < cap ? need : cap);
   cudaStream_t st = as_stream(stream);
   if (cplx)

@@ -110,8 +110,9 @@ extern "C" int jsvd_colnorm_ef(jsvd_field field, int64_t m, int64_t n, const voi
   if (m > 0 && !A) return -4;
   if (lda < (m > 0 ? m : 1)) return -5;
   cudaStream_t st = as_stream(stream);
+  JSVD_SMS(sms);
   if (m > kShortRows) {
-    const int64_t cap = (int64_t)sm_count() * 2;
+    const int64_t cap = (int64_t)sms * 2;
     const int grid = (int)(n < cap ? n : cap);
     if (field == JSVD_COMPLEX)
       colnorm_ef_long_kernel<true><<<grid, 1024, 0, st>>>(m, n, (const double *)A, lda, e_out, f_out);
@@ -121,7 +122,7 @@ extern "C" int jsvd_colnorm_ef(jsvd_field field, int64_t m, int64_t n, const voi
     return JSVD_OK;
   }
   const int64_t need = (n * 32 + 255) / 256;
-  const int64_t cap = (int64_t)sm_count() * 8;
+  const int64_t cap = (int64_t)sms * 8;
   const int grid = (int)(need < cap ? need : cap);
   if (field == JSVD_COMPLEX)
     colnorm_ef_kernel<true><<<grid, 256, 0, st>>>(m, n, (const double *)A, lda, e_out, f_out);

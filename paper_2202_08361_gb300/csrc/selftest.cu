@@ -110,7 +110,8 @@ extern "C" int jsvd_selftest_barrier(int blocks, int absent, int rounds, int64_t
                                      int32_t *status, void *stream)
 {
   using namespace jsvd;
-  if (blocks < 1 || blocks > sm_count()) return -1;
+  JSVD_SMS(sms);
+  if (blocks < 1 || blocks > sms) return -1;
   if (rounds < 1 || rounds > 1000) return -3;
   if (limit_ns < 1000000 || limit_ns > 5000000000ll) return -4;  // 1 ms .. 5 s
   if (!status) return -5;
@@ -169,7 +170,8 @@ extern "C" int jsvd_selftest_fp32div(int64_t n, uint64_t seed, unsigned long lon
   if (n < 0) return -1;
   if (!mismatches) return -3;
   if (n == 0) return JSVD_OK;
-  const int blocks = (int)std::min<int64_t>((n + 255) / 256, (int64_t)jsvd::sm_count() * 8);
+  JSVD_SMS(sms);
+  const int blocks = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sms * 8);
   jsvd::selftest32_kernel<<<blocks, 256, 0, jsvd::as_stream(stream)>>>(n, seed, mismatches);
   JSVD_CHECK_LAUNCH();
   return JSVD_OK;
@@ -181,7 +183,8 @@ extern "C" int jsvd_selftest_fp64(int64_t n, uint64_t seed, unsigned long long *
   if (n < 0) return -1;
   if (!mismatches) return -3;
   if (n == 0) return JSVD_OK;
-  const int blocks = (int)std::min<int64_t>((n + 255) / 256, (int64_t)jsvd::sm_count() * 8);
+  JSVD_SMS(sms);
+  const int blocks = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sms * 8);
   jsvd::selftest_kernel<<<blocks, 256, 0, jsvd::as_stream(stream)>>>(n, seed, mismatches);
   JSVD_CHECK_LAUNCH();
   return JSVD_OK;

@@ -449,7 +449,7 @@ template <bool CPLX>
 static int phase_init(const MatView &M, const double *A, int64_t lda, SvdState *state, int rexp,
                       cudaStream_t st)
 {
-  const int sms = sm_count();
+  JSVD_SMS(sms);
   const int64_t m = M.m, n = M.n;
   JSVD_CUDA(cudaMemsetAsync(state, 0, sizeof(SvdState), st));
   const int64_t rows = CPLX ? 2 * m : m;
@@ -471,7 +471,7 @@ static int launch_sweeps(const MatViewT<T> &M, SvdState *state, double ups, int 
 {
   const int nt = M.n + (M.n & 1);
   const int Lp = nt / 2;
-  const int sms = sm_count();
+  JSVD_SMS(sms);
   // The step form: each warp alone unless the chunked form is asked for.
   // Measured on GB300 for 256 x 128 to 4096 x 2048, real and complex, FP64
   // and mixed: the per-warp form is 2-15 % faster everywhere (its extra
@@ -524,7 +524,7 @@ static int phase_finish(const MatView &M, int *e, double *f, int *rank, SvdState
                         double *sigma_e, double *sigma_f, double *V, int64_t ldv, jsvd_info *info,
                         cudaStream_t st)
 {
-  const int sms = sm_count();
+  JSVD_SMS(sms);
   const int64_t m = M.m, n = M.n;
   const int blocks = (int)std::min<int64_t>((n * 32 + 255) / 256, (int64_t)sms * 8);
   colnorm_kernel<CPLX><<<blocks, 256, 0, st>>>(M, e, f);
@@ -625,7 +625,7 @@ static int svd_mixed_run_t(int64_t m, int64_t n, const double *A, int64_t lda, d
   // the FP64 phase restarts the step state from the max-norm of the new G
   JSVD_CUDA(cudaMemsetAsync(st64->Mbuf, 0, sizeof(st64->Mbuf), st));
   {
-    const int sms = sm_count();
+    JSVD_SMS(sms);
     int64_t blocks = ((int64_t)L.mp * n + 255) / 256;
     if (blocks > (int64_t)sms * 8) blocks = (int64_t)sms * 8;
     maxnorm_kernel<<<(int)blocks, 256, 0, st>>>(M64.gr, L.ldg, L.mp, n, &st64->Mbuf[0]);
@@ -922,7 +922,7 @@ static int svd_f32_run(int64_t m, int64_t n, const float *A, int64_t lda, float 
   int *e = reinterpret_cast<int *>(work + L.e);
   double *f = reinterpret_cast<double *>(work + L.f);
   int *rank = reinterpret_cast<int *>(work + L.rank);
-  const int sms = sm_count();
+  JSVD_SMS(sms);
   JSVD_CUDA(cudaMemsetAsync(state, 0, sizeof(SvdState), st));
   const int64_t rows = CPLX ? 2 * m : m, ld = CPLX ? 2 * lda : lda;
   int64_t blocks = (rows * n + 255) / 256;

@@ -441,7 +441,8 @@ extern "C" int jsvd_svd_batched_prepare(jsvd_field field, const jsvd_opts *opts,
     auto k1 = (field == JSVD_COMPLEX) ? batched_kernel<true, false, false>
                                       : batched_kernel<false, false, false>;
     JSVD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k1, 32, 0));
-    remember_auto(work, batch_auto_warps(count, m, n, per_sm * sm_count()));
+    JSVD_SMS(sms);
+    remember_auto(work, batch_auto_warps(count, m, n, per_sm * sms));
   }
   BatchHdr h = {0, (int)count, 0, 0};
   char *w = (char *)work;
@@ -495,7 +496,8 @@ extern "C" int jsvd_svd_batched_launch(jsvd_field field, const jsvd_opts *opts, 
   }
   JSVD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
   if (per_sm < 1) return JSVD_E_UNSUPPORTED;
-  const int grid = (int)std::min<int64_t>(count, (int64_t)per_sm * sm_count());
+  JSVD_SMS(sms);
+  const int grid = (int)std::min<int64_t>(count, (int64_t)per_sm * sms);
   kern<<<grid, threads, smem, st>>>(reinterpret_cast<const BatchDesc *>(w + L.desc),
                                     reinterpret_cast<const int *>(w + L.order),
                                     reinterpret_cast<BatchHdr *>(w + L.hdr), w, info, S, rexp,

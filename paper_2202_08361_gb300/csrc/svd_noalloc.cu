@@ -13,11 +13,12 @@
 // The array is part of the library's device image: every GPU on which the
 // library's module is loaded holds it until the process exits.  Host code
 // never passes the array's name to a kernel (on the host that name is only
-// a stand-in, not a device address); it passes the address that
-// cudaGetSymbolAddress returns for the current device, looked up once per
-// device by the first call made on it.
-#include <mutex>
-
+// a stand-in, not a device address); every call asks cudaGetSymbolAddress
+// for the array's address in the current device's current context and
+// passes that.  The lookup is a host-side query and allocates nothing once
+// the module is loaded; doing it on every call (rather than caching it per
+// device) keeps the address right after cudaDeviceReset or when the caller
+// makes another context current.
 #include "common.cuh"
 #include "jsvd_internal.h"
 
@@ -26,24 +27,14 @@ namespace {
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[JSVD_NOALLOC_SCRATCH_BYTES];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_noalloc_mu;
-void *g_noalloc_addr[kMaxDevices];
-
-// Device address of the scratch array on the current device.
+// Device address of the scratch array in the current context.
 int noalloc_scratch(void **out)
 {
-  int dev = -1;
-  JSVD_CUDA(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= kMaxDevices) return JSVD_E_UNSUPPORTED;
-  std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (!g_noalloc_addr[dev]) {
-    void *p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || p == nullptr) return cuda_fail(e != cudaSuccess ? e : cudaErrorInvalidSymbol);
-    g_noalloc_addr[dev] = p;
-  }
-  *out = g_noalloc_addr[dev];
+  void *p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess) return cuda_fail(e);
+  if (p == nullptr) return cuda_fail(cudaErrorInvalidSymbol);
+  *out = p;
   return JSVD_OK;
 }
 
