@@ -13,15 +13,23 @@ Under torchrun (N > 1) every rank processes its own batch (independent
 matrices, no data-path collective: weak scaling); timing is the max over
 ranks.  --impl reference times the CPU oracle on the host cores instead.
 """
-import argparse
-import hashlib
-import json
 import os
-import statistics
-import subprocess
-import sys
-import threading
-import time
+
+# The CPU oracle's OpenMP environment, as the paper runs its CPU code
+# (threads spread over the cores, one per core, no dynamic adjustment).  Set
+# before anything loads an OpenMP runtime: a runtime reads these once, when
+# it starts.  The binding in force is read back and reported.
+for _k, _v in (("OMP_PROC_BIND", "spread"), ("OMP_PLACES", "cores"), ("OMP_DYNAMIC", "false")):
+    os.environ.setdefault(_k, _v)
+
+import argparse  # noqa: E402
+import hashlib  # noqa: E402
+import json  # noqa: E402
+import statistics  # noqa: E402
+import subprocess  # noqa: E402
+import sys  # noqa: E402
+import threading  # noqa: E402
+import time  # noqa: E402
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
@@ -48,6 +56,9 @@ def parse():
                    help="log2 of the matrices per kernel per step (24 = the full workload)")
     p.add_argument("--no-svd", action="store_true",
                    help="skip the SVD measurements (C1, C3 plain/mixed, C4, C5)")
+    p.add_argument("--c4-loop", type=int, default=120,
+                   help="matrices of the 10,000-matrix batch timed through jsvd_svd one by "
+                        "one (a random sample scaled by m n^2; 10000 = the whole loop)")
     return p.parse_args()
 
 
@@ -163,9 +174,6 @@ def recorded_traffic(kernel):
 
 def cpu_oracle_evd(r, seed_salt=0):
     """Time the oracle (as it stands) on r real + r complex matrices."""
-    os.environ.setdefault("OMP_PROC_BIND", "spread")
-    os.environ.setdefault("OMP_PLACES", "cores")
-    os.environ.setdefault("OMP_DYNAMIC", "false")
     import oracle
     from paper_2202_08361_gb300 import workloads
     re_ = workloads.evd_batch(r, False, seed_salt)
@@ -177,28 +185,101 @@ def cpu_oracle_evd(r, seed_salt=0):
     return dt, oracle.num_threads()
 
 
-def cpu_oracle_svd(A):
+def cpu_oracle_svd(A, nthreads=0, max_steps=0):
     """Time the oracle's SVD (as it stands, OpenMP over the pairs of a step)
-    on the host matrix A once; (ms, threads, sweeps)."""
-    os.environ.setdefault("OMP_PROC_BIND", "spread")
-    os.environ.setdefault("OMP_PLACES", "cores")
-    os.environ.setdefault("OMP_DYNAMIC", "false")
+    on the host matrix A once, all cores (nthreads 0) or nthreads, for at
+    most max_steps parallel steps (0: to convergence); (ms, threads, sweeps,
+    steps run)."""
     import oracle
     t0 = time.perf_counter()
-    r = oracle.vjsvd(A)
+    r = oracle.vjsvd(A, nthreads=nthreads, max_steps=max_steps)
     dt = time.perf_counter() - t0
-    return 1e3 * dt, oracle.num_threads(), int(r["sweeps"])
+    n = A.shape[1]
+    nt = n + (n & 1)
+    steps = r["sweeps"] * (nt - 1) if max_steps <= 0 else min(max_steps, r["sweeps"] * (nt - 1))
+    return 1e3 * dt, (nthreads if nthreads > 0 else oracle.num_threads()), int(r["sweeps"]), steps
+
+
+def cpu_oracle_evd_threads(r, nthreads, seed_salt=0):
+    """cpu_oracle_evd with the oracle's OpenMP loops on nthreads threads."""
+    import oracle
+    from paper_2202_08361_gb300 import workloads
+    re_ = workloads.evd_batch(r, False, seed_salt)
+    cx = workloads.evd_batch(r, True, seed_salt)
+    t0 = time.perf_counter()
+    oracle.dsjac2(*re_, nthreads=nthreads)
+    oracle.zsjac2(*cx, nthreads=nthreads)
+    return time.perf_counter() - t0, nthreads
+
+
+def oracle_env():
+    """The OpenMP threads and binding in force for the oracle."""
+    import oracle
+    return oracle.omp_state()
 
 
 
 # ---------------------------------------------------------------------------
 # the SVD workloads (reported beside the EVD headline)
 
-DFMA_FLOPS = 0.99e12  # FP64 FMA rate measured on GB300 by an FMA throughput probe (2 flops per fma)
-
-
 def _ev(torch):
     return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+# FP64-pipe operations per matrix of the batched EVD in its default division
+# placement (evd2.cu: only sqrt(tan2^2 + 1) runs on the FP64 pipe; every
+# other division and square root, and all exponent, sign and min/max work,
+# run on the integer pipe), counted from evd2.cuh: (adds, multiplies and
+# fmas; IEEE square roots).  Real: a11 - a22, fma(tan2, tan2, 1),
+# 1 + sqrt(.), fma(tan, tan, 1) for sec^2, two fmas for each lambda'.
+# Complex: those 8 plus fma(q, q, 1) and the product by M of Alg. hypot,
+# and cos(alpha) tan(phi), sin(alpha) tan(phi).
+EVD_FP64_OPS = {"evd2_kernel<real>": (8, 1), "evd2_kernel<complex>": (12, 1)}
+
+
+def fp64_pipe_rates(torch, J, dev):
+    """The FP64 pipe's throughput measured now, on this GPU: fused
+    multiply-adds, IEEE square roots and IEEE divisions per second over the
+    whole GPU (jsvd_probe_fp64_rate: 8 blocks of 256 threads per SM, 8
+    independent chains per thread, best of 3 launches timed with CUDA
+    events)."""
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    blocks = sms * 8
+    sink = torch.zeros(1, dtype=torch.float64, device=dev)
+    st = torch.cuda.current_stream(dev)
+    res = {}
+    for kind, name, iters in ((0, "fma", 4000), (1, "sqrt", 400), (2, "div", 400)):
+        J.probe_fp64_rate(kind, 8, blocks, sink)
+        best = None
+        for _ in range(3):
+            e0, e1 = _ev(torch)
+            e0.record(st)
+            J.probe_fp64_rate(kind, iters, blocks, sink)
+            e1.record(st)
+            torch.cuda.synchronize(dev)
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+        res[name + "_per_s"] = blocks * 256 * 8 * iters / (best * 1e-3)
+    res["fma_flops"] = 2 * res["fma_per_s"]
+    res["sqrt_in_fma"] = res["fma_per_s"] / res["sqrt_per_s"]
+    res["div_in_fma"] = res["fma_per_s"] / res["div_per_s"]
+    res["method"] = ("jsvd_probe_fp64_rate: %d blocks x 256 threads x 8 independent chains; "
+                     "best of 3 CUDA-event-timed launches" % blocks)
+    return res
+
+
+def evd_fp64_roofline(kernel, ms, r, rates):
+    """The EVD kernel against the pipe that binds it: FP64-pipe work per
+    matrix (counted, the square roots converted to fmas at the measured
+    rate ratio) x matrices / kernel time, over the measured fma rate."""
+    nf, ns = EVD_FP64_OPS[kernel]
+    ops = nf + ns * rates["sqrt_in_fma"]
+    achieved = ops * r / (ms * 1e-3)
+    return {"bound": "fp64_pipe", "kernel": kernel, "achieved": achieved,
+            "peak": rates["fma_per_s"], "unit": "FP64 lane-ops/s (fma equivalents)",
+            "frac": achieved / rates["fma_per_s"], "ops_per_matrix": ops,
+            "counted": {"add_mul_fma": nf, "ieee_sqrt": ns}, "peak_kind": "measured in this run",
+            "avg_launch_ms": ms}
 
 
 def _svd_flops(m, n, sweeps, rotations, cplx):
@@ -239,9 +320,14 @@ def evd_f32_bench(torch, J, workloads, dev, peaks, reps=50):
     return res
 
 
-def svd_bench(torch, J, workloads, dev):
+def svd_bench(torch, J, workloads, dev, rates, cpu=True, loop_count=120):
+    """The SVD workloads beside the EVD headline: per workload the GPU time,
+    accuracy, FP64 rate against the measured fma rate, and (cpu) the oracle
+    timed on the host cores, all cores and one thread, on the whole workload
+    or a stated bounded sample of it."""
     import numpy as np
     out = {}
+    DFMA_FLOPS = rates["fma_flops"]
     eps = np.finfo(np.float64).eps
     st = torch.cuda.current_stream(dev)
 
@@ -271,12 +357,16 @@ def svd_bench(torch, J, workloads, dev):
     c1 = {"ms_per_svd": ms, "sweeps": info["sweeps"], "rotations": info["rotations"],
           "fp64_gflops": fl / ms / 1e6, "fp64_frac": fl / (ms * 1e-3) / DFMA_FLOPS}
     c1.update(accuracy(A1, r))
-    try:
-        ms_o, thr_o, sw_o = cpu_oracle_svd(workloads.svd_normal())
-        c1["cpu_oracle"] = {"ms_per_svd": ms_o, "threads": thr_o, "sweeps": sw_o,
-                            "kind": "oracle", "sample": "the same matrix, once"}
-    except Exception as exc:  # host-side context only: the GPU figures stand without it
-        c1["cpu_oracle"] = {"error": repr(exc)}
+    if cpu:
+        try:
+            co = {"kind": "oracle", "sample": "the same matrix, once, to convergence"}
+            for key, thr in (("all_cores", 0), ("one_thread", 1)):
+                ms_o, thr_o, sw_o, _ = cpu_oracle_svd(workloads.svd_normal(), nthreads=thr)
+                co[key] = {"ms_per_svd": ms_o, "threads": thr_o, "sweeps": sw_o,
+                           "gpu_speedup": ms_o / ms}
+            c1["cpu_oracle"] = co
+        except Exception as exc:  # host-side context only: the GPU figures stand without it
+            c1["cpu_oracle"] = {"error": repr(exc)}
     out["C1_real_256x128"] = c1
 
     # the same matrix in single precision (jsvd_svd_f32)
@@ -352,7 +442,8 @@ def svd_bench(torch, J, workloads, dev):
     # C3: complex 4096 x 2048, cond 1e6, plain FP64 and mixed FP32 -> FP64
     A3np, s3 = workloads.svd_complex_geometric()
     A3 = torch.from_numpy(A3np).to(dev)
-    del A3np
+    from tests.golden import c3_fixture
+    fx = c3_fixture.load()
     c3 = {}
     sig = {}
     for mode in ("fp64", "mixed"):
@@ -369,6 +460,13 @@ def svd_bench(torch, J, workloads, dev):
         d.update(accuracy(A3, r))
         sig[mode] = r["sigma"].cpu().numpy()
         d["sigma_err_vs_prescribed"] = float(np.abs(sig[mode] - s3).max() / s3[0])
+        if fx is not None:
+            cols = torch.from_numpy(fx["cols"]).to(dev)
+            e = c3_fixture.errors(sig[mode], r["U"][:, cols].cpu().numpy(),
+                                  r["V"][:, cols].cpu().numpy(), fx)
+            e["input_bit_equal_to_oracle_run"] = c3_fixture.input_matches(A3np, fx)
+            e["oracle"] = "tests/golden/c3_oracle_4096x2048.npz (the oracle's FP64 SVD, %d sweeps)" % int(fx["sweeps"])
+            d["err_vs_oracle"] = e
         if mode == "fp64":
             fl = _svd_flops(4096, 2048, info["sweeps"], info["rotations"], True)
             d["fp64_tflops"] = fl / (ms * 1e-3) / 1e12
@@ -377,8 +475,33 @@ def svd_bench(torch, J, workloads, dev):
         del r
     c3["speedup_mixed_vs_fp64"] = c3["fp64"]["s"] / c3["mixed"]["s"]
     c3["sigma_mixed_vs_fp64_max_rel"] = float(np.abs(sig["mixed"] - sig["fp64"]).max() / s3[0])
-    out["C3_complex_4096x2048"] = c3
     del A3
+    if cpu:
+        # the oracle's FP64 SVD on the same matrix: a bounded sample (the
+        # first parallel steps of the first sweep, where every pair rotates),
+        # extrapolated to the oracle's whole run (its sweeps x 2047 steps)
+        try:
+            full_steps = 2047 * int(fx["sweeps"] if fx is not None else c3["fp64"]["sweeps_fp64"])
+            co = {"kind": "oracle", "full_run_steps": full_steps,
+                  "sample": "the first K parallel steps of sweep 1 on the same matrix, scaled "
+                            "to the full run's steps (later sweeps rotate fewer pairs, so an "
+                            "upper estimate)"}
+            for key, thr, K in (("all_cores", 0, 512), ("one_thread", 1, 24)):
+                ms_o, thr_o, _, steps = cpu_oracle_svd(A3np, nthreads=thr, max_steps=K)
+                est = ms_o / steps * full_steps / 1e3
+                co[key] = {"threads": thr_o, "steps_timed": steps, "s_timed": ms_o / 1e3,
+                           "s_per_step": ms_o / steps / 1e3, "s_full_svd_est": est,
+                           "gpu_fp64_speedup_est": est / c3["fp64"]["s"],
+                           "gpu_mixed_speedup_est": est / c3["mixed"]["s"]}
+            if fx is not None:
+                co["measured_full_run_elsewhere"] = {
+                    "s": float(fx["seconds"]), "threads": int(fx["threads"]),
+                    "where": "the run that wrote the stored oracle result (x86-64 host)"}
+            c3["cpu_oracle"] = co
+        except Exception as exc:
+            c3["cpu_oracle"] = {"error": repr(exc)}
+    del A3np
+    out["C3_complex_4096x2048"] = c3
 
     # C4: 10,000 uneven real matrices, one persistent launch vs a per-matrix loop
     A4, m4, n4 = workloads.uneven_batch_device(device=dev)
@@ -393,20 +516,22 @@ def svd_bench(torch, J, workloads, dev):
     infos = J.decode_info(B.info)
     fl = sum(_svd_flops(int(m4[i]), int(n4[i]), infos[i]["sweeps"], infos[i]["rotations"], False)
              for i in range(len(m4)))
+    # the per-matrix launch loop: jsvd_svd on each matrix of a random sample,
+    # one after another on one stream, scaled to the batch by m n^2
     g = np.random.default_rng(0)
-    idx = g.choice(len(m4), 40, replace=False)
-    mats = [A4[int(B.offA[i]):int(B.offA[i] + m4[i] * n4[i])].view(int(n4[i]), int(m4[i])).t()
-            for i in idx]
-    J.svd(mats[0])
+    idx = g.choice(len(m4), loop_count, replace=False) if loop_count < len(m4) else np.arange(len(m4))
+    mat = lambda i: A4[int(B.offA[i]):int(B.offA[i] + m4[i] * n4[i])].view(int(n4[i]), int(m4[i])).t()
+    J.svd(mat(idx[0]))
     torch.cuda.synchronize(dev)
     e2, e3 = _ev(torch)
     e2.record(st)
-    for M_ in mats:
-        J.svd(M_)
+    for i in idx:
+        J.svd(mat(i))
     e3.record(st)
     torch.cuda.synchronize(dev)
     cost = (m4 * n4 * n4).astype(float)
-    loop_s = e2.elapsed_time(e3) / 1e3 * cost.sum() / cost[idx].sum()
+    loop_meas_s = e2.elapsed_time(e3) / 1e3
+    loop_s = loop_meas_s * cost.sum() / cost[idx].sum()
     # the autotuner's choice (each candidate timed on the batch, 2 sweeps)
     import time as _time
     t0 = _time.perf_counter()
@@ -419,16 +544,66 @@ def svd_bench(torch, J, workloads, dev):
     e1.record(st)
     torch.cuda.synchronize(dev)
     ms_tuned = e0.elapsed_time(e1)
-    out["C4_uneven_10000"] = {
+    # the same batch as one captured CUDA graph, replayed (the launch with the
+    # tuned warps captured once; each replay redoes the whole batch)
+    gs = torch.cuda.Stream(dev)
+    gs.wait_stream(st)
+    with torch.cuda.stream(gs):
+        B.launch(gs)
+    torch.cuda.synchronize(dev)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=gs):
+        B.launch(gs)
+    torch.cuda.synchronize(dev)
+    reps = 2
+    e0, e1 = _ev(torch)
+    e0.record(st)
+    for _ in range(reps):
+        graph.replay()
+    e1.record(st)
+    torch.cuda.synchronize(dev)
+    ms_graph = e0.elapsed_time(e1) / reps
+    infos_g = J.decode_info(B.info)
+    c4 = {
         "s": ms / 1e3, "matrices_per_s": len(m4) / (ms * 1e-3),
         "autotuned": {"warps": B.warps, "s": ms_tuned / 1e3, "tuning_s": tune_s,
                       "two_sweep_ms": {str(k): v for k, v in times.items()}},
+        "graph_replay": {"s": ms_graph / 1e3, "matrices_per_s": len(m4) / (ms_graph * 1e-3),
+                         "replays_timed": reps, "warps": B.warps,
+                         "converged": int(sum(1 for x in infos_g if x["status"] == 0))},
         "converged": int(sum(1 for x in infos if x["status"] == 0)),
         "sweeps_mean": float(np.mean([x["sweeps"] for x in infos])),
         "fp64_tflops": fl / (ms * 1e-3) / 1e12, "fp64_frac": fl / (ms * 1e-3) / DFMA_FLOPS,
-        "per_matrix_loop_s_est": loop_s, "speedup_vs_loop": loop_s / (ms / 1e3),
-        "loop_sample": "40 random matrices through jsvd_svd one by one, scaled by m n^2"}
-    del A4, B, mats
+        "per_matrix_loop": {"matrices_timed": int(len(idx)), "s_timed": loop_meas_s,
+                            "s_full_batch": loop_s,
+                            "scaled": bool(len(idx) < len(m4)),
+                            "how": "jsvd_svd on each matrix in turn on one stream"
+                                   + (", a random sample scaled to the batch by m n^2"
+                                      if len(idx) < len(m4) else ", the whole batch")},
+        "speedup_graph_vs_loop": loop_s / (ms_graph / 1e3)}
+    if cpu:
+        # the oracle over matrices of the same random sample, the OpenMP
+        # threads sharing out the matrices, scaled to the batch by m n^2
+        try:
+            import oracle
+            co = {"kind": "oracle", "sample": "matrices of the random sample above (all cores: "
+                  "all of it, one thread: the first 8), scaled to the batch by m n^2"}
+            for key, thr, k in (("all_cores", 0, len(idx)), ("one_thread", 1, 8)):
+                sel = idx[:k]
+                host = [mat(i).cpu().numpy() for i in sel]
+                t0 = _time.perf_counter()
+                sg, _, _, stt = oracle.vjsvd_batch(host, nthreads=thr)
+                dt = _time.perf_counter() - t0
+                est = dt * cost.sum() / cost[sel].sum()
+                co[key] = {"threads": thr if thr else oracle.num_threads(),
+                           "matrices_timed": int(k), "s_timed": dt, "s_full_batch_est": est,
+                           "all_converged": all(x == 0 for x in stt),
+                           "gpu_graph_speedup_est": est / (ms_graph / 1e3)}
+            c4["cpu_oracle"] = co
+        except Exception as exc:
+            c4["cpu_oracle"] = {"error": repr(exc)}
+    out["C4_uneven_10000"] = c4
+    del A4, B, graph
 
     # C5: differentiated batch, 4096 real 64 x 32, loss sum w sigma + <C, U[:, :8]>
     A5, w5, C5 = workloads.diff_batch_device(device=dev)
@@ -447,8 +622,45 @@ def svd_bench(torch, J, workloads, dev):
         torch.cuda.synchronize(dev)
         t = (e0.elapsed_time(e2), e0.elapsed_time(e1))
         best = t if best is None or t[1] < best[1] else best
-    out["C5_diff_4096x64x32"] = {"forward_ms": best[0], "forward_backward_ms": best[1],
-                                 "matrices_per_s": 4096 / (best[1] * 1e-3)}
+    c5 = {"forward_ms": best[0], "forward_backward_ms": best[1],
+          "matrices_per_s": 4096 / (best[1] * 1e-3)}
+    if cpu:
+        # the FP64 CPU reference of the same gradient: the oracle's SVD (the
+        # threads sharing out the matrices), the sign gauge, the oracle's
+        # adjoint; all 4096 matrices on all cores, 256 on one thread
+        try:
+            import oracle
+            G5 = X.grad.cpu().numpy()
+            A5h, w5h, C5h = A5.cpu().numpy(), w5.cpu().numpy(), C5.cpu().numpy()
+            kk = C5h.shape[2]
+            co = {"kind": "oracle", "sample": "all cores: the whole batch; one thread: the "
+                  "first 1024 matrices, scaled by 4"}
+            for key, thr, k in (("all_cores", 0, A5h.shape[0]), ("one_thread", 1, 1024)):
+                t0 = time.perf_counter()
+                sg, Us, Vs, stt = oracle.vjsvd_batch(list(A5h[:k]), nthreads=thr)
+                g = [oracle.sign_gauge(u, v) for u, v in zip(Us, Vs)]
+                U = np.stack([a for a, _ in g])
+                V = np.stack([b for _, b in g])
+                Ub = np.zeros_like(U)
+                Ub[:, :, :kk] = C5h[:k]
+                Gref = oracle.svd_adjoint_batch(U, np.stack(sg), V, Ub, w5h[:k], nthreads=thr)
+                dt = time.perf_counter() - t0
+                co[key] = {"threads": thr if thr else oracle.num_threads(), "matrices_timed": k,
+                           "s_timed": dt, "s_full_batch_est": dt * A5h.shape[0] / k,
+                           "all_converged": all(x == 0 for x in stt),
+                           "gpu_speedup_est": dt * A5h.shape[0] / k / (best[1] * 1e-3)}
+                if thr == 0:
+                    err = (np.abs(G5[:k] - Gref).max(axis=(1, 2))
+                           / np.maximum(np.abs(Gref).max(axis=(1, 2)), 1e-300))
+                    c5["grad_err_vs_cpu_reference"] = {
+                        "matrices": int(k), "max_rel": float(err.max()),
+                        "median_rel": float(np.median(err)),
+                        "above_1e-9": int((err > 1e-9).sum()),
+                        "measure": "per matrix max|G - G_ref| / max|G_ref|"}
+            c5["cpu_oracle"] = co
+        except Exception as exc:
+            c5["cpu_oracle"] = {"error": repr(exc)}
+    out["C5_diff_4096x64x32"] = c5
     return out
 
 
@@ -618,9 +830,16 @@ def run_ours(args):
                 "pipes_active": recorded_pipes(dom_name),
                 "algorithmic_bytes_per_launch": dom_bytes, "avg_launch_ms": dom_ms}
 
+    # the pipe that binds the EVD: its FP64 work against the FP64 pipe's
+    # throughput, measured now on this GPU
+    rates = fp64_pipe_rates(torch, J, dev)
+    roof_fp64 = {name: evd_fp64_roofline(name, t, R_EVD, rates)
+                 for name, t in (("evd2_kernel<real>", t_real), ("evd2_kernel<complex>", t_cplx))}
+
     svd = None
     if rank == 0 and world == 1 and not args.no_svd:
-        svd = svd_bench(torch, J, workloads, dev)
+        svd = svd_bench(torch, J, workloads, dev, rates, cpu=not args.no_cpu_baseline,
+                        loop_count=args.c4_loop)
     evd32 = None
     if rank == 0 and world == 1:
         evd32 = evd_f32_bench(torch, J, workloads, dev, peaks)
@@ -628,8 +847,13 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         dt, cores = cpu_oracle_evd(R_EVD)
+        r1 = 1 << 21
+        dt1, _ = cpu_oracle_evd_threads(r1, 1)
         cpu = {"value": 2 * R_EVD / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": "the full step: 2^24 real + 2^24 complex matrices, once"}
+               "sample": "the full step: 2^24 real + 2^24 complex matrices, once",
+               "one_thread": {"value": 2 * r1 / dt1, "unit": UNIT, "cores": 1,
+                              "sample": "2^21 real + 2^21 complex matrices, once"},
+               "omp": oracle_env()}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
@@ -651,6 +875,9 @@ def run_ours(args):
                         "staged": {"value": e2e_staged_value, "ms_per_step": e2e_staged_ms,
                                    "api": "the same call with JSVD_TUNE_EVD_HOST = 1 (copies "
                                           "to a device workspace in pipelined chunks)"}},
+                "roofline_fp64_pipe": roof_fp64[dom_name],
+                "roofline_fp64_pipe_other": roof_fp64[[k for k in roof_fp64 if k != dom_name][0]],
+                "fp64_pipe_rates": rates,
                 "cpu_baseline": cpu, "clocks": clk, "gpu_launches": gpu_launches,
                 "evd_fp32": evd32, "svd": svd}
         print(json.dumps(line), flush=True)

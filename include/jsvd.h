@@ -438,6 +438,17 @@ JSVD_API int jsvd_selftest_fp32div(int64_t n, uint64_t seed, unsigned long long 
 JSVD_API int jsvd_selftest_fp64(int64_t n, uint64_t seed, unsigned long long *mismatches,
                                 void *stream);
 
+/* Throughput probe of the FP64 pipe, the measured denominator of an
+ * FP64-pipe roofline (the paper has no counterpart): `blocks` blocks of 256
+ * threads, each thread 8 independent chains of `iters` operations of one
+ * kind -- 0: fused multiply-add (lane operations = blocks * 256 * 8 *
+ * iters); 1: the IEEE square root; 2: the IEEE division -- so that the pipe's
+ * throughput, not its latency, sets the time; the caller times the launch
+ * on `stream`.  sink: one DEVICE double the kernel writes.  Errors: -1 kind,
+ * -2 iters < 1, -3 blocks < 1, -4 sink NULL, JSVD_E_CUDA. */
+JSVD_API int jsvd_probe_fp64_rate(int kind, int64_t iters, int blocks, double *sink,
+                                  void *stream);
+
 /* Failure-detection self-test of the bounded grid barrier the persistent
  * SVD kernel uses between steps: a cooperative launch of `blocks` blocks
  * (1 .. number of SMs) takes `rounds` barriers; block `absent` (-1: none)

@@ -38,9 +38,10 @@ def lib():
         # check that the pins catch a planted mistake (run in a subprocess)
         path = os.environ.get("ORC_LIB") or _build.build()
         L = ctypes.CDLL(path)
-        L.orc_dsjac2.argtypes = [ctypes.c_int64, _d, _d, _d, _d, _d, _d, _d, _i32]
+        L.orc_dsjac2.argtypes = [ctypes.c_int64, _d, _d, _d, _d, _d, _d, _d, _i32, ctypes.c_int]
         L.orc_dsjac2.restype = None
-        L.orc_zsjac2.argtypes = [ctypes.c_int64, _d, _d, _d, _d, _d, _d, _d, _d, _d, _i32]
+        L.orc_zsjac2.argtypes = [ctypes.c_int64, _d, _d, _d, _d, _d, _d, _d, _d, _d, _i32,
+                                 ctypes.c_int]
         L.orc_zsjac2.restype = None
         L.orc_zsjac2_scaled.argtypes = [ctypes.c_int64, _d, _d, _d, _d, _d, _d]
         L.orc_zsjac2_scaled.restype = None
@@ -60,7 +61,7 @@ def lib():
         L.orc_pairs.restype = ctypes.c_int
         L.orc_vjsvd.argtypes = [ctypes.c_int64, ctypes.c_int64, _d, _d, ctypes.c_int64, _d, _d,
                                 _d, _d, _d, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
-                                ctypes.c_int, _i32, _i64]
+                                ctypes.c_int64, ctypes.c_int, _i32, _i64]
         L.orc_vjsvd.restype = ctypes.c_int
         L.orc_dpscl.argtypes = [ctypes.c_int64, _d, _d, _d, _d, ctypes.c_int, ctypes.c_double,
                                 ctypes.c_int, ctypes.c_double, ctypes.c_int, _d]
@@ -68,6 +69,14 @@ def lib():
         L.orc_svd_adjoint.argtypes = [ctypes.c_int64, ctypes.c_int64, _d, _d, _d, _d, _d, _d, _d]
         L.orc_svd_adjoint.restype = ctypes.c_int
         L.orc_num_threads.restype = ctypes.c_int
+        L.orc_vjsvd_batch.argtypes = [ctypes.c_int64, _i64, _i64, _i64, _i64, _i64, _d, _d, _d,
+                                      ctypes.c_int, ctypes.c_int, _i32]
+        L.orc_vjsvd_batch.restype = ctypes.c_int
+        L.orc_svd_adjoint_batch.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, _d, _d,
+                                            _d, _d, _d, _d, ctypes.c_int]
+        L.orc_svd_adjoint_batch.restype = ctypes.c_int
+        L.orc_omp_state.argtypes = [_i32]
+        L.orc_omp_state.restype = None
         _lib = L
     return _lib
 
@@ -75,6 +84,18 @@ def lib():
 def num_threads():
     """OpenMP threads the oracle's parallel loops use."""
     return int(lib().orc_num_threads())
+
+
+_BIND = {0: "false", 1: "true", 2: "primary", 3: "close", 4: "spread"}
+
+
+def omp_state():
+    """The OpenMP environment in force for the oracle's loops: dict(threads,
+    proc_bind, places, dynamic)."""
+    out = np.zeros(4, dtype=np.int32)
+    lib().orc_omp_state(out.ctypes.data_as(_i32))
+    return {"threads": int(out[0]), "proc_bind": _BIND.get(int(out[1]), str(int(out[1]))),
+            "places": int(out[2]), "dynamic": bool(out[3])}
 
 
 def _dp(a):
@@ -117,19 +138,20 @@ def csjac2(a11, a22, a21r, a21i):
     return (*out, zp)
 
 
-def dsjac2(a11, a22, a21):
+def dsjac2(a11, a22, a21, nthreads=0):
     """Real symmetric 2x2 EVD of each (a11, a22, a21): returns
-    (cos_phi, sign(a21) tan_phi, lambda1, lambda2, zeta_p)."""
+    (cos_phi, sign(a21) tan_phi, lambda1, lambda2, zeta_p).  nthreads > 0
+    sets the OpenMP threads (else the default)."""
     a11, a22, a21 = _f64(a11), _f64(a22), _f64(a21)
     r = a11.size
     out = [np.empty(r) for _ in range(4)]
     zp = np.empty(r, dtype=np.int32)
     lib().orc_dsjac2(r, _dp(a11), _dp(a22), _dp(a21), *[_dp(o) for o in out],
-                     zp.ctypes.data_as(_i32))
+                     zp.ctypes.data_as(_i32), int(nthreads))
     return (*out, zp)
 
 
-def zsjac2(a11, a22, a21r, a21i):
+def zsjac2(a11, a22, a21r, a21i, nthreads=0):
     """Complex Hermitian 2x2 EVD (section 2, Alg. z8jac2): returns (cos_phi,
     cos_alpha tan_phi, sin_alpha tan_phi, lambda1, lambda2, zeta_p)."""
     a11, a22, a21r, a21i = _f64(a11), _f64(a22), _f64(a21r), _f64(a21i)
@@ -137,7 +159,7 @@ def zsjac2(a11, a22, a21r, a21i):
     out = [np.empty(r) for _ in range(5)]
     zp = np.empty(r, dtype=np.int32)
     lib().orc_zsjac2(r, _dp(a11), _dp(a22), _dp(a21r), _dp(a21i), *[_dp(o) for o in out],
-                     zp.ctypes.data_as(_i32))
+                     zp.ctypes.data_as(_i32), int(nthreads))
     return (*out, zp)
 
 
@@ -160,12 +182,15 @@ def pairs(n):
     return tab[: nt - 1] if nt >= 2 else tab[:0]
 
 
-def vjsvd(A, max_sweeps=100, nthreads=0, permute=False, compensated=False, skr_shift=0):
+def vjsvd(A, max_sweeps=100, nthreads=0, permute=False, compensated=False, skr_shift=0,
+          max_steps=0):
     """One-sided Jacobi SVD of A (m x n, m >= n; real or complex).  permute
     applies the column swap P of section 2 during the sweeps; compensated
     forms the scaled dot-products by Alg. zdpscl' / ddpscl'; skr_shift > 0
     lowers the per-step rescaling threshold of section 3.2 (Eq. e:skr) by
-    2^skr_shift, so that the rescaling branch runs (results unchanged).
+    2^skr_shift, so that the rescaling branch runs (results unchanged);
+    max_steps > 0 stops after that many parallel steps (for timing a bounded
+    sample; status then NOT_CONVERGED).
 
     Returns dict(U, sigma, sigma_e, sigma_f, V, status, sweeps, rotations,
     rescales).  sigma is sorted non-increasingly; A ~= U diag(sigma) V^H.
@@ -182,7 +207,8 @@ def vjsvd(A, max_sweeps=100, nthreads=0, permute=False, compensated=False, skr_s
     rot = np.zeros(1, dtype=np.int64)
     rc = lib().orc_vjsvd(m, n, _dp(Gr), _dp(Gi), m, _dp(Vr), _dp(Vi), _dp(sig), _dp(se),
                          _dp(sf), int(max_sweeps), 1 if permute else 0,
-                         1 if compensated else 0, int(skr_shift), int(nthreads),
+                         1 if compensated else 0, int(skr_shift), int(max_steps),
+                         int(nthreads),
                          info.ctypes.data_as(_i32),
                          rot.ctypes.data_as(_i64))
     if rc < 0:
@@ -192,6 +218,48 @@ def vjsvd(A, max_sweeps=100, nthreads=0, permute=False, compensated=False, skr_s
     return dict(U=U, sigma=sig, sigma_e=se, sigma_f=sf,
                 V=V, status=int(info[0]), sweeps=int(info[1]), rotations=int(rot[0]),
                 rescales=int(info[3]), gs=int(info[4]))
+
+
+def vjsvd_batch(mats, max_sweeps=100, nthreads=0):
+    """Real SVDs of a list of matrices, the OpenMP threads sharing out the
+    matrices (each matrix's SVD on one thread).  Returns (sigmas, Us, Vs,
+    statuses), lists in the order of mats."""
+    m = np.array([a.shape[0] for a in mats], dtype=np.int64)
+    n = np.array([a.shape[1] for a in mats], dtype=np.int64)
+    offA = np.concatenate([[0], np.cumsum(m * n)[:-1]]).astype(np.int64)
+    offV = np.concatenate([[0], np.cumsum(n * n)[:-1]]).astype(np.int64)
+    offS = np.concatenate([[0], np.cumsum(n)[:-1]]).astype(np.int64)
+    G = np.concatenate([np.asarray(a, dtype=np.float64).ravel(order="F") for a in mats])
+    V = np.zeros(int((n * n).sum()))
+    sig = np.zeros(int(n.sum()))
+    st = np.zeros(len(mats), dtype=np.int32)
+    rc = lib().orc_vjsvd_batch(len(mats), m.ctypes.data_as(_i64), n.ctypes.data_as(_i64),
+                               offA.ctypes.data_as(_i64), offV.ctypes.data_as(_i64),
+                               offS.ctypes.data_as(_i64), _dp(G), _dp(V), _dp(sig),
+                               int(max_sweeps), int(nthreads), st.ctypes.data_as(_i32))
+    if rc != 0:
+        raise ValueError("orc_vjsvd_batch failed with %d" % rc)
+    sigmas = [sig[o:o + k] for o, k in zip(offS, n)]
+    Us = [G[o:o + a * b].reshape(b, a).T for o, a, b in zip(offA, m, n)]
+    Vs = [V[o:o + k * k].reshape(k, k).T for o, k in zip(offV, n)]
+    return sigmas, Us, Vs, [int(x) for x in st]
+
+
+def svd_adjoint_batch(U, s, V, Ubar, sbar, nthreads=0):
+    """svd_adjoint for a batch of one shape: U, Ubar [count, m, n], V
+    [count, n, n], s, sbar [count, n] (each matrix stored column-major,
+    i.e. arrays indexed [i, row, col] are transposed per matrix here).
+    Returns Abar [count, m, n]."""
+    count, m, n = U.shape
+    f = lambda X: np.ascontiguousarray(np.swapaxes(X, 1, 2), dtype=np.float64)  # column-major
+    Uc, Vc, Ubc = f(U), f(V), f(Ubar)
+    sc, sbc = _f64(s), _f64(sbar)
+    Ab = np.zeros((count, n, m))
+    rc = lib().orc_svd_adjoint_batch(count, m, n, _dp(Uc), _dp(sc), _dp(Vc), _dp(Ubc), _dp(sbc),
+                                     _dp(Ab), int(nthreads))
+    if rc != 0:
+        raise ValueError("orc_svd_adjoint_batch failed with %d" % rc)
+    return np.swapaxes(Ab, 1, 2)
 
 
 def dpscl(q, p, compensated=False, eq=0, fq=1.0, ep=0, fp=1.0):

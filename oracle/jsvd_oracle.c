@@ -80,6 +80,17 @@
 #endif
 #define MUT(k, good, bad) ((ORC_MUTANT == (k)) ? (bad) : (good))
 
+/* Threads of a parallel loop: nthreads if positive, else the default. */
+static int omp_threads(int nthreads)
+{
+#ifdef _OPENMP
+  return (nthreads > 0) ? nthreads : omp_get_max_threads();
+#else
+  (void)nthreads;
+  return 1;
+#endif
+}
+
 /* ------------------------------------------------------------------------
  * The 2x2 Hermitian EVD of section 2, restated from its equations:
  *   Eq. "e:z"       the power-of-two scaling A' = 2^zeta A;
@@ -232,9 +243,10 @@ static int32_t pack_zp(int zeta, int p)
 /* Batched real EVD (Alg. dbjac2): outputs cos(phi), sign(a21) tan(phi),
  * lambda1, lambda2 and the packed (zeta', p); lam1, lam2, zp may be NULL. */
 ORC_EXPORT void orc_dsjac2(int64_t r, const double *a11, const double *a22, const double *a21,
-                           double *cphi, double *tphi, double *lam1, double *lam2, int32_t *zp)
+                           double *cphi, double *tphi, double *lam1, double *lam2, int32_t *zp,
+                           int nthreads)
 {
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for schedule(static) num_threads(omp_threads(nthreads))
   for (int64_t i = 0; i < r; ++i) {
     struct evd2 o;
     evd2_real(a11[i], a22[i], a21[i], &o);
@@ -250,9 +262,9 @@ ORC_EXPORT void orc_dsjac2(int64_t r, const double *a11, const double *a22, cons
  * sin(alpha) tan(phi), lambda1, lambda2 and the packed (zeta', p). */
 ORC_EXPORT void orc_zsjac2(int64_t r, const double *a11, const double *a22, const double *a21r,
                            const double *a21i, double *cphi, double *catphi, double *satphi,
-                           double *lam1, double *lam2, int32_t *zp)
+                           double *lam1, double *lam2, int32_t *zp, int nthreads)
 {
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for schedule(static) num_threads(omp_threads(nthreads))
   for (int64_t i = 0; i < r; ++i) {
     struct evd2 o;
     evd2_complex(a11[i], a22[i], a21r[i], a21i[i], &o);
@@ -782,16 +794,21 @@ ORC_EXPORT int orc_num_threads(void)
  *     grows by about 2m; a positive shift makes the branch run on ordinary
  *     inputs, so that the tests can pin it.  Power-of-two scaling is exact,
  *     so without underflow the results do not depend on the shift.
+ *   max_steps > 0 stops the sweeps after that many parallel steps (status
+ *     not converged), so that a run can be timed on a bounded sample of a
+ *     large problem; <= 0: no limit.
  * nthreads <= 0 leaves the OpenMP default.
  */
 ORC_EXPORT int orc_vjsvd(int64_t m, int64_t n, double *Gr, double *Gi, int64_t ld, double *Vr,
                          double *Vi, double *sig, double *sig_e, double *sig_f, int max_sweeps,
-                         int permute, int compensated, int skr_shift, int nthreads,
-                         int32_t *out_info, int64_t *rotations64)
+                         int permute, int compensated, int skr_shift, int64_t max_steps,
+                         int nthreads, int32_t *out_info, int64_t *rotations64)
 {
   if (m < 1 || n < 1 || m < n || ld < m || max_sweeps < 1 || skr_shift < 0) return ORC_E_ARG;
 #ifdef _OPENMP
-  if (nthreads > 0) omp_set_num_threads(nthreads);
+  /* a num_threads clause, not omp_set_num_threads: later calls keep the
+   * default */
+  const int n_thr = (nthreads > 0) ? nthreads : omp_get_max_threads();
 #else
   (void)nthreads;
 #endif
@@ -829,9 +846,16 @@ ORC_EXPORT int orc_vjsvd(int64_t m, int64_t n, double *Gr, double *Gi, int64_t l
     const double ups = ldexp(sqrt((double)m), -53);
     const int K = nt - 1, L = nt / 2;
     int converged = (nt < 2);
-    for (int C = 0; C < max_sweeps && !converged; ++C) {
+    int64_t steps_done = 0;
+    int stopped = 0;
+    for (int C = 0; C < max_sweeps && !converged && !stopped; ++C) {
       int64_t T = 0;
       for (int k = 0; k < K; ++k) {
+        if (max_steps > 0 && steps_done == max_steps) {
+          stopped = 1;
+          break;
+        }
+        ++steps_done;
         /* steps 2-4 of the heuristic: s_(k) < 0 (Eq. "e:skr") => G is
          * downscaled by 2^{s_[k]} (Eq. "e:skn"), M~ with it, and s_[k] is
          * added to the running scale exponent s */
@@ -849,7 +873,8 @@ ORC_EXPORT int orc_vjsvd(int64_t m, int64_t n, double *Gr, double *Gi, int64_t l
         }
         int64_t t = 0;
         double Mstep = 0.0;
-#pragma omp parallel for schedule(static) reduction(+ : t, gs_count) reduction(max : Mstep)
+#pragma omp parallel for schedule(static) num_threads(n_thr) reduction(+ : t, gs_count) \
+    reduction(max : Mstep)
         for (int l = 0; l < L; ++l) {
           const int p = tab[2 * ((int64_t)k * L + l)], q = tab[2 * ((int64_t)k * L + l) + 1];
           if (q >= n) continue; /* phantom column */
@@ -929,7 +954,7 @@ ORC_EXPORT int orc_vjsvd(int64_t m, int64_t n, double *Gr, double *Gi, int64_t l
       }
       rotations += T;
       sweeps = C + 1;
-      if (T == 0) converged = 1;
+      if (T == 0 && !stopped) converged = 1;
     }
     if (!converged) status = ORC_NOT_CONVERGED;
   }
@@ -1076,4 +1101,66 @@ ORC_EXPORT int orc_svd_adjoint(int64_t m, int64_t n, const double *U, const doub
   free(In);
   free(W);
   return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------
+ * Batches for the timings of the batched workloads: the matrices are
+ * independent, so the OpenMP threads share them out (dynamic schedule),
+ * each matrix's SVD running on one thread.  Nothing here changes what one
+ * SVD or one adjoint computes. */
+
+/* Real SVDs of count matrices packed column-major back to back: matrix i
+ * (m[i] x n[i], leading dimension m[i]) at G + offA[i], overwritten by U;
+ * V_i (n[i] x n[i]) at V + offV[i]; sigma_i at sig + offS[i].  status[i]
+ * receives orc_vjsvd's return value.  nthreads <= 0: the OpenMP default. */
+ORC_EXPORT int orc_vjsvd_batch(int64_t count, const int64_t *m, const int64_t *n,
+                               const int64_t *offA, const int64_t *offV, const int64_t *offS,
+                               double *G, double *V, double *sig, int max_sweeps, int nthreads,
+                               int32_t *status)
+{
+  if (count < 0 || !m || !n || !offA || !offV || !offS || !G || !V || !sig || !status)
+    return ORC_E_ARG;
+#ifdef _OPENMP
+  const int nt = (nthreads > 0) ? nthreads : omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nt)
+#endif
+  for (int64_t i = 0; i < count; ++i)
+    status[i] = orc_vjsvd(m[i], n[i], G + offA[i], NULL, m[i], V + offV[i], NULL, sig + offS[i],
+                          NULL, NULL, max_sweeps, 0, 0, 0, 0, 1, NULL, NULL);
+  return ORC_OK;
+}
+
+/* orc_svd_adjoint for count matrices of one shape m x n packed back to
+ * back (U, Ubar, Abar: m n each; V: n n; s, sbar: n); Vbar is zero. */
+ORC_EXPORT int orc_svd_adjoint_batch(int64_t count, int64_t m, int64_t n, const double *U,
+                                     const double *s, const double *V, const double *Ubar,
+                                     const double *sbar, double *Abar, int nthreads)
+{
+  if (count < 0 || m < 1 || n < 1) return ORC_E_ARG;
+  int bad = 0;
+#ifdef _OPENMP
+  const int nt = (nthreads > 0) ? nthreads : omp_get_max_threads();
+#pragma omp parallel for schedule(static) num_threads(nt) reduction(| : bad)
+#endif
+  for (int64_t i = 0; i < count; ++i)
+    bad |= (orc_svd_adjoint(m, n, U + i * m * n, s + i * n, V + i * n * n, Ubar + i * m * n,
+                            sbar + i * n, NULL, Abar + i * m * n) != ORC_OK);
+  return bad ? ORC_E_ARG : ORC_OK;
+}
+
+/* The OpenMP environment in force for the oracle's parallel loops:
+ * out[0] = threads a parallel region gets, out[1] = omp_get_proc_bind()
+ * (0 false, 1 true, 2 primary, 3 close, 4 spread), out[2] = number of
+ * places, out[3] = omp_get_dynamic().  Without OpenMP: {1, 0, 0, 0}. */
+ORC_EXPORT void orc_omp_state(int32_t *out)
+{
+#ifdef _OPENMP
+  out[0] = omp_get_max_threads();
+  out[1] = (int32_t)omp_get_proc_bind();
+  out[2] = omp_get_num_places();
+  out[3] = omp_get_dynamic();
+#else
+  out[0] = 1;
+  out[1] = out[2] = out[3] = 0;
+#endif
 }

@@ -326,6 +326,16 @@ def ordering(n, stream=None):
     return tab
 
 
+def probe_fp64_rate(kind, iters, blocks, sink, stream=None):
+    """Enqueue the FP64-pipe throughput probe (jsvd_probe_fp64_rate): kind 0
+    fused multiply-add, 1 IEEE square root, 2 IEEE division; blocks x 256
+    threads x 8 chains x iters operations.  sink: a float64 CUDA tensor of
+    at least one element.  The caller times the launch."""
+    _native.check(_native.lib().jsvd_probe_fp64_rate(int(kind), int(iters), int(blocks),
+                                                     sink.data_ptr(), _stream_handle(stream)),
+                  "jsvd_probe_fp64_rate")
+
+
 def dgemm(A, B, *, transA=False, alpha=1.0, beta=0.0, C=None, stream=None):
     """C = alpha op(A) B + beta C (jsvd_dgemm) for float64 CUDA tensors, any
     layout (column-major copies are made when needed)."""

@@ -6,7 +6,10 @@
 //     precision EVD (evd2f.cuh) against the FP32 pipe's IEEE division;
 //   jsvd_selftest_barrier: the bounded grid barrier of the persistent SVD
 //     kernel, with one block that never arrives, so the others' wait runs
-//     out and they report JSVD_E_TIMEOUT (no fault, no trap).
+//     out and they report JSVD_E_TIMEOUT (no fault, no trap);
+//   jsvd_probe_fp64_rate: a throughput probe of the FP64 pipe (FMA, IEEE
+//     square root, IEEE division), the denominator of the FP64-pipe
+//     rooflines the benchmark reports.
 #include <algorithm>
 
 #include "common.cuh"
@@ -162,7 +165,60 @@ __global__ void selftest32_kernel(int64_t n, uint64_t seed, unsigned long long *
   if (bd) atomicAdd(bad, bd);
 }
 
+// Throughput probe of the FP64 pipe: every thread runs kChains independent
+// chains of `iters` operations of one kind, so the pipe, not latency,
+// limits the rate.  kind 0: x = fma(x, a, b) (the DFMA rate); kind 1: the
+// IEEE square root __dsqrt_rn of a fresh operand each time; kind 2: the
+// IEEE division __ddiv_rn.  The fresh operands of kinds 1 and 2 come from
+// integer increments of a bit pattern and the results are folded with
+// integer XOR, so that only the operation itself runs on the FP64 pipe.
+// One thread writes the folded value to sink[0] (keeps the work alive).
+constexpr int kProbeChains = 8;
+
+__global__ void __launch_bounds__(256) probe_fp64_kernel(int kind, int64_t iters, double *sink)
+{
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  uint64_t fold = 0;
+  if (kind == 0) {
+    double x[kProbeChains];
+#pragma unroll
+    for (int c = 0; c < kProbeChains; ++c) x[c] = 1.0 + 1e-9 * (t + c);
+    const double a = 0.999999999, b = 1e-9;
+    for (int64_t i = 0; i < iters; ++i) {
+#pragma unroll
+      for (int c = 0; c < kProbeChains; ++c) x[c] = __fma_rn(x[c], a, b);
+    }
+#pragma unroll
+    for (int c = 0; c < kProbeChains; ++c) fold ^= bits(x[c]);
+  } else {
+    uint64_t u[kProbeChains];
+#pragma unroll
+    for (int c = 0; c < kProbeChains; ++c) u[c] = 0x3FF8000000000000ull + 977ull * (t * kProbeChains + c);
+    for (int64_t i = 0; i < iters; ++i) {
+#pragma unroll
+      for (int c = 0; c < kProbeChains; ++c) {
+        const double r = (kind == 1) ? __dsqrt_rn(dbl(u[c])) : __ddiv_rn(1.25, dbl(u[c]));
+        fold ^= bits(r);
+        u[c] += 0x10001ull;
+      }
+    }
+  }
+  if (t == 0 || fold == 0x123456789ull) sink[0] = dbl(fold & 0x3FFFFFFFFFFFFFFFull);
+}
+
 }  // namespace jsvd
+
+extern "C" int jsvd_probe_fp64_rate(int kind, int64_t iters, int blocks, double *sink,
+                                    void *stream)
+{
+  if (kind < 0 || kind > 2) return -1;
+  if (iters < 1) return -2;
+  if (blocks < 1) return -3;
+  if (!sink) return -4;
+  jsvd::probe_fp64_kernel<<<blocks, 256, 0, jsvd::as_stream(stream)>>>(kind, iters, sink);
+  JSVD_CHECK_LAUNCH();
+  return JSVD_OK;
+}
 
 extern "C" int jsvd_selftest_fp32div(int64_t n, uint64_t seed, unsigned long long *mismatches,
                                      void *stream)

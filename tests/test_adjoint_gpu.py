@@ -42,21 +42,26 @@ def test_adjoint_kernel_against_oracle_formula():
 
 def test_gradient_against_cpu_reference():
     """Gradient of the loss vs the FP64 CPU reference (oracle SVD, sign
-    gauge, oracle adjoint)."""
+    gauge, oracle adjoint) on 64 matrices of the differentiated workload's
+    shape and conditioning (64 x 32, condition 1e3)."""
     torch = _torch()
     k = 8
-    A, w, C = workloads.diff_batch(count=6, m=64, n=32, k=k)
+    count = 64
+    A, w, C = workloads.diff_batch(count=count, m=64, n=32, k=k)
     At = torch.from_numpy(A).cuda().requires_grad_(True)
     L = loss_gpu(At, torch.from_numpy(w).cuda(), torch.from_numpy(C).cuda(), k)
     L.backward()
     G = At.grad.cpu().numpy()
-    for i in range(6):
-        r = oracle.vjsvd(A[i])
-        U, V = oracle.sign_gauge(r["U"], r["V"])
-        Ub = np.zeros_like(U)
-        Ub[:, :k] = C[i]
-        ref = oracle.svd_adjoint(U, r["sigma"], V, Ub, w[i])
-        assert np.abs(G[i] - ref).max() <= 1e-9 * np.abs(ref).max(), i
+    sg, Us, Vs, st = oracle.vjsvd_batch(list(A))
+    assert all(x == oracle.OK for x in st)
+    gauged = [oracle.sign_gauge(u, v) for u, v in zip(Us, Vs)]
+    U = np.stack([u for u, _ in gauged])
+    V = np.stack([v for _, v in gauged])
+    Ub = np.zeros_like(U)
+    Ub[:, :, :k] = C
+    ref = oracle.svd_adjoint_batch(U, np.stack(sg), V, Ub, w)
+    for i in range(count):
+        assert np.abs(G[i] - ref[i]).max() <= 1e-9 * np.abs(ref[i]).max(), i
 
 
 def test_gradient_central_differences_small():

@@ -1,7 +1,8 @@
 """The batched uneven SVD (jsvd_svd_batched): every matrix gives the same
 bits as jsvd_svd on it alone, whatever the batch, the position in it and
-the block shape; parity with the oracle; the full 10,000-matrix workload
-meets the acceptance bounds on a sample; a captured CUDA graph replays it."""
+the block shape; parity with the oracle; every matrix of the full 10,000-matrix workload meets the
+acceptance bounds, and 50 of them match the oracle; a captured CUDA graph
+replays it."""
 import numpy as np
 import pytest
 
@@ -166,8 +167,11 @@ def test_batched_edge_cases():
 
 def test_full_workload_10000_uneven():
     """The 10,000-matrix uneven workload (n ~ U{16..256}, m ~ U{n..2n},
-    condition 1e4): all converge; a sample meets the bounds and matches the
-    oracle; the prescribed spectra are recovered."""
+    condition 1e4): every matrix converges and meets the bounds -- residual,
+    both orthogonalities and the prescribed spectrum, checked for all 10,000
+    on the GPU (matrices of one n padded to 2n rows with zeros, which change
+    none of the measures) -- and 50 of them, among them the smallest and one
+    of the largest (n = 256), match the oracle's singular values."""
     import paper_2202_08361_gb300 as J
     torch = _torch()
     A, m, n = workloads.uneven_batch_device()
@@ -175,21 +179,49 @@ def test_full_workload_10000_uneven():
     torch.cuda.synchronize()
     info = J.decode_info(B.info)
     assert all(x["status"] == 0 for x in info)
+    worst = {"res": 0.0, "orth": 0.0, "sigma": 0.0}
+    for nv in np.unique(n):
+        idx = np.nonzero(n == nv)[0]
+        nv = int(nv)
+        k = len(idx)
+        Ap = torch.zeros((k, 2 * nv, nv), dtype=torch.float64, device="cuda")
+        Up = torch.zeros_like(Ap)
+        Vb = torch.empty((k, nv, nv), dtype=torch.float64, device="cuda")
+        Sb = torch.empty((k, nv), dtype=torch.float64, device="cuda")
+        for t, i in enumerate(idx):
+            mi = int(m[i])
+            Ap[t, :mi] = A[int(B.offA[i]):int(B.offA[i]) + mi * nv].view(nv, mi).t()
+            U, s, V = B.matrix(int(i))
+            Up[t, :mi] = U
+            Vb[t] = V
+            Sb[t] = s
+        I = torch.eye(nv, dtype=torch.float64, device="cuda")
+        res = (torch.linalg.norm(Ap - (Up * Sb[:, None, :]) @ Vb.transpose(1, 2), dim=(1, 2))
+               / torch.linalg.norm(Ap, dim=(1, 2)))
+        ou = (Up.transpose(1, 2) @ Up - I).abs().amax(dim=(1, 2))
+        ov = (Vb.transpose(1, 2) @ Vb - I).abs().amax(dim=(1, 2))
+        sref = torch.as_tensor(workloads.geometric_sigma(nv, 1e4), device="cuda")
+        es = (Sb - sref).abs().amax(dim=1) / sref[0]
+        b = tol(nv)
+        worst["res"] = max(worst["res"], res.max().item() / b)
+        worst["orth"] = max(worst["orth"], max(ou.max().item(), ov.max().item()) / b)
+        worst["sigma"] = max(worst["sigma"], es.max().item() / b)
+        assert res.max().item() <= b, (nv, res.max().item())
+        assert ou.max().item() <= b and ov.max().item() <= b, (nv, ou.max().item(), ov.max().item())
+        assert es.max().item() <= b, (nv, es.max().item())
+    # the oracle on 50 matrices (the OpenMP threads share them out)
     g = np.random.default_rng(11)
-    sample = sorted(set(g.choice(len(m), 12, replace=False).tolist() + [int(np.argmin(m * n))]))
-    for i in sample:
-        mi, ni = int(m[i]), int(n[i])
-        Ai = A[int(B.offA[i]):int(B.offA[i]) + mi * ni].view(ni, mi).t().cpu().numpy()
-        U, s, V = (t.cpu().numpy() for t in B.matrix(i))
-        res = np.linalg.norm(Ai - (U * s) @ V.T) / np.linalg.norm(Ai)
-        assert res <= tol(ni), (i, res)
-        assert np.abs(U.T @ U - np.eye(ni)).max() <= tol(ni)
-        assert np.abs(V.T @ V - np.eye(ni)).max() <= tol(ni)
-        sref = workloads.geometric_sigma(ni, 1e4)
-        assert np.abs(s - sref).max() <= tol(ni) * sref[0]
-        if mi * ni <= 64 * 64:
-            o = oracle.vjsvd(Ai)
-            assert np.abs(s - o["sigma"]).max() <= tol(ni) * o["sigma"][0]
+    big = int(np.nonzero(n == n.max())[0][np.argmax(m[n == n.max()])])
+    sample = sorted(set(g.choice(len(m), 48, replace=False).tolist()
+                        + [int(np.argmin(m * n)), big]))
+    assert len(sample) >= 50 and int(n[big]) == 256
+    host = [A[int(B.offA[i]):int(B.offA[i]) + int(m[i] * n[i])].view(int(n[i]), int(m[i])).t()
+            .cpu().numpy() for i in sample]
+    sg, _, _, st = oracle.vjsvd_batch(host)
+    assert all(x == oracle.OK for x in st)
+    for i, so in zip(sample, sg):
+        s = B.matrix(i)[1].cpu().numpy()
+        assert np.abs(s - so).max() <= tol(int(n[i])) * so[0], i
 
 
 def test_cuda_graph_replay():

@@ -9,6 +9,7 @@ import pytest
 
 import oracle
 from paper_2202_08361_gb300 import workloads
+from tests.golden import c3_fixture
 
 pytestmark = pytest.mark.gpu
 
@@ -104,6 +105,17 @@ def test_mixed_full_size_complex_4096x2048():
     assert (U.conj().T @ U - I).abs().max().item() <= tol(n)
     assert (V.conj().T @ V - I).abs().max().item() <= tol(n)
     assert np.abs(sg.cpu().numpy() - s).max() <= tol(n) * s[0]
+    # against the oracle's FP64 SVD of the same matrix (stored by
+    # tests/golden/make_c3_oracle.py): sigma normwise within 64 n eps, and
+    # the sampled singular vectors within the perturbation bound 64 n eps
+    # sigma_1 / gap_j
+    fx = c3_fixture.load()
+    assert fx is not None, "tests/golden/c3_oracle_4096x2048.npz is missing"
+    cols = torch.from_numpy(fx["cols"]).cuda()
+    e = c3_fixture.errors(sg.cpu().numpy(), U[:, cols].cpu().numpy(), V[:, cols].cpu().numpy(), fx)
+    assert e["sigma_max_err_normwise"] <= tol(n), e
+    for eu, ev, b in zip(e["U_col_err"], e["V_col_err"], e["col_bound_64neps_over_gap"]):
+        assert eu <= b and ev <= b, e
 
 
 def test_mixed_nonfinite_and_zero():
