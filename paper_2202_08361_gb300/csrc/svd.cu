@@ -23,6 +23,8 @@
 #include <algorithm>
 #include <climits>
 
+#include <cooperative_groups.h>
+
 #include "common.cuh"
 #include "jsvd_internal.h"
 #include "svd_core.cuh"
@@ -158,14 +160,17 @@ __global__ void __launch_bounds__(256) sweeps_kernel(MatViewT<T> M, SvdState *st
 {
   __shared__ PairSums s_sums[8];
   __shared__ PairOut s_out[8];
+  __shared__ double s_gsum[kGroupWarps];
   if (st->nonfinite) return;
+  const bool group = (flags & kFlagGroupStep) != 0;
+  GroupV<CPLX> gv;
   const int nt = M.n + (M.n & 1);
   const int K = nt - 1, L = nt / 2;
   const int lane = threadIdx.x & 31, W = blockDim.x >> 5;
   const bool warp_step = (flags & kFlagWarpStep) != 0;
   // V's transformation held over to the next step (DeferredV) when every
   // warp has at most one pair per step and V's rows take one trip
-  const bool defer = warp_step && (int64_t)gridDim.x * W >= L &&
+  const bool defer = !group && warp_step && (int64_t)gridDim.x * W >= L &&
                      M.np <= 32 * DeferredV<T, CPLX>::kRows;
   DeferredV<T, CPLX> dv;
   if (K < 1) {
@@ -195,7 +200,13 @@ __global__ void __launch_bounds__(256) sweeps_kernel(MatViewT<T> M, SvdState *st
       }
       unsigned long long Mloc = 0ull;
       int rots = 0, gsn = 0;
-      if (warp_step)
+      if constexpr (sizeof(T) == 8 && !COMP) {
+        if (group)
+          step_group<CPLX>(M, k, nt, ups, rk, (flags & kFlagPermute) != 0, Mloc, rots, gsn, gv,
+                           s_gsum);
+      }
+      if (group) {
+      } else if (warp_step)
         step_warps<T, CPLX, COMP>(M, k, nt, ups, rk, (flags & kFlagPermute) != 0, Mloc, rots, gsn,
                                   defer, dv);
       else
@@ -216,10 +227,106 @@ __global__ void __launch_bounds__(256) sweeps_kernel(MatViewT<T> M, SvdState *st
     dv.load(M);
     dv.apply(M);
   }
+  if constexpr (sizeof(T) == 8 && !COMP) {
+    if (group && gv.p >= 0) {
+      gv.load(M, threadIdx.x >> 5);
+      gv.apply(M, threadIdx.x >> 5);
+    }
+  }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     st->sweeps = sweep;
     st->converged = converged ? 1 : 0;
   }
+}
+
+// The sweeps of a small matrix inside one thread-block cluster of R = 2^lgR
+// blocks (one per SM): the steps are separated by the cluster's hardware
+// barrier (barrier.cluster with release / acquire semantics, which orders
+// the blocks' global-memory accesses at cluster scope) instead of a grid
+// barrier polling global memory, and the running max-norm M~ and the
+// sweep's rotation count live in rank 0's shared memory.  G and V stay in
+// the workspace, reached through L2 as in sweeps_kernel, and the per-warp
+// step is the one of sweeps_kernel (step_warps): the same operations in
+// the same order, so the same bits.  (Holding G and V in the blocks'
+// shared memory, reached through the cluster's shared window, measured
+// slower on GB300: 256 x 128 15.0 vs 14.4 ms.)
+constexpr int kClusterMax = 16;
+
+template <typename T, bool CPLX, bool COMP>
+__global__ void __launch_bounds__(256) sweeps_cluster_kernel(MatViewT<T> M, SvdState *st,
+                                                             double ups, int max_sweeps,
+                                                             int rescale_exp, int flags)
+{
+  namespace cgr = cooperative_groups;
+  cgr::cluster_group cluster = cgr::this_cluster();
+  __shared__ unsigned long long s_M[3];  // rank 0's is M~ (triple-buffered by step)
+  __shared__ int s_T[3];                 // rank 0's counts a sweep's rotations
+  if (st->nonfinite) return;  // the same for every block: none reaches a barrier
+  const int rank = (int)cluster.block_rank();
+  const int nt = M.n + (M.n & 1);
+  const int K = nt - 1, L = nt / 2;
+  const int lane = threadIdx.x & 31, W = blockDim.x >> 5;
+  if (threadIdx.x < 3) {
+    s_M[threadIdx.x] = (threadIdx.x == 0) ? ((volatile unsigned long long *)st->Mbuf)[0] : 0ull;
+    s_T[threadIdx.x] = 0;
+  }
+  unsigned long long *M0 = cluster.map_shared_rank(s_M, 0);
+  int *T0 = cluster.map_shared_rank(s_T, 0);
+  const bool defer = (int64_t)gridDim.x * W >= L && M.np <= 32 * DeferredV<T, CPLX>::kRows;
+  DeferredV<T, CPLX> dv;
+  cluster.sync();
+  if (K < 1) {
+    if (rank == 0 && threadIdx.x == 0) {
+      st->sweeps = 1;
+      st->converged = 1;
+    }
+    return;
+  }
+  unsigned long long gstep = 0;
+  int sweep = 0;
+  bool converged = false;
+  for (; sweep < max_sweeps && !converged; ++sweep) {
+    for (int k = 0; k < K; ++k, ++gstep) {
+      const int cur = (int)(gstep % 3), nxt = (int)((gstep + 1) % 3), old = (int)((gstep + 2) % 3);
+      const double Mcur = dbl(((volatile unsigned long long *)M0)[cur]);
+      // section 3.2, step 2: rescale when M~ has grown past 2^rescale_exp
+      const int rk =
+          (bits(Mcur) != 0ull && flg(Mcur) >= rescale_exp) ? scale_target(rescale_exp) - flg(Mcur) : 0;
+      if (rank == 0 && threadIdx.x == 0) {
+        s_M[old] = 0ull;
+        atomicMax(&s_M[nxt], bits(rk ? ldexp_rn(Mcur, rk) : Mcur));
+        if (k == 0) s_T[(sweep + 1) % 3] = 0;  // read last at the end of sweep - 2
+        if (rk) {
+          st->s += rk;
+          st->rescales += 1;
+        }
+      }
+      unsigned long long Mloc = 0ull;
+      int rots = 0, gsn = 0;
+      step_warps<T, CPLX, COMP>(M, k, nt, ups, rk, (flags & kFlagPermute) != 0, Mloc, rots, gsn,
+                                defer, dv);
+      Mloc = warp_umax(Mloc);
+      if (lane == 0) {
+        if (Mloc) atomicMax(M0 + nxt, bits(magbits_to_double(Mloc, T(0))));
+        if (rots) {
+          atomicAdd(T0 + sweep % 3, rots);
+          atomicAdd(&st->T[sweep], rots);
+        }
+        if (gsn) atomicAdd(&st->gs, (unsigned long long)gsn);
+      }
+      cluster.sync();
+    }
+    converged = (((volatile int *)T0)[sweep % 3] == 0);
+  }
+  if (defer && dv.p >= 0) {  // the last step's V
+    dv.load(M);
+    dv.apply(M);
+  }
+  if (rank == 0 && threadIdx.x == 0) {
+    st->sweeps = sweep;
+    st->converged = converged ? 1 : 0;
+  }
+  cluster.sync();  // no block leaves while another may still read rank 0's counters
 }
 
 // Final column norms as (e, f); a zero column gets e = INT_MIN.
@@ -286,11 +393,14 @@ __global__ void output_kernel(MatView M, const int *e, const double *f, const in
 
 static int g_svd_grid_cap = 0;
 static int g_svd_warps = 0;
-static int g_svd_step = 0;  // 0 or 2: per warp; 1: chunked
+static int g_svd_step = 0;  // 0: four warps per pair where that fits, else per warp in one
+                            // cluster where that fits, else per warp; 1: chunked; 2: per warp
+                            // (grid barrier); 3: per warp in one cluster where it fits;
+                            // 4: four warps per pair where it fits
 
 int svd_set_step_mode(int v)
 {
-  if (v < 0 || v > 2) return -2;
+  if (v < 0 || v > 4) return -2;
   g_svd_step = v;
   return JSVD_OK;
 }
@@ -464,7 +574,49 @@ static int phase_init(const MatView &M, const double *A, int64_t lda, SvdState *
   return JSVD_OK;
 }
 
-// A2-A8: every sweep, in one cooperative launch.
+// The cluster form (sweeps_cluster_kernel) for a matrix whose steps have at
+// most kClusterWarps pairs per block of a kClusterMax-block cluster, if the
+// GPU can place such a cluster.  Returns JSVD_OK if it launched, 1 if the
+// form does not apply.
+constexpr int kClusterWarps = 4;
+
+template <typename T, bool CPLX, bool COMP>
+static int launch_sweeps_cluster(const MatViewT<T> &M, SvdState *state, double ups, int S,
+                                 int rexp, int flags, cudaStream_t st)
+{
+  const int nt = M.n + (M.n & 1);
+  const int Lp = nt / 2;
+  auto kern = sweeps_cluster_kernel<T, CPLX, COMP>;
+  for (int R = kClusterMax; R >= 8; R /= 2) {
+    if (R * kClusterWarps < Lp) return 1;
+    const int W = std::max(1, (Lp + R - 1) / R);
+    if (R > 8) JSVD_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(R);
+    cfg.blockDim = dim3(32 * W);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = R;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int clusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&clusters, kern, &cfg) != cudaSuccess) {
+      (void)cudaGetLastError();  // a size this GPU cannot place: try a smaller cluster
+      continue;
+    }
+    if (clusters < 1) continue;
+    MatViewT<T> Mk = M;
+    JSVD_CUDA(cudaLaunchKernelEx(&cfg, kern, Mk, state, ups, S, rexp, flags));
+    return JSVD_OK;
+  }
+  return 1;
+}
+
+// A2-A8: every sweep, in one cooperative (or one cluster) launch.
 template <typename T, bool CPLX, bool COMP>
 static int launch_sweeps(const MatViewT<T> &M, SvdState *state, double ups, int S, int rexp,
                          int flags, cudaStream_t st)
@@ -472,6 +624,33 @@ static int launch_sweeps(const MatViewT<T> &M, SvdState *state, double ups, int 
   const int nt = M.n + (M.n & 1);
   const int Lp = nt / 2;
   JSVD_SMS(sms);
+  // four warps on each pair (step_group) for FP64 sweeps of a matrix whose
+  // pairs fit one per SM and whose columns fit one load trip
+  if constexpr (sizeof(T) == 8 && !COMP) {
+    const bool fits = Lp <= sms && M.mp <= 32 * (CPLX ? 4 : 8) &&
+                      M.np <= 32 * kGroupWarps * GroupV<CPLX>::kRows;
+    if (fits && ((g_svd_step == 0 && g_svd_grid_cap == 0 && g_svd_warps == 0) || g_svd_step == 4)) {
+      auto kern = sweeps_kernel<T, CPLX, COMP>;
+      int per_sm = 0;
+      JSVD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * kGroupWarps, 0));
+      if (per_sm < 1) return JSVD_E_UNSUPPORTED;
+      const int grid = std::max(1, std::min(Lp, per_sm * sms));
+      MatViewT<T> Mk = M;
+      SvdState *sk = state;
+      int Sk = S, rk = rexp, pk = flags | kFlagGroupStep;
+      double upsk = ups;
+      void *args[] = {&Mk, &sk, &upsk, &Sk, &rk, &pk};
+      JSVD_CUDA(cudaLaunchCooperativeKernel((const void *)kern, dim3(grid), dim3(32 * kGroupWarps),
+                                            args, 0, st));
+      return JSVD_OK;
+    }
+  }
+  // the cluster form where it applies, unless a launch shape for the grid
+  // forms is asked for
+  if ((g_svd_step == 0 && g_svd_grid_cap == 0 && g_svd_warps == 0) || g_svd_step == 3) {
+    const int rc = launch_sweeps_cluster<T, CPLX, COMP>(M, state, ups, S, rexp, flags, st);
+    if (rc != 1) return rc;
+  }
   // The step form: each warp alone unless the chunked form is asked for.
   // Measured on GB300 for 256 x 128 to 4096 x 2048, real and complex, FP64
   // and mixed: the per-warp form is 2-15 % faster everywhere (its extra

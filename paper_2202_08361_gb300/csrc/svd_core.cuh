@@ -57,27 +57,35 @@ __device__ __forceinline__ double magbits_to_double(unsigned long long b, float)
   return (double)__int_as_float((int)(unsigned)b);  // exact widening
 }
 
+// How the kernels reach the iteration matrix's columns.
+constexpr int kAccPlain = 0;  // plain loads and stores: one block owns the matrix (in
+                              // global or in shared memory); block barriers order the
+                              // accesses and L1 may serve them
+constexpr int kAccL2 = 1;     // through L2 only (ldg2/stg2): blocks on several SMs
+                              // update the matrix
+
 // The iteration matrix G (m x n) and V (n x n) in column precision T.
-// CG: every access goes through L2 only (ldg2/stg2), for matrices that
-// blocks on several SMs update; otherwise plain loads and stores, for a
-// matrix that one block owns (in global or in shared memory), where the
-// block barriers order the accesses and L1 may serve them.
-template <typename T, bool CG = true>
+template <typename T, int CG = kAccL2>
 struct MatViewT {
-  T *gr, *gi;        // G planes (gi == nullptr for real), column j at + j*ldg
-  T *vr, *vi;        // V planes, column j at + j*ldv
+  T *gr, *gi;        // G planes (gi == nullptr for real), column j at Gr(j)
+  T *vr, *vi;        // V planes, column j at Vr(j)
   int m, n;          // true sizes
   int mp, np;        // rows padded to a multiple of 32 (padding rows are 0)
   int64_t ldg, ldv;
 
+  __device__ __forceinline__ T *Gr(int j) const { return gr + j * ldg; }
+  __device__ __forceinline__ T *Gi(int j) const { return gi + j * ldg; }
+  __device__ __forceinline__ T *Vr(int j) const { return vr + j * ldv; }
+  __device__ __forceinline__ T *Vi(int j) const { return vi + j * ldv; }
+
   static __device__ __forceinline__ T ld(const T *p)
   {
-    if constexpr (CG) return ldg2(p);
+    if constexpr (CG == kAccL2) return ldg2(p);
     else return *p;
   }
   static __device__ __forceinline__ void st(T *p, T v)
   {
-    if constexpr (CG) stg2(p, v);
+    if constexpr (CG == kAccL2) stg2(p, v);
     else *p = v;
   }
 };
@@ -187,7 +195,7 @@ __device__ __forceinline__ double hypot_naive(double x, double y)
 __device__ __forceinline__ float ldexp_rn(float x, int k) { return scalbnf(x, k); }
 
 // Scale a column by 2^k in place (rows < mp).
-template <typename T, bool CG>
+template <typename T, int CG>
 __device__ __forceinline__ void scale_col(const MatViewT<T, CG> &M, T *x, int k, int lane)
 {
   for (int i = lane; i < M.mp; i += 32) M.st(x + i, ldexp_rn(M.ld(x + i), k));
@@ -510,12 +518,12 @@ constexpr unsigned long long kWideBelow = 0x0360000000000000ull;
 // wide-exponent method of Alg. rnF, pass 2 the dot-product of the columns
 // prescaled by 2^-e_j (in the canonical lane order, compensated if COMP).
 // FP64 columns only.
-template <bool CPLX, bool CG, bool COMP>
+template <bool CPLX, int CG, bool COMP>
 __device__ __noinline__ PairSums pair_sums_wide(const MatViewT<double, CG> &M, int p, int q)
 {
   const int lane = threadIdx.x & 31;
-  const double *gpr = M.gr + p * M.ldg, *gqr = M.gr + q * M.ldg;
-  const double *gpi = CPLX ? M.gi + p * M.ldg : nullptr, *gqi = CPLX ? M.gi + q * M.ldg : nullptr;
+  const double *gpr = M.Gr(p), *gqr = M.Gr(q);
+  const double *gpi = CPLX ? M.Gi(p) : nullptr, *gqi = CPLX ? M.Gi(q) : nullptr;
   EF np = {kNegInfE, 1.0}, nq = {kNegInfE, 1.0};
   for (int i = lane; i < M.mp; i += 32) {
     ef_fma_step(M.ld(gpr + i), np);
@@ -575,7 +583,7 @@ __device__ __noinline__ PairSums pair_sums_wide(const MatViewT<double, CG> &M, i
 // in every lane).  rk != 0 downscales both columns of G by 2^rk first (section 3.2,
 // step 2; FP64 only).  COMP forms g_q^* g_p by the compensated summation
 // (FP64 only); the squared norms stay plain fma sums.
-template <typename T, bool CPLX, bool CG, bool COMP = false, int U = (sizeof(T) == 4) ? 8 : 4>
+template <typename T, bool CPLX, int CG, bool COMP = false, int U = (sizeof(T) == 4) ? 8 : 4>
 __device__ __forceinline__ PairSums pair_sums(const MatViewT<T, CG> &M, int p, int q, int rk)
 {
   static_assert(!COMP || sizeof(T) == 8, "the compensated sums are FP64 only");
@@ -586,8 +594,8 @@ __device__ __forceinline__ PairSums pair_sums(const MatViewT<T, CG> &M, int p, i
   // masked FP64 instruction takes the pipe like a full one): wide trips
   // only where the column fills them.
   const int lane = threadIdx.x & 31;
-  T *gpr = M.gr + p * M.ldg, *gqr = M.gr + q * M.ldg;
-  T *gpi = CPLX ? M.gi + p * M.ldg : nullptr, *gqi = CPLX ? M.gi + q * M.ldg : nullptr;
+  T *gpr = M.Gr(p), *gqr = M.Gr(q);
+  T *gpi = CPLX ? M.Gi(p) : nullptr, *gqi = CPLX ? M.Gi(q) : nullptr;
   T spp = T(0), sqq = T(0), sqr = T(0), sqi = T(0);
   CompSum cr = {0.0, 0.0, 0.0, 0.0}, ci = {0.0, 0.0, 0.0, 0.0};
   for (int base = lane; base < M.mp; base += 32 * U) {
@@ -692,14 +700,14 @@ __device__ __forceinline__ PairSums pair_sums(const MatViewT<T, CG> &M, int p, i
 // column y <- (y / 2^ey - psi x / 2^ex) 2^ey, the source x unchanged, the
 // pair swapped afterwards if o.swap; Mloc takes the max-norm of both new
 // columns.  One full warp, FP64 columns.
-template <bool CPLX, bool CG>
+template <bool CPLX, int CG>
 __device__ __forceinline__ void gs_apply(const MatViewT<double, CG> &M, int p, int q,
                                          const PairOut &o, unsigned long long &Mloc)
 {
   const int lane = threadIdx.x & 31;
   const int src = (o.gs == 1) ? p : q, dst = (o.gs == 1) ? q : p;
-  double *xr = M.gr + src * M.ldg, *yr = M.gr + dst * M.ldg;
-  double *xi = CPLX ? M.gi + src * M.ldg : nullptr, *yi = CPLX ? M.gi + dst * M.ldg : nullptr;
+  double *xr = M.Gr(src), *yr = M.Gr(dst);
+  double *xi = CPLX ? M.Gi(src) : nullptr, *yi = CPLX ? M.Gi(dst) : nullptr;
   // with the swap the new target lands in the source's place and back
   double *ox_r = o.swap ? yr : xr, *oy_r = o.swap ? xr : yr;
   double *ox_i = o.swap ? yi : xi, *oy_i = o.swap ? xi : yi;
@@ -754,7 +762,7 @@ __device__ __forceinline__ void rotate_row(T pr, T pi, T qr, T qi, T c, T C, T S
 // so that a trip may hold rows of both -- one trip for a short pair of
 // columns, at the price of a pointer select per row.  G_ONLY leaves V to the
 // caller (DeferredV).
-template <typename T, bool CPLX, bool CG, int U = (sizeof(T) == 4) ? 8 : 4, bool MERGED = false,
+template <typename T, bool CPLX, int CG, int U = (sizeof(T) == 4) ? 8 : 4, bool MERGED = false,
           bool G_ONLY = false>
 __device__ __forceinline__ void pair_apply(const MatViewT<T, CG> &M, int p, int q, const PairOut &o,
                                            unsigned long long &Mloc)
@@ -790,10 +798,10 @@ __device__ __forceinline__ void pair_apply(const MatViewT<T, CG> &M, int p, int 
         if (onG) Mloc = max(Mloc, max(magbits(npr), magbits(nqr)));
       }
     };
-    T *gpr = M.gr + p * M.ldg, *gqr = M.gr + q * M.ldg;
-    T *vpr = M.vr + p * M.ldv, *vqr = M.vr + q * M.ldv;
-    T *gpi = CPLX ? M.gi + p * M.ldg : nullptr, *gqi = CPLX ? M.gi + q * M.ldg : nullptr;
-    T *vpi = CPLX ? M.vi + p * M.ldv : nullptr, *vqi = CPLX ? M.vi + q * M.ldv : nullptr;
+    T *gpr = M.Gr(p), *gqr = M.Gr(q);
+    T *vpr = M.Vr(p), *vqr = M.Vr(q);
+    T *gpi = CPLX ? M.Gi(p) : nullptr, *gqi = CPLX ? M.Gi(q) : nullptr;
+    T *vpi = CPLX ? M.Vi(p) : nullptr, *vqi = CPLX ? M.Vi(q) : nullptr;
     if constexpr (MERGED) {
       const int r0 = gdone ? M.mp : 0, R = G_ONLY ? M.mp : M.mp + M.np;
       for (int base = r0 + lane; base < R; base += 32 * U) {
@@ -864,10 +872,10 @@ __device__ __forceinline__ void pair_apply(const MatViewT<T, CG> &M, int p, int 
     for (int pass = 0; pass < (G_ONLY ? 1 : 2); ++pass) {
       const bool onG = (pass == 0);
       const int rows = onG ? M.mp : M.np;
-      T *xpr = onG ? M.gr + p * M.ldg : M.vr + p * M.ldv;
-      T *xqr = onG ? M.gr + q * M.ldg : M.vr + q * M.ldv;
-      T *xpi = CPLX ? (onG ? M.gi + p * M.ldg : M.vi + p * M.ldv) : nullptr;
-      T *xqi = CPLX ? (onG ? M.gi + q * M.ldg : M.vi + q * M.ldv) : nullptr;
+      T *xpr = onG ? M.Gr(p) : M.Vr(p);
+      T *xqr = onG ? M.Gr(q) : M.Vr(q);
+      T *xpi = CPLX ? (onG ? M.Gi(p) : M.Vi(p)) : nullptr;
+      T *xqi = CPLX ? (onG ? M.Gi(q) : M.Vi(q)) : nullptr;
       for (int i = lane; i < rows; i += 32) {
         const T a = M.ld(xpr + i), b = M.ld(xqr + i);
         M.st(xpr + i, b);
@@ -894,7 +902,7 @@ __device__ __forceinline__ void pair_apply(const MatViewT<T, CG> &M, int p, int 
 // Every pair's arithmetic is the same whatever the chunking.  rots counts
 // (in each warp's lane 0) the transformed pairs and gsn those of them that
 // took the Gram-Schmidt step; Mloc collects magbits().
-template <typename T, bool CPLX, bool CG, bool COMP = false>
+template <typename T, bool CPLX, int CG, bool COMP = false>
 __device__ __forceinline__ void step_chunk(const MatViewT<T, CG> &M, int k, int nt, int base, int CH,
                                            double ups, int rk, bool permute, PairSums *s_sums,
                                            PairOut *s_out, unsigned long long &Mloc, int &rots,
@@ -911,8 +919,8 @@ __device__ __forceinline__ void step_chunk(const MatViewT<T, CG> &M, int k, int 
       const PairSums sm = pair_sums<T, CPLX, CG, COMP>(M, p, q, rk);
       if (lane == 0) s_sums[i] = sm;
     } else if (rk) {  // phantom partner: only a pending rescale applies
-      scale_col(M, M.gr + p * M.ldg, rk, lane);
-      if (CPLX) scale_col(M, M.gi + p * M.ldg, rk, lane);
+      scale_col(M, M.Gr(p), rk, lane);
+      if (CPLX) scale_col(M, M.Gi(p), rk, lane);
     }
   }
   __syncthreads();
@@ -960,11 +968,12 @@ struct DeferredV {
   PairOut o;
   T pr[kRows], qr[kRows], pi[kRows], qi[kRows];
 
-  __device__ __forceinline__ void load(const MatViewT<T, true> &M)
+  template <int CG>
+  __device__ __forceinline__ void load(const MatViewT<T, CG> &M)
   {
     const int lane = threadIdx.x & 31;
-    const T *xp = M.vr + p * M.ldv, *xq = M.vr + q * M.ldv;
-    const T *xpi = CPLX ? M.vi + p * M.ldv : nullptr, *xqi = CPLX ? M.vi + q * M.ldv : nullptr;
+    const T *xp = M.Vr(p), *xq = M.Vr(q);
+    const T *xpi = CPLX ? M.Vi(p) : nullptr, *xqi = CPLX ? M.Vi(q) : nullptr;
 #pragma unroll
     for (int u = 0; u < kRows; ++u) {
       const int i = lane + 32 * u;
@@ -982,11 +991,12 @@ struct DeferredV {
 
   // the transformation (or the swap alone) of the loaded rows, as
   // pair_apply's V pass would do it
-  __device__ __forceinline__ void apply(const MatViewT<T, true> &M)
+  template <int CG>
+  __device__ __forceinline__ void apply(const MatViewT<T, CG> &M)
   {
     const int lane = threadIdx.x & 31;
-    T *xp = M.vr + p * M.ldv, *xq = M.vr + q * M.ldv;
-    T *xpi = CPLX ? M.vi + p * M.ldv : nullptr, *xqi = CPLX ? M.vi + q * M.ldv : nullptr;
+    T *xp = M.Vr(p), *xq = M.Vr(q);
+    T *xpi = CPLX ? M.Vi(p) : nullptr, *xqi = CPLX ? M.Vi(q) : nullptr;
     T *dp = o.swap ? xq : xp, *dq = o.swap ? xp : xq;
     T *dpi = o.swap ? xqi : xpi, *dqi = o.swap ? xpi : xqi;
     const T c = to_t(o.c, T(0)), C = to_t(o.C, T(0)), S = CPLX ? to_t(o.S, T(0)) : T(0);
@@ -1014,8 +1024,8 @@ struct DeferredV {
 // its transformation, with no block barrier in between.  For the
 // persistent single-matrix sweep, where a step has at most a few pairs per
 // block and its time is the chain of one pair.
-template <typename T, bool CPLX, bool COMP = false>
-__device__ __forceinline__ void step_warps(const MatViewT<T, true> &M, int k, int nt, double ups, int rk,
+template <typename T, bool CPLX, bool COMP = false, int CG = kAccL2>
+__device__ __forceinline__ void step_warps(const MatViewT<T, CG> &M, int k, int nt, double ups, int rk,
                                            bool permute, unsigned long long &Mloc, int &rots, int &gsn,
                                            bool defer, DeferredV<T, CPLX> &dv)
 {
@@ -1031,26 +1041,26 @@ __device__ __forceinline__ void step_warps(const MatViewT<T, true> &M, int k, in
       constexpr int US = CPLX ? 4 : 8, UA = CPLX ? 6 : 12;
       const bool wide_sums = sizeof(T) == 8 && M.mp % (32 * US) == 0;
       const bool wide_apply = sizeof(T) == 8 && (M.mp + M.np) % (32 * UA) == 0;
-      const PairSums sm = wide_sums ? pair_sums<T, CPLX, true, COMP, US>(M, p, q, rk)
-                                    : pair_sums<T, CPLX, true, COMP>(M, p, q, rk);
+      const PairSums sm = wide_sums ? pair_sums<T, CPLX, CG, COMP, US>(M, p, q, rk)
+                                    : pair_sums<T, CPLX, CG, COMP>(M, p, q, rk);
       if (defer && dv.p >= 0) dv.load(M);  // the last step's V rows, in flight during the rotation
       PairOut o = pair_rotation_warp<CPLX>(sm, ups);
       o.swap = o.swap && permute;
       if (defer) {
         if (dv.p >= 0) dv.apply(M);
         if (wide_sums)
-          pair_apply<T, CPLX, true, US, false, true>(M, p, q, o, Mloc);
+          pair_apply<T, CPLX, CG, US, false, true>(M, p, q, o, Mloc);
         else
-          pair_apply<T, CPLX, true, (sizeof(T) == 4) ? 8 : 4, false, true>(M, p, q, o, Mloc);
+          pair_apply<T, CPLX, CG, (sizeof(T) == 4) ? 8 : 4, false, true>(M, p, q, o, Mloc);
         if (o.rot || o.swap) {
           dv.p = p;
           dv.q = q;
           dv.o = o;
         }
       } else if (wide_apply) {
-        pair_apply<T, CPLX, true, UA, true>(M, p, q, o, Mloc);
+        pair_apply<T, CPLX, CG, UA, true>(M, p, q, o, Mloc);
       } else {
-        pair_apply<T, CPLX, true>(M, p, q, o, Mloc);
+        pair_apply<T, CPLX, CG>(M, p, q, o, Mloc);
       }
       if (lane == 0 && o.rot) ++rots;
       if (lane == 0 && o.gs) ++gsn;
@@ -1060,9 +1070,224 @@ __device__ __forceinline__ void step_warps(const MatViewT<T, true> &M, int k, in
         dv.apply(M);
       }
       if (rk) {  // phantom partner: only a pending rescale applies
-        scale_col(M, M.gr + p * M.ldg, rk, lane);
-        if (CPLX) scale_col(M, M.gi + p * M.ldg, rk, lane);
+        scale_col(M, M.Gr(p), rk, lane);
+        if (CPLX) scale_col(M, M.Gi(p), rk, lane);
       }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// A step of a small matrix with four warps of a block on each pivot pair.
+// A warp issues at most one FP64 instruction every few dozen cycles (on
+// GB300 about 64), whatever their dependences, so a step whose time is one
+// pair's chain is shortened by spreading the pair's FP64 instructions over
+// four warps, which sit on the SM's four schedulers:
+//   - every warp loads the pair's G rows (lane l: rows l, l + 32, ...) and
+//     forms ONE of the sums (warp 0 ||g_p||^2, 1 ||g_q||^2, 2 Re g_q^* g_p,
+//     3 Im g_q^* g_p) over them in the canonical order, reduced by the
+//     butterfly warp_sum -- bit for bit the slot of pair_sums' tree;
+//   - every warp computes the same rotation (pair_rotation_warp);
+//   - warp g transforms the G rows u = g, g + 4, ... of its lanes from the
+//     registers it loaded, and V's rows likewise one step late (GroupV).
+// The columns' values, the sums and the rotations are those of the other
+// step forms, so are the bits.  FP64 columns, plain sums; mp <= 32 U rows.
+constexpr int kGroupWarps = 4;
+
+template <bool CPLX>
+struct GroupV {
+  static constexpr int kRows = 2;  // V rows per lane and warp: np <= 32 * 4 * kRows
+  int p = -1, q = -1;
+  PairOut o;
+  double pr[kRows], qr[kRows], pi[kRows], qi[kRows];
+
+  template <int CG>
+  __device__ __forceinline__ void load(const MatViewT<double, CG> &M, int g)
+  {
+    const int lane = threadIdx.x & 31;
+    const double *xp = M.Vr(p), *xq = M.Vr(q);
+    const double *xpi = CPLX ? M.Vi(p) : nullptr, *xqi = CPLX ? M.Vi(q) : nullptr;
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) {
+      const int i = lane + 32 * (g + kGroupWarps * r);
+      pr[r] = qr[r] = pi[r] = qi[r] = 0.0;
+      if (i < M.np) {
+        pr[r] = M.ld(xp + i);
+        qr[r] = M.ld(xq + i);
+        if (CPLX) {
+          pi[r] = M.ld(xpi + i);
+          qi[r] = M.ld(xqi + i);
+        }
+      }
+    }
+  }
+
+  template <int CG>
+  __device__ __forceinline__ void apply(const MatViewT<double, CG> &M, int g)
+  {
+    const int lane = threadIdx.x & 31;
+    double *xp = M.Vr(p), *xq = M.Vr(q);
+    double *xpi = CPLX ? M.Vi(p) : nullptr, *xqi = CPLX ? M.Vi(q) : nullptr;
+    double *dp = o.swap ? xq : xp, *dq = o.swap ? xp : xq;
+    double *dpi = o.swap ? xqi : xpi, *dqi = o.swap ? xpi : xqi;
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) {
+      const int i = lane + 32 * (g + kGroupWarps * r);
+      if (i < M.np) {
+        double npr = pr[r], npi = pi[r], nqr = qr[r], nqi = qi[r];
+        if (o.rot) rotate_row<double, CPLX>(pr[r], pi[r], qr[r], qi[r], o.c, o.C, o.S, npr, npi, nqr, nqi);
+        M.st(dp + i, npr);
+        M.st(dq + i, nqr);
+        if (CPLX) {
+          M.st(dpi + i, npi);
+          M.st(dqi + i, nqi);
+        }
+      }
+    }
+    p = q = -1;
+  }
+};
+
+// The block's pairs of step k (l = blockIdx.x, + gridDim.x, ...), each by
+// the block's four warps; s_sum: four doubles of shared memory.
+template <bool CPLX, int CG>
+__device__ __forceinline__ void step_group(const MatViewT<double, CG> &M, int k, int nt, double ups,
+                                           int rk, bool permute, unsigned long long &Mloc, int &rots,
+                                           int &gsn, GroupV<CPLX> &gv, double *s_sum)
+{
+  constexpr int U = CPLX ? 4 : 8;  // G rows per lane: mp <= 32 U
+  const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
+  const int L = nt / 2;
+  const int urows = M.mp >> 5;  // rows per lane (mp is a multiple of 32)
+  for (int l = blockIdx.x; l < L; l += gridDim.x) {
+    int p, q;
+    pair_of(k, l, nt, p, q);
+    if (q >= M.n) {
+      if (gv.p >= 0) {  // no pair this step: settle the last one's V
+        gv.load(M, g);
+        gv.apply(M, g);
+      }
+      if (rk && g == 0) {  // phantom partner: only a pending rescale applies
+        scale_col(M, M.Gr(p), rk, lane);
+        if (CPLX) scale_col(M, M.Gi(p), rk, lane);
+      }
+      continue;
+    }
+    double *gpr = M.Gr(p), *gqr = M.Gr(q);
+    double *gpi = CPLX ? M.Gi(p) : nullptr, *gqi = CPLX ? M.Gi(q) : nullptr;
+    double xpr[U], xqr[U], xpi[U], xqi[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = lane + 32 * u;
+      xpr[u] = xqr[u] = xpi[u] = xqi[u] = 0.0;
+      if (u < urows) {
+        xpr[u] = M.ld(gpr + i);
+        xqr[u] = M.ld(gqr + i);
+        if (CPLX) {
+          xpi[u] = M.ld(gpi + i);
+          xqi[u] = M.ld(gqi + i);
+        }
+      }
+    }
+    if (rk) {  // section 3.2, step 2: both columns downscaled by 2^rk first
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (u < urows) {
+          xpr[u] = ldexp_rn(xpr[u], rk);
+          xqr[u] = ldexp_rn(xqr[u], rk);
+          if (CPLX) {
+            xpi[u] = ldexp_rn(xpi[u], rk);
+            xqi[u] = ldexp_rn(xqi[u], rk);
+          }
+          if ((u & (kGroupWarps - 1)) == g) {  // each row stored by one warp
+            const int i = lane + 32 * u;
+            M.st(gpr + i, xpr[u]);
+            M.st(gqr + i, xqr[u]);
+            if (CPLX) {
+              M.st(gpi + i, xpi[u]);
+              M.st(gqi + i, xqi[u]);
+            }
+          }
+        }
+      }
+    }
+    // this warp's sum, the rows in ascending order as pair_sums forms it
+    double acc = 0.0;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (u < urows) {
+        if (g == 0) {
+          acc = __fma_rn(xpr[u], xpr[u], acc);
+          if (CPLX) acc = __fma_rn(xpi[u], xpi[u], acc);
+        } else if (g == 1) {
+          acc = __fma_rn(xqr[u], xqr[u], acc);
+          if (CPLX) acc = __fma_rn(xqi[u], xqi[u], acc);
+        } else if (g == 2) {
+          acc = __fma_rn(xqr[u], xpr[u], acc);
+          if (CPLX) acc = __fma_rn(xqi[u], xpi[u], acc);
+        } else if (CPLX) {
+          acc = __fma_rn(xqr[u], xpi[u], acc);
+          acc = __fma_rn(-xqi[u], xpr[u], acc);
+        }
+      }
+    }
+    if (CPLX || g < 3) {
+      acc = warp_sum(acc);
+      if (lane == 0) s_sum[g] = acc;
+    }
+    __syncthreads();
+    PairSums sm;
+    sm.pp = s_sum[0];
+    sm.qq = s_sum[1];
+    sm.qr = s_sum[2];
+    sm.qi = CPLX ? s_sum[3] : 0.0;
+    sm.fp = sm.fq = 1.0;
+    sm.ep = sm.eq = 0;
+    sm.wide = 0;
+    __syncthreads();  // s_sum is free for the next pair
+    // squares below 2^-1022 may have lost bits: the wide-exponent sums
+    // (every warp the same, from the columns as stored)
+    if (bits(sm.pp) < kWideBelow || bits(sm.qq) < kWideBelow) {
+      sm = pair_sums_wide<CPLX, CG, false>(M, p, q);
+      __syncthreads();  // every warp has read the columns before any writes them
+    }
+    if (gv.p >= 0) gv.load(M, g);  // the last step's V rows, in flight during the rotation
+    PairOut o = pair_rotation_warp<CPLX>(sm, ups);
+    o.swap = o.swap && permute;
+    if (gv.p >= 0) gv.apply(M, g);
+    double *dpr = o.swap ? gqr : gpr, *dqr = o.swap ? gpr : gqr;
+    double *dpi = o.swap ? gqi : gpi, *dqi = o.swap ? gpi : gqi;
+    if (o.rot && o.gs) {  // Eq. e:GS replaces the rotation on G: one warp
+      if (g == 0) gs_apply<CPLX, CG>(M, p, q, o, Mloc);
+    } else if (o.rot || o.swap) {
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (u < urows && (u & (kGroupWarps - 1)) == g) {
+          const int i = lane + 32 * u;
+          double npr = xpr[u], npi = xpi[u], nqr = xqr[u], nqi = xqi[u];
+          if (o.rot) {
+            rotate_row<double, CPLX>(xpr[u], xpi[u], xqr[u], xqi[u], o.c, o.C, o.S, npr, npi, nqr,
+                                     nqi);
+            Mloc = max(Mloc, max(magbits(npr), magbits(nqr)));
+            if (CPLX) Mloc = max(Mloc, max(magbits(npi), magbits(nqi)));
+          }
+          M.st(dpr + i, npr);
+          M.st(dqr + i, nqr);
+          if (CPLX) {
+            M.st(dpi + i, npi);
+            M.st(dqi + i, nqi);
+          }
+        }
+      }
+    }
+    if (o.rot || o.swap) {
+      gv.p = p;
+      gv.q = q;
+      gv.o = o;
+    }
+    if (g == 0 && lane == 0) {
+      if (o.rot) ++rots;
+      if (o.gs) ++gsn;
     }
   }
 }
@@ -1074,11 +1299,11 @@ __device__ __forceinline__ void step_warps(const MatViewT<T, true> &M, int k, in
 // Column j's norm as (e, f) by one warp in the canonical order (the
 // wide-exponent norm when the plain sum of squares is too small to trust);
 // a zero column gets e = INT_MIN, f = 1.
-template <bool CPLX, bool CG>
+template <bool CPLX, int CG>
 __device__ __forceinline__ void colnorm_warp(const MatViewT<double, CG> &M, int j, int lane, int *e_out,
                                              double *f_out)
 {
-  const double *xr = M.gr + j * M.ldg, *xi = CPLX ? M.gi + j * M.ldg : nullptr;
+  const double *xr = M.Gr(j), *xi = CPLX ? M.Gi(j) : nullptr;
   double s = 0.0;
   for (int i = lane; i < M.mp; i += 32) {
     const double a = M.ld(xr + i);
@@ -1136,7 +1361,7 @@ __device__ __forceinline__ int rank_of(int n, const int *e, const double *f, int
 
 // One element (row i) of output column j, which goes to position r:
 // U(i, r) = G(i, j) 2^{-e_j} / f_j (i < m), V(i, r) = V_k(i, j) (i < n).
-template <bool CPLX, bool CG>
+template <bool CPLX, int CG>
 __device__ __forceinline__ void output_elem(const MatViewT<double, CG> &M, int i, int j, int r, int ej,
                                             double fj, bool bad, double *U, int64_t ldu,
                                             double *V, int64_t ldv)
@@ -1148,8 +1373,8 @@ __device__ __forceinline__ void output_elem(const MatViewT<double, CG> &M, int i
     if (bad) {
       ur = ui = nan;
     } else if (!zero) {
-      ur = __ddiv_rn(ldexp_rn(M.ld(M.gr + j * M.ldg + i), -ej), fj);
-      if (CPLX) ui = __ddiv_rn(ldexp_rn(M.ld(M.gi + j * M.ldg + i), -ej), fj);
+      ur = __ddiv_rn(ldexp_rn(M.ld(M.Gr(j) + i), -ej), fj);
+      if (CPLX) ui = __ddiv_rn(ldexp_rn(M.ld(M.Gi(j) + i), -ej), fj);
     }
     if (CPLX) {
       U[2 * (r * ldu + i)] = ur;
@@ -1159,10 +1384,10 @@ __device__ __forceinline__ void output_elem(const MatViewT<double, CG> &M, int i
     }
   }
   if (i < M.n) {
-    const double vr = bad ? nan : M.ld(M.vr + j * M.ldv + i);
+    const double vr = bad ? nan : M.ld(M.Vr(j) + i);
     if (CPLX) {
       V[2 * (r * ldv + i)] = vr;
-      V[2 * (r * ldv + i) + 1] = bad ? nan : M.ld(M.vi + j * M.ldv + i);
+      V[2 * (r * ldv + i) + 1] = bad ? nan : M.ld(M.Vi(j) + i);
     } else {
       V[r * ldv + i] = vr;
     }

@@ -212,31 +212,36 @@ def _step_cases():
     A6[:, 3] = 0.0                                                   # a zero column
     return [("real256x128", A1, {}), ("cplx128x64", A2, {}), ("ragged", A3, {}),
             ("permute", A3, {"permute": True}), ("compensated", A2, {"compensated": True}),
-            ("wide", A4, {}), ("gram_schmidt", A5, {}), ("zero_col", A6, {})]
+            ("wide", A4, {}), ("gram_schmidt", A5, {}), ("zero_col", A6, {}),
+            ("rescale", A1, {"rescale_exp": 1}), ("mixed", A1, {"mode": "mixed"})]
 
 
-@pytest.mark.parametrize("case", range(8))
+@pytest.mark.parametrize("case", range(10))
 def test_step_forms_bit_identical(case):
-    """The two forms of a sweep step (JSVD_TUNE_SVD_STEP: chunks with one
-    rotation per lane, or each warp alone with the rotation's independent
-    divisions and roots spread over its lanes) give the same bits, on
-    one-trip and ragged columns, odd n, column swaps, compensated sums,
-    the wide-exponent fallback, Gram-Schmidt steps and a zero column."""
+    """The three forms of a sweep step (JSVD_TUNE_SVD_STEP: chunks with one
+    rotation per lane; each warp alone with the rotation's independent
+    divisions and roots spread over its lanes, G and V in L2; the same per
+    warp inside one thread-block cluster with G and V in the blocks' shared
+    memory) give the same bits, on one-trip and ragged columns, odd n,
+    column swaps, compensated sums, the wide-exponent fallback,
+    Gram-Schmidt steps, a zero column, forced rescaling and the mixed
+    mode's FP32 phase."""
     import paper_2202_08361_gb300 as J
     name, A, kw = _step_cases()[case]
     outs = []
     try:
-        for mode in (1, 2):
+        for mode in (1, 2, 3, 4):
             J.tune_set(J.JSVD_TUNE_SVD_STEP, mode)
             outs.append(gpu_svd(A, **kw))
     finally:
         J.tune_set(J.JSVD_TUNE_SVD_STEP, 0)
-    a, b = outs
+    a = outs[0]
     assert a["info"]["status"] == 0, name
-    for k in ("U", "V", "sigma", "sigma_e", "sigma_f"):
-        assert np.array_equal(np.ascontiguousarray(a[k]).view(np.uint8),
-                              np.ascontiguousarray(b[k]).view(np.uint8)), (name, k)
-    assert a["info"] == b["info"], name
+    for b in outs[1:]:
+        for k in ("U", "V", "sigma", "sigma_e", "sigma_f"):
+            assert np.array_equal(np.ascontiguousarray(a[k]).view(np.uint8),
+                                  np.ascontiguousarray(b[k]).view(np.uint8)), (name, k)
+        assert a["info"] == b["info"], name
 
 
 def test_argument_errors():
