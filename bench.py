@@ -282,6 +282,18 @@ def evd_fp64_roofline(kernel, ms, r, rates):
             "avg_launch_ms": ms}
 
 
+def _svd_lane_ops(m, n, sweeps, rotations, cplx):
+    """FP64-pipe lane operations of the sweeps (each add, multiply or fma
+    counts one, as the pipe issues them): every visited pair forms its sums
+    (3 fma per row real, 8 complex), every rotated pair transforms m + n
+    rows (2 fma + 2 mul real; 8 fma + 4 mul complex, Eq. e:transf with the
+    complex fma of Eq. e:zfma)."""
+    pairs = sweeps * n * (n - 1) // 2
+    if cplx:
+        return pairs * 8 * m + rotations * 12 * (m + n)
+    return pairs * 3 * m + rotations * 4 * (m + n)
+
+
 def _svd_flops(m, n, sweeps, rotations, cplx):
     """FP64 flops of the sweeps (fma = 2): every visited pair forms its sums
     (3m fma real, 8m complex), every rotated pair transforms m + n rows
@@ -354,8 +366,10 @@ def svd_bench(torch, J, workloads, dev, rates, cpu=True, loop_count=120):
     ms = e0.elapsed_time(e1) / reps
     info = J.decode_info(r["info"])
     fl = _svd_flops(256, 128, info["sweeps"], info["rotations"], False)
+    lo = _svd_lane_ops(256, 128, info["sweeps"], info["rotations"], False)
     c1 = {"ms_per_svd": ms, "sweeps": info["sweeps"], "rotations": info["rotations"],
-          "fp64_gflops": fl / ms / 1e6, "fp64_frac": fl / (ms * 1e-3) / DFMA_FLOPS}
+          "fp64_gflops": fl / ms / 1e6, "fp64_frac": fl / (ms * 1e-3) / DFMA_FLOPS,
+          "fp64_pipe_frac": lo / (ms * 1e-3) / rates["fma_per_s"]}
     c1.update(accuracy(A1, r))
     if cpu:
         try:
@@ -469,8 +483,10 @@ def svd_bench(torch, J, workloads, dev, rates, cpu=True, loop_count=120):
             d["err_vs_oracle"] = e
         if mode == "fp64":
             fl = _svd_flops(4096, 2048, info["sweeps"], info["rotations"], True)
+            lo = _svd_lane_ops(4096, 2048, info["sweeps"], info["rotations"], True)
             d["fp64_tflops"] = fl / (ms * 1e-3) / 1e12
             d["fp64_frac"] = fl / (ms * 1e-3) / DFMA_FLOPS
+            d["fp64_pipe_frac"] = lo / (ms * 1e-3) / rates["fma_per_s"]
         c3[mode] = d
         del r
     c3["speedup_mixed_vs_fp64"] = c3["fp64"]["s"] / c3["mixed"]["s"]
@@ -516,6 +532,8 @@ def svd_bench(torch, J, workloads, dev, rates, cpu=True, loop_count=120):
     infos = J.decode_info(B.info)
     fl = sum(_svd_flops(int(m4[i]), int(n4[i]), infos[i]["sweeps"], infos[i]["rotations"], False)
              for i in range(len(m4)))
+    lo4 = sum(_svd_lane_ops(int(m4[i]), int(n4[i]), infos[i]["sweeps"], infos[i]["rotations"],
+                            False) for i in range(len(m4)))
     # the per-matrix launch loop: jsvd_svd on each matrix of a random sample,
     # one after another on one stream, scaled to the batch by m n^2
     g = np.random.default_rng(0)
@@ -574,6 +592,7 @@ def svd_bench(torch, J, workloads, dev, rates, cpu=True, loop_count=120):
         "converged": int(sum(1 for x in infos if x["status"] == 0)),
         "sweeps_mean": float(np.mean([x["sweeps"] for x in infos])),
         "fp64_tflops": fl / (ms * 1e-3) / 1e12, "fp64_frac": fl / (ms * 1e-3) / DFMA_FLOPS,
+        "fp64_pipe_frac": lo4 / (ms_graph * 1e-3) / rates["fma_per_s"],
         "per_matrix_loop": {"matrices_timed": int(len(idx)), "s_timed": loop_meas_s,
                             "s_full_batch": loop_s,
                             "scaled": bool(len(idx) < len(m4)),

@@ -105,11 +105,21 @@ JSVD_API const char *jsvd_last_cuda_error(void);
  *     in chunks.  The results are identical. */
 #define JSVD_TUNE_EVD_HOST 7
 /*   JSVD_TUNE_SVD_STEP: the form of a step in the single-matrix sweep
- *     kernel: 2 (or 0, the default) = each warp runs its pairs alone, a
- *     rotation's independent divisions and square roots spread over its
- *     lanes; 1 = chunks of pairs in three block phases, one pair's rotation
- *     per lane.  The results are identical. */
+ *     kernel: 0 (the default) = four warps on each pair where a step's pairs
+ *     fit one per SM and the columns one load trip, else each warp alone in
+ *     one thread-block cluster where the pairs fit it, else each warp alone;
+ *     1 = chunks of pairs in three block phases, one pair's rotation per
+ *     lane; 2 = each warp runs its pairs alone, a rotation's independent
+ *     divisions and square roots spread over its lanes, steps separated by a
+ *     grid barrier; 3 = the same in one cluster where it fits; 4 = four
+ *     warps on each pair where it fits.  The results are identical. */
 #define JSVD_TUNE_SVD_STEP 8
+/*   JSVD_TUNE_SVD_SKIP: value = 1 (default): the single-matrix sweeps skip
+ *     a pivot pair neither of whose columns has changed since the pair was
+ *     last taken, one sweep earlier (its rotation test would fail again on
+ *     the same columns); 0: every pair is formed.  The results are
+ *     identical. */
+#define JSVD_TUNE_SVD_SKIP 9
 /* Sets one of the knobs above for the whole process (not thread-safe with
  * respect to launches running concurrently on other host threads).
  * Errors: -1 unknown knob, -2 value out of range, -3 value2 out of range. */

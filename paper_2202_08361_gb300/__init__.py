@@ -11,6 +11,7 @@ from ._native import (JSVD_COMPLEX, JSVD_E_CUDA, JSVD_E_NONFINITE, JSVD_E_TIMEOU
                       JSVD_E_UNSUPPORTED, JSVD_E_WORKSPACE, JSVD_FP64, JSVD_MIXED_FP32_FP64,
                       JSVD_NOT_CONVERGED, JSVD_OK, JSVD_REAL, JSVD_TUNE_BATCH_SMEM,
                       JSVD_TUNE_EVD32_DIV, JSVD_TUNE_EVD_HOST, JSVD_TUNE_SVD_STEP,
+                      JSVD_TUNE_SVD_SKIP,
                       JSVD_TUNE_BATCH_WARPS, JSVD_TUNE_EVD_ARITH, JSVD_TUNE_EVD_LAUNCH,
                       JSVD_TUNE_SVD_GRID, JsvdError)
 

@@ -28,6 +28,7 @@ JSVD_TUNE_BATCH_SMEM = 5
 JSVD_TUNE_EVD32_DIV = 6
 JSVD_TUNE_EVD_HOST = 7
 JSVD_TUNE_SVD_STEP = 8
+JSVD_TUNE_SVD_SKIP = 9
 
 JSVD_FP64 = 0
 JSVD_MIXED_FP32_FP64 = 1

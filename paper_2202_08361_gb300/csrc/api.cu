@@ -72,6 +72,7 @@ extern "C" int jsvd_tune_set(int knob, int value, int value2)
     case JSVD_TUNE_EVD32_DIV: return jsvd::evd2f_set_fast(value, value2);
     case JSVD_TUNE_EVD_HOST: return jsvd::evd2_set_host_path(value);
     case JSVD_TUNE_SVD_STEP: return jsvd::svd_set_step_mode(value);
+    case JSVD_TUNE_SVD_SKIP: return jsvd::svd_set_skip(value);
     default: return -1;
   }
 }

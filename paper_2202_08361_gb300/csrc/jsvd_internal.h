@@ -12,6 +12,7 @@ int batch_set_smem(int kib);
 int evd2f_set_fast(int v, int fields);
 int evd2_set_host_path(int v);
 int svd_set_step_mode(int v);
+int svd_set_skip(int v);
 }  // namespace jsvd
 
 #include <cuda_runtime.h>

@@ -156,7 +156,8 @@ __global__ void init_kernel(const double *__restrict__ A, int64_t lda, MatView M
 // the mixed SVD).
 template <typename T, bool CPLX, bool COMP>
 __global__ void __launch_bounds__(256) sweeps_kernel(MatViewT<T> M, SvdState *st, double ups,
-                                                     int max_sweeps, int rescale_exp, int flags)
+                                                     int max_sweeps, int rescale_exp, int flags,
+                                                     int *lastmod)
 {
   __shared__ PairSums s_sums[8];
   __shared__ PairOut s_out[8];
@@ -183,6 +184,7 @@ __global__ void __launch_bounds__(256) sweeps_kernel(MatViewT<T> M, SvdState *st
   unsigned long long gstep = 0;
   int sweep = 0;
   bool converged = false;
+  int last_rescale = INT_MIN / 2;  // the last step that rescaled G (the same in every block)
   for (; sweep < max_sweeps && !converged; ++sweep) {
     for (int k = 0; k < K; ++k, ++gstep) {
       const int cur = (int)(gstep % 3), nxt = (int)((gstep + 1) % 3), old = (int)((gstep + 2) % 3);
@@ -205,10 +207,11 @@ __global__ void __launch_bounds__(256) sweeps_kernel(MatViewT<T> M, SvdState *st
           step_group<CPLX>(M, k, nt, ups, rk, (flags & kFlagPermute) != 0, Mloc, rots, gsn, gv,
                            s_gsum);
       }
+      if (rk) last_rescale = (int)gstep;
       if (group) {
       } else if (warp_step)
         step_warps<T, CPLX, COMP>(M, k, nt, ups, rk, (flags & kFlagPermute) != 0, Mloc, rots, gsn,
-                                  defer, dv);
+                                  defer, dv, lastmod, (int)gstep, last_rescale);
       else
         for (int base = blockIdx.x * W; base < L; base += gridDim.x * W)
           step_chunk<T, CPLX, true, COMP>(M, k, nt, base, W, ups, rk, (flags & kFlagPermute) != 0,
@@ -255,7 +258,8 @@ constexpr int kClusterMax = 16;
 template <typename T, bool CPLX, bool COMP>
 __global__ void __launch_bounds__(256) sweeps_cluster_kernel(MatViewT<T> M, SvdState *st,
                                                              double ups, int max_sweeps,
-                                                             int rescale_exp, int flags)
+                                                             int rescale_exp, int flags,
+                                                             int *lastmod)
 {
   namespace cgr = cooperative_groups;
   cgr::cluster_group cluster = cgr::this_cluster();
@@ -285,6 +289,7 @@ __global__ void __launch_bounds__(256) sweeps_cluster_kernel(MatViewT<T> M, SvdS
   unsigned long long gstep = 0;
   int sweep = 0;
   bool converged = false;
+  int last_rescale = INT_MIN / 2;
   for (; sweep < max_sweeps && !converged; ++sweep) {
     for (int k = 0; k < K; ++k, ++gstep) {
       const int cur = (int)(gstep % 3), nxt = (int)((gstep + 1) % 3), old = (int)((gstep + 2) % 3);
@@ -303,8 +308,9 @@ __global__ void __launch_bounds__(256) sweeps_cluster_kernel(MatViewT<T> M, SvdS
       }
       unsigned long long Mloc = 0ull;
       int rots = 0, gsn = 0;
+      if (rk) last_rescale = (int)gstep;
       step_warps<T, CPLX, COMP>(M, k, nt, ups, rk, (flags & kFlagPermute) != 0, Mloc, rots, gsn,
-                                defer, dv);
+                                defer, dv, lastmod, (int)gstep, last_rescale);
       Mloc = warp_umax(Mloc);
       if (lane == 0) {
         if (Mloc) atomicMax(M0 + nxt, bits(magbits_to_double(Mloc, T(0))));
@@ -390,6 +396,15 @@ __global__ void output_kernel(MatView M, const int *e, const double *f, const in
 }
 
 // ---------------------------------------------------------------------------
+
+static int g_svd_skip = 1;  // skip the pairs whose columns did not change (same results)
+
+int svd_set_skip(int v)
+{
+  if (v != 0 && v != 1) return -2;
+  g_svd_skip = v;
+  return JSVD_OK;
+}
 
 static int g_svd_grid_cap = 0;
 static int g_svd_warps = 0;
@@ -582,7 +597,7 @@ constexpr int kClusterWarps = 4;
 
 template <typename T, bool CPLX, bool COMP>
 static int launch_sweeps_cluster(const MatViewT<T> &M, SvdState *state, double ups, int S,
-                                 int rexp, int flags, cudaStream_t st)
+                                 int rexp, int flags, int *lastmod, cudaStream_t st)
 {
   const int nt = M.n + (M.n & 1);
   const int Lp = nt / 2;
@@ -610,7 +625,7 @@ static int launch_sweeps_cluster(const MatViewT<T> &M, SvdState *state, double u
     }
     if (clusters < 1) continue;
     MatViewT<T> Mk = M;
-    JSVD_CUDA(cudaLaunchKernelEx(&cfg, kern, Mk, state, ups, S, rexp, flags));
+    JSVD_CUDA(cudaLaunchKernelEx(&cfg, kern, Mk, state, ups, S, rexp, flags, lastmod));
     return JSVD_OK;
   }
   return 1;
@@ -619,8 +634,11 @@ static int launch_sweeps_cluster(const MatViewT<T> &M, SvdState *state, double u
 // A2-A8: every sweep, in one cooperative (or one cluster) launch.
 template <typename T, bool CPLX, bool COMP>
 static int launch_sweeps(const MatViewT<T> &M, SvdState *state, double ups, int S, int rexp,
-                         int flags, cudaStream_t st)
+                         int flags, int *lastmod, cudaStream_t st)
 {
+  // the columns' last changes for skipping unchanged pairs (before any step)
+  if (!g_svd_skip) lastmod = nullptr;
+  if (lastmod) JSVD_CUDA(cudaMemsetAsync(lastmod, 0xFF, sizeof(int) * (size_t)M.n, st));
   const int nt = M.n + (M.n & 1);
   const int Lp = nt / 2;
   JSVD_SMS(sms);
@@ -639,7 +657,8 @@ static int launch_sweeps(const MatViewT<T> &M, SvdState *state, double ups, int 
       SvdState *sk = state;
       int Sk = S, rk = rexp, pk = flags | kFlagGroupStep;
       double upsk = ups;
-      void *args[] = {&Mk, &sk, &upsk, &Sk, &rk, &pk};
+      int *lm = nullptr;  // the group form forms every pair (its steps are latency-bound)
+      void *args[] = {&Mk, &sk, &upsk, &Sk, &rk, &pk, &lm};
       JSVD_CUDA(cudaLaunchCooperativeKernel((const void *)kern, dim3(grid), dim3(32 * kGroupWarps),
                                             args, 0, st));
       return JSVD_OK;
@@ -648,7 +667,7 @@ static int launch_sweeps(const MatViewT<T> &M, SvdState *state, double ups, int 
   // the cluster form where it applies, unless a launch shape for the grid
   // forms is asked for
   if ((g_svd_step == 0 && g_svd_grid_cap == 0 && g_svd_warps == 0) || g_svd_step == 3) {
-    const int rc = launch_sweeps_cluster<T, CPLX, COMP>(M, state, ups, S, rexp, flags, st);
+    const int rc = launch_sweeps_cluster<T, CPLX, COMP>(M, state, ups, S, rexp, flags, lastmod, st);
     if (rc != 1) return rc;
   }
   // The step form: each warp alone unless the chunked form is asked for.
@@ -681,19 +700,21 @@ static int launch_sweeps(const MatViewT<T> &M, SvdState *state, double ups, int 
   SvdState *sk = state;
   int Sk = S, rk = rexp, pk = flags | (warp_step ? kFlagWarpStep : 0);
   double upsk = ups;
-  void *args[] = {&Mk, &sk, &upsk, &Sk, &rk, &pk};
+  int *lm = warp_step ? lastmod : nullptr;
+  void *args[] = {&Mk, &sk, &upsk, &Sk, &rk, &pk, &lm};
   JSVD_CUDA(cudaLaunchCooperativeKernel((const void *)kern, dim3(grid), dim3(32 * W), args, 0, st));
   return JSVD_OK;
 }
 
 template <typename T, bool CPLX>
 static int phase_sweeps(const MatViewT<T> &M, SvdState *state, double ups, int S, int rexp,
-                        int flags, cudaStream_t st)
+                        int flags, int *lastmod, cudaStream_t st)
 {
   if constexpr (sizeof(T) == 8) {
-    if (flags & kFlagComp) return launch_sweeps<T, CPLX, true>(M, state, ups, S, rexp, flags, st);
+    if (flags & kFlagComp)
+      return launch_sweeps<T, CPLX, true>(M, state, ups, S, rexp, flags, lastmod, st);
   }
-  return launch_sweeps<T, CPLX, false>(M, state, ups, S, rexp, flags, st);
+  return launch_sweeps<T, CPLX, false>(M, state, ups, S, rexp, flags, lastmod, st);
 }
 
 // A9: norms, order, U = G 2^{-e_j}/f_j, sigma, V, info.
@@ -728,7 +749,9 @@ static int svd_fp64_run(int64_t m, int64_t n, const double *A, int64_t lda, doub
   SvdState *state = reinterpret_cast<SvdState *>(work + L.state);
   const MatView M = view_at<double>(work, L.gr, L.gi, L.vr, L.vi, CPLX, L, m, n);
   JSVD_TRY(phase_init<CPLX>(M, A, lda, state, rexp, st));
-  JSVD_TRY(phase_sweeps<double, CPLX>(M, state, ldexp(sqrt((double)m), -53), S, rexp, flags, st));
+  // the rank array serves the sweeps as the columns' last-change steps
+  JSVD_TRY(phase_sweeps<double, CPLX>(M, state, ldexp(sqrt((double)m), -53), S, rexp, flags,
+                                      reinterpret_cast<int *>(work + L.rank), st));
   return phase_finish<CPLX>(M, reinterpret_cast<int *>(work + L.e),
                             reinterpret_cast<double *>(work + L.f),
                             reinterpret_cast<int *>(work + L.rank), state, nullptr, U, ldu, sigma,
@@ -770,7 +793,8 @@ static int svd_mixed_run_t(int64_t m, int64_t n, const double *A, int64_t lda, d
   to_fp32_kernel<CPLX><<<grid, 256, 0, st>>>(M0, M32, st64, st32, scale_target(rexp));
   JSVD_CHECK_LAUNCH();
   const double ups32 = ldexp(sqrt((double)m), kMixedTolExp);
-  JSVD_TRY(phase_sweeps<float, CPLX>(M32, st32, ups32, S, 1 << 20, flags, st));
+  JSVD_TRY(phase_sweeps<float, CPLX>(M32, st32, ups32, S, 1 << 20, flags,
+                                     reinterpret_cast<int *>(work + L.rank), st));
   // V0 = orth(V32) in FP64 (in M64.v = the FP64 layout's V planes)
   dim3 gv((unsigned)((L.np + 255) / 256), (unsigned)std::min<int64_t>(n, 65535));
   v_to_fp64_kernel<CPLX><<<gv, 256, 0, st>>>(M32, M64.vr, M64.vi, L.ldv);
@@ -814,7 +838,8 @@ static int svd_mixed_run_t(int64_t m, int64_t n, const double *A, int64_t lda, d
       JSVD_CHECK_LAUNCH();
     }
   }
-  JSVD_TRY(phase_sweeps<double, CPLX>(M64, st64, ldexp(sqrt((double)m), -53), S, rexp, flags, st));
+  JSVD_TRY(phase_sweeps<double, CPLX>(M64, st64, ldexp(sqrt((double)m), -53), S, rexp, flags,
+                                      reinterpret_cast<int *>(work + L.rank), st));
   return phase_finish<CPLX>(M64, reinterpret_cast<int *>(work + L.e),
                             reinterpret_cast<double *>(work + L.f),
                             reinterpret_cast<int *>(work + L.rank), st64, st32, U, ldu, sigma,
@@ -1112,7 +1137,7 @@ static int svd_f32_run(int64_t m, int64_t n, const float *A, int64_t lda, float 
   init32_kernel<CPLX><<<grid, 256, 0, st>>>(A, lda, M, state);
   JSVD_CHECK_LAUNCH();
   JSVD_TRY(phase_sweeps<float, CPLX>(M, state, ldexp(sqrt((double)m), kF32TolExp), S, 1 << 20,
-                                     flags & kFlagPermute, st));
+                                     flags & kFlagPermute, rank, st));
   const int nb = (int)std::min<int64_t>((n * 32 + 255) / 256, (int64_t)sms * 8);
   colnorm32_kernel<CPLX><<<nb, 256, 0, st>>>(M, e, f);
   JSVD_CHECK_LAUNCH();

@@ -1024,17 +1024,36 @@ struct DeferredV {
 // its transformation, with no block barrier in between.  For the
 // persistent single-matrix sweep, where a step has at most a few pairs per
 // block and its time is the chain of one pair.
+//
+// Unchanged pairs (lastmod != nullptr): lastmod[j] is the last global step
+// (gstep counts the steps of the launch) at which column j was transformed,
+// swapped or rescaled (-1: never).  A pair met again one sweep (K = nt - 1
+// steps) after its last meeting with neither column changed since, and no
+// rescaling since (last_rescale), has the same columns bit for bit, so its
+// rotation test fails again: it is skipped, with the same results.
 template <typename T, bool CPLX, bool COMP = false, int CG = kAccL2>
 __device__ __forceinline__ void step_warps(const MatViewT<T, CG> &M, int k, int nt, double ups, int rk,
                                            bool permute, unsigned long long &Mloc, int &rots, int &gsn,
-                                           bool defer, DeferredV<T, CPLX> &dv)
+                                           bool defer, DeferredV<T, CPLX> &dv, int *lastmod = nullptr,
+                                           int gstep = 0, int last_rescale = 0)
 {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
   const int L = nt / 2;
+  const int K = nt - 1;
   for (int l = blockIdx.x * W + warp; l < L; l += gridDim.x * W) {
     int p, q;
     pair_of(k, l, nt, p, q);
-    if (q < M.n) {
+    bool skip = false;
+    if (lastmod != nullptr && q < M.n && rk == 0 && gstep - K > last_rescale) {
+      const int before = gstep - K;  // the pair's last meeting
+      skip = __ldcg(lastmod + p) < before && __ldcg(lastmod + q) < before;
+    }
+    if (skip) {
+      if (defer && dv.p >= 0) {  // settle the last step's V
+        dv.load(M);
+        dv.apply(M);
+      }
+    } else if (q < M.n) {
       // FP64 columns that fill them take wider load trips: sums 8 rows per
       // lane (4 complex), the transformation 12 (6 complex) of G's and V's
       // rows together -- one trip each for 256 + 128 rows
@@ -1064,6 +1083,10 @@ __device__ __forceinline__ void step_warps(const MatViewT<T, CG> &M, int k, int 
       }
       if (lane == 0 && o.rot) ++rots;
       if (lane == 0 && o.gs) ++gsn;
+      if (lastmod != nullptr && lane == 0 && (o.rot || o.swap)) {
+        __stcg(lastmod + p, gstep);
+        __stcg(lastmod + q, gstep);
+      }
     } else {
       if (defer && dv.p >= 0) {  // no pair of its own this step: settle the last one's V
         dv.load(M);

@@ -244,6 +244,32 @@ def test_step_forms_bit_identical(case):
         assert a["info"] == b["info"], name
 
 
+@pytest.mark.parametrize("case", range(10))
+def test_skipping_unchanged_pairs_bit_identical(case):
+    """Skipping a pivot pair whose columns have not changed since its last
+    meeting (JSVD_TUNE_SVD_SKIP) changes no result, in the per-warp and the
+    cluster step forms, on the step-form cases (rescaling and the mixed
+    mode's two phases among them)."""
+    import paper_2202_08361_gb300 as J
+    name, A, kw = _step_cases()[case]
+    try:
+        for mode in (2, 3):
+            J.tune_set(J.JSVD_TUNE_SVD_STEP, mode)
+            outs = []
+            for skip in (0, 1):
+                J.tune_set(J.JSVD_TUNE_SVD_SKIP, skip)
+                outs.append(gpu_svd(A, **kw))
+            a, b = outs
+            assert a["info"]["status"] == 0, name
+            for k in ("U", "V", "sigma", "sigma_e", "sigma_f"):
+                assert np.array_equal(np.ascontiguousarray(a[k]).view(np.uint8),
+                                      np.ascontiguousarray(b[k]).view(np.uint8)), (name, mode, k)
+            assert a["info"] == b["info"], name
+    finally:
+        J.tune_set(J.JSVD_TUNE_SVD_STEP, 0)
+        J.tune_set(J.JSVD_TUNE_SVD_SKIP, 1)
+
+
 def test_argument_errors():
     import ctypes
     torch = _torch()
