@@ -126,6 +126,17 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def sm_clock_mhz(local_rank):
+    """The SM clock nvidia-smi reports now (MHz), or None."""
+    try:
+        out = subprocess.run(["nvidia-smi", "-i", str(gpu_index(local_rank)),
+                              "--query-gpu=clocks.sm", "--format=csv,noheader,nounits"],
+                             capture_output=True, text=True, timeout=10).stdout
+        return float(out.strip().splitlines()[0])
+    except Exception:
+        return None
+
+
 def gpu_index(local_rank):
     vis = os.environ.get("CUDA_VISIBLE_DEVICES")
     if vis:
@@ -260,6 +271,21 @@ def fp64_pipe_rates(torch, J, dev):
             ms = e0.elapsed_time(e1)
             best = ms if best is None else min(best, ms)
         res[name + "_per_s"] = blocks * 256 * 8 * iters / (best * 1e-3)
+    # one warp alone, and one warp on each of an SM's four schedulers (one
+    # block of 32 or 128 threads): the time per FP64 instruction of a warp,
+    # also in SM clocks at the clock nvidia-smi reports just after
+    for warps in (1, 4):
+        J.probe_fp64_rate(0, 8, 1, sink, threads=32 * warps)
+        e0, e1 = _ev(torch)
+        e0.record(st)
+        J.probe_fp64_rate(0, 2000, 1, sink, threads=32 * warps)
+        e1.record(st)
+        torch.cuda.synchronize(dev)
+        ns_per_instr = e0.elapsed_time(e1) * 1e6 / (2000 * 8)
+        res["warp_fma_issue_ns_%dw" % warps] = ns_per_instr
+        clk = sm_clock_mhz(dev.index or 0)
+        if clk:
+            res["warp_fma_issue_cycles_%dw" % warps] = ns_per_instr * clk * 1e-3
     res["fma_flops"] = 2 * res["fma_per_s"]
     res["sqrt_in_fma"] = res["fma_per_s"] / res["sqrt_per_s"]
     res["div_in_fma"] = res["fma_per_s"] / res["div_per_s"]

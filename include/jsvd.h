@@ -449,15 +449,17 @@ JSVD_API int jsvd_selftest_fp64(int64_t n, uint64_t seed, unsigned long long *mi
                                 void *stream);
 
 /* Throughput probe of the FP64 pipe, the measured denominator of an
- * FP64-pipe roofline (the paper has no counterpart): `blocks` blocks of 256
- * threads, each thread 8 independent chains of `iters` operations of one
- * kind -- 0: fused multiply-add (lane operations = blocks * 256 * 8 *
- * iters); 1: the IEEE square root; 2: the IEEE division -- so that the pipe's
- * throughput, not its latency, sets the time; the caller times the launch
- * on `stream`.  sink: one DEVICE double the kernel writes.  Errors: -1 kind,
- * -2 iters < 1, -3 blocks < 1, -4 sink NULL, JSVD_E_CUDA. */
-JSVD_API int jsvd_probe_fp64_rate(int kind, int64_t iters, int blocks, double *sink,
-                                  void *stream);
+ * FP64-pipe roofline (the paper has no counterpart): `blocks` blocks of
+ * `threads` threads (32 .. 256, a multiple of 32), each thread 8
+ * independent chains of `iters` operations of one kind -- 0: fused
+ * multiply-add (lane operations = blocks * threads * 8 * iters); 1: the IEEE
+ * square root; 2: the IEEE division.  With many blocks the pipe's
+ * throughput sets the time; with one block of 32 threads, one warp's FP64
+ * issue rate.  The caller times the launch on `stream`.  sink: one DEVICE
+ * double the kernel writes.  Errors: -1 kind, -2 iters < 1, -3 blocks < 1,
+ * -4 threads, -5 sink NULL, JSVD_E_CUDA. */
+JSVD_API int jsvd_probe_fp64_rate(int kind, int64_t iters, int blocks, int threads,
+                                  double *sink, void *stream);
 
 /* Failure-detection self-test of the bounded grid barrier the persistent
  * SVD kernel uses between steps: a cooperative launch of `blocks` blocks

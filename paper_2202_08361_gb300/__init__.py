@@ -327,13 +327,14 @@ def ordering(n, stream=None):
     return tab
 
 
-def probe_fp64_rate(kind, iters, blocks, sink, stream=None):
+def probe_fp64_rate(kind, iters, blocks, sink, threads=256, stream=None):
     """Enqueue the FP64-pipe throughput probe (jsvd_probe_fp64_rate): kind 0
-    fused multiply-add, 1 IEEE square root, 2 IEEE division; blocks x 256
+    fused multiply-add, 1 IEEE square root, 2 IEEE division; blocks x
     threads x 8 chains x iters operations.  sink: a float64 CUDA tensor of
     at least one element.  The caller times the launch."""
     _native.check(_native.lib().jsvd_probe_fp64_rate(int(kind), int(iters), int(blocks),
-                                                     sink.data_ptr(), _stream_handle(stream)),
+                                                     int(threads), sink.data_ptr(),
+                                                     _stream_handle(stream)),
                   "jsvd_probe_fp64_rate")
 
 

@@ -147,7 +147,8 @@ def lib():
         L.jsvd_selftest_barrier.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _i64, _vp,
                                             _vp]
         L.jsvd_selftest_barrier.restype = ctypes.c_int
-        L.jsvd_probe_fp64_rate.argtypes = [ctypes.c_int, _i64, ctypes.c_int, _vp, _vp]
+        L.jsvd_probe_fp64_rate.argtypes = [ctypes.c_int, _i64, ctypes.c_int, ctypes.c_int, _vp,
+                                           _vp]
         L.jsvd_probe_fp64_rate.restype = ctypes.c_int
         L.jsvd_ordering.argtypes = [ctypes.c_int32, _vp, _vp]
         L.jsvd_ordering.restype = ctypes.c_int

@@ -208,14 +208,15 @@ __global__ void __launch_bounds__(256) probe_fp64_kernel(int kind, int64_t iters
 
 }  // namespace jsvd
 
-extern "C" int jsvd_probe_fp64_rate(int kind, int64_t iters, int blocks, double *sink,
-                                    void *stream)
+extern "C" int jsvd_probe_fp64_rate(int kind, int64_t iters, int blocks, int threads,
+                                    double *sink, void *stream)
 {
   if (kind < 0 || kind > 2) return -1;
   if (iters < 1) return -2;
   if (blocks < 1) return -3;
-  if (!sink) return -4;
-  jsvd::probe_fp64_kernel<<<blocks, 256, 0, jsvd::as_stream(stream)>>>(kind, iters, sink);
+  if (threads < 32 || threads > 256 || threads % 32 != 0) return -4;
+  if (!sink) return -5;
+  jsvd::probe_fp64_kernel<<<blocks, threads, 0, jsvd::as_stream(stream)>>>(kind, iters, sink);
   JSVD_CHECK_LAUNCH();
   return JSVD_OK;
 }
