@@ -105,14 +105,17 @@ JSVD_API const char *jsvd_last_cuda_error(void);
  *     in chunks.  The results are identical. */
 #define JSVD_TUNE_EVD_HOST 7
 /*   JSVD_TUNE_SVD_STEP: the form of a step in the single-matrix sweep
- *     kernel: 0 (the default) = four warps on each pair where a step's pairs
- *     fit one per SM and the columns one load trip, else each warp alone in
- *     one thread-block cluster where the pairs fit it, else each warp alone;
- *     1 = chunks of pairs in three block phases, one pair's rotation per
- *     lane; 2 = each warp runs its pairs alone, a rotation's independent
- *     divisions and square roots spread over its lanes, steps separated by a
- *     grid barrier; 3 = the same in one cluster where it fits; 4 = four
- *     warps on each pair where it fits.  The results are identical. */
+ *     kernel: 0 (the default) = four warps on each pair, the rows in
+ *     registers, where a step's pairs fit one per SM and the columns one
+ *     load trip; else each warp alone in one thread-block cluster for steps
+ *     of at most 64 pairs; else two or four warps on each pair with the rows
+ *     streamed, up to 4 pairs per SM; else each warp alone.  1 = chunks of
+ *     pairs in three block phases, one pair's rotation per lane; 2 = each
+ *     warp runs its pairs alone, a rotation's independent divisions and
+ *     square roots spread over its lanes, steps separated by a grid barrier;
+ *     3 = the same in one cluster where it fits; 4 = four warps per pair,
+ *     rows in registers, where it fits; 5 = two or four warps per pair, rows
+ *     streamed.  The results are identical. */
 #define JSVD_TUNE_SVD_STEP 8
 /*   JSVD_TUNE_SVD_SKIP: value = 1 (default): the single-matrix sweeps skip
  *     a pivot pair neither of whose columns has changed since the pair was

@@ -154,7 +154,7 @@ __global__ void init_kernel(const double *__restrict__ A, int64_t lda, MatView M
 //     at the price of two block barriers per chunk).
 // T is the precision of the columns (double; float in the FP32 phase of
 // the mixed SVD).
-template <typename T, bool CPLX, bool COMP>
+template <typename T, bool CPLX, bool COMP, int STREAM = 0>
 __global__ void __launch_bounds__(256) sweeps_kernel(MatViewT<T> M, SvdState *st, double ups,
                                                      int max_sweeps, int rescale_exp, int flags,
                                                      int *lastmod)
@@ -164,6 +164,9 @@ __global__ void __launch_bounds__(256) sweeps_kernel(MatViewT<T> M, SvdState *st
   __shared__ double s_gsum[kGroupWarps];
   if (st->nonfinite) return;
   const bool group = (flags & kFlagGroupStep) != 0;
+  // STREAM (2 or 4 warps per pair, rows streamed) is an instantiation of
+  // its own, so that its registers bind no other form
+  constexpr bool gstream = STREAM != 0;
   GroupV<CPLX> gv;
   const int nt = M.n + (M.n & 1);
   const int K = nt - 1, L = nt / 2;
@@ -171,7 +174,7 @@ __global__ void __launch_bounds__(256) sweeps_kernel(MatViewT<T> M, SvdState *st
   const bool warp_step = (flags & kFlagWarpStep) != 0;
   // V's transformation held over to the next step (DeferredV) when every
   // warp has at most one pair per step and V's rows take one trip
-  const bool defer = !group && warp_step && (int64_t)gridDim.x * W >= L &&
+  const bool defer = !group && !gstream && warp_step && (int64_t)gridDim.x * W >= L &&
                      M.np <= 32 * DeferredV<T, CPLX>::kRows;
   DeferredV<T, CPLX> dv;
   if (K < 1) {
@@ -202,13 +205,15 @@ __global__ void __launch_bounds__(256) sweeps_kernel(MatViewT<T> M, SvdState *st
       }
       unsigned long long Mloc = 0ull;
       int rots = 0, gsn = 0;
-      if constexpr (sizeof(T) == 8 && !COMP) {
-        if (group)
+      if (rk) last_rescale = (int)gstep;
+      if constexpr (gstream && !COMP) {
+        step_group_stream<T, CPLX, kAccL2, STREAM>(M, k, nt, ups, rk, (flags & kFlagPermute) != 0,
+                                                   Mloc, rots, gsn, s_gsum, lastmod, (int)gstep,
+                                                   last_rescale);
+      } else if (group) {
+        if constexpr (sizeof(T) == 8 && !COMP)
           step_group<CPLX>(M, k, nt, ups, rk, (flags & kFlagPermute) != 0, Mloc, rots, gsn, gv,
                            s_gsum);
-      }
-      if (rk) last_rescale = (int)gstep;
-      if (group) {
       } else if (warp_step)
         step_warps<T, CPLX, COMP>(M, k, nt, ups, rk, (flags & kFlagPermute) != 0, Mloc, rots, gsn,
                                   defer, dv, lastmod, (int)gstep, last_rescale);
@@ -408,14 +413,17 @@ int svd_set_skip(int v)
 
 static int g_svd_grid_cap = 0;
 static int g_svd_warps = 0;
-static int g_svd_step = 0;  // 0: four warps per pair where that fits, else per warp in one
-                            // cluster where that fits, else per warp; 1: chunked; 2: per warp
-                            // (grid barrier); 3: per warp in one cluster where it fits;
-                            // 4: four warps per pair where it fits
+static int g_svd_step = 0;  // 0: four warps per pair with the rows in registers where that
+                            // fits, else per warp in one cluster for steps of at most 64
+                            // pairs, else two or four warps per pair with the rows streamed up
+                            // to 4 pairs per SM, else per warp; 1: chunked; 2: per warp (grid
+                            // barrier); 3: per warp in one cluster where it fits; 4: four
+                            // warps per pair, rows in registers, where it fits; 5: two or four
+                            // warps per pair, rows streamed
 
 int svd_set_step_mode(int v)
 {
-  if (v < 0 || v > 4) return -2;
+  if (v < 0 || v > 5) return -2;
   g_svd_step = v;
   return JSVD_OK;
 }
@@ -664,11 +672,39 @@ static int launch_sweeps(const MatViewT<T> &M, SvdState *state, double ups, int 
       return JSVD_OK;
     }
   }
-  // the cluster form where it applies, unless a launch shape for the grid
-  // forms is asked for
-  if ((g_svd_step == 0 && g_svd_grid_cap == 0 && g_svd_warps == 0) || g_svd_step == 3) {
+  // the cluster form for short steps that the four-warp form does not take
+  // (the FP32 phase of the mixed mode, the compensated sums), unless a
+  // launch shape for the grid forms is asked for
+  const bool auto_form = g_svd_step == 0 && g_svd_grid_cap == 0 && g_svd_warps == 0;
+  if (auto_form || g_svd_step == 3) {
     const int rc = launch_sweeps_cluster<T, CPLX, COMP>(M, state, ups, S, rexp, flags, lastmod, st);
     if (rc != 1) return rc;
+  }
+  // two or four warps on each pair with the rows streamed
+  // (step_group_stream): four when every pair of a step gets a block at
+  // once, else two when that holds with two.  The default up to 4 pairs per
+  // SM; with more pairs each SM already holds enough one-warp pairs
+  if constexpr (!COMP) {
+    if ((auto_form && Lp <= 4 * sms) || g_svd_step == 5) {
+      auto k4 = sweeps_kernel<T, CPLX, COMP, 4>;
+      auto k2 = sweeps_kernel<T, CPLX, COMP, 2>;
+      int per4 = 0, per2 = 0;
+      JSVD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per4, k4, 128, 0));
+      JSVD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per2, k2, 64, 0));
+      const bool four = (int64_t)per4 * sms >= Lp || (int64_t)per2 * sms < Lp;
+      const int per_sm = four ? per4 : per2;
+      if (per_sm < 1) return JSVD_E_UNSUPPORTED;
+      const int grid = std::max(1, std::min(Lp, per_sm * sms));
+      MatViewT<T> Mk = M;
+      SvdState *sk = state;
+      int Sk = S, rk = rexp, pk = flags | kFlagGroupStream;
+      double upsk = ups;
+      int *lm = lastmod;
+      void *args[] = {&Mk, &sk, &upsk, &Sk, &rk, &pk, &lm};
+      JSVD_CUDA(cudaLaunchCooperativeKernel(four ? (const void *)k4 : (const void *)k2, dim3(grid),
+                                            dim3(four ? 128 : 64), args, 0, st));
+      return JSVD_OK;
+    }
   }
   // The step form: each warp alone unless the chunked form is asked for.
   // Measured on GB300 for 256 x 128 to 4096 x 2048, real and complex, FP64

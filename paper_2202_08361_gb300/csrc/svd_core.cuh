@@ -1315,6 +1315,205 @@ __device__ __forceinline__ void step_group(const MatViewT<double, CG> &M, int k,
   }
 }
 
+// GW = 2 or 4 warps of a block on each pair for long columns (step_group
+// keeps a pair's rows in registers; here they stream through in trips of U
+// rows per lane).  Warp g forms the sums s = g, g + GW, ... of (0 ||g_p||^2,
+// 1 ||g_q||^2, 2 Re g_q^* g_p, 3 Im g_q^* g_p) over all the rows, each in
+// the canonical lane order (lane l: rows l, l + 32, ... ascending), as
+// pair_sums forms that sum, and reduces each by warp_sum; every warp
+// computes the rotation; the transformation of G's and then V's rows is
+// shared out by trips, warp g taking trips g, g + GW, ...  A warp's FP64 (or
+// FP32) instruction stream per step is then about 1/GW of the one-warp
+// form's, and GW times as many warps keep the SM's pipes and memory busy.
+// The same sums, rotations and transformed rows, so the same bits.  lastmod
+// etc.: as in step_warps.
+template <typename T, bool CPLX, int CG, int GW>
+__device__ __forceinline__ void step_group_stream(const MatViewT<T, CG> &M, int k, int nt, double ups,
+                                                  int rk, bool permute, unsigned long long &Mloc,
+                                                  int &rots, int &gsn, double *s_sum, int *lastmod,
+                                                  int gstep, int last_rescale)
+{
+  static_assert(GW == 2 || GW == 4, "2 or 4 warps per pair");
+  constexpr int U = (sizeof(T) == 4) ? 8 : 4;  // rows per lane per trip
+  constexpr int NS = 4 / GW;                    // sums per warp
+  const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
+  const int L = nt / 2, K = nt - 1;
+  const int nsum = CPLX ? 4 : 3;
+  for (int l = blockIdx.x; l < L; l += gridDim.x) {
+    int p, q;
+    pair_of(k, l, nt, p, q);
+    if (q >= M.n) {
+      if (rk && g == 0) {  // phantom partner: only a pending rescale applies
+        scale_col(M, M.Gr(p), rk, lane);
+        if (CPLX) scale_col(M, M.Gi(p), rk, lane);
+      }
+      continue;
+    }
+    if (lastmod != nullptr && rk == 0 && gstep - K > last_rescale) {
+      const int before = gstep - K;  // the pair's last meeting, one sweep ago
+      if (__ldcg(lastmod + p) < before && __ldcg(lastmod + q) < before) continue;
+    }
+    T *gpr = M.Gr(p), *gqr = M.Gr(q);
+    T *gpi = CPLX ? M.Gi(p) : nullptr, *gqi = CPLX ? M.Gi(q) : nullptr;
+    if (rk) {  // section 3.2, step 2: both columns downscaled by 2^rk, trips shared out
+      for (int base = lane + 32 * U * g; base < M.mp; base += 32 * U * GW) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int i = base + 32 * u;
+          if (i < M.mp) {
+            M.st(gpr + i, ldexp_rn(M.ld(gpr + i), rk));
+            M.st(gqr + i, ldexp_rn(M.ld(gqr + i), rk));
+            if (CPLX) {
+              M.st(gpi + i, ldexp_rn(M.ld(gpi + i), rk));
+              M.st(gqi + i, ldexp_rn(M.ld(gqi + i), rk));
+            }
+          }
+        }
+      }
+      __syncthreads();  // every row scaled before any warp sums
+    }
+    // this warp's sums; it loads only the planes they read (sum 0: g_p,
+    // 1: g_q, 2 and 3: both)
+    const bool need_p = GW == 2 || g != 1, need_q = GW == 2 || g != 0;
+    T acc[NS];
+#pragma unroll
+    for (int j = 0; j < NS; ++j) acc[j] = T(0);
+    if (g < nsum) {
+      for (int base = lane; base < M.mp; base += 32 * U) {
+        T xpr[U], xqr[U], xpi[U], xqi[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int i = base + 32 * u;
+          xpr[u] = xqr[u] = xpi[u] = xqi[u] = T(0);
+          if (i < M.mp) {
+            if (need_p) {
+              xpr[u] = M.ld(gpr + i);
+              if (CPLX) xpi[u] = M.ld(gpi + i);
+            }
+            if (need_q) {
+              xqr[u] = M.ld(gqr + i);
+              if (CPLX) xqi[u] = M.ld(gqi + i);
+            }
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          if (base + 32 * u < M.mp) {
+#pragma unroll
+            for (int j = 0; j < NS; ++j) {
+              const int sidx = g + GW * j;
+              if (sidx == 0) {
+                acc[j] = fma_t(xpr[u], xpr[u], acc[j]);
+                if (CPLX) acc[j] = fma_t(xpi[u], xpi[u], acc[j]);
+              } else if (sidx == 1) {
+                acc[j] = fma_t(xqr[u], xqr[u], acc[j]);
+                if (CPLX) acc[j] = fma_t(xqi[u], xqi[u], acc[j]);
+              } else if (sidx == 2) {
+                acc[j] = fma_t(xqr[u], xpr[u], acc[j]);
+                if (CPLX) acc[j] = fma_t(xqi[u], xpi[u], acc[j]);
+              } else if (CPLX) {
+                acc[j] = fma_t(xqr[u], xpi[u], acc[j]);
+                acc[j] = fma_t(-xqi[u], xpr[u], acc[j]);
+              }
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < NS; ++j) {
+        const int sidx = g + GW * j;
+        if (sidx < nsum) {
+          const double tot = warp_sum((double)acc[j]);
+          if (lane == 0) s_sum[sidx] = tot;
+        }
+      }
+    }
+    __syncthreads();
+    PairSums sm;
+    sm.pp = s_sum[0];
+    sm.qq = s_sum[1];
+    sm.qr = s_sum[2];
+    sm.qi = CPLX ? s_sum[3] : 0.0;
+    sm.fp = sm.fq = 1.0;
+    sm.ep = sm.eq = 0;
+    sm.wide = 0;
+    __syncthreads();  // s_sum is free for the next pair
+    if constexpr (sizeof(T) == 8) {
+      // squares below 2^-1022 may have lost bits: the wide-exponent sums
+      if (bits(sm.pp) < kWideBelow || bits(sm.qq) < kWideBelow) {
+        sm = pair_sums_wide<CPLX, CG, false>(M, p, q);
+        __syncthreads();  // every warp has read the columns before any writes them
+      }
+    }
+    PairOut o = pair_rotation_warp<CPLX>(sm, ups);
+    o.swap = o.swap && permute;
+    if (o.rot || o.swap) {
+      const T c = to_t(o.c, T(0)), C = to_t(o.C, T(0));
+      const T S = CPLX ? to_t(o.S, T(0)) : T(0);
+      bool gdone = false;
+      if constexpr (sizeof(T) == 8) {
+        if (o.rot && o.gs) {  // Eq. e:GS replaces the rotation on G: one warp
+          if (g == 0) gs_apply<CPLX, CG>(M, p, q, o, Mloc);
+          gdone = true;
+        }
+      }
+      for (int pass = gdone ? 1 : 0; pass < 2; ++pass) {
+        const bool onG = (pass == 0);
+        const int rows = onG ? M.mp : M.np;
+        T *xpr = onG ? gpr : M.Vr(p), *xqr = onG ? gqr : M.Vr(q);
+        T *xpi = CPLX ? (onG ? gpi : M.Vi(p)) : nullptr;
+        T *xqi = CPLX ? (onG ? gqi : M.Vi(q)) : nullptr;
+        T *dpr = o.swap ? xqr : xpr, *dqr = o.swap ? xpr : xqr;
+        T *dpi = o.swap ? xqi : xpi, *dqi = o.swap ? xpi : xqi;
+        for (int base = lane + 32 * U * g; base < rows; base += 32 * U * GW) {
+          T pr[U], qr[U], pi[U], qi[U];
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            const int i = base + 32 * u;
+            pr[u] = qr[u] = pi[u] = qi[u] = T(0);
+            if (i < rows) {
+              pr[u] = M.ld(xpr + i);
+              qr[u] = M.ld(xqr + i);
+              if (CPLX) {
+                pi[u] = M.ld(xpi + i);
+                qi[u] = M.ld(xqi + i);
+              }
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            const int i = base + 32 * u;
+            if (i < rows) {
+              T npr = pr[u], npi = pi[u], nqr = qr[u], nqi = qi[u];
+              if (o.rot) {
+                rotate_row<T, CPLX>(pr[u], pi[u], qr[u], qi[u], c, C, S, npr, npi, nqr, nqi);
+                if (onG) {
+                  Mloc = max(Mloc, max(magbits(npr), magbits(nqr)));
+                  if (CPLX) Mloc = max(Mloc, max(magbits(npi), magbits(nqi)));
+                }
+              }
+              M.st(dpr + i, npr);
+              M.st(dqr + i, nqr);
+              if (CPLX) {
+                M.st(dpi + i, npi);
+                M.st(dqi + i, nqi);
+              }
+            }
+          }
+        }
+      }
+    }
+    if (g == 0 && lane == 0) {
+      if (o.rot) ++rots;
+      if (o.gs) ++gsn;
+      if (lastmod != nullptr && (o.rot || o.swap)) {
+        __stcg(lastmod + p, gstep);
+        __stcg(lastmod + q, gstep);
+      }
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Finalisation pieces (section 4.2.1), shared by the single-matrix and the
 // batched kernels so that both produce the same bits.

@@ -24,7 +24,7 @@ int main(void)
   memset(&s, 0, sizeof s);
   printf("evd_missing_stream %d\n", jsvd_evd2x2_batched(JSVD_REAL, &s, 10, NULL));
   printf("evd_empty %d\n", jsvd_evd2x2_batched(JSVD_REAL, &s, 0, NULL));
-  printf("tune_bad %d\n", jsvd_tune_set(JSVD_TUNE_SVD_STEP, 5, 0));
+  printf("tune_bad %d\n", jsvd_tune_set(JSVD_TUNE_SVD_STEP, 6, 0));
   printf("tune_ok %d\n", jsvd_tune_set(JSVD_TUNE_SVD_STEP, 0, 0));
   printf("message %s\n", jsvd_strerror(JSVD_E_WORKSPACE));
   return 0;

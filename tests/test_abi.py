@@ -85,7 +85,7 @@ def test_argument_errors_need_no_gpu(lib):
     assert L.jsvd_tune_set(_native.JSVD_TUNE_EVD32_DIV, 8, 0) == -2   # placements 0..7
     assert L.jsvd_tune_set(_native.JSVD_TUNE_EVD32_DIV, 1, 3) == -3   # fields 0..2
     assert L.jsvd_tune_set(_native.JSVD_TUNE_EVD32_DIV, -1, 0) == 0
-    assert L.jsvd_tune_set(_native.JSVD_TUNE_SVD_STEP, 5, 0) == -2
+    assert L.jsvd_tune_set(_native.JSVD_TUNE_SVD_STEP, 6, 0) == -2
     assert L.jsvd_tune_set(_native.JSVD_TUNE_SVD_SKIP, 2, 0) == -2
     assert L.jsvd_tune_set(_native.JSVD_TUNE_SVD_SKIP, 1, 0) == 0
     assert L.jsvd_tune_set(_native.JSVD_TUNE_SVD_STEP, 0, 0) == 0

@@ -218,19 +218,19 @@ def _step_cases():
 
 @pytest.mark.parametrize("case", range(10))
 def test_step_forms_bit_identical(case):
-    """The three forms of a sweep step (JSVD_TUNE_SVD_STEP: chunks with one
+    """The five forms of a sweep step (JSVD_TUNE_SVD_STEP: chunks with one
     rotation per lane; each warp alone with the rotation's independent
-    divisions and roots spread over its lanes, G and V in L2; the same per
-    warp inside one thread-block cluster with G and V in the blocks' shared
-    memory) give the same bits, on one-trip and ragged columns, odd n,
-    column swaps, compensated sums, the wide-exponent fallback,
-    Gram-Schmidt steps, a zero column, forced rescaling and the mixed
-    mode's FP32 phase."""
+    divisions and roots spread over its lanes; the same inside one
+    thread-block cluster; four warps per pair with the rows in registers;
+    two or four warps per pair with the rows streamed) give the same bits,
+    on one-trip and ragged columns, odd n, column swaps, compensated sums,
+    the wide-exponent fallback, Gram-Schmidt steps, a zero column, forced
+    rescaling and the mixed mode's FP32 phase."""
     import paper_2202_08361_gb300 as J
     name, A, kw = _step_cases()[case]
     outs = []
     try:
-        for mode in (1, 2, 3, 4):
+        for mode in (1, 2, 3, 4, 5):
             J.tune_set(J.JSVD_TUNE_SVD_STEP, mode)
             outs.append(gpu_svd(A, **kw))
     finally:
@@ -247,13 +247,13 @@ def test_step_forms_bit_identical(case):
 @pytest.mark.parametrize("case", range(10))
 def test_skipping_unchanged_pairs_bit_identical(case):
     """Skipping a pivot pair whose columns have not changed since its last
-    meeting (JSVD_TUNE_SVD_SKIP) changes no result, in the per-warp and the
-    cluster step forms, on the step-form cases (rescaling and the mixed
+    meeting (JSVD_TUNE_SVD_SKIP) changes no result, in the per-warp, the
+    cluster and the streamed multi-warp step forms, on the step-form cases (rescaling and the mixed
     mode's two phases among them)."""
     import paper_2202_08361_gb300 as J
     name, A, kw = _step_cases()[case]
     try:
-        for mode in (2, 3):
+        for mode in (2, 3, 5):
             J.tune_set(J.JSVD_TUNE_SVD_STEP, mode)
             outs = []
             for skip in (0, 1):
