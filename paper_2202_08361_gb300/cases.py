@@ -2,7 +2,7 @@
 
     python -m paper_2202_08361_gb300.cases evd   [--log2 23] [--f32]
     python -m paper_2202_08361_gb300.cases svd   [--m 1024 --n 512 --complex --normal
-                                                  --mode fp64|mixed --reps 1]
+                                                  --mode fp64|mixed --step 0..5 --reps 1]
     python -m paper_2202_08361_gb300.cases batch [--count 1000] [--shape 64x32]
     python -m paper_2202_08361_gb300.cases diff  [--count 4096]
 
@@ -39,11 +39,15 @@ def main(argv=None):
                         "instead of the uneven shapes")
     p.add_argument("--warps", type=int, default=0, help="batch: warps per block (0: default)")
     p.add_argument("--smem", type=int, default=-1, help="batch: shared-memory KiB (-1: default)")
+    p.add_argument("--step", type=int, default=-1,
+                   help="svd: JSVD_TUNE_SVD_STEP form of the sweep steps (-1: the default)")
     p.add_argument("--warmup", type=int, default=1)
     p.add_argument("--reps", type=int, default=1)
     a = p.parse_args(argv)
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
+    if a.step >= 0:
+        J.tune_set(J.JSVD_TUNE_SVD_STEP, a.step)
 
     if a.case == "evd":
         r = 1 << a.log2
