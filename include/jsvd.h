@@ -117,11 +117,12 @@ JSVD_API const char *jsvd_last_cuda_error(void);
  *     rows in registers, where it fits; 5 = two or four warps per pair, rows
  *     streamed.  The results are identical. */
 #define JSVD_TUNE_SVD_STEP 8
-/*   JSVD_TUNE_SVD_SKIP: value = 1 (default): the single-matrix sweeps skip
- *     a pivot pair neither of whose columns has changed since the pair was
- *     last taken, one sweep earlier (its rotation test would fail again on
- *     the same columns); 0: every pair is formed.  The results are
- *     identical. */
+/*   JSVD_TUNE_SVD_SKIP: value = 1 (default): the sweeps (single-matrix and
+ *     batched) skip a pivot pair neither of whose columns has changed since
+ *     the pair was last taken, one sweep earlier (its rotation test would
+ *     fail again on the same columns); 0: every pair is formed.  A batched
+ *     launch takes the value in force when it is launched (or captured).
+ *     The results are identical. */
 #define JSVD_TUNE_SVD_SKIP 9
 /* Sets one of the knobs above for the whole process (not thread-safe with
  * respect to launches running concurrently on other host threads).

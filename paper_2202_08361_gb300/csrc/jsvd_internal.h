@@ -25,6 +25,8 @@ constexpr int kFlagComp = 2;     // compensated dot-products (FP64 sweeps)
 constexpr int kFlagWarpStep = 4; // each warp runs its pairs alone (sweep kernel)
 constexpr int kFlagGroupStep = 8; // four warps of a block on each pair (sweep kernel)
 constexpr int kFlagGroupStream = 16; // 2 or 4 warps on each pair, rows streamed
+constexpr int kFlagSkip = 32;     // batched sweeps skip unchanged pairs
+int svd_skip_on();
 int svd_check_opts(const jsvd_opts *o, int &S, int &mode, int &rexp, int &flags);
 size_t svd_fp64_workspace(bool cplx, int64_t m, int64_t n);
 size_t svd_mixed_workspace(bool cplx, int64_t m, int64_t n);

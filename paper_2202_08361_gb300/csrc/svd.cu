@@ -404,6 +404,8 @@ __global__ void output_kernel(MatView M, const int *e, const double *f, const in
 
 static int g_svd_skip = 1;  // skip the pairs whose columns did not change (same results)
 
+int svd_skip_on() { return g_svd_skip; }
+
 int svd_set_skip(int v)
 {
   if (v != 0 && v != 1) return -2;

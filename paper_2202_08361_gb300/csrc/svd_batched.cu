@@ -223,6 +223,14 @@ __device__ __forceinline__ void batch_one(BatchShared &sh, const BatchDesc &d, i
       conv = true;
     }
     unsigned long long gstep = 0;
+    // the rank array holds the columns' last-change steps during the sweeps
+    // (pairs unchanged since their last meeting are skipped, as in
+    // step_warps)
+    int *lastmod = (flags & kFlagSkip) ? rank : nullptr;
+    if (lastmod)
+      for (int j = threadIdx.x; j < d.n; j += blockDim.x) lastmod[j] = -1;
+    __syncthreads();
+    int last_rescale = INT_MIN / 2;
     for (int sweep = 0; sweep < S && !conv; ++sweep) {
       for (int k = 0; k < K; ++k, ++gstep) {
         const int cur = (int)(gstep % 3), nxt = (int)((gstep + 1) % 3), old = (int)((gstep + 2) % 3);
@@ -239,10 +247,11 @@ __device__ __forceinline__ void batch_one(BatchShared &sh, const BatchDesc &d, i
         }
         unsigned long long Mloc = 0ull;
         int rots = 0, gsn = 0;
+        if (rk) last_rescale = (int)gstep;
         for (int base = 0; base < L; base += 32)
           step_chunk<double, CPLX, CG, COMP>(M, k, nt, base, 32, ups, rk,
                                              (flags & kFlagPermute) != 0, sh.sums, sh.out, Mloc,
-                                             rots, gsn);
+                                             rots, gsn, lastmod, (int)gstep, last_rescale);
         Mloc = warp_umax(Mloc);
         if (lane == 0) {
           if (Mloc) atomicMax(&sh.M[nxt], Mloc);
@@ -466,6 +475,7 @@ extern "C" int jsvd_svd_batched_launch(jsvd_field field, const jsvd_opts *opts, 
   if (field != JSVD_REAL && field != JSVD_COMPLEX) return -1;
   int S, mode, rexp, flags;
   if (svd_check_opts(opts, S, mode, rexp, flags) || mode != JSVD_FP64) return -2;
+  if (svd_skip_on()) flags |= kFlagSkip;  // JSVD_TUNE_SVD_SKIP
   if (count < 0 || count > (1 << 26)) return -3;
   if (!work || ((uintptr_t)work & 255)) return -4;
   if (count == 0) return JSVD_OK;

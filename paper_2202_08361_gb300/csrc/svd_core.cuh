@@ -906,16 +906,25 @@ template <typename T, bool CPLX, int CG, bool COMP = false>
 __device__ __forceinline__ void step_chunk(const MatViewT<T, CG> &M, int k, int nt, int base, int CH,
                                            double ups, int rk, bool permute, PairSums *s_sums,
                                            PairOut *s_out, unsigned long long &Mloc, int &rots,
-                                           int &gsn)
+                                           int &gsn, int *lastmod = nullptr, int gstep = 0,
+                                           int last_rescale = 0)
 {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
-  const int L = nt / 2;
+  const int L = nt / 2, K = nt - 1;
+  constexpr int kSkipped = 2;  // PairSums::wide of a pair skipped as unchanged (step_warps)
   for (int i = warp; i < CH; i += W) {
     const int l = base + i;
     if (l >= L) break;
     int p, q;
     pair_of(k, l, nt, p, q);
-    if (q < M.n) {
+    bool skip = false;
+    if (lastmod != nullptr && q < M.n && rk == 0 && gstep - K > last_rescale) {
+      const int before = gstep - K;  // the pair's last meeting, one sweep ago
+      skip = __ldcg(lastmod + p) < before && __ldcg(lastmod + q) < before;
+    }
+    if (skip) {
+      if (lane == 0) s_sums[i].wide = kSkipped;
+    } else if (q < M.n) {
       const PairSums sm = pair_sums<T, CPLX, CG, COMP>(M, p, q, rk);
       if (lane == 0) s_sums[i] = sm;
     } else if (rk) {  // phantom partner: only a pending rescale applies
@@ -931,8 +940,17 @@ __device__ __forceinline__ void step_chunk(const MatViewT<T, CG> &M, int k, int 
       pair_of(k, l, nt, p, q);
       if (q < M.n) {
         const PairSums sm = s_sums[i];
-        PairOut o = pair_rotation<CPLX>(sm, ups);
-        o.swap = o.swap && permute;
+        PairOut o;
+        if (sm.wide == kSkipped) {  // unchanged since its last meeting: no rotation, no swap
+          o.rot = o.swap = false;
+          o.c = 1.0;
+          o.C = o.S = 0.0;
+          o.gs = o.ex = o.ey = 0;
+          o.psr = o.psi = 0.0;
+        } else {
+          o = pair_rotation<CPLX>(sm, ups);
+          o.swap = o.swap && permute;
+        }
         s_out[i] = o;
       }
     }
@@ -948,6 +966,10 @@ __device__ __forceinline__ void step_chunk(const MatViewT<T, CG> &M, int k, int 
       pair_apply<T, CPLX>(M, p, q, o, Mloc);
       if (lane == 0 && o.rot) ++rots;
       if (lane == 0 && o.gs) ++gsn;
+      if (lastmod != nullptr && lane == 0 && (o.rot || o.swap)) {
+        __stcg(lastmod + p, gstep);
+        __stcg(lastmod + q, gstep);
+      }
     }
   }
   __syncthreads();

@@ -224,6 +224,29 @@ def test_full_workload_10000_uneven():
         assert np.abs(s - so).max() <= tol(int(n[i])) * so[0], i
 
 
+@pytest.mark.parametrize("cplx", [False, True])
+def test_skipping_unchanged_pairs_bit_identical(cplx):
+    """The batched sweeps skip the pairs whose columns have not changed since
+    their last meeting (JSVD_TUNE_SVD_SKIP); the results are the bits of the
+    run that forms every pair."""
+    import paper_2202_08361_gb300 as J
+    torch = _torch()
+    mats = mats_mixed(cplx, seed=51 + cplx) + workloads.diff_batch(count=6, m=64, n=32, k=8)[0].tolist()
+    mats = [np.asarray(a, dtype=np.complex128 if cplx else np.float64) for a in mats]
+    outs = []
+    try:
+        for skip in (0, 1):
+            J.tune_set(J.JSVD_TUNE_SVD_SKIP, skip)
+            B = J.svd_batched(mats)
+            torch.cuda.synchronize()
+            outs.append((B.U.clone(), B.V.clone(), B.sigma.clone(), J.decode_info(B.info)))
+    finally:
+        J.tune_set(J.JSVD_TUNE_SVD_SKIP, 1)
+    for a, b in zip(outs[0][:3], outs[1][:3]):
+        assert same(a, b)
+    assert outs[0][3] == outs[1][3]
+
+
 def test_cuda_graph_replay():
     import paper_2202_08361_gb300 as J
     torch = _torch()
