@@ -434,7 +434,8 @@ JSVD_API int jsvd_dgemm(int transA, int64_t M, int64_t N, int64_t K, double alph
                         double *C, int64_t ldc, void *stream);
 
 /* Self-test of the library's integer-pipe binary64 division and square
- * root against the GPU's IEEE FP64 instructions: n generated operand pairs
+ * root (both their branching and their select-based forms) against the
+ * GPU's IEEE FP64 instructions: n generated operand pairs
  * (several families: arbitrary bit patterns, subnormals, powers of two,
  * extremes), from seed; atomically ADDS the number of differing divisions
  * to mismatches[0] and of square roots to mismatches[1] (DEVICE memory, two

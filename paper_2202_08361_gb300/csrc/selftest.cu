@@ -1,7 +1,7 @@
 // selftest.cu -- self-tests that run on the device:
 //   jsvd_selftest_fp64: the integer-pipe binary64 division and square root
-//     (fp64soft.cuh) against the FP64 pipe's IEEE instructions on generated
-//     operands, counting mismatching bit patterns;
+//     (fp64soft.cuh, both forms) against the FP64 pipe's IEEE instructions
+//     on generated operands, counting mismatching bit patterns;
 //   jsvd_selftest_fp32div: the branch-free binary32 division of the single
 //     precision EVD (evd2f.cuh) against the FP32 pipe's IEEE division;
 //   jsvd_selftest_barrier: the bounded grid barrier of the persistent SVD
@@ -58,9 +58,13 @@ __global__ void selftest_kernel(int64_t n, uint64_t seed, unsigned long long *ba
     const double a = family(splitmix(k), splitmix(k + 1));
     double b = family(splitmix(k + 2), splitmix(k + 3));
     if ((__double_as_longlong(b) & 0x7FFFFFFFFFFFFFFFll) == 0) b = 1.0;
-    if (__double_as_longlong(__ddiv_rn(a, b)) != __double_as_longlong(soft::div_rn(a, b))) ++bd;
+    const long long q = __double_as_longlong(__ddiv_rn(a, b));
+    if (q != __double_as_longlong(soft::div_rn(a, b))) ++bd;
+    if (q != __double_as_longlong(soft::div_rn_sel(a, b))) ++bd;
     const double x = dabs(a);
-    if (__double_as_longlong(__dsqrt_rn(x)) != __double_as_longlong(soft::sqrt_rn(x))) ++bs;
+    const long long r = __double_as_longlong(__dsqrt_rn(x));
+    if (r != __double_as_longlong(soft::sqrt_rn(x))) ++bs;
+    if (r != __double_as_longlong(soft::sqrt_rn_sel(x))) ++bs;
   }
   if (bd) atomicAdd(&bad[0], bd);
   if (bs) atomicAdd(&bad[1], bs);

@@ -1,7 +1,10 @@
 // Host check of the integer-pipe binary64 division and square root
 // (paper_2202_08361_gb300/csrc/fp64soft.cuh) against the host's IEEE
 // arithmetic (SSE2 / AArch64 FP: correctly rounded to nearest even).
-// Usage: soft_fp64_check N seed -> prints "div_bad sqrt_bad" and exits 0.
+// The select-based forms (div_rn_sel, sqrt_rn_sel, ldexp_rn_sel) are
+// checked the same way, ldexp_rn_sel against the host's ldexp.
+// Usage: soft_fp64_check N seed -> prints "div_bad sqrt_bad div_sel_bad
+// sqrt_sel_bad ldexp_sel_bad" and exits 0.
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
@@ -63,7 +66,7 @@ int main(int argc, char **argv)
 {
   const long n = argc > 1 ? atol(argv[1]) : 1000000;
   s_state = argc > 2 ? strtoull(argv[2], nullptr, 10) : 1;
-  long bad_div = 0, bad_sqrt = 0;
+  long bad_div = 0, bad_sqrt = 0, bad_div_sel = 0, bad_sqrt_sel = 0, bad_ldexp_sel = 0;
   for (long i = 0; i < n; ++i) {
     double a = draw(), b = draw();
     if (b == 0.0) b = 1.0;
@@ -75,6 +78,7 @@ int main(int argc, char **argv)
     }
     const double ref = a / b;
     const double got = jsvd::soft::div_rn(a, b);
+    if (dbits(ref) != dbits(jsvd::soft::div_rn_sel(a, b))) ++bad_div_sel;
     if (dbits(ref) != dbits(got)) {
       if (bad_div < 5)
         fprintf(stderr, "div %a / %a: ref %a got %a\n", a, b, ref, got);
@@ -89,11 +93,19 @@ int main(int argc, char **argv)
     }
     const double rs = sqrt(x);
     const double gs = jsvd::soft::sqrt_rn(x);
+    if (dbits(rs) != dbits(jsvd::soft::sqrt_rn_sel(x))) ++bad_sqrt_sel;
+    // x 2^k over the whole range, subnormal results (rounded) included
+    const int k = (int)(rnd() % 4200) - 2100;
+    const double y = draw();
+    if (dbits(ldexp(y, k)) != dbits(jsvd::soft::ldexp_rn_sel(y, k))) {
+      if (bad_ldexp_sel < 5) fprintf(stderr, "ldexp %a %d: ref %a got %a\n", y, k, ldexp(y, k), jsvd::soft::ldexp_rn_sel(y, k));
+      ++bad_ldexp_sel;
+    }
     if (dbits(rs) != dbits(gs)) {
       if (bad_sqrt < 5) fprintf(stderr, "sqrt %a: ref %a got %a\n", x, rs, gs);
       ++bad_sqrt;
     }
   }
-  printf("%ld %ld\n", bad_div, bad_sqrt);
+  printf("%ld %ld %ld %ld %ld\n", bad_div, bad_sqrt, bad_div_sel, bad_sqrt_sel, bad_ldexp_sel);
   return 0;
 }
