@@ -433,6 +433,25 @@ JSVD_API int jsvd_dgemm(int transA, int64_t M, int64_t N, int64_t K, double alph
                         const double *A, int64_t lda, const double *B, int64_t ldb, double beta,
                         double *C, int64_t ldc, void *stream);
 
+/* Complex C = alpha op(A) B + beta C on split planes (real and imaginary
+ * parts each a column-major FP64 matrix with the same leading dimension),
+ * on the same tensor path by the 3M form: T1 = op(Ar) Br, T2 = op(Ai) Bi,
+ * T3 = op(Ar +- Ai)(Br + Bi) give Re = T1 -+ T2 and Im = (T3 - T1) -+ T2,
+ * three real products in place of four.  The mixed SVD's complex products
+ * (G = A V0, Newton-Schulz on V) use it.  op(A) = A (M x K, lda >= M) for
+ * transA == 0, the conjugate transpose A^H (A stored K x M, lda >= K) for
+ * transA == 1; B is K x N (ldb >= K); C is M x N (ldc >= M) and must not
+ * overlap A or B.  Each entry's imaginary part carries an error of order
+ * K eps (|Ar| + |Ai|)(|Br| + |Bi|).  herm == 1 computes the Hermitian
+ * C = alpha A^H A: it requires transA == 1, N == M, Br == Ar, Bi == Ai,
+ * ldb == lda and beta == 0, forms only the tiles on and above the diagonal,
+ * writes both triangles (C == C^H exactly) and a zero imaginary diagonal.
+ * M, N or K = 0 is allowed.  Errors: -i for argument i, JSVD_E_CUDA. */
+JSVD_API int jsvd_zgemm(int transA, int herm, int64_t M, int64_t N, int64_t K, double alpha,
+                        const double *Ar, const double *Ai, int64_t lda, const double *Br,
+                        const double *Bi, int64_t ldb, double beta, double *Cr, double *Ci,
+                        int64_t ldc, void *stream);
+
 /* Self-test of the library's integer-pipe binary64 division and square
  * root (both their branching and their select-based forms) against the
  * GPU's IEEE FP64 instructions: n generated operand pairs

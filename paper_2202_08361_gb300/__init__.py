@@ -16,7 +16,7 @@ from ._native import (JSVD_COMPLEX, JSVD_E_CUDA, JSVD_E_NONFINITE, JSVD_E_TIMEOU
                       JSVD_TUNE_SVD_GRID, JsvdError)
 
 __all__ = ["evd2x2_batched", "evd2x2_batched_host", "evd2x2_host_workspace_size", "svd",
-           "svd_workspace_size", "colnorm_ef", "ordering", "decode_info", "dgemm", "BatchedSVD", "pack_matrices", "svd_batched", "svd_adjoint_batched",
+           "svd_workspace_size", "colnorm_ef", "ordering", "decode_info", "dgemm", "zgemm", "BatchedSVD", "pack_matrices", "svd_batched", "svd_adjoint_batched",
            "sign_gauge_batched", "svd_diff", "version", "tune_set", "JsvdError", "JSVD_REAL",
            "JSVD_COMPLEX"]
 
@@ -360,6 +360,45 @@ def dgemm(A, B, *, transA=False, alpha=1.0, beta=0.0, C=None, stream=None):
                                   _stream_handle(stream))
     _native.check(rc, "jsvd_dgemm")
     return C
+
+
+def zgemm(A, B=None, *, transA=False, herm=False, alpha=1.0, beta=0.0, C=None, stream=None):
+    """C = alpha op(A) B + beta C (jsvd_zgemm, the 3M form on split planes)
+    for complex128 CUDA tensors; op(A) = A^H when transA.  herm=True gives
+    the Hermitian alpha A^H A (B must be None or A, beta 0).  Returns C as a
+    complex128 tensor (a new one; C, when given, supplies the beta term)."""
+    torch = _torch()
+    if herm:
+        if B is not None and B is not A:
+            raise ValueError("herm=True computes A^H A: B must be None or A")
+        if not transA or beta != 0.0:
+            raise ValueError("herm=True needs transA=True and beta=0")
+        B = A
+    M = A.shape[1] if transA else A.shape[0]
+    K = A.shape[0] if transA else A.shape[1]
+    N = B.shape[1]
+    if B.shape[0] != K:
+        raise ValueError("inner dimensions differ")
+    Ar, lda = colmajor(A.real.contiguous())
+    Ai, _ = colmajor(A.imag.contiguous())
+    if herm:
+        Br, Bi, ldb = Ar, Ai, lda
+    else:
+        Br, ldb = colmajor(B.real.contiguous())
+        Bi, _ = colmajor(B.imag.contiguous())
+    Cr = colmajor_empty(M, N, torch.float64, A.device)
+    Ci = colmajor_empty(M, N, torch.float64, A.device)
+    if C is not None and beta != 0.0:
+        Cr.copy_(C.real)
+        Ci.copy_(C.imag)
+    else:
+        beta = 0.0
+    rc = _native.lib().jsvd_zgemm(1 if transA else 0, 1 if herm else 0, M, N, K, float(alpha),
+                                  Ar.data_ptr(), Ai.data_ptr(), lda, Br.data_ptr(), Bi.data_ptr(),
+                                  ldb, float(beta), Cr.data_ptr(), Ci.data_ptr(), max(M, 1),
+                                  _stream_handle(stream))
+    _native.check(rc, "jsvd_zgemm")
+    return torch.complex(Cr, Ci)
 
 
 # ---------------------------------------------------------------------------

@@ -123,6 +123,10 @@ def lib():
         L.jsvd_dgemm.argtypes = [ctypes.c_int, _i64, _i64, _i64, ctypes.c_double, _vp, _i64, _vp,
                                  _i64, ctypes.c_double, _vp, _i64, _vp]
         L.jsvd_dgemm.restype = ctypes.c_int
+        L.jsvd_zgemm.argtypes = [ctypes.c_int, ctypes.c_int, _i64, _i64, _i64, ctypes.c_double,
+                                 _vp, _vp, _i64, _vp, _vp, _i64, ctypes.c_double, _vp, _vp, _i64,
+                                 _vp]
+        L.jsvd_zgemm.restype = ctypes.c_int
         _pi64 = ctypes.POINTER(ctypes.c_int64)
         _pvp = ctypes.POINTER(ctypes.c_void_p)
         L.jsvd_svd_batched_workspace_size.argtypes = [ctypes.c_int, ctypes.POINTER(Opts), _i64,

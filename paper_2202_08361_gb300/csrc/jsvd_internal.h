@@ -32,9 +32,9 @@ size_t svd_fp64_workspace(bool cplx, int64_t m, int64_t n);
 size_t svd_mixed_workspace(bool cplx, int64_t m, int64_t n);
 int dgemm(bool transA, int M, int N, int K, double alpha, const double *A, int64_t lda,
           const double *B, int64_t ldb, double beta, double *C, int64_t ldc, cudaStream_t st);
-int zgemm_split(bool conjtransA, int M, int N, int K, double alpha, const double *Ar,
-                const double *Ai, int64_t lda, const double *Br, const double *Bi, int64_t ldb,
-                double beta, double *Cr, double *Ci, int64_t ldc, cudaStream_t st);
+int zgemm3m(bool conjtransA, bool herm, int M, int N, int K, double alpha, const double *Ar,
+            const double *Ai, int64_t lda, const double *Br, const double *Bi, int64_t ldb,
+            double beta, double *Cr, double *Ci, int64_t ldc, cudaStream_t st);
 int svd_mixed_run(bool cplx, int64_t m, int64_t n, const void *A, int64_t lda, void *U,
                   int64_t ldu, double *sigma, double *sigma_e, double *sigma_f, void *V,
                   int64_t ldv, char *work, jsvd_info *info, int S, int rexp, int flags,

@@ -87,8 +87,9 @@ __global__ void barrier_test_kernel(int absent, int rounds, unsigned long long l
   BarrierTestState *b = &g_bar_test;
   if ((int)blockIdx.x == absent) return;
   int done = 0;
+  unsigned int phase = barrier_phase(&b->word);
   for (int r = 0; r < rounds; ++r) {
-    if (!grid_barrier(&b->word, &b->err, limit_ns)) break;
+    if (!grid_barrier(&b->word, &b->err, limit_ns, phase)) break;
     ++done;
   }
   if (threadIdx.x == 0) {

@@ -38,7 +38,7 @@ constexpr unsigned long long kBarrierLimitNs = 20ull * 1000ull * 1000ull * 1000u
 struct SvdState {
   unsigned long long Mbuf[3];  // running max-norm (bits), triple-buffered by step
   unsigned long long M0;       // ||A||_max bits
-  unsigned int bar_word;        // grid barrier (0 at launch)
+  unsigned int bar_word;        // grid barrier (low 31 bits 0 at launch)
   int err;                     // barrier timeout
   int nonfinite;
   int s;                       // accumulated scaling exponent: G = 2^s (A V)
@@ -188,6 +188,7 @@ __global__ void __launch_bounds__(256) sweeps_kernel(MatViewT<T> M, SvdState *st
   int sweep = 0;
   bool converged = false;
   int last_rescale = INT_MIN / 2;  // the last step that rescaled G (the same in every block)
+  unsigned int bphase = barrier_phase(&st->bar_word);
   for (; sweep < max_sweeps && !converged; ++sweep) {
     for (int k = 0; k < K; ++k, ++gstep) {
       const int cur = (int)(gstep % 3), nxt = (int)((gstep + 1) % 3), old = (int)((gstep + 2) % 3);
@@ -227,7 +228,7 @@ __global__ void __launch_bounds__(256) sweeps_kernel(MatViewT<T> M, SvdState *st
         if (rots) atomicAdd(&st->T[sweep], rots);
         if (gsn) atomicAdd(&st->gs, (unsigned long long)gsn);
       }
-      if (!grid_barrier(&st->bar_word, &st->err, kBarrierLimitNs)) return;
+      if (!grid_barrier(&st->bar_word, &st->err, kBarrierLimitNs, bphase)) return;
     }
     converged = (((volatile int *)st->T)[sweep] == 0);
   }
@@ -844,10 +845,12 @@ static int svd_mixed_run_t(int64_t m, int64_t n, const double *A, int64_t lda, d
     double *Vr = M64.vr, *Vi = M64.vi;
     // B = V^H V; X = 1.5 V - 0.5 V B; V = X
     if (CPLX) {
-      JSVD_TRY(zgemm_split(true, ni, ni, npi, 1.0, Vr, Vi, L.ldv, Vr, Vi, L.ldv, 0.0, Br, Bi, L.ldv, st));
+      JSVD_TRY(zgemm3m(true, true, ni, ni, npi, 1.0, Vr, Vi, L.ldv, Vr, Vi, L.ldv, 0.0, Br, Bi,
+                       L.ldv, st));
       JSVD_CUDA(cudaMemcpyAsync(Xr, Vr, sizeof(double) * L.ldv * n, cudaMemcpyDeviceToDevice, st));
       JSVD_CUDA(cudaMemcpyAsync(Xi, Vi, sizeof(double) * L.ldv * n, cudaMemcpyDeviceToDevice, st));
-      JSVD_TRY(zgemm_split(false, npi, ni, ni, -0.5, Vr, Vi, L.ldv, Br, Bi, L.ldv, 1.5, Xr, Xi, L.ldv, st));
+      JSVD_TRY(zgemm3m(false, false, npi, ni, ni, -0.5, Vr, Vi, L.ldv, Br, Bi, L.ldv, 1.5, Xr, Xi,
+                       L.ldv, st));
       JSVD_CUDA(cudaMemcpyAsync(Vr, Xr, sizeof(double) * L.ldv * n, cudaMemcpyDeviceToDevice, st));
       JSVD_CUDA(cudaMemcpyAsync(Vi, Xi, sizeof(double) * L.ldv * n, cudaMemcpyDeviceToDevice, st));
     } else {
@@ -859,8 +862,8 @@ static int svd_mixed_run_t(int64_t m, int64_t n, const double *A, int64_t lda, d
   }
   // G = 2^{s_0} A V0 (FP64 GEMM on the FP64 tensor path)
   if (CPLX)
-    JSVD_TRY(zgemm_split(false, mpi, ni, ni, 1.0, M0.gr, M0.gi, L.ldg, M64.vr, M64.vi, L.ldv, 0.0,
-                         M64.gr, M64.gi, L.ldg, st));
+    JSVD_TRY(zgemm3m(false, false, mpi, ni, ni, 1.0, M0.gr, M0.gi, L.ldg, M64.vr, M64.vi, L.ldv,
+                     0.0, M64.gr, M64.gi, L.ldg, st));
   else
     JSVD_TRY(dgemm(false, mpi, ni, ni, 1.0, M0.gr, L.ldg, M64.vr, L.ldv, 0.0, M64.gr, L.ldg, st));
   // the FP64 phase restarts the step state from the max-norm of the new G

@@ -1661,35 +1661,62 @@ __device__ __forceinline__ unsigned long long global_ns()
   return t;
 }
 
-// Grid barrier for a cooperative (co-resident) launch, one atomic per
+// Grid barrier for a cooperative (co-resident) launch, one reduction per
 // block: block 0 adds 2^31 - (gridDim.x - 1) to *word and every other
 // block 1, so the top bit of *word flips exactly when the last block
 // arrives (the partial sums stay below 2^31 past the value at the start),
-// and each block waits until the top bit differs from the one it saw when
-// it arrived.  A block already at the next barrier cannot flip the bit
-// back before every block has left this one.  The wait is bounded: after
-// limit_ns it sets *err = 1 and returns, so a lost block can never hang the
-// GPU; callers then leave the kernel.  *word must be 0 at launch.
-__device__ __forceinline__ bool grid_barrier(unsigned int *word, volatile int *err,
-                                             unsigned long long limit_ns)
+// and each block waits until the top bit differs from the phase it holds.
+// A block already at the next barrier cannot flip the bit back before every
+// block has left this one.  Thread 0 of each block keeps that phase: read
+// once before its first arrival (barrier_phase; the bit cannot flip before
+// every block has arrived) and toggled at each barrier, so the arrival is a
+// reduction that returns nothing (red.release.gpu: the block's writes,
+// ordered before it by the block barrier, are released with it) and the
+// wait polls with acquire loads (ld.acquire.gpu), with no full fences.
+// The wait is bounded: after limit_ns (or once another block has reported
+// a timeout in *err, read every 64 polls) it sets *err = 1 and returns
+// false, so a lost block can never hang the GPU; callers then leave the
+// kernel.  The low 31 bits of *word must be 0 at launch.
+__device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int *p)
 {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void red_release_gpu_add(unsigned int *p, unsigned int v)
+{
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// The phase thread 0 starts with: call before the block's first arrival.
+__device__ __forceinline__ unsigned int barrier_phase(const unsigned int *word)
+{
+  return (threadIdx.x == 0) ? (*(const volatile unsigned int *)word >> 31) : 0u;
+}
+
+__device__ __forceinline__ bool grid_barrier(unsigned int *word, volatile int *err,
+                                             unsigned long long limit_ns, unsigned int &phase)
+{
+  __shared__ int s_fail;
   __syncthreads();
   if (threadIdx.x == 0) {
     const unsigned int add = (blockIdx.x == 0) ? (0x80000000u - (gridDim.x - 1u)) : 1u;
-    __threadfence();
-    const unsigned int old = atomicAdd(word, add);
+    red_release_gpu_add(word, add);
+    int fail = 0;
     const unsigned long long t0 = global_ns();
-    while (((*(volatile unsigned int *)word ^ old) & 0x80000000u) == 0u) {
-      if (*err) break;
-      if (global_ns() - t0 > limit_ns) {
+    for (unsigned int it = 1; (ld_acquire_gpu(word) >> 31) == phase; ++it) {
+      if ((it & 63u) == 0u && (*err || global_ns() - t0 > limit_ns)) {
         *err = 1;
+        fail = 1;
         break;
       }
     }
-    __threadfence();
+    phase ^= 1u;
+    s_fail = fail;
   }
   __syncthreads();
-  return *err == 0;
+  return s_fail == 0;
 }
 
 }  // namespace jsvd

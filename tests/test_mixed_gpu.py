@@ -45,6 +45,49 @@ def test_dgemm_against_torch(M, N, K, transA):
     assert (C2 - opA @ B).abs().max().item() <= bound
 
 
+@pytest.mark.parametrize("transA", [False, True])
+@pytest.mark.parametrize("M,N,K", [(1, 1, 1), (7, 5, 3), (64, 32, 16), (65, 130, 17), (130, 65, 100),
+                                   (256, 128, 256), (33, 1, 64), (5, 9, 0)])
+def test_zgemm_3m_against_torch(M, N, K, transA):
+    """jsvd_zgemm's 3M form against torch's complex product, within the 3M
+    bound K eps (|Ar| + |Ai|)(|Br| + |Bi|) per entry (times a safety 4)."""
+    torch = _torch()
+    import paper_2202_08361_gb300 as J
+    g = torch.Generator(device="cpu").manual_seed(M * 1000 + N * 10 + K + 7)
+    A = torch.randn((K, M) if transA else (M, K), generator=g, dtype=torch.complex128).cuda()
+    B = torch.randn((K, N), generator=g, dtype=torch.complex128).cuda()
+    C0 = torch.randn((M, N), generator=g, dtype=torch.complex128).cuda()
+    opA = A.conj().t() if transA else A
+    C = J.zgemm(A, B, transA=transA, alpha=-0.75, beta=1.5, C=C0)
+    ref = -0.75 * (opA @ B) + 1.5 * C0
+    l1 = lambda z: z.real.abs() + z.imag.abs()
+    bound = 4 * max(K, 1) * EPS * ((l1(opA) @ l1(B)) + l1(C0)).max().item() + 1e-300
+    assert (C - ref).abs().max().item() <= bound
+    C2 = J.zgemm(A, B, transA=transA)
+    assert (C2 - opA @ B).abs().max().item() <= bound
+
+
+@pytest.mark.parametrize("K,M", [(1, 1), (17, 33), (100, 64), (300, 97), (2048, 256)])
+def test_zgemm_hermitian_gram(K, M):
+    """herm=True: A^H A from the tiles on and above the diagonal, exactly
+    Hermitian with a zero imaginary diagonal, equal to the general product
+    where both form the same entries."""
+    torch = _torch()
+    import paper_2202_08361_gb300 as J
+    g = torch.Generator(device="cpu").manual_seed(K * 31 + M)
+    A = torch.randn((K, M), generator=g, dtype=torch.complex128).cuda()
+    H = J.zgemm(A, transA=True, herm=True)
+    assert torch.equal(H, H.conj().t())
+    assert torch.equal(H.diagonal().imag, torch.zeros(M, dtype=torch.float64, device=H.device))
+    full = J.zgemm(A, A, transA=True)
+    iu = torch.triu_indices(M, M, offset=1, device=H.device)
+    assert torch.equal(H[iu[0], iu[1]], full[iu[0], iu[1]])
+    assert torch.equal(H.diagonal().real, full.diagonal().real)
+    l1 = A.real.abs() + A.imag.abs()
+    bound = 4 * K * EPS * (l1.t() @ l1).max().item()
+    assert (H - A.conj().t() @ A).abs().max().item() <= bound
+
+
 def gpu_svd(A, **kw):
     torch = _torch()
     import paper_2202_08361_gb300 as J
