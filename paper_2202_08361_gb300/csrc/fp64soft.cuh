@@ -412,5 +412,44 @@ SOFT_FN double ldexp_rn_sel(double x, int k)
   return as_f64(sign | r);
 }
 
+// ldexp_rn_sel behind a call, for the rare operands of the fast paths
+// below: the call keeps the compiler from evaluating it on every path.
+#if defined(__CUDACC__)
+static __device__ __host__ __noinline__ double ldexp_rn_call(double x, int k)
+#else
+static double ldexp_rn_call(double x, int k)
+#endif
+{
+  return ldexp_rn_sel(x, k);
+}
+
+// x 2^k, the values of ldexp_rn_sel, for an x and k that every lane of the
+// warp shares: when x and x 2^k are both normal the result is one integer
+// add to the exponent field; otherwise (zero, subnormal, overflow) the
+// select-based routine.  The branch is then taken alike by all lanes.
+SOFT_FN double ldexp_rn_uni(double x, int k)
+{
+  const uint64_t u = as_u64(x);
+  const int E = (int)((u >> 52) & 0x7FF);
+  const int E2 = E + k;
+  if ((unsigned)(E - 1) < 2046u && (unsigned)(E2 - 1) < 2046u)
+    return as_f64(u + ((uint64_t)(int64_t)k << 52));
+  return ldexp_rn_call(x, k);
+}
+
+// fl(q 2^d) > u as binary64 bit patterns, i.e. the comparison of the
+// rounded product with u, for q, u finite.  For q > 0 normal and u > 0
+// normal no rounding is needed: q 2^d below the normal range rounds to at
+// most 2^-1022 <= u, above it overflows to infinity, and in it the exponent
+// add is exact.  Other operands take ldexp_rn_sel.
+SOFT_FN bool gt_scaled(double q, int d, double u)
+{
+  const uint64_t b = as_u64(q), ub = as_u64(u);
+  const int E = (int)(b >> 52), E2 = E + d;
+  if ((unsigned)(E - 1) < 2046u && ub >= kOne52 && ub < 0x7FF0000000000000ull)
+    return (E2 >= 2047) || (E2 >= 1 && b + ((uint64_t)(int64_t)d << 52) > ub);
+  return as_u64(ldexp_rn_call(q, d)) > ub;
+}
+
 }  // namespace soft
 }  // namespace jsvd

@@ -192,7 +192,10 @@ __global__ void __launch_bounds__(256) sweeps_kernel(MatViewT<T> M, SvdState *st
   for (; sweep < max_sweeps && !converged; ++sweep) {
     for (int k = 0; k < K; ++k, ++gstep) {
       const int cur = (int)(gstep % 3), nxt = (int)((gstep + 1) % 3), old = (int)((gstep + 2) % 3);
-      const double Mcur = dbl(((volatile unsigned long long *)st->Mbuf)[cur]);
+      // a weak L2 load, ordered after the other blocks' updates by the
+      // barrier's acquire, which the compiler may issue beside the step's
+      // column loads
+      const double Mcur = dbl(__ldcg(&st->Mbuf[cur]));
       // section 3.2, step 2: rescale when M~ has grown past 2^rescale_exp
       const int rk =
           (bits(Mcur) != 0ull && flg(Mcur) >= rescale_exp) ? scale_target(rescale_exp) - flg(Mcur) : 0;

@@ -167,14 +167,15 @@ __device__ __forceinline__ double warp_slot(double x, int k)
   return __shfl_sync(0xffffffffu, x, k * (32 / N));
 }
 
+// Max over the warp of a 64-bit unsigned value (all lanes active): the
+// largest upper half by one redux.sync, then the largest lower half among
+// the lanes that hold it.
 __device__ __forceinline__ unsigned long long warp_umax(unsigned long long x)
 {
-#pragma unroll
-  for (int o = 16; o; o >>= 1) {
-    const unsigned long long y = __shfl_xor_sync(0xffffffffu, x, o);
-    x = (y > x) ? y : x;
-  }
-  return x;
+  const unsigned int hi = (unsigned int)(x >> 32);
+  const unsigned int mh = __reduce_max_sync(0xffffffffu, hi);
+  const unsigned int ml = __reduce_max_sync(0xffffffffu, (hi == mh) ? (unsigned int)x : 0u);
+  return ((unsigned long long)mh << 32) | ml;
 }
 
 // |x| bits of a finite double: ordered like the magnitudes
@@ -206,18 +207,21 @@ struct PairOut {
   double c, C, S;
   // Gram-Schmidt step (Eq. e:GS) in place of the rotation on G: gs = 1
   // orthogonalises g_q against g_p, gs = 2 g_p against g_q; the source
-  // column is scaled by 2^-ex, the target by 2^-ey, psi = psr + i psi_i
+  // column is scaled by 2^-ex, the target by 2^-ey, psi = (psr + i psi) psq
+  // (the product is formed by gs_apply, off the rotation's path)
   int gs, ex, ey;
-  double psr, psi;
+  double psr, psi, psq;
 };
 
 // Eq. e:GScond in (e, f) form: ||x|| > 2^eta^ upsilon ||y||, eta^ = 1023,
-// with q = fx / fy already formed.
+// with q = fx / fy already formed: fl(q 2^d) > upsilon, d = ex - ey - 1023
+// (clamped), compared without the rounding where it cannot matter
+// (soft::gt_scaled).
 __device__ __forceinline__ bool gs_cond(int ex, int ey, double q, double ups)
 {
   int d = ex - ey - 1023;
   d = d > 4000 ? 4000 : (d < -4000 ? -4000 : d);
-  return bits(ldexp_rn(q, d)) > bits(ups);
+  return soft::gt_scaled(q, d, ups);
 }
 
 // Section 3.5.1: for a pair to be rotated whose norms are this far apart,
@@ -233,14 +237,16 @@ __device__ __forceinline__ void gs_select(PairOut &o, int ep, int eq, double q12
     o.gs = 1;
     o.ex = ep;
     o.ey = eq;
-    o.psr = __dmul_rn(zr, q21);
-    o.psi = -__dmul_rn(zi, q21);
+    o.psr = zr;
+    o.psi = dbl(bits(zi) ^ kSign);  // conj(a21')
+    o.psq = q21;
   } else if (gs_cond(eq, ep, q21, ups)) {
     o.gs = 2;
     o.ex = eq;
     o.ey = ep;
-    o.psr = __dmul_rn(zr, q12);
-    o.psi = __dmul_rn(zi, q12);
+    o.psr = zr;
+    o.psi = zi;
+    o.psq = q12;
   }
 }
 
@@ -271,7 +277,7 @@ __device__ __forceinline__ PairOut pair_rotation(const PairSums &sm, double ups)
   o.S = 0.0;
   o.gs = 0;
   o.ex = o.ey = 0;
-  o.psr = o.psi = 0.0;
+  o.psr = o.psi = o.psq = 0.0;
   int ep, eq, shift;
   double fp, fq;
   if (sm.wide) {
@@ -363,7 +369,7 @@ __device__ __forceinline__ PairOut pair_rotation_warp(const PairSums &sm, double
   o.S = 0.0;
   o.gs = 0;
   o.ex = o.ey = 0;
-  o.psr = o.psi = 0.0;
+  o.psr = o.psi = o.psq = 0.0;
   int ep, eq, shift;
   double fp, fq;
   if (sm.wide) {
@@ -385,35 +391,68 @@ __device__ __forceinline__ PairOut pair_rotation_warp(const PairSums &sm, double
     }
     const double s1 = soft::sqrt_rn_sel(r == 0 ? sm.pp : sm.qq);  // stage 1
     const double rp = from(s1, 0), rq = from(s1, 1);
-    ep = flg(rp);
-    eq = flg(rq);
-    fp = soft::ldexp_rn_sel(rp, -ep);
-    fq = soft::ldexp_rn_sel(rq, -eq);
+    // the square roots of positive normal sums are positive and normal:
+    // their exponents and mantissas in [1, 2) straight from the bits
+    ep = (int)(bits(rp) >> 52) - 1023;
+    eq = (int)(bits(rq) >> 52) - 1023;
+    fp = dbl((bits(rp) & kMant) | (1023ull << 52));
+    fq = dbl((bits(rq) & kMant) | (1023ull << 52));
     shift = -(ep + eq);
   }
   // stage 2: a21' = (g_q/2^eq)^* (g_p/2^ep) / (f_q f_p), f_p/f_q, f_q/f_p
   const double d = __dmul_rn(fq, fp);
-  const double n2 = (r == 0) ? soft::ldexp_rn_sel(sm.qr, shift)
-                    : (r == 1) ? (CPLX ? soft::ldexp_rn_sel(sm.qi, shift) : 1.0)
+  const double sqr = soft::ldexp_rn_uni(sm.qr, shift);
+  const double sqi = CPLX ? soft::ldexp_rn_uni(sm.qi, shift) : 1.0;
+  const double n2 = (r == 0) ? sqr
+                    : (r == 1) ? sqi
                     : (r == 2) ? fp : fq;
   const double d2 = (r == 0) ? d : (r == 1) ? (CPLX ? d : 1.0) : (r == 2) ? fq : fp;
   const double v2 = soft::div_rn_sel(n2, d2);
   const double zr = from(v2, 0), zi = CPLX ? from(v2, 1) : 0.0;
   const double q12 = from(v2, 2), q21 = from(v2, 3);
-  // Alg. Gram
-  double f12 = q12, f21 = q21;
-  const int e12 = ep - eq + flg(f12), e21 = eq - ep + flg(f21);
-  f12 = soft::ldexp_rn_sel(f12, -flg(f12));
-  f21 = soft::ldexp_rn_sel(f21, -flg(f21));
-  const int sA = min(1023 - max(e12, e21), 0);
-  double a11 = soft::ldexp_rn_sel(f12, e12 + sA), a22 = soft::ldexp_rn_sel(f21, e21 + sA);
-  double a21r = soft::ldexp_rn_sel(zr, sA), a21i = CPLX ? soft::ldexp_rn_sel(zi, sA) : 0.0;
-  // the EVD (Alg. d8jac2 / Listing 1): Eq. e:z
-  const int zeta = 1020 - flg_max(a11, a22, a21r, a21i);  // a21i = 0 when real
-  a11 = soft::ldexp_rn_sel(a11, zeta);
-  a22 = soft::ldexp_rn_sel(a22, zeta);
-  a21r = soft::ldexp_rn_sel(a21r, zeta);
-  if (CPLX) a21i = soft::ldexp_rn_sel(a21i, zeta);
+  // Alg. Gram, then Eq. e:z's scaling of the EVD (Alg. d8jac2 / Listing 1)
+  double a11, a22, a21r, a21i;
+  {
+    // Every x 2^k here is exact while its result stays normal, which holds
+    // for all but pairs whose norms are some 2^1000 apart: the scaling is
+    // then done on the bit patterns (one check for the whole chain), and
+    // otherwise by the same steps through ldexp_rn_uni.
+    const uint64_t b12 = bits(q12), b21 = bits(q21);
+    const int E12 = (int)(b12 >> 52), E21 = (int)(b21 >> 52);  // q12, q21 > 0
+    const int e12 = ep - eq + E12 - 1023, e21 = eq - ep + E21 - 1023;  // exact if normal
+    const int sA = min(1023 - max(e12, e21), 0);
+    const unsigned long long x11 = ((unsigned long long)(1023 + e12) << 52) | (b12 & kMant);  // f12 2^e12
+    const unsigned long long x22 = ((unsigned long long)(1023 + e21) << 52) | (b21 & kMant);
+    const int zeta = 1020 - flg_sat(dbl(max(max(x11, x22), max(abits(zr), abits(zi)))));
+    const unsigned long long zrb = abits(zr), zib = abits(zi);
+    const int Er = (int)(zrb >> 52), Ei = (int)(zib >> 52);
+    const bool fast = (unsigned)(E12 - 1) < 2046u && (unsigned)(E21 - 1) < 2046u && sA == 0 &&
+                      e12 >= -1022 && e21 >= -1022 && (unsigned)(e12 + zeta + 1022) < 2046u &&
+                      (unsigned)(e21 + zeta + 1022) < 2046u &&
+                      (zrb == 0ull || ((unsigned)(Er - 1) < 2046u && (unsigned)(Er + zeta - 1) < 2046u)) &&
+                      (zib == 0ull || ((unsigned)(Ei - 1) < 2046u && (unsigned)(Ei + zeta - 1) < 2046u));
+    if (fast) {
+      const unsigned long long kz = (unsigned long long)(long long)zeta << 52;
+      a11 = dbl(x11 + kz);
+      a22 = dbl(x22 + kz);
+      a21r = zrb ? dbl(bits(zr) + kz) : zr;
+      a21i = zib ? dbl(bits(zi) + kz) : zi;
+    } else {
+      const int g12 = flg(q12), g21 = flg(q21);
+      const int h12 = ep - eq + g12, h21 = eq - ep + g21;
+      const double f12 = soft::ldexp_rn_uni(q12, -g12), f21 = soft::ldexp_rn_uni(q21, -g21);
+      const int tA = min(1023 - max(h12, h21), 0);
+      a11 = soft::ldexp_rn_uni(f12, h12 + tA);
+      a22 = soft::ldexp_rn_uni(f21, h21 + tA);
+      a21r = soft::ldexp_rn_uni(zr, tA);
+      a21i = CPLX ? soft::ldexp_rn_uni(zi, tA) : 0.0;
+      const int z2 = 1020 - flg_max(a11, a22, a21r, a21i);  // a21i = 0 when real
+      a11 = soft::ldexp_rn_uni(a11, z2);
+      a22 = soft::ldexp_rn_uni(a22, z2);
+      a21r = soft::ldexp_rn_uni(a21r, z2);
+      if (CPLX) a21i = soft::ldexp_rn_uni(a21i, z2);
+    }
+  }
   double az, aa21, ar = dabs(a21r);
   bool zero = false;
   if (CPLX) {
@@ -714,21 +753,22 @@ __device__ __forceinline__ void gs_apply(const MatViewT<double, CG> &M, int p, i
   // with the swap the new target lands in the source's place and back
   double *ox_r = o.swap ? yr : xr, *oy_r = o.swap ? xr : yr;
   double *ox_i = o.swap ? yi : xi, *oy_i = o.swap ? xi : yi;
+  const double psr = __dmul_rn(o.psr, o.psq), psi = __dmul_rn(o.psi, o.psq);
   for (int i = lane; i < M.mp; i += 32) {
     const double x1 = M.ld(xr + i), y1 = M.ld(yr + i);
     const double sx1 = ldexp_rn(x1, -o.ex), sy1 = ldexp_rn(y1, -o.ey);
     if (CPLX) {
       const double x2 = M.ld(xi + i), y2 = M.ld(yi + i);
       const double sx2 = ldexp_rn(x2, -o.ex), sy2 = ldexp_rn(y2, -o.ey);
-      const double nr = ldexp_rn(__fma_rn(-o.psr, sx1, __fma_rn(o.psi, sx2, sy1)), o.ey);
-      const double ni = ldexp_rn(__fma_rn(-o.psr, sx2, __fma_rn(-o.psi, sx1, sy2)), o.ey);
+      const double nr = ldexp_rn(__fma_rn(-psr, sx1, __fma_rn(psi, sx2, sy1)), o.ey);
+      const double ni = ldexp_rn(__fma_rn(-psr, sx2, __fma_rn(-psi, sx1, sy2)), o.ey);
       M.st(ox_r + i, x1);
       M.st(ox_i + i, x2);
       M.st(oy_r + i, nr);
       M.st(oy_i + i, ni);
       Mloc = max(Mloc, max(max(magbits(x1), magbits(x2)), max(magbits(nr), magbits(ni))));
     } else {
-      const double nr = ldexp_rn(__fma_rn(-o.psr, sx1, sy1), o.ey);
+      const double nr = ldexp_rn(__fma_rn(-psr, sx1, sy1), o.ey);
       M.st(ox_r + i, x1);
       M.st(oy_r + i, nr);
       Mloc = max(Mloc, max(magbits(x1), magbits(nr)));
@@ -949,7 +989,7 @@ __device__ __forceinline__ void step_chunk(const MatViewT<T, CG> &M, int k, int 
           o.c = 1.0;
           o.C = o.S = 0.0;
           o.gs = o.ex = o.ey = 0;
-          o.psr = o.psi = 0.0;
+          o.psr = o.psi = o.psq = 0.0;
         } else {
           o = pair_rotation<CPLX>(sm, ups);
           o.swap = o.swap && permute;

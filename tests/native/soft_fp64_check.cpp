@@ -2,9 +2,10 @@
 // (paper_2202_08361_gb300/csrc/fp64soft.cuh) against the host's IEEE
 // arithmetic (SSE2 / AArch64 FP: correctly rounded to nearest even).
 // The select-based forms (div_rn_sel, sqrt_rn_sel, ldexp_rn_sel) are
-// checked the same way, ldexp_rn_sel against the host's ldexp.
+// checked the same way, ldexp_rn_sel and ldexp_rn_uni against the host's
+// ldexp, and gt_scaled against the comparison of the host's ldexp result.
 // Usage: soft_fp64_check N seed -> prints "div_bad sqrt_bad div_sel_bad
-// sqrt_sel_bad ldexp_sel_bad" and exits 0.
+// sqrt_sel_bad ldexp_sel_bad ldexp_uni_bad gt_scaled_bad" and exits 0.
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
@@ -67,6 +68,7 @@ int main(int argc, char **argv)
   const long n = argc > 1 ? atol(argv[1]) : 1000000;
   s_state = argc > 2 ? strtoull(argv[2], nullptr, 10) : 1;
   long bad_div = 0, bad_sqrt = 0, bad_div_sel = 0, bad_sqrt_sel = 0, bad_ldexp_sel = 0;
+  long bad_ldexp_uni = 0, bad_gt = 0;
   for (long i = 0; i < n; ++i) {
     double a = draw(), b = draw();
     if (b == 0.0) b = 1.0;
@@ -101,11 +103,27 @@ int main(int argc, char **argv)
       if (bad_ldexp_sel < 5) fprintf(stderr, "ldexp %a %d: ref %a got %a\n", y, k, ldexp(y, k), jsvd::soft::ldexp_rn_sel(y, k));
       ++bad_ldexp_sel;
     }
+    if (dbits(ldexp(y, k)) != dbits(jsvd::soft::ldexp_rn_uni(y, k))) ++bad_ldexp_uni;
+    // fl(q 2^d) > u on bit patterns; u also from the normal range near q 2^d
+    {
+      const double q = draw();
+      const int d = (int)(rnd() % 8001) - 4000;
+      double u = draw();
+      if ((i & 3) == 0) {
+        const double t = ldexp(q, d);
+        const double at = fabs(t);
+        const uint64_t pick = rnd() % 3;  // just above, just below, equal
+        if (std::isfinite(t) && t != 0.0)
+          u = pick == 2 ? at : nextafter(at, pick ? INFINITY : 0.0);
+      }
+      if ((dbits(ldexp(q, d)) > dbits(u)) != jsvd::soft::gt_scaled(q, d, u)) ++bad_gt;
+    }
     if (dbits(rs) != dbits(gs)) {
       if (bad_sqrt < 5) fprintf(stderr, "sqrt %a: ref %a got %a\n", x, rs, gs);
       ++bad_sqrt;
     }
   }
-  printf("%ld %ld %ld %ld %ld\n", bad_div, bad_sqrt, bad_div_sel, bad_sqrt_sel, bad_ldexp_sel);
+  printf("%ld %ld %ld %ld %ld %ld %ld\n", bad_div, bad_sqrt, bad_div_sel, bad_sqrt_sel,
+         bad_ldexp_sel, bad_ldexp_uni, bad_gt);
   return 0;
 }
