@@ -412,7 +412,7 @@ SOFT_FN double ldexp_rn_sel(double x, int k)
   return as_f64(sign | r);
 }
 
-// ldexp_rn_sel behind a call, for the rare operands of the fast paths
+// ldexp_rn_sel behind a call, for the rare operands of the fast path
 // below: the call keeps the compiler from evaluating it on every path.
 #if defined(__CUDACC__)
 static __device__ __host__ __noinline__ double ldexp_rn_call(double x, int k)
@@ -437,18 +437,15 @@ SOFT_FN double ldexp_rn_uni(double x, int k)
   return ldexp_rn_call(x, k);
 }
 
-// fl(q 2^d) > u as binary64 bit patterns, i.e. the comparison of the
-// rounded product with u, for q, u finite.  For q > 0 normal and u > 0
-// normal no rounding is needed: q 2^d below the normal range rounds to at
-// most 2^-1022 <= u, above it overflows to infinity, and in it the exponent
-// add is exact.  Other operands take ldexp_rn_sel.
-SOFT_FN bool gt_scaled(double q, int d, double u)
+// fl(q 2^d) > u as binary64 bit patterns (the comparison of the rounded
+// product with u) for q and u positive and normal, without rounding or a
+// branch: q 2^d below the normal range rounds to at most 2^-1022 <= u,
+// above it overflows to infinity, and in it the exponent add is exact.
+SOFT_FN bool gt_scaled_pos(double q, int d, double u)
 {
-  const uint64_t b = as_u64(q), ub = as_u64(u);
-  const int E = (int)(b >> 52), E2 = E + d;
-  if ((unsigned)(E - 1) < 2046u && ub >= kOne52 && ub < 0x7FF0000000000000ull)
-    return (E2 >= 2047) || (E2 >= 1 && b + ((uint64_t)(int64_t)d << 52) > ub);
-  return as_u64(ldexp_rn_call(q, d)) > ub;
+  const uint64_t b = as_u64(q);
+  const int E2 = (int)(b >> 52) + d;
+  return (E2 >= 2047) || (E2 >= 1 && b + ((uint64_t)(int64_t)d << 52) > as_u64(u));
 }
 
 }  // namespace soft

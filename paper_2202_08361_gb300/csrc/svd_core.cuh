@@ -215,39 +215,33 @@ struct PairOut {
 
 // Eq. e:GScond in (e, f) form: ||x|| > 2^eta^ upsilon ||y||, eta^ = 1023,
 // with q = fx / fy already formed: fl(q 2^d) > upsilon, d = ex - ey - 1023
-// (clamped), compared without the rounding where it cannot matter
-// (soft::gt_scaled).
+// (clamped).  q = f_p / f_q or f_q / f_p lies in [1/2, 2] (f in [1, 2)) and
+// upsilon = 2^-53 sqrt(m) (2^-20 sqrt(m) in the FP32 phase) is normal, so
+// the comparison needs no rounding (soft::gt_scaled_pos).
 __device__ __forceinline__ bool gs_cond(int ex, int ey, double q, double ups)
 {
   int d = ex - ey - 1023;
   d = d > 4000 ? 4000 : (d < -4000 ? -4000 : d);
-  return soft::gt_scaled(q, d, ups);
+  return soft::gt_scaled_pos(q, d, ups);
 }
 
 // Section 3.5.1: for a pair to be rotated whose norms are this far apart,
 // Eq. e:GS replaces the rotation of G (Alg. zvjsvd checks Eq. e:GScond
 // before zjrot); V still takes the rotation.  gs = 1 orthogonalises g_q
 // against g_p (psi = conj(a21') f_q / f_p), gs = 2 g_p against g_q
-// (psi = a21' f_p / f_q).
+// (psi = a21' f_p / f_q).  Selects only, so that the compiler may place it
+// beside the rotation's chain; o's Gram-Schmidt fields are 0 when gs = 0.
 __device__ __forceinline__ void gs_select(PairOut &o, int ep, int eq, double q12, double q21,
                                           double zr, double zi, double ups)
 {
-  if (!o.rot) return;
-  if (gs_cond(ep, eq, q12, ups)) {
-    o.gs = 1;
-    o.ex = ep;
-    o.ey = eq;
-    o.psr = zr;
-    o.psi = dbl(bits(zi) ^ kSign);  // conj(a21')
-    o.psq = q21;
-  } else if (gs_cond(eq, ep, q21, ups)) {
-    o.gs = 2;
-    o.ex = eq;
-    o.ey = ep;
-    o.psr = zr;
-    o.psi = zi;
-    o.psq = q12;
-  }
+  const bool c1 = gs_cond(ep, eq, q12, ups), c2 = gs_cond(eq, ep, q21, ups);
+  const int gs = !o.rot ? 0 : c1 ? 1 : c2 ? 2 : 0;
+  o.gs = gs;
+  o.ex = (gs == 1) ? ep : (gs == 2) ? eq : 0;
+  o.ey = (gs == 1) ? eq : (gs == 2) ? ep : 0;
+  o.psr = gs ? zr : 0.0;
+  o.psi = (gs == 1) ? dbl(bits(zi) ^ kSign) : (gs == 2) ? zi : 0.0;  // conj(a21') for gs = 1
+  o.psq = (gs == 1) ? q21 : (gs == 2) ? q12 : 0.0;
 }
 
 
@@ -1222,13 +1216,13 @@ struct GroupV {
     for (int r = 0; r < kRows; ++r) {
       const int i = lane + 32 * (g + kGroupWarps * r);
       if (i < M.np) {
-        double npr = pr[r], npi = pi[r], nqr = qr[r], nqi = qi[r];
-        if (o.rot) rotate_row<double, CPLX>(pr[r], pi[r], qr[r], qi[r], o.c, o.C, o.S, npr, npi, nqr, nqi);
-        M.st(dp + i, npr);
-        M.st(dq + i, nqr);
+        double npr, npi, nqr, nqi;  // a swap without rotation stores the rows as they are
+        rotate_row<double, CPLX>(pr[r], pi[r], qr[r], qi[r], o.c, o.C, o.S, npr, npi, nqr, nqi);
+        M.st(dp + i, o.rot ? npr : pr[r]);
+        M.st(dq + i, o.rot ? nqr : qr[r]);
         if (CPLX) {
-          M.st(dpi + i, npi);
-          M.st(dqi + i, nqi);
+          M.st(dpi + i, o.rot ? npi : pi[r]);
+          M.st(dqi + i, o.rot ? nqi : qi[r]);
         }
       }
     }
@@ -1299,23 +1293,22 @@ __device__ __forceinline__ void step_group(const MatViewT<double, CG> &M, int k,
         }
       }
     }
-    // this warp's sum, the rows in ascending order as pair_sums forms it
+    // this warp's sum, the rows in ascending order as pair_sums forms it:
+    //   g = 0: xpr xpr (+ xpi xpi)     g = 1: xqr xqr (+ xqi xqi)
+    //   g = 2: xqr xpr (+ xqi xpi)     g = 3: xqr xpi + (-xqi) xpr (complex)
+    // with the operands picked by selects, so that the loop has no branch
+    // (a real pair's warp 3 forms a sum nobody reads)
     double acc = 0.0;
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       if (u < urows) {
-        if (g == 0) {
-          acc = __fma_rn(xpr[u], xpr[u], acc);
-          if (CPLX) acc = __fma_rn(xpi[u], xpi[u], acc);
-        } else if (g == 1) {
-          acc = __fma_rn(xqr[u], xqr[u], acc);
-          if (CPLX) acc = __fma_rn(xqi[u], xqi[u], acc);
-        } else if (g == 2) {
-          acc = __fma_rn(xqr[u], xpr[u], acc);
-          if (CPLX) acc = __fma_rn(xqi[u], xpi[u], acc);
-        } else if (CPLX) {
-          acc = __fma_rn(xqr[u], xpi[u], acc);
-          acc = __fma_rn(-xqi[u], xpr[u], acc);
+        const double a1 = (g == 0) ? xpr[u] : xqr[u];
+        const double b1 = (g == 0 || g == 2) ? xpr[u] : (g == 1) ? xqr[u] : xpi[u];
+        acc = __fma_rn(a1, b1, acc);
+        if (CPLX) {
+          const double a2 = (g == 0) ? xpi[u] : (g == 3) ? dbl(bits(xqi[u]) ^ kSign) : xqi[u];
+          const double b2 = (g == 0 || g == 2) ? xpi[u] : (g == 1) ? xqi[u] : xpr[u];
+          acc = __fma_rn(a2, b2, acc);
         }
       }
     }
@@ -1348,22 +1341,34 @@ __device__ __forceinline__ void step_group(const MatViewT<double, CG> &M, int k,
     if (o.rot && o.gs) {  // Eq. e:GS replaces the rotation on G: one warp
       if (g == 0) gs_apply<CPLX, CG>(M, p, q, o, Mloc);
     } else if (o.rot || o.swap) {
+      // warp g's rows u = g + 4 j, picked from the registers by selects
+      // (no branch per row); a swap without rotation stores the rows as
+      // they are
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        if (u < urows && (u & (kGroupWarps - 1)) == g) {
-          const int i = lane + 32 * u;
-          double npr = xpr[u], npi = xpi[u], nqr = xqr[u], nqi = xqi[u];
-          if (o.rot) {
-            rotate_row<double, CPLX>(xpr[u], xpi[u], xqr[u], xqi[u], o.c, o.C, o.S, npr, npi, nqr,
-                                     nqi);
-            Mloc = max(Mloc, max(magbits(npr), magbits(nqr)));
-            if (CPLX) Mloc = max(Mloc, max(magbits(npi), magbits(nqi)));
-          }
-          M.st(dpr + i, npr);
-          M.st(dqr + i, nqr);
+      for (int j = 0; j < U / kGroupWarps; ++j) {
+        const int u0 = kGroupWarps * j, u = u0 + g;
+        double pr = xpr[u0], pi = xpi[u0], qr = xqr[u0], qi = xqi[u0];
+#pragma unroll
+        for (int t = 1; t < kGroupWarps; ++t) {
+          pr = (g == t) ? xpr[u0 + t] : pr;
+          qr = (g == t) ? xqr[u0 + t] : qr;
           if (CPLX) {
-            M.st(dpi + i, npi);
-            M.st(dqi + i, nqi);
+            pi = (g == t) ? xpi[u0 + t] : pi;
+            qi = (g == t) ? xqi[u0 + t] : qi;
+          }
+        }
+        if (u < urows) {
+          const int i = lane + 32 * u;
+          double npr, npi, nqr, nqi;
+          rotate_row<double, CPLX>(pr, pi, qr, qi, o.c, o.C, o.S, npr, npi, nqr, nqi);
+          unsigned long long mr = max(magbits(npr), magbits(nqr));
+          if (CPLX) mr = max(mr, max(magbits(npi), magbits(nqi)));
+          Mloc = o.rot ? max(Mloc, mr) : Mloc;
+          M.st(dpr + i, o.rot ? npr : pr);
+          M.st(dqr + i, o.rot ? nqr : qr);
+          if (CPLX) {
+            M.st(dpi + i, o.rot ? npi : pi);
+            M.st(dqi + i, o.rot ? nqi : qi);
           }
         }
       }

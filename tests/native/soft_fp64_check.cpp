@@ -3,9 +3,11 @@
 // arithmetic (SSE2 / AArch64 FP: correctly rounded to nearest even).
 // The select-based forms (div_rn_sel, sqrt_rn_sel, ldexp_rn_sel) are
 // checked the same way, ldexp_rn_sel and ldexp_rn_uni against the host's
-// ldexp, and gt_scaled against the comparison of the host's ldexp result.
+// ldexp, and gt_scaled_pos against the comparison of the host's ldexp
+// result (positive normal operands).
 // Usage: soft_fp64_check N seed -> prints "div_bad sqrt_bad div_sel_bad
-// sqrt_sel_bad ldexp_sel_bad ldexp_uni_bad gt_scaled_bad" and exits 0.
+// sqrt_sel_bad ldexp_sel_bad ldexp_uni_bad gt_scaled_pos_bad" and exits 0.
+#include <cfloat>
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
@@ -104,19 +106,24 @@ int main(int argc, char **argv)
       ++bad_ldexp_sel;
     }
     if (dbits(ldexp(y, k)) != dbits(jsvd::soft::ldexp_rn_uni(y, k))) ++bad_ldexp_uni;
-    // fl(q 2^d) > u on bit patterns; u also from the normal range near q 2^d
+    // fl(q 2^d) > u on bit patterns, q and u positive normal; u also just
+    // above, just below or equal to q 2^d
     {
-      const double q = draw();
+      auto pos_normal = [&]() {
+        double v = fabs(draw());
+        return (v >= 0x1p-1022) ? v : ldexp(1.0 + (double)(rnd() >> 11) * 0x1p-53, (int)(rnd() % 2046) - 1022);
+      };
+      const double q = pos_normal();
       const int d = (int)(rnd() % 8001) - 4000;
-      double u = draw();
+      double u = pos_normal();
       if ((i & 3) == 0) {
         const double t = ldexp(q, d);
         const double at = fabs(t);
         const uint64_t pick = rnd() % 3;  // just above, just below, equal
-        if (std::isfinite(t) && t != 0.0)
-          u = pick == 2 ? at : nextafter(at, pick ? INFINITY : 0.0);
+        const double c = pick == 2 ? at : nextafter(at, pick ? INFINITY : 0.0);
+        if (c >= 0x1p-1022 && c <= DBL_MAX) u = c;
       }
-      if ((dbits(ldexp(q, d)) > dbits(u)) != jsvd::soft::gt_scaled(q, d, u)) ++bad_gt;
+      if ((dbits(ldexp(q, d)) > dbits(u)) != jsvd::soft::gt_scaled_pos(q, d, u)) ++bad_gt;
     }
     if (dbits(rs) != dbits(gs)) {
       if (bad_sqrt < 5) fprintf(stderr, "sqrt %a: ref %a got %a\n", x, rs, gs);
