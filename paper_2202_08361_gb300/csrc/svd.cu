@@ -155,7 +155,7 @@ __global__ void init_kernel(const double *__restrict__ A, int64_t lda, MatView M
 // T is the precision of the columns (double; float in the FP32 phase of
 // the mixed SVD).
 template <typename T, bool CPLX, bool COMP, int STREAM = 0>
-__global__ void __launch_bounds__(256) sweeps_kernel(MatViewT<T> M, SvdState *st, double ups,
+__global__ void __launch_bounds__(256, 1) sweeps_kernel(MatViewT<T> M, SvdState *st, double ups,
                                                      int max_sweeps, int rescale_exp, int flags,
                                                      int *lastmod)
 {
@@ -163,10 +163,11 @@ __global__ void __launch_bounds__(256) sweeps_kernel(MatViewT<T> M, SvdState *st
   __shared__ PairOut s_out[8];
   __shared__ double s_gsum[kGroupWarps];
   if (st->nonfinite) return;
-  const bool group = (flags & kFlagGroupStep) != 0;
-  // STREAM (2 or 4 warps per pair, rows streamed) is an instantiation of
-  // its own, so that its registers bind no other form
-  constexpr bool gstream = STREAM != 0;
+  // STREAM = 1 (four warps per pair, rows in registers) and STREAM = 2 or 4
+  // (2 or 4 warps per pair, rows streamed) are instantiations of their own,
+  // so that their code and registers bind no other form
+  constexpr bool group = STREAM == 1;
+  constexpr bool gstream = STREAM >= 2;
   GroupV<CPLX> gv;
   const int nt = M.n + (M.n & 1);
   const int K = nt - 1, L = nt / 2;
@@ -214,7 +215,7 @@ __global__ void __launch_bounds__(256) sweeps_kernel(MatViewT<T> M, SvdState *st
         step_group_stream<T, CPLX, kAccL2, STREAM>(M, k, nt, ups, rk, (flags & kFlagPermute) != 0,
                                                    Mloc, rots, gsn, s_gsum, lastmod, (int)gstep,
                                                    last_rescale);
-      } else if (group) {
+      } else if constexpr (group) {
         if constexpr (sizeof(T) == 8 && !COMP)
           step_group<CPLX>(M, k, nt, ups, rk, (flags & kFlagPermute) != 0, Mloc, rots, gsn, gv,
                            s_gsum);
@@ -239,8 +240,8 @@ __global__ void __launch_bounds__(256) sweeps_kernel(MatViewT<T> M, SvdState *st
     dv.load(M);
     dv.apply(M);
   }
-  if constexpr (sizeof(T) == 8 && !COMP) {
-    if (group && gv.p >= 0) {
+  if constexpr (group && sizeof(T) == 8 && !COMP) {
+    if (gv.p >= 0) {
       gv.load(M, threadIdx.x >> 5);
       gv.apply(M, threadIdx.x >> 5);
     }
@@ -662,7 +663,7 @@ static int launch_sweeps(const MatViewT<T> &M, SvdState *state, double ups, int 
     const bool fits = Lp <= sms && M.mp <= 32 * (CPLX ? 4 : 8) &&
                       M.np <= 32 * kGroupWarps * GroupV<CPLX>::kRows;
     if (fits && ((g_svd_step == 0 && g_svd_grid_cap == 0 && g_svd_warps == 0) || g_svd_step == 4)) {
-      auto kern = sweeps_kernel<T, CPLX, COMP>;
+      auto kern = sweeps_kernel<T, CPLX, COMP, 1>;
       int per_sm = 0;
       JSVD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * kGroupWarps, 0));
       if (per_sm < 1) return JSVD_E_UNSUPPORTED;
