@@ -266,7 +266,7 @@ __global__ void __launch_bounds__(256, 1) sweeps_kernel(MatViewT<T> M, SvdState 
 constexpr int kClusterMax = 16;
 
 template <typename T, bool CPLX, bool COMP>
-__global__ void __launch_bounds__(256) sweeps_cluster_kernel(MatViewT<T> M, SvdState *st,
+__global__ void __launch_bounds__(256, 1) sweeps_cluster_kernel(MatViewT<T> M, SvdState *st,
                                                              double ups, int max_sweeps,
                                                              int rescale_exp, int flags,
                                                              int *lastmod)
