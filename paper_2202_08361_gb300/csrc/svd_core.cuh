@@ -840,8 +840,15 @@ __device__ __forceinline__ void pair_apply(const MatViewT<T, CG> &M, int p, int 
     T *gpi = CPLX ? M.Gi(p) : nullptr, *gqi = CPLX ? M.Gi(q) : nullptr;
     T *vpi = CPLX ? M.Vi(p) : nullptr, *vqi = CPLX ? M.Vi(q) : nullptr;
     if constexpr (MERGED) {
+      // G's trips from the last to the first (the sums just read those rows
+      // in ascending order, so the latest are the likeliest still in L2),
+      // then V's in order; the rows are independent, so the order changes
+      // no bits
       const int r0 = gdone ? M.mp : 0, R = G_ONLY ? M.mp : M.mp + M.np;
-      for (int base = r0 + lane; base < R; base += 32 * U) {
+      const int ntrip = (R - r0 + 32 * U - 1) / (32 * U);
+      const int ntg = (M.mp - r0 + 32 * U - 1) / (32 * U);  // trips that start in G
+      for (int j = 0; j < ntrip; ++j) {
+        const int base = r0 + lane + 32 * U * ((j < ntg) ? ntg - 1 - j : j);
         T pr[U], qr[U], pi[U], qi[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
