@@ -89,6 +89,23 @@ def test_argument_errors_need_no_gpu(lib):
     assert L.jsvd_tune_set(_native.JSVD_TUNE_SVD_SKIP, 2, 0) == -2
     assert L.jsvd_tune_set(_native.JSVD_TUNE_SVD_SKIP, 1, 0) == 0
     assert L.jsvd_tune_set(_native.JSVD_TUNE_SVD_STEP, 0, 0) == 0
+    # the complex 3M product: argument checks come before any CUDA call
+    d = ctypes.c_void_p(16)  # never dereferenced: every call below fails its checks
+    z = L.jsvd_zgemm
+    assert z(2, 0, 4, 4, 4, 1.0, d, d, 4, d, d, 4, 0.0, d, d, 4, None) == -1
+    assert z(0, 2, 4, 4, 4, 1.0, d, d, 4, d, d, 4, 0.0, d, d, 4, None) == -2
+    assert z(0, 1, 4, 4, 4, 1.0, d, d, 4, d, d, 4, 0.0, d, d, 4, None) == -2  # herm needs A^H
+    assert z(1, 1, 4, 5, 4, 1.0, d, d, 4, d, d, 4, 0.0, d, d, 4, None) == -4  # herm needs N = M
+    assert z(0, 0, -1, 4, 4, 1.0, d, d, 4, d, d, 4, 0.0, d, d, 4, None) == -3
+    assert z(0, 0, 4, 4, 4, 1.0, None, d, 4, d, d, 4, 0.0, d, d, 4, None) == -7
+    assert z(0, 0, 4, 4, 4, 1.0, d, None, 4, d, d, 4, 0.0, d, d, 4, None) == -8
+    assert z(0, 0, 8, 4, 4, 1.0, d, d, 4, d, d, 4, 0.0, d, d, 8, None) == -9   # lda < M
+    assert z(0, 0, 4, 4, 4, 1.0, d, d, 4, d, None, 4, 0.0, d, d, 4, None) == -11
+    e = ctypes.c_void_p(32)
+    assert z(1, 1, 4, 4, 4, 1.0, d, d, 4, e, d, 4, 0.0, d, d, 4, None) == -10  # herm: B = A
+    assert z(1, 1, 4, 4, 4, 1.0, d, d, 4, d, d, 4, 0.5, d, d, 4, None) == -13  # herm: beta = 0
+    assert z(0, 0, 4, 4, 4, 1.0, d, d, 4, d, d, 4, 0.0, d, None, 4, None) == -15
+    assert z(0, 0, 4, 4, 4, 1.0, d, d, 4, d, d, 4, 0.0, d, d, 3, None) == -16
 
 
 def test_plain_c_user_compiles_and_runs(tmp_path):
