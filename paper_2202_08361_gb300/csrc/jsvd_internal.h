@@ -23,8 +23,6 @@ namespace jsvd {
 constexpr int kFlagPermute = 1;  // the column swap P during the sweeps
 constexpr int kFlagComp = 2;     // compensated dot-products (FP64 sweeps)
 constexpr int kFlagWarpStep = 4; // each warp runs its pairs alone (sweep kernel)
-constexpr int kFlagGroupStep = 8; // four warps of a block on each pair (sweep kernel)
-constexpr int kFlagGroupStream = 16; // 2 or 4 warps on each pair, rows streamed
 constexpr int kFlagSkip = 32;     // batched sweeps skip unchanged pairs
 int svd_skip_on();
 int svd_check_opts(const jsvd_opts *o, int &S, int &mode, int &rexp, int &flags);

@@ -670,7 +670,7 @@ static int launch_sweeps(const MatViewT<T> &M, SvdState *state, double ups, int 
       const int grid = std::max(1, std::min(Lp, per_sm * sms));
       MatViewT<T> Mk = M;
       SvdState *sk = state;
-      int Sk = S, rk = rexp, pk = flags | kFlagGroupStep;
+      int Sk = S, rk = rexp, pk = flags;  // the form is the instantiation's
       double upsk = ups;
       int *lm = nullptr;  // the group form forms every pair (its steps are latency-bound)
       void *args[] = {&Mk, &sk, &upsk, &Sk, &rk, &pk, &lm};
@@ -704,7 +704,7 @@ static int launch_sweeps(const MatViewT<T> &M, SvdState *state, double ups, int 
       const int grid = std::max(1, std::min(Lp, per_sm * sms));
       MatViewT<T> Mk = M;
       SvdState *sk = state;
-      int Sk = S, rk = rexp, pk = flags | kFlagGroupStream;
+      int Sk = S, rk = rexp, pk = flags;  // the form is the instantiation's
       double upsk = ups;
       int *lm = lastmod;
       void *args[] = {&Mk, &sk, &upsk, &Sk, &rk, &pk, &lm};
