@@ -1,7 +1,8 @@
 // selftest.cu -- self-tests that run on the device:
 //   jsvd_selftest_fp64: the integer-pipe binary64 division and square root
-//     (fp64soft.cuh, both forms) against the FP64 pipe's IEEE instructions
-//     on generated operands, counting mismatching bit patterns;
+//     (fp64soft.cuh and the select-based forms of fp64sel.cuh) against the
+//     FP64 pipe's IEEE instructions on generated operands, counting
+//     mismatching bit patterns;
 //   jsvd_selftest_fp32div: the branch-free binary32 division of the single
 //     precision EVD (evd2f.cuh) against the FP32 pipe's IEEE division;
 //   jsvd_selftest_barrier: the bounded grid barrier of the persistent SVD
@@ -15,6 +16,7 @@
 #include "common.cuh"
 #include "evd2f.cuh"
 #include "fp64bits.cuh"
+#include "fp64sel.cuh"
 #include "fp64soft.cuh"
 #include "jsvd_internal.h"
 #include "svd_core.cuh"

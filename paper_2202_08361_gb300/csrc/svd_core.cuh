@@ -17,6 +17,7 @@
 #include <climits>
 
 #include "evd2.cuh"
+#include "fp64sel.cuh"
 #include "normef.cuh"
 
 namespace jsvd {
@@ -348,7 +349,7 @@ __device__ __forceinline__ PairOut pair_rotation(const PairSums &sm, double ups)
 // (complex) long instead of the 12 or 19 one lane would run.  For launches
 // with one pair per warp, whose step time is this chain.  Since its lanes
 // run different operations, the chain uses the select-based division,
-// square root and x 2^k of fp64soft.cuh (same results, no divergent
+// square root and x 2^k of fp64sel.cuh (same results, no divergent
 // branches): real 7960 -> 6680 cycles per rotation, complex 10630 -> 9230.
 // A lane whose stage has a zero divisor (a result the selects below then
 // discard) divides by 1 instead.

@@ -1,6 +1,6 @@
 // Host check of the integer-pipe binary64 division and square root
-// (paper_2202_08361_gb300/csrc/fp64soft.cuh) against the host's IEEE
-// arithmetic (SSE2 / AArch64 FP: correctly rounded to nearest even).
+// (paper_2202_08361_gb300/csrc/fp64soft.cuh, fp64sel.cuh) against the host's
+// IEEE arithmetic (SSE2 / AArch64 FP: correctly rounded to nearest even).
 // The select-based forms (div_rn_sel, sqrt_rn_sel, ldexp_rn_sel) are
 // checked the same way, ldexp_rn_sel and ldexp_rn_uni against the host's
 // ldexp, and gt_scaled_pos against the comparison of the host's ldexp
@@ -15,6 +15,7 @@
 #include <cstring>
 
 #include "fp64soft.cuh"
+#include "fp64sel.cuh"
 
 static uint64_t s_state;
 static uint64_t rnd()

@@ -1,4 +1,4 @@
-"""The integer-pipe binary64 division and square root (csrc/fp64soft.cuh),
+"""The integer-pipe binary64 division and square root (csrc/fp64soft.cuh, fp64sel.cuh),
 and their select-based forms with the exact x 2^k (also its fast path for
 warp-uniform operands) and the scaled comparison of Eq. e:GScond, bit for
 bit against IEEE
